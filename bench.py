@@ -1,0 +1,521 @@
+#!/usr/bin/env python3
+"""Benchmark: detected uplink Gbit/s of decentralized baseband processing.
+
+Workload (the uplink frame the headline metric is quoted on): B = 128 base-
+station antennas in C = 8 clusters of S = 16, U = 8 users, 16-QAM, W = 1200
+subcarriers x N = 14 OFDM symbols (channel fixed per subcarrier over the 14),
+i.i.d. Rayleigh channel, FP32 complex.  One step detects one frame with the
+decentralized ADMM detector (3 iterations) and with the decentralized CG
+detector (8 iterations); both detections count, so one step carries
+2 x U log2(M) W N = 1,075,200 detected bits.  Frames rotate over the SNR sweep
+0, 2, ..., 20 dB (8 resident frames, 226 MB of inputs, more than the 126 MB
+L2), so every step reads its inputs from HBM.
+
+Also measured in the same run and reported as sub-objects: the decentralized
+ADMM downlink precoder on the B = 256 / C = 16 / U = 16 / 64-QAM / 1200 x 14
+frame (5 iterations), the end-to-end rate through the host-buffer C ABI, and
+the FP64 CPU oracle on the machine's host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dbp|reference]
+For N > 1, launch under torch.distributed.run; each rank detects its own
+frames (subcarrier-parallel weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+from paper_1702_04458_b300.accounting import (Workload, algorithmic_bytes,  # noqa: E402
+                                              algorithmic_mults, detected_bits,
+                                              fp32_simt_peak_tflops)
+
+METRIC = "detected uplink Gbit/s"
+UL = Workload(B=128, C=8, U=8, W=1200, N=14, M=16, T=3)
+UL_T_CG = 8
+DL = Workload(B=256, C=16, U=16, W=1200, N=14, M=64, T=5)
+SNRS_DB = [float(2 * i) for i in range(11)]
+ROTATE = 8
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["dbp", "reference"], default="dbp")
+    ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-downlink", action="store_true")
+    a = ap.parse_args(argv)
+    a.warmup = max(a.warmup, 3)
+    return a
+
+
+def workload_name(wl: Workload, what: str) -> str:
+    return (f"{what}: B={wl.B} C={wl.C} S={wl.S} U={wl.U} {wl.M}-QAM W={wl.W} N={wl.N} "
+            "i.i.d. Rayleigh, fp32 complex")
+
+
+# ---------------------------------------------------------------------------
+# Multi-rank plumbing (timing only; the data path never communicates)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Largest value over all ranks (all_reduce MAX); identity for one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region (NVML)
+# ---------------------------------------------------------------------------
+
+_REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+            0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+            0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+            0x100: "display_clock_setting"}
+
+
+class ClockSampler:
+    def __init__(self, uuid: str, period_s: float = 0.005):
+        self.uuid, self.period = uuid, period_s
+        self.error = None
+        self.samples = []
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._thr = None
+        self.ok = False
+
+    def __enter__(self):
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self._nv = pynvml
+            self._h = self._handle(pynvml)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
+            self.ok = True
+        except Exception as e:  # clocks stay unreported rather than guessed
+            self.error = repr(e)
+            return self
+        self._thr = threading.Thread(target=self._run, daemon=True)
+        self._thr.start()
+        return self
+
+    def _handle(self, nv):
+        """NVML handle of the CUDA device (NVML enumerates every GPU of the
+        node, so match by UUID rather than by index)."""
+        want = self.uuid.replace("GPU-", "").lower()
+        for i in range(nv.nvmlDeviceGetCount()):
+            h = nv.nvmlDeviceGetHandleByIndex(i)
+            u = nv.nvmlDeviceGetUUID(h)
+            u = u.decode() if isinstance(u, bytes) else u
+            if u.replace("GPU-", "").lower() == want:
+                return h
+        raise RuntimeError(f"no NVML device with UUID {self.uuid}")
+
+    def _run(self):
+        nv = self._nv
+        while not self._stop.is_set():
+            try:
+                mhz = nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM)
+                rs = nv.nvmlDeviceGetCurrentClocksEventReasons(self._h)
+                self.samples.append((mhz, rs))
+            except Exception:
+                pass
+            time.sleep(self.period)
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        if self._thr is not None:
+            self._thr.join()
+        return False
+
+    def summary(self):
+        if not self.ok or not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0,
+                    "error": self.error}
+        busy = [m for m, r in self.samples if not (r & 0x1)] or [m for m, _ in self.samples]
+        reasons = set()
+        for _, r in self.samples:
+            for bit, name in _REASONS.items():
+                if r & bit and bit != 0x1:
+                    reasons.add(name)
+        return {"sm_mhz": float(statistics.median(busy)), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# Peaks, traffic records
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    csrc = os.path.join(ROOT, "paper_1702_04458_b300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if f.get("kernel") == kernel and f.get("src") == src:
+            return float(f["bytes_per_launch"])
+    return None
+
+
+def roofline(kernel: str, alg: str, wl: Workload, avg_ms: float, hbm_peak: float, hbm_src: str,
+             alu_peak: float):
+    flops = 2.0 * algorithmic_mults(alg, wl) * wl.W
+    byts = algorithmic_bytes(alg, wl) * wl.W
+    t = avg_ms / 1e3
+    t_alu = flops / (alu_peak * 1e12)
+    t_hbm = byts / (hbm_peak * 1e9)
+    traffic = recorded_traffic(kernel)
+    if t_alu >= t_hbm:
+        ach = flops / t / 1e12
+        r = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+             "frac": ach / alu_peak,
+             "peak_source": "derived: SMs x 128 FP32 lanes x 2 flops x 2032 MHz"}
+    else:
+        ach = byts / t / 1e9
+        r = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+             "frac": ach / hbm_peak, "peak_source": f"hbm_gbs of {hbm_src}"}
+    r.update({"traffic": traffic, "kernel": kernel, "algorithmic_bytes": byts,
+              "algorithmic_flops": flops, "avg_launch_ms": avg_ms,
+              "hbm_view": {"achieved_gbs": byts / t / 1e9, "frac": byts / t / 1e9 / hbm_peak},
+              "alu_view": {"achieved_tflops": flops / t / 1e12, "frac": flops / t / 1e12 / alu_peak}})
+    return r
+
+
+# ---------------------------------------------------------------------------
+# Frames
+# ---------------------------------------------------------------------------
+
+def ul_frames(rank: int, count: int):
+    out = []
+    for i in range(count):
+        snr = SNRS_DB[i % len(SNRS_DB)]
+        f = synth.uplink_frame(UL.W, UL.N, UL.B, UL.U, UL.M, snr,
+                               seed=synth.frame_seed(2, i) + 100000 * rank)
+        out.append(f)
+    return out
+
+
+def dl_frames(rank: int, count: int):
+    return [synth.downlink_frame(DL.W, DL.N, DL.B, DL.U, DL.M,
+                                 seed=synth.frame_seed(3, i) + 100000 * rank) for i in range(count)]
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline / reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_step(f, idx):
+    import oracle
+    H = f["H"][idx].astype(np.complex64).astype(np.complex128)
+    y = f["y"][idx].astype(np.complex64).astype(np.complex128)
+    oracle.admm_ul(H, y, C=UL.C, rho=1.0, N0=f["N0"], T_max=UL.T)
+    oracle.cg_ul(H, y, C=UL.C, rho=f["N0"], T_max=UL_T_CG)
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(frames, seconds: float):
+    import oracle
+    oracle.build()
+    idx = np.arange(UL.W)
+    oracle_step(frames[0], idx[:8])          # load / warm the library
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle_step(frames[reps % len(frames)], idx)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and reps >= 1:
+            break
+    bits = 2 * detected_bits(UL) * reps
+    return {"value": bits / el / 1e9, "unit": "Gbit/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{reps} full frames (1200 x 14, ADMM T=3 + CG T=8), {el:.1f} s, FP64 OpenMP over subcarriers"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    frames = ul_frames(0, 2)
+    sample = 60                               # subcarriers per step
+    rng = np.random.default_rng(0)
+    steps_idx = [np.sort(rng.choice(UL.W, size=sample, replace=False)) for _ in range(4)]
+    for k in range(args.warmup):
+        oracle_step(frames[k % 2], steps_idx[k % 4])
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle_step(frames[k % 2], steps_idx[k % 4])
+    el = time.perf_counter() - t0
+    bits = 2 * detected_bits(Workload(UL.B, UL.C, UL.U, sample, UL.N, UL.M, UL.T)) * args.steps
+    val = bits / el / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Gbit/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(UL, "uplink ADMM T=3 + CG T=8"),
+                       "sample_subcarriers_per_step": sample},
+            "cpu_baseline": {"value": val, "unit": "Gbit/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": f"{sample} of 1200 subcarriers x 14 symbols per step"},
+            "e2e": {"value": val, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main(argv=None) -> int:
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1702_04458_b300 as dbp
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+
+    h = dbp.dbp_create(local)
+    stream = torch.cuda.current_stream(device)
+    props = torch.cuda.get_device_properties(device)
+    sms = props.multi_processor_count
+    alu_peak = fp32_simt_peak_tflops(sms, 2032.0)
+    hbm_peak, hbm_src = measured_peaks()
+
+    # ---- resident uplink frames --------------------------------------------
+    frames = ul_frames(rank, ROTATE)
+    dev = []
+    for f in frames:
+        dev.append({
+            "H": torch.from_numpy(f["H"].astype(np.complex64)).to(device),
+            "y": torch.from_numpy(f["y"].astype(np.complex64)).to(device),
+            "N0": f["N0"],
+        })
+    xa = torch.empty((UL.W, UL.N, UL.U), dtype=torch.complex64, device=device)
+    la = torch.empty((UL.W, UL.N, UL.U), dtype=torch.uint8, device=device)
+    xc = torch.empty_like(xa)
+    lc = torch.empty_like(la)
+
+    def descs(N0):
+        da = dbp.frame_desc(UL.B, UL.C, UL.U, UL.W, UL.N, qam_order=UL.M, T_max=UL.T,
+                            regularizer=dbp.DBP_REG_MMSE, rho=1.0, N0=N0, Es=1.0)
+        dc = dbp.frame_desc(UL.B, UL.C, UL.U, UL.W, UL.N, qam_order=UL.M, T_max=UL_T_CG,
+                            regularizer=dbp.DBP_REG_MMSE, N0=N0, Es=1.0)
+        return da, dc
+
+    D = [descs(d["N0"]) for d in dev]
+    sp = stream.cuda_stream
+
+    def step(k, ev=None):
+        d = dev[k % ROTATE]
+        da, dc = D[k % ROTATE]
+        if ev is not None:
+            ev[0].record(stream)
+        dbp.dbp_uplink_admm(h, da, d["H"], d["y"], xa, la, sp)
+        if ev is not None:
+            ev[1].record(stream)
+        dbp.dbp_uplink_cg(h, dc, d["H"], d["y"], xc, lc, sp)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize(device)
+    barrier(world, device)
+    torch.cuda.synchronize(device)
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(str(props.uuid)) as clk:
+        t_start.record(stream)
+        for k in range(K):
+            step(k, evs[k])
+        t_end.record(stream)
+        torch.cuda.synchronize(device)
+    total_ms = t_start.elapsed_time(t_end)
+    admm_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    cg_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    barrier(world, device)
+    torch.cuda.synchronize(device)
+    total_ms_max = max_over_ranks(total_ms, world, device)
+
+    bits_step = 2 * detected_bits(UL)
+    value = world * bits_step * K / (total_ms_max / 1e3) / 1e9
+    admm_avg = statistics.fmean(admm_ms)
+    cg_avg = statistics.fmean(cg_ms)
+    rf_admm = roofline("admm_ul", "admm_ul", UL, admm_avg, hbm_peak, hbm_src, alu_peak)
+    rf_cg = roofline("cg_ul", "cg_ul", Workload(UL.B, UL.C, UL.U, UL.W, UL.N, UL.M, UL_T_CG),
+                     cg_avg, hbm_peak, hbm_src, alu_peak)
+    dominant = rf_cg if cg_avg >= admm_avg else rf_admm
+
+    # ---- downlink precoder (B=256, C=16, U=16) -------------------------------
+    downlink = None
+    if not args.no_downlink:
+        del dev
+        torch.cuda.empty_cache()
+        dfr = dl_frames(rank, ROTATE)
+        ddev = [{"H": torch.from_numpy(f["H"].astype(np.complex64)).to(device),
+                 "s": torch.from_numpy(f["s"].astype(np.complex64)).to(device)} for f in dfr]
+        xd = torch.empty((DL.W, DL.N, DL.B), dtype=torch.complex64, device=device)
+        ddesc = dbp.frame_desc(DL.B, DL.C, DL.U, DL.W, DL.N, T_max=DL.T, rho=1.0)
+        for k in range(args.warmup):
+            dbp.dbp_downlink_admm(h, ddesc, ddev[k % ROTATE]["H"], ddev[k % ROTATE]["s"], xd, None, sp)
+        torch.cuda.synchronize(device)
+        KD = max(min(K, 1000), 10)
+        devs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(KD)]
+        for k in range(KD):
+            devs[k][0].record(stream)
+            dbp.dbp_downlink_admm(h, ddesc, ddev[k % ROTATE]["H"], ddev[k % ROTATE]["s"], xd, None, sp)
+            devs[k][1].record(stream)
+        torch.cuda.synchronize(device)
+        dl_ms = statistics.fmean(e[0].elapsed_time(e[1]) for e in devs)
+        downlink = {"workload": workload_name(DL, "downlink ADMM T=5"),
+                    "value": detected_bits(DL) / (dl_ms / 1e3) / 1e9, "unit": "Gbit/s (precoded)",
+                    "ms_per_frame": dl_ms, "launches": KD,
+                    "roofline": roofline("admm_dl", "admm_dl", DL, dl_ms, hbm_peak, hbm_src, alu_peak)}
+        del ddev, xd
+        torch.cuda.empty_cache()
+
+    # ---- end to end through the host-buffer C ABI ----------------------------
+    e2e = None
+    if not args.no_e2e:
+        f0 = frames[0]
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        Hh = pin(f0["H"].astype(np.complex64))
+        yh = pin(f0["y"].astype(np.complex64))
+        xh = pin(np.zeros((UL.W, UL.N, UL.U), dtype=np.complex64))
+        lh = pin(np.zeros((UL.W, UL.N, UL.U), dtype=np.uint8))
+        da, dc = descs(f0["N0"])
+        for _ in range(3):
+            dbp.dbp_uplink_admm_host(h, da, Hh, yh, xh, lh, sp)
+            dbp.dbp_uplink_cg_host(h, dc, Hh, yh, xh, lh, sp)
+        KE = args.e2e_steps
+        barrier(world, device)
+        t0 = time.perf_counter()
+        for _ in range(KE):
+            dbp.dbp_uplink_admm_host(h, da, Hh, yh, xh, lh, sp)
+            dbp.dbp_uplink_cg_host(h, dc, Hh, yh, xh, lh, sp)
+        el = max_over_ranks(time.perf_counter() - t0, world, device)
+        e2e = {"value": world * bits_step * KE / el / 1e9, "unit": "Gbit/s",
+               "h2d_bytes_per_step": 2 * (Hh.nbytes + yh.nbytes),
+               "d2h_bytes_per_step": 2 * (xh.nbytes + lh.nbytes),
+               "api": "dbp_uplink_admm_host + dbp_uplink_cg_host (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(frames, args.cpu_seconds)
+
+    dbp.dbp_destroy(h)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": total_ms_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {
+                "workload": workload_name(UL, "uplink ADMM T=3 + CG T=8 per step"),
+                "B": UL.B, "C": UL.C, "S": UL.S, "U": UL.U, "qam": UL.M, "subcarriers": UL.W,
+                "symbols": UL.N, "admm_iterations": UL.T, "cg_iterations": UL_T_CG,
+                "bits_per_step": bits_step, "snr_db": "rotating 0..14 dB over 8 resident frames",
+                "l2": "inputs larger than L2: 8 rotating frames, 226 MB resident",
+                "parallelism": f"subcarrier-parallel, {world} independent rank(s)",
+            },
+            "per_detector": {
+                "admm_ul": {"ms": admm_avg, "gbit_s": detected_bits(UL) / (admm_avg / 1e3) / 1e9},
+                "cg_ul": {"ms": cg_avg, "gbit_s": detected_bits(UL) / (cg_avg / 1e3) / 1e9},
+            },
+            "roofline": dominant,
+            "roofline_other": rf_admm if dominant is rf_cg else rf_cg,
+            "downlink": downlink,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 2 * K,
+            "clocks": clk.summary(),
+            "kernel_src": kernel_source_hash(),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * dbp.h -- C ABI of the B300 (sm_103a) decentralized baseband processing
+ * library libdbp.so.
+ *
+ * The library runs the per-subcarrier, per-antenna-cluster hot path of
+ * decentralized massive MU-MIMO baseband processing (Li, Sharan, Chen,
+ * Goldstein, Cavallaro, Studer, "Decentralized Baseband Processing for
+ * Massive MU-MIMO Systems"):
+ *   - decentralized consensus-ADMM uplink detection   (Alg. 1, Sec. III-B/C)
+ *   - decentralized conjugate-gradient uplink detection (Alg. 2, Sec. III-D)
+ *   - decentralized ADMM downlink beamforming          (Alg. 3, Sec. IV-B/C)
+ * as hand-written CUDA kernels.  There is no CPU fallback: every compute
+ * entry point fails with DBP_ERR_CUDA when no usable GPU is present.
+ *
+ * Shapes (Sec. II): B base-station antennas in C clusters of S = B / C
+ * antennas, U single-antenna users, W subcarriers, N OFDM symbols per
+ * subcarrier (the channel is constant over the N symbols of a subcarrier).
+ *
+ * Memory layouts: row-major, complex numbers interleaved (re, im):
+ *   H      [W][B][U]  uplink channel; cluster c owns rows c*S .. c*S+S-1
+ *                     (row-wise partition of Sec. II-A.2).  The downlink
+ *                     uses the same buffer: H^d = (H^u)^T (reciprocity,
+ *                     Sec. II-B).
+ *   y      [W][N][B]  uplink receive vectors
+ *   x_hat  [W][N][U]  equaliser outputs (uplink)
+ *   labels [W][N][U]  uint8 Gray bit labels of the sliced symbols: for
+ *                     M = L*L points and m = log2 M, label =
+ *                     (g(kI) << m/2) | g(kQ), g(k) = k ^ (k >> 1), where the
+ *                     PAM index k maps to amplitude (2k-(L-1))*sqrt(3/(2(M-1)))
+ *   s      [W][N][U]  downlink transmit symbols
+ *   x      [W][N][B]  downlink beamforming vectors
+ * Element type by precision: DBP_FP32 -> float complex (8 B),
+ * DBP_FP64 -> double complex (16 B).  All device pointers must be aligned
+ * to the element size.
+ *
+ * Ownership: the caller owns every input and output buffer and keeps it
+ * alive until the work enqueued on `stream` has completed.  The library
+ * owns its handle, its workspace and its host staging buffers; descriptors
+ * are copied at call time.  `stream` is a cudaStream_t (NULL = the legacy
+ * default stream).  Compute calls are stream-ordered: DBP_OK means the work
+ * was validated and enqueued.  No C++ exception crosses this interface.
+ */
+#ifndef DBP_H
+#define DBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dbp_status {
+    DBP_OK = 0,
+    DBP_ERR_INVALID_ARG = 1,   /* bad shape, parameter or pointer            */
+    DBP_ERR_UNSUPPORTED = 2,   /* valid but outside what the kernels handle  */
+    DBP_ERR_NOMEM = 3,         /* device or host allocation failed           */
+    DBP_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed       */
+    DBP_ERR_TIMEOUT = 5,       /* a bounded wait ran out                     */
+    DBP_ERR_UNIMPLEMENTED = 6, /* entry point not available in this build    */
+    DBP_PENDING = 7            /* submitted work has not completed yet       */
+} dbp_status;
+
+typedef enum dbp_precision {
+    DBP_FP32 = 0,              /* complex float in, FP32 arithmetic          */
+    DBP_FP64 = 1               /* complex double in, FP64 arithmetic         */
+} dbp_precision;
+
+/* Regulariser g(s) of the equalisation problem (E0), Sec. III-A, and its
+ * proximal step (E2), Lemma 1. */
+typedef enum dbp_regularizer {
+    DBP_REG_ZF = 0,            /* g = 0                 : s = v              */
+    DBP_REG_MMSE = 1,          /* g = N0/(2Es)||s||^2   : (E2-MMSE)          */
+    DBP_REG_BOX = 2            /* g = box indicator     : (E2-BOX), radius r */
+} dbp_regularizer;
+
+/* Descriptor flags. */
+#define DBP_FLAG_NORMALIZE 1u  /* downlink: scale x to unit mean per-antenna
+                                  power over the frame (one scalar beta)    */
+
+typedef struct dbp_config {
+    int32_t device;            /* CUDA device ordinal                        */
+    int32_t reserved;
+    uint64_t hbm_budget_bytes; /* workspace budget; 0 = no limit             */
+} dbp_config;
+
+typedef struct dbp_frame_desc {
+    int32_t B, C, U;           /* antennas, clusters (B % C == 0), users     */
+    int32_t W, N;              /* subcarriers, OFDM symbols per subcarrier   */
+    int32_t qam_order;         /* 4, 16, 64 or 256: slicer alphabet; 0 = no
+                                  labels                                     */
+    int32_t T_max;             /* iterations: ADMM counts the init as the
+                                  first (T_max >= 1); CG counts loop trips
+                                  (T_max >= 0)                               */
+    int32_t regularizer;       /* dbp_regularizer (uplink ADMM; CG uses
+                                  rho = N0/Es for MMSE, 0 for ZF)            */
+    int32_t precision;         /* dbp_precision                              */
+    uint32_t flags;            /* DBP_FLAG_*                                 */
+    double rho;                /* ADMM penalty rho > 0 (Alg. 1 and Alg. 3)   */
+    double gamma;              /* dual step gamma (the paper uses 1)         */
+    double N0;                 /* noise variance per complex entry           */
+    double Es;                 /* symbol energy E[|s_u|^2] > 0               */
+    double box_r;              /* box radius r for DBP_REG_BOX               */
+} dbp_frame_desc;
+
+/* Launch-shape tuning (the autotuner's knobs; results do not depend on them
+ * beyond floating-point rounding of the consensus, which is summed in the
+ * same cluster order under every shape). */
+typedef enum dbp_mapping {
+    DBP_MAP_AUTO = 0,          /* CTA mapping when one CTA holds all C warps */
+    DBP_MAP_CTA = 1,           /* P whole subcarriers per CTA, shared-memory
+                                  consensus                                  */
+    DBP_MAP_CLUSTER = 2        /* one subcarrier per thread-block cluster of
+                                  cluster_size CTAs, DSMEM consensus         */
+} dbp_mapping;
+
+typedef struct dbp_tuning {
+    int32_t mapping;           /* dbp_mapping                                */
+    int32_t cluster_size;      /* CTAs per cluster (divides C, <= 16); 0 =
+                                  smallest that fits                         */
+    int32_t warps_per_cta;     /* CTA mapping: target warps per CTA; 0 = 8   */
+} dbp_tuning;
+
+typedef struct dbp_context *dbp_handle_t;
+
+/* Create a handle bound to cfg->device (NULL cfg = device 0, no budget).
+ * Returns DBP_ERR_CUDA when the device cannot be used. */
+dbp_status dbp_create(dbp_handle_t *out, const dbp_config *cfg);
+
+/* Release the handle and its workspace.  Waits for nothing: the caller
+ * synchronises its streams first. */
+dbp_status dbp_destroy(dbp_handle_t h);
+
+/* Text of the last error on this handle ("" if none).  Valid until the next
+ * call on the handle. */
+const char *dbp_last_error(dbp_handle_t h);
+
+/* Library version string. */
+const char *dbp_version(void);
+
+/* Set the launch-shape knobs used by later calls on this handle.
+ * DBP_ERR_INVALID_ARG for out-of-range values; a shape that does not fit a
+ * frame is reported by the compute call (DBP_ERR_UNSUPPORTED). */
+dbp_status dbp_set_tuning(dbp_handle_t h, const dbp_tuning *t);
+
+/* Decentralized ADMM-based data detection, Alg. 1 (Sec. III-B, III-C):
+ * per subcarrier w and symbol n, C clusters each solve (E1) locally with
+ * their own H_c, y_c; the consensus w = sum_c (z_c + lambda_c) is formed on
+ * chip and every cluster applies the (E2) proximal step of Lemma 1 itself.
+ * Inputs H [W][B][U], y [W][N][B] (device).  Outputs x_hat = s^(T_max)
+ * [W][N][U] (device) and, if labels != NULL and qam_order > 0, the sliced
+ * Gray labels [W][N][U] (device, uint8). */
+dbp_status dbp_uplink_admm(dbp_handle_t h, const dbp_frame_desc *d,
+                           const void *H, const void *y, void *x_hat,
+                           uint8_t *labels, void *stream);
+
+/* Decentralized CG-based data detection, Alg. 2 (Sec. III-D): MRC
+ * y = sum_c H_c^H y_c, then T_max CG iterations on (H^H H + rho I) x = y
+ * with the Gram product decentralized as sum_c H_c^H H_c p; every cluster
+ * keeps its own copy of the CG state.  rho = N0/Es for DBP_REG_MMSE and
+ * 0 for DBP_REG_ZF.  Same buffers as dbp_uplink_admm. */
+dbp_status dbp_uplink_cg(dbp_handle_t h, const dbp_frame_desc *d,
+                         const void *H, const void *y, void *x_hat,
+                         uint8_t *labels, void *stream);
+
+/* Decentralized ADMM-based beamforming, Alg. 3 (Sec. IV-B, IV-C) with
+ * eps = 0: per subcarrier and symbol, cluster c computes its own part x_c of
+ * the beamforming vector from H^d_c = (H^u_c)^T and the consensus
+ * w = sum_c (H^d_c x_c - lambda_c).  Inputs H [W][B][U] (uplink layout),
+ * s [W][N][U] (device).  Output x [W][N][B] (device).  With
+ * DBP_FLAG_NORMALIZE, x is scaled in place by beta = sqrt(B*W*N / sum|x|^2)
+ * and, if beta_out != NULL, beta is stored there (device, one double). */
+dbp_status dbp_downlink_admm(dbp_handle_t h, const dbp_frame_desc *d,
+                             const void *H, const void *s, void *x,
+                             double *beta_out, void *stream);
+
+/* Host-memory variants (end-to-end path): the same computations with every
+ * buffer in host memory.  The call copies the inputs to library-owned
+ * device buffers on `stream`, runs the kernels, copies the outputs back
+ * and synchronises `stream` before returning.  Pinned host memory gives
+ * the fastest copies; pageable memory also works. */
+dbp_status dbp_uplink_admm_host(dbp_handle_t h, const dbp_frame_desc *d,
+                                const void *H, const void *y, void *x_hat,
+                                uint8_t *labels, void *stream);
+dbp_status dbp_uplink_cg_host(dbp_handle_t h, const dbp_frame_desc *d,
+                              const void *H, const void *y, void *x_hat,
+                              uint8_t *labels, void *stream);
+dbp_status dbp_downlink_admm_host(dbp_handle_t h, const dbp_frame_desc *d,
+                                  const void *H, const void *s, void *x,
+                                  double *beta_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DBP_H */

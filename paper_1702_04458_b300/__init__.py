@@ -1,0 +1,191 @@
+"""B300-native decentralized baseband processing (sm_103a CUDA behind a C ABI).
+
+Thin Python binding of ``libdbp.so`` (declared in ``include/dbp.h``): the
+functions here carry the C names and only marshal arguments.  Every step of
+the computation runs in the library's CUDA kernels; there is no Python or CPU
+fallback, and importing this package fails loudly when the library is absent.
+
+Device buffers are passed as torch CUDA tensors (or raw integer addresses);
+host buffers for the ``*_host`` variants as numpy arrays or CPU tensors.
+Streams are ``torch.cuda.Stream`` objects, raw ``cudaStream_t`` integers or
+None (the current torch stream is then used for device calls).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdbp.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -m paper_1702_04458_b300.build` "
+        "(there is no fallback implementation)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---------------------------------------------------------------------------
+# Types mirrored from include/dbp.h
+# ---------------------------------------------------------------------------
+DBP_OK = 0
+DBP_ERR_INVALID_ARG = 1
+DBP_ERR_UNSUPPORTED = 2
+DBP_ERR_NOMEM = 3
+DBP_ERR_CUDA = 4
+DBP_ERR_TIMEOUT = 5
+DBP_ERR_UNIMPLEMENTED = 6
+DBP_PENDING = 7
+
+DBP_FP32, DBP_FP64 = 0, 1
+DBP_REG_ZF, DBP_REG_MMSE, DBP_REG_BOX = 0, 1, 2
+DBP_FLAG_NORMALIZE = 1
+DBP_MAP_AUTO, DBP_MAP_CTA, DBP_MAP_CLUSTER = 0, 1, 2
+
+_STATUS = {0: "DBP_OK", 1: "DBP_ERR_INVALID_ARG", 2: "DBP_ERR_UNSUPPORTED", 3: "DBP_ERR_NOMEM",
+           4: "DBP_ERR_CUDA", 5: "DBP_ERR_TIMEOUT", 6: "DBP_ERR_UNIMPLEMENTED", 7: "DBP_PENDING"}
+
+
+class dbp_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("hbm_budget_bytes", ctypes.c_uint64)]
+
+
+class dbp_frame_desc(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int32), ("C", ctypes.c_int32), ("U", ctypes.c_int32),
+                ("W", ctypes.c_int32), ("N", ctypes.c_int32), ("qam_order", ctypes.c_int32),
+                ("T_max", ctypes.c_int32), ("regularizer", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("rho", ctypes.c_double), ("gamma", ctypes.c_double), ("N0", ctypes.c_double),
+                ("Es", ctypes.c_double), ("box_r", ctypes.c_double)]
+
+
+class dbp_tuning(ctypes.Structure):
+    _fields_ = [("mapping", ctypes.c_int32), ("cluster_size", ctypes.c_int32),
+                ("warps_per_cta", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_H = ctypes.c_void_p
+_S = ctypes.c_int
+
+_lib.dbp_version.restype = ctypes.c_char_p
+_lib.dbp_version.argtypes = []
+_lib.dbp_create.restype = _S
+_lib.dbp_create.argtypes = [ctypes.POINTER(_H), ctypes.POINTER(dbp_config)]
+_lib.dbp_destroy.restype = _S
+_lib.dbp_destroy.argtypes = [_H]
+_lib.dbp_last_error.restype = ctypes.c_char_p
+_lib.dbp_last_error.argtypes = [_H]
+_lib.dbp_set_tuning.restype = _S
+_lib.dbp_set_tuning.argtypes = [_H, ctypes.POINTER(dbp_tuning)]
+for _name in ("dbp_uplink_admm", "dbp_uplink_cg", "dbp_uplink_admm_host", "dbp_uplink_cg_host"):
+    getattr(_lib, _name).restype = _S
+    getattr(_lib, _name).argtypes = [_H, ctypes.POINTER(dbp_frame_desc), _P, _P, _P, _P, _P]
+for _name in ("dbp_downlink_admm", "dbp_downlink_admm_host"):
+    getattr(_lib, _name).restype = _S
+    getattr(_lib, _name).argtypes = [_H, ctypes.POINTER(dbp_frame_desc), _P, _P, _P, _P, _P]
+
+
+class DbpError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def _ptr(x):
+    """Address of a torch tensor, numpy array, ctypes object or integer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    return ctypes.addressof(x)
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(h, status: int):
+    if status != DBP_OK:
+        msg = _lib.dbp_last_error(h)
+        raise DbpError(status, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------------------
+# C entry points (same names)
+# ---------------------------------------------------------------------------
+
+def dbp_version() -> str:
+    return _lib.dbp_version().decode()
+
+
+def dbp_create(device: int = 0, hbm_budget_bytes: int = 0):
+    h = _H()
+    cfg = dbp_config(device, 0, hbm_budget_bytes)
+    st = _lib.dbp_create(ctypes.byref(h), ctypes.byref(cfg))
+    if st != DBP_OK:
+        raise DbpError(st, "dbp_create failed (no usable CUDA device?)")
+    return h
+
+
+def dbp_destroy(h) -> None:
+    _check(h, _lib.dbp_destroy(h))
+
+
+def dbp_last_error(h) -> str:
+    return _lib.dbp_last_error(h).decode()
+
+
+def dbp_set_tuning(h, mapping: int = DBP_MAP_AUTO, cluster_size: int = 0, warps_per_cta: int = 0) -> None:
+    t = dbp_tuning(mapping, cluster_size, warps_per_cta)
+    _check(h, _lib.dbp_set_tuning(h, ctypes.byref(t)))
+
+
+def frame_desc(B, C, U, W, N, qam_order=0, T_max=3, regularizer=DBP_REG_MMSE,
+               precision=DBP_FP32, flags=0, rho=1.0, gamma=1.0, N0=0.0, Es=1.0,
+               box_r=0.0) -> dbp_frame_desc:
+    return dbp_frame_desc(B, C, U, W, N, qam_order, T_max, regularizer, precision, flags,
+                          rho, gamma, N0, Es, box_r)
+
+
+def dbp_uplink_admm(h, d, H, y, x_hat, labels=None, stream=None) -> None:
+    _check(h, _lib.dbp_uplink_admm(h, ctypes.byref(d), _ptr(H), _ptr(y), _ptr(x_hat),
+                                   _ptr(labels), _stream(stream)))
+
+
+def dbp_uplink_cg(h, d, H, y, x_hat, labels=None, stream=None) -> None:
+    _check(h, _lib.dbp_uplink_cg(h, ctypes.byref(d), _ptr(H), _ptr(y), _ptr(x_hat),
+                                 _ptr(labels), _stream(stream)))
+
+
+def dbp_downlink_admm(h, d, H, s, x, beta_out=None, stream=None) -> None:
+    _check(h, _lib.dbp_downlink_admm(h, ctypes.byref(d), _ptr(H), _ptr(s), _ptr(x),
+                                     _ptr(beta_out), _stream(stream)))
+
+
+def dbp_uplink_admm_host(h, d, H, y, x_hat, labels=None, stream=0) -> None:
+    _check(h, _lib.dbp_uplink_admm_host(h, ctypes.byref(d), _ptr(H), _ptr(y), _ptr(x_hat),
+                                        _ptr(labels), _stream(stream)))
+
+
+def dbp_uplink_cg_host(h, d, H, y, x_hat, labels=None, stream=0) -> None:
+    _check(h, _lib.dbp_uplink_cg_host(h, ctypes.byref(d), _ptr(H), _ptr(y), _ptr(x_hat),
+                                      _ptr(labels), _stream(stream)))
+
+
+def dbp_downlink_admm_host(h, d, H, s, x, beta_out=None, stream=0) -> None:
+    _check(h, _lib.dbp_downlink_admm_host(h, ctypes.byref(d), _ptr(H), _ptr(s), _ptr(x),
+                                          _ptr(beta_out), _stream(stream)))
+
+
+__all__ = [n for n in dir() if n.startswith(("dbp_", "DBP_")) or n in ("frame_desc", "DbpError", "LIB_PATH")]

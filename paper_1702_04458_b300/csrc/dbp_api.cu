@@ -1,0 +1,382 @@
+// dbp_api.cu -- C ABI of libdbp.so: handles, argument checks, launch-shape
+// selection and the host-buffer (end-to-end) entry points.  The compute runs
+// in the fused kernels of dbp_fused.cuh; there is no host fallback.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "dbp.h"
+#include "dbp_launch.cuh"
+
+using dbp::FusedParams;
+using dbp::Shape;
+
+struct dbp_context {
+    int device = 0;
+    uint64_t budget = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    std::string err;
+    dbp_tuning tuning{};
+    double *energy = nullptr;            // downlink power accumulator
+    void *dev[4] = {nullptr, nullptr, nullptr, nullptr};   // host-variant buffers
+    size_t dev_cap[4] = {0, 0, 0, 0};
+};
+
+namespace {
+
+dbp_status fail(dbp_context *h, dbp_status st, const char *fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return st;
+}
+
+dbp_status cuda_fail(dbp_context *h, cudaError_t e, const char *what) {
+    return fail(h, DBP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int next_pow2_ut(int U) {
+    int ut = 4;
+    while (ut < U) ut <<= 1;
+    return ut;
+}
+
+int max_warps_for(int prec, int UT) {
+    // Must agree with dbp::Bounds<T, UT>::max_warps.
+    if (prec == DBP_FP32) return (UT <= 4) ? 32 : (UT <= 16) ? 16 : 8;
+    return (UT <= 4) ? 16 : 8;
+}
+
+size_t smem_bytes_for(int prec, int UT, int nwarps) {
+    size_t elems = 0;
+    switch (UT) {
+    case 4: elems = dbp::fused_smem_elems<4>(nwarps); break;
+    case 8: elems = dbp::fused_smem_elems<8>(nwarps); break;
+    case 16: elems = dbp::fused_smem_elems<16>(nwarps); break;
+    default: elems = dbp::fused_smem_elems<32>(nwarps); break;
+    }
+    return elems * (prec == DBP_FP32 ? sizeof(float2) : sizeof(double2));
+}
+
+size_t elem_bytes(int prec) { return prec == DBP_FP32 ? 8 : 16; }
+
+enum Kind { K_ADMM_UL = dbp::ALG_ADMM_UL, K_CG_UL = dbp::ALG_CG_UL, K_ADMM_DL = dbp::ALG_ADMM_DL };
+
+dbp_status validate(dbp_context *h, const dbp_frame_desc *d, Kind kind) {
+    if (!h) return DBP_ERR_INVALID_ARG;
+    if (!d) return fail(h, DBP_ERR_INVALID_ARG, "descriptor is NULL");
+    if (d->B <= 0 || d->C <= 0 || d->U <= 0 || d->W < 0 || d->N < 0)
+        return fail(h, DBP_ERR_INVALID_ARG, "shape must have B, C, U > 0 and W, N >= 0 (B=%d C=%d U=%d W=%d N=%d)",
+                    d->B, d->C, d->U, d->W, d->N);
+    if (d->B % d->C != 0)
+        return fail(h, DBP_ERR_INVALID_ARG, "B=%d is not a multiple of C=%d", d->B, d->C);
+    if (d->precision != DBP_FP32 && d->precision != DBP_FP64)
+        return fail(h, DBP_ERR_INVALID_ARG, "unknown precision %d", d->precision);
+    const int umax = (d->precision == DBP_FP32) ? 32 : 16;
+    if (d->U > umax)
+        return fail(h, DBP_ERR_UNSUPPORTED, "U=%d exceeds %d users for this precision", d->U, umax);
+    if (d->qam_order != 0 && d->qam_order != 4 && d->qam_order != 16 && d->qam_order != 64 && d->qam_order != 256)
+        return fail(h, DBP_ERR_INVALID_ARG, "qam_order %d is not 0, 4, 16, 64 or 256", d->qam_order);
+    if (kind == K_CG_UL) {
+        if (d->T_max < 0) return fail(h, DBP_ERR_INVALID_ARG, "CG needs T_max >= 0");
+        if (d->regularizer != DBP_REG_ZF && d->regularizer != DBP_REG_MMSE)
+            return fail(h, DBP_ERR_INVALID_ARG, "CG supports the ZF and MMSE regularisers only");
+    } else {
+        if (d->T_max < 1) return fail(h, DBP_ERR_INVALID_ARG, "ADMM needs T_max >= 1");
+        if (!(d->rho > 0.0) || !std::isfinite(d->rho))
+            return fail(h, DBP_ERR_INVALID_ARG, "ADMM needs a finite rho > 0");
+        if (!std::isfinite(d->gamma)) return fail(h, DBP_ERR_INVALID_ARG, "gamma must be finite");
+    }
+    if (kind == K_ADMM_UL) {
+        if (d->regularizer < DBP_REG_ZF || d->regularizer > DBP_REG_BOX)
+            return fail(h, DBP_ERR_INVALID_ARG, "unknown regulariser %d", d->regularizer);
+        if (d->regularizer == DBP_REG_BOX && !(d->box_r > 0.0))
+            return fail(h, DBP_ERR_INVALID_ARG, "BOX regulariser needs box_r > 0");
+    }
+    if (kind != K_ADMM_DL && d->regularizer == DBP_REG_MMSE) {
+        if (!(d->Es > 0.0) || !(d->N0 >= 0.0) || !std::isfinite(d->N0))
+            return fail(h, DBP_ERR_INVALID_ARG, "MMSE needs Es > 0 and finite N0 >= 0");
+    }
+    return DBP_OK;
+}
+
+dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Shape &s) {
+    const int UT = next_pow2_ut(d->U);
+    const int maxw = max_warps_for(d->precision, UT);
+    const int C = d->C;
+    const dbp_tuning &t = h->tuning;
+    bool want_clu = (t.mapping == DBP_MAP_CLUSTER) || (t.mapping == DBP_MAP_AUTO && C > maxw);
+    if (t.mapping == DBP_MAP_CTA && C > maxw)
+        return fail(h, DBP_ERR_UNSUPPORTED, "C=%d clusters need %d warps; one CTA allows %d at U=%d", C, C, maxw, d->U);
+    if (!want_clu) {
+        const int target = t.warps_per_cta > 0 ? t.warps_per_cta : 8;
+        int P = target / C;
+        if (P < 1) P = 1;
+        while (P > 1 && (P * C > maxw || smem_bytes_for(d->precision, UT, P * C) > h->smem_optin)) --P;
+        s.clu = false;
+        s.P = P;
+        s.CPB = C;
+        s.CL = 1;
+        s.nwarps = P * C;
+        s.grid = (d->W + P - 1) / P;
+    } else {
+        int CL = 0;
+        if (t.mapping == DBP_MAP_CLUSTER && t.cluster_size > 0) {
+            CL = t.cluster_size;
+            if (C % CL != 0 || C / CL > maxw || CL > 16)
+                return fail(h, DBP_ERR_INVALID_ARG, "cluster size %d does not fit C=%d", CL, C);
+        } else {
+            for (int k = 1; k <= 16; ++k)
+                if (C % k == 0 && C / k <= maxw) { CL = k; break; }
+            if (t.mapping == DBP_MAP_CLUSTER && CL == 1 && C % 2 == 0) CL = 2;
+        }
+        if (CL == 0)
+            return fail(h, DBP_ERR_UNSUPPORTED, "no thread-block cluster of <= 16 CTAs holds C=%d at U=%d", C, d->U);
+        s.clu = true;
+        s.P = 1;
+        s.CL = CL;
+        s.CPB = C / CL;
+        s.nwarps = s.CPB;
+        s.grid = (long long)d->W * CL;
+    }
+    s.smem = smem_bytes_for(d->precision, UT, s.nwarps);
+    if (s.smem > h->smem_optin)
+        return fail(h, DBP_ERR_UNSUPPORTED, "needs %zu B shared memory per CTA, device allows %zu", s.smem, h->smem_optin);
+    if (s.grid > 0x7fffffffLL) return fail(h, DBP_ERR_UNSUPPORTED, "grid too large");
+    return DBP_OK;
+}
+
+void fill_params(FusedParams &p, const dbp_frame_desc *d, const Shape &s) {
+    std::memset(&p, 0, sizeof p);
+    p.W = d->W; p.N = d->N; p.B = d->B; p.C = d->C; p.U = d->U; p.S = d->B / d->C; p.T = d->T_max;
+    p.P = s.P; p.CPB = s.CPB; p.CL = s.CL;
+    p.reg = d->regularizer;
+    p.rho = d->rho;
+    p.gamma = d->gamma;
+    p.invC = 1.0 / d->C;
+    p.box_r = d->box_r;
+    if (d->regularizer == DBP_REG_MMSE && d->rho > 0.0)
+        p.e2_scale = 1.0 / (d->N0 / (d->rho * d->Es) + d->C);    // Alg. 1 scaling
+    else
+        p.e2_scale = 1.0 / d->C;                                 // (E2-ZF)
+    p.rho_cg = (d->regularizer == DBP_REG_MMSE) ? d->N0 / d->Es : 0.0;
+    p.kappa = std::fmax((double)d->U / d->B, 1.0 / d->C);
+    p.inv_rho = d->rho > 0.0 ? 1.0 / d->rho : 0.0;
+    if (d->qam_order > 0) {
+        const int M = d->qam_order;
+        int L = 1;
+        while (L * L < M) ++L;
+        int m = 0;
+        while ((1 << m) < M) ++m;
+        p.qam_M = M;
+        p.qam_L = L;
+        p.qam_half = m / 2;
+        p.qam_inv_a = 1.0 / std::sqrt(3.0 / (2.0 * (M - 1)));
+    }
+}
+
+bool aligned(const void *ptr, size_t a) { return (reinterpret_cast<uintptr_t>(ptr) % a) == 0; }
+
+dbp_status run(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void *H, const void *vin,
+               void *out, uint8_t *labels, double *beta_out, cudaStream_t st) {
+    dbp_status v = validate(h, d, kind);
+    if (v != DBP_OK) return v;
+    if ((long long)d->W * d->N == 0) return DBP_OK;   // nothing to compute
+    if (!H || !vin || !out) return fail(h, DBP_ERR_INVALID_ARG, "NULL data pointer");
+    const size_t eb = elem_bytes(d->precision);
+    if (!aligned(H, eb) || !aligned(vin, eb) || !aligned(out, eb))
+        return fail(h, DBP_ERR_INVALID_ARG, "data pointers must be aligned to %zu bytes", eb);
+    Shape s;
+    v = choose_shape(h, d, s);
+    if (v != DBP_OK) return v;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+
+    FusedParams p;
+    fill_params(p, d, s);
+    p.H = H;
+    p.vin = vin;
+    p.out = out;
+    p.labels = (kind != K_ADMM_DL && d->qam_order > 0) ? labels : nullptr;
+    const bool norm = (kind == K_ADMM_DL) && (d->flags & DBP_FLAG_NORMALIZE);
+    if (norm) {
+        if (!h->energy) {
+            e = cudaMalloc(&h->energy, sizeof(double));
+            if (e != cudaSuccess) return fail(h, DBP_ERR_NOMEM, "cudaMalloc(energy): %s", cudaGetErrorString(e));
+        }
+        e = cudaMemsetAsync(h->energy, 0, sizeof(double), st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+        p.energy = h->energy;
+    }
+    const int UT = next_pow2_ut(d->U);
+    switch (kind) {
+    case K_ADMM_UL:
+        p.delta = d->rho;                 // B_c = H_c^H H_c + rho I
+        e = dbp_launch_admm_ul(d->precision, UT, p, s, st);
+        break;
+    case K_CG_UL:
+        p.delta = 0.0;                    // G_c = H_c^H H_c
+        e = dbp_launch_cg_ul(d->precision, UT, p, s, st);
+        break;
+    default:
+        p.delta = 1.0 / d->rho;           // B_c = H^d_c H^dH_c + rho^{-1} I
+        e = dbp_launch_admm_dl(d->precision, UT, p, s, st);
+        break;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+    if (norm) {
+        const size_t n = (size_t)d->W * d->N * d->B;
+        const double count = (double)n;   // unit mean power per antenna and sample
+        const int blocks = h->num_sms * 4;
+        if (d->precision == DBP_FP32)
+            dbp::dbp_scale_kernel<float><<<blocks, 256, 0, st>>>((float2 *)out, n, h->energy, count, beta_out);
+        else
+            dbp::dbp_scale_kernel<double><<<blocks, 256, 0, st>>>((double2 *)out, n, h->energy, count, beta_out);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(h, e, "normalisation launch");
+    }
+    return DBP_OK;
+}
+
+dbp_status ensure_dev(dbp_context *h, int slot, size_t bytes) {
+    if (h->dev_cap[slot] >= bytes) return DBP_OK;
+    if (h->dev[slot]) cudaFree(h->dev[slot]);
+    h->dev[slot] = nullptr;
+    h->dev_cap[slot] = 0;
+    if (bytes == 0) return DBP_OK;
+    cudaError_t e = cudaMalloc(&h->dev[slot], bytes);
+    if (e != cudaSuccess) return fail(h, DBP_ERR_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    h->dev_cap[slot] = bytes;
+    return DBP_OK;
+}
+
+dbp_status run_host(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void *H, const void *vin,
+                    void *out, uint8_t *labels, double *beta_out, cudaStream_t st) {
+    dbp_status v = validate(h, d, kind);
+    if (v != DBP_OK) return v;
+    if ((long long)d->W * d->N == 0) return DBP_OK;
+    if (!H || !vin || !out) return fail(h, DBP_ERR_INVALID_ARG, "NULL data pointer");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    const size_t eb = elem_bytes(d->precision);
+    const size_t W = d->W, N = d->N, B = d->B, U = d->U;
+    const size_t bH = W * B * U * eb;
+    const size_t bin = (kind == K_ADMM_DL) ? W * N * U * eb : W * N * B * eb;
+    const size_t bout = (kind == K_ADMM_DL) ? W * N * B * eb : W * N * U * eb;
+    const bool want_labels = (kind != K_ADMM_DL) && labels && d->qam_order > 0;
+    const size_t blab = want_labels ? W * N * U : 0;
+    const bool want_beta = (kind == K_ADMM_DL) && beta_out && (d->flags & DBP_FLAG_NORMALIZE);
+    if ((v = ensure_dev(h, 0, bH)) != DBP_OK) return v;
+    if ((v = ensure_dev(h, 1, bin)) != DBP_OK) return v;
+    if ((v = ensure_dev(h, 2, bout)) != DBP_OK) return v;
+    const size_t lab_pad = ((blab + 15) / 16) * 16;
+    if ((v = ensure_dev(h, 3, lab_pad + (want_beta ? 16 : 0))) != DBP_OK) return v;
+    uint8_t *dlab = want_labels ? (uint8_t *)h->dev[3] : nullptr;
+    double *dbeta = want_beta ? (double *)((char *)h->dev[3] + lab_pad) : nullptr;
+    if ((e = cudaMemcpyAsync(h->dev[0], H, bH, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(h, e, "copy H");
+    if ((e = cudaMemcpyAsync(h->dev[1], vin, bin, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(h, e, "copy input");
+    v = run(h, d, kind, h->dev[0], h->dev[1], h->dev[2], dlab, dbeta, st);
+    if (v != DBP_OK) return v;
+    if ((e = cudaMemcpyAsync(out, h->dev[2], bout, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_fail(h, e, "copy output");
+    if (want_labels && (e = cudaMemcpyAsync(labels, dlab, blab, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(h, e, "copy labels");
+    if (want_beta && (e = cudaMemcpyAsync(beta_out, dbeta, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(h, e, "copy beta");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    return DBP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dbp_version(void) { return "dbp-b300 0.1 (sm_103a)"; }
+
+dbp_status dbp_create(dbp_handle_t *out, const dbp_config *cfg) {
+    if (!out) return DBP_ERR_INVALID_ARG;
+    *out = nullptr;
+    dbp_context *h = new (std::nothrow) dbp_context();
+    if (!h) return DBP_ERR_NOMEM;
+    h->device = cfg ? cfg->device : 0;
+    h->budget = cfg ? cfg->hbm_budget_bytes : 0;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev <= h->device || h->device < 0) {
+        delete h;
+        return DBP_ERR_CUDA;
+    }
+    if ((e = cudaSetDevice(h->device)) != cudaSuccess) { delete h; return DBP_ERR_CUDA; }
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, h->device)) != cudaSuccess) { delete h; return DBP_ERR_CUDA; }
+    h->num_sms = prop.multiProcessorCount;
+    h->smem_optin = prop.sharedMemPerBlockOptin;
+    h->tuning.mapping = DBP_MAP_AUTO;
+    h->tuning.cluster_size = 0;
+    h->tuning.warps_per_cta = 0;
+    *out = h;
+    return DBP_OK;
+}
+
+dbp_status dbp_destroy(dbp_handle_t h) {
+    if (!h) return DBP_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    if (h->energy) cudaFree(h->energy);
+    for (int i = 0; i < 4; ++i)
+        if (h->dev[i]) cudaFree(h->dev[i]);
+    delete h;
+    return DBP_OK;
+}
+
+const char *dbp_last_error(dbp_handle_t h) { return h ? h->err.c_str() : "NULL handle"; }
+
+dbp_status dbp_set_tuning(dbp_handle_t h, const dbp_tuning *t) {
+    if (!h || !t) return DBP_ERR_INVALID_ARG;
+    if (t->mapping < DBP_MAP_AUTO || t->mapping > DBP_MAP_CLUSTER || t->cluster_size < 0 || t->cluster_size > 16 ||
+        t->warps_per_cta < 0 || t->warps_per_cta > 32)
+        return fail(h, DBP_ERR_INVALID_ARG, "bad tuning values");
+    h->tuning = *t;
+    return DBP_OK;
+}
+
+dbp_status dbp_uplink_admm(dbp_handle_t h, const dbp_frame_desc *d, const void *H, const void *y, void *x_hat,
+                           uint8_t *labels, void *stream) {
+    return run(h, d, K_ADMM_UL, H, y, x_hat, labels, nullptr, (cudaStream_t)stream);
+}
+
+dbp_status dbp_uplink_cg(dbp_handle_t h, const dbp_frame_desc *d, const void *H, const void *y, void *x_hat,
+                         uint8_t *labels, void *stream) {
+    return run(h, d, K_CG_UL, H, y, x_hat, labels, nullptr, (cudaStream_t)stream);
+}
+
+dbp_status dbp_downlink_admm(dbp_handle_t h, const dbp_frame_desc *d, const void *H, const void *s, void *x,
+                             double *beta_out, void *stream) {
+    return run(h, d, K_ADMM_DL, H, s, x, nullptr, beta_out, (cudaStream_t)stream);
+}
+
+dbp_status dbp_uplink_admm_host(dbp_handle_t h, const dbp_frame_desc *d, const void *H, const void *y,
+                                void *x_hat, uint8_t *labels, void *stream) {
+    return run_host(h, d, K_ADMM_UL, H, y, x_hat, labels, nullptr, (cudaStream_t)stream);
+}
+
+dbp_status dbp_uplink_cg_host(dbp_handle_t h, const dbp_frame_desc *d, const void *H, const void *y, void *x_hat,
+                              uint8_t *labels, void *stream) {
+    return run_host(h, d, K_CG_UL, H, y, x_hat, labels, nullptr, (cudaStream_t)stream);
+}
+
+dbp_status dbp_downlink_admm_host(dbp_handle_t h, const dbp_frame_desc *d, const void *H, const void *s, void *x,
+                                  double *beta_out, void *stream) {
+    return run_host(h, d, K_ADMM_DL, H, s, x, nullptr, beta_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,6 @@
+// dbp_k_admm_dl.cu -- instantiates the fused kernels of one algorithm.
+#include "dbp_launch.cuh"
+
+cudaError_t dbp_launch_admm_dl(int prec, int UT, const dbp::FusedParams &p, const dbp::Shape &s, cudaStream_t st) {
+    return dbp::launch_alg<dbp::ALG_ADMM_DL>(prec, UT, p, s, st);
+}

@@ -1,0 +1,6 @@
+// dbp_k_cg_ul.cu -- instantiates the fused kernels of one algorithm.
+#include "dbp_launch.cuh"
+
+cudaError_t dbp_launch_cg_ul(int prec, int UT, const dbp::FusedParams &p, const dbp::Shape &s, cudaStream_t st) {
+    return dbp::launch_alg<dbp::ALG_CG_UL>(prec, UT, p, s, st);
+}
