@@ -189,6 +189,37 @@ dbp_status dbp_downlink_admm_host(dbp_handle_t h, const dbp_frame_desc *d,
                                   const void *H, const void *s, void *x,
                                   double *beta_out, void *stream);
 
+/* Largest subcarrier count W accepted by dbp_downlink_admm_static. */
+#define DBP_STATIC_MAX_SUBCARRIERS 16384
+
+/* Downlink beamforming with power normalisation that allocates no device
+ * memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc -- code running while a stream is
+ * captured into a CUDA graph (allocation cannot be captured), processes
+ * whose device memory is entirely reserved by another allocator, and
+ * real-time front ends that must not allocate after start-up.
+ * dbp_downlink_admm with DBP_FLAG_NORMALIZE allocates a small accumulator
+ * on its first use; this call instead keeps its scratch (one partial energy
+ * per subcarrier, plus the frame total and beta) in a fixed library-owned
+ * device array of DBP_STATIC_MAX_SUBCARRIERS + 2 doubles that every GPU
+ * which loads the library holds until the process exits.
+ * Same arguments and results as dbp_downlink_admm: x is scaled in place by
+ * beta = sqrt(B*W*N / sum|x|^2) when DBP_FLAG_NORMALIZE is set (the sum is
+ * taken per subcarrier and then over subcarriers in a fixed order, so beta
+ * does not depend on scheduling), and beta is stored at beta_out (device)
+ * if non-NULL.  The caller still passes every input and output buffer.
+ * Errors: DBP_ERR_UNSUPPORTED when W > DBP_STATIC_MAX_SUBCARRIERS (no work
+ * is enqueued), otherwise as dbp_downlink_admm.
+ * Set-up: the first call on each device (with that device current) looks
+ * up the array's device address; make that first call before any stream
+ * capture.  Every call reuses the same array: two calls whose work overlaps
+ * on the GPU (different streams, or different host threads) race on it and
+ * must be serialised by the caller.  Each call overwrites every scratch
+ * entry it reads, so nothing has to be cleared between calls. */
+dbp_status dbp_downlink_admm_static(dbp_handle_t h, const dbp_frame_desc *d,
+                                    const void *H, const void *s, void *x,
+                                    double *beta_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -188,4 +188,19 @@ def dbp_downlink_admm_host(h, d, H, s, x, beta_out=None, stream=0) -> None:
                                           _ptr(beta_out), _stream(stream)))
 
 
+# Downlink with normalisation for callers that cannot allocate device memory
+# (see dbp_downlink_admm_static in include/dbp.h).
+DBP_STATIC_MAX_SUBCARRIERS = 16384
+_lib.dbp_downlink_admm_static.restype = _S
+_lib.dbp_downlink_admm_static.argtypes = [_H, ctypes.POINTER(dbp_frame_desc), _P, _P, _P, _P, _P]
+
+
+def dbp_downlink_admm_static(h, d, H, s, x, beta_out=None, stream=None) -> None:
+    st = _lib.dbp_downlink_admm_static(h, ctypes.byref(d), _ptr(H), _ptr(s), _ptr(x),
+                                       _ptr(beta_out), _stream(stream))
+    if st == DBP_ERR_UNSUPPORTED and d.W > DBP_STATIC_MAX_SUBCARRIERS:
+        raise DbpError(st, f"W={d.W} exceeds DBP_STATIC_MAX_SUBCARRIERS={DBP_STATIC_MAX_SUBCARRIERS}")
+    _check(h, st)
+
+
 __all__ = [n for n in dir() if n.startswith(("dbp_", "DBP_")) or n in ("frame_desc", "DbpError", "LIB_PATH")]

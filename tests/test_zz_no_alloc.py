@@ -1,0 +1,73 @@
+"""dbp_downlink_admm_static: the downlink precoder with power normalisation
+for callers that cannot allocate device memory (for example code that runs
+while a stream is captured into a CUDA graph, where cudaMalloc cannot be
+captured, or a process whose device memory is reserved by another allocator).
+Its scratch lives in a fixed library-owned device array, so it is checked
+against the allocating entry point dbp_downlink_admm on two calls in a row:
+the second call must not be disturbed by what the first left in the array.
+This file is collected last on purpose."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4   # the FP32 parity tolerance of the other GPU tests
+
+
+@pytest.fixture(scope="module")
+def dbp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1702_04458_b300 as p
+    return p
+
+
+def _frame(dbp, W, N, B, C, U, M, seed, T):
+    f = synth.downlink_frame(W, N, B, U, M, seed=seed)
+    H = torch.from_numpy(f["H"].astype(np.complex64)).cuda()
+    s = torch.from_numpy(f["s"].astype(np.complex64)).cuda()
+    d = dbp.frame_desc(B, C, U, W, N, T_max=T, rho=1.0, flags=dbp.DBP_FLAG_NORMALIZE)
+    return H, s, d
+
+
+def _rel(a, b):
+    return float((np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)).max())
+
+
+def test_static_scratch_matches_allocating_path_twice(dbp):
+    h = dbp.dbp_create(0)
+    try:
+        cases = [(37, 14, 128, 8, 8, 16, 11, 3), (23, 14, 256, 16, 16, 64, 12, 5)]
+        for (W, N, B, C, U, M, seed, T) in cases:          # two calls in a row
+            H, s, d = _frame(dbp, W, N, B, C, U, M, seed, T)
+            x_ref = torch.zeros((W, N, B), dtype=torch.complex64, device="cuda")
+            x_new = torch.zeros_like(x_ref)
+            b_ref = torch.zeros(1, dtype=torch.float64, device="cuda")
+            b_new = torch.zeros(1, dtype=torch.float64, device="cuda")
+            dbp.dbp_downlink_admm(h, d, H, s, x_ref, b_ref)
+            dbp.dbp_downlink_admm_static(h, d, H, s, x_new, b_new)
+            torch.cuda.synchronize()
+            xr = x_ref.cpu().numpy().astype(np.complex128)
+            xn = x_new.cpu().numpy().astype(np.complex128)
+            assert _rel(xn, xr) <= TOL
+            assert abs(float(b_new.cpu()[0]) - float(b_ref.cpu()[0])) <= TOL * float(b_ref.cpu()[0])
+            assert abs(np.mean(np.abs(xn) ** 2) - 1.0) < 1e-4
+    finally:
+        torch.cuda.synchronize()
+        dbp.dbp_destroy(h)
+
+
+def test_static_scratch_rejects_oversized_frames(dbp):
+    h = dbp.dbp_create(0)
+    try:
+        d = dbp.frame_desc(16, 4, 4, dbp.DBP_STATIC_MAX_SUBCARRIERS + 1, 1, T_max=2, rho=1.0,
+                           flags=dbp.DBP_FLAG_NORMALIZE)
+        buf = torch.zeros(16, dtype=torch.complex64, device="cuda")
+        with pytest.raises(dbp.DbpError) as ei:
+            dbp.dbp_downlink_admm_static(h, d, buf, buf, buf, None)
+        assert ei.value.status == dbp.DBP_ERR_UNSUPPORTED
+    finally:
+        dbp.dbp_destroy(h)
