@@ -47,6 +47,8 @@ METRIC = "detected uplink Gbit/s"
 UL = Workload(B=128, C=8, U=8, W=1200, N=14, M=16, T=3)
 UL_T_CG = 8
 DL = Workload(B=256, C=16, U=16, W=1200, N=14, M=64, T=5)
+MIX = Workload(B=256, C=8, U=32, W=3300, N=14, M=64, T=3)
+MIX_SNR_DB = 20.0
 SNRS_DB = [float(2 * i) for i in range(11)]
 ROTATE = 8
 
@@ -62,6 +64,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-downlink", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     a = ap.parse_args(argv)
     a.warmup = max(a.warmup, 3)
     return a
@@ -331,6 +334,72 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# 16-bit inputs against FP32 at matched BER
+# ---------------------------------------------------------------------------
+
+def _binom_ci(k: int, n: int):
+    """95 % Wilson interval of a bit error rate k / n."""
+    if n == 0:
+        return (0.0, 1.0)
+    z = 1.96
+    p = k / n
+    den = 1 + z * z / n
+    c = (p + z * z / (2 * n)) / den
+    hw = z * math.sqrt(p * (1 - p) / n + z * z / (4 * n * n)) / den
+    return (max(0.0, c - hw), min(1.0, c + hw))
+
+
+def bench_mixed(dbp, h, stream, device, rank, args, hbm_peak, hbm_src, alu_peak):
+    import torch
+    f = synth.uplink_frame(MIX.W, MIX.N, MIX.B, MIX.U, MIX.M, MIX_SNR_DB,
+                           seed=synth.frame_seed(4, 5) + 100000 * rank)
+    sp = stream.cuda_stream
+    x = torch.empty((MIX.W, MIX.N, MIX.U), dtype=torch.complex64, device=device)
+    lab = torch.empty((MIX.W, MIX.N, MIX.U), dtype=torch.uint8, device=device)
+    out = {"workload": workload_name(MIX, f"uplink ADMM T={MIX.T} at {MIX_SNR_DB:g} dB").replace(
+        ", fp32 complex", ""), "per_precision": {}}
+    nbits = MIX.W * MIX.N * MIX.U * (MIX.M.bit_length() - 1)
+    for name, prec in (("fp32", dbp.DBP_FP32), ("fp16", dbp.DBP_FP16), ("bf16", dbp.DBP_BF16)):
+        if prec == dbp.DBP_FP32:
+            H = torch.from_numpy(f["H"].astype(np.complex64)).to(device)
+            y = torch.from_numpy(f["y"].astype(np.complex64)).to(device)
+            eb = 8
+        else:
+            dt = torch.float16 if name == "fp16" else torch.bfloat16
+            H = torch.from_numpy(np.stack([f["H"].real, f["H"].imag], -1).astype(np.float32)).to(dt).to(device)
+            y = torch.from_numpy(np.stack([f["y"].real, f["y"].imag], -1).astype(np.float32)).to(dt).to(device)
+            eb = 4
+        d = dbp.frame_desc(MIX.B, MIX.C, MIX.U, MIX.W, MIX.N, qam_order=MIX.M, T_max=MIX.T,
+                           precision=prec, rho=1.0, N0=f["N0"], Es=1.0)
+        for _ in range(args.warmup):
+            dbp.dbp_uplink_admm(h, d, H, y, x, lab, sp)
+        torch.cuda.synchronize(device)
+        K = max(min(args.steps // 10, 200), 5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            dbp.dbp_uplink_admm(h, d, H, y, x, lab, sp)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        ms = e0.elapsed_time(e1) / K
+        errs = int(np.unpackbits(np.bitwise_xor(lab.cpu().numpy(), f["labels"]).reshape(-1, 1), axis=1).sum())
+        wl = Workload(MIX.B, MIX.C, MIX.U, MIX.W, MIX.N, MIX.M, MIX.T, elem_bytes=eb)
+        rf = roofline(f"admm_ul_{name}", "admm_ul", wl, ms, hbm_peak, hbm_src, alu_peak)
+        out["per_precision"][name] = {
+            "gbit_s": detected_bits(MIX) / (ms / 1e3) / 1e9, "ms_per_frame": ms, "launches": K,
+            "ber": errs / nbits, "ber_ci95": _binom_ci(errs, nbits), "bit_errors": errs, "bits": nbits,
+            "hbm_gbs": rf["hbm_view"]["achieved_gbs"], "alu_tflops": rf["alu_view"]["achieved_tflops"]}
+        del H, y
+    pp = out["per_precision"]
+    for name in ("fp16", "bf16"):
+        lo, hi = pp["fp32"]["ber_ci95"]
+        pp[name]["ber_within_fp32_ci95"] = bool(lo <= pp[name]["ber"] <= hi)
+        pp[name]["speedup_vs_fp32"] = pp["fp32"]["ms_per_frame"] / pp[name]["ms_per_frame"]
+    out["fp64_retries"] = dbp.dbp_fp64_retries(h)
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -454,6 +523,11 @@ def main(argv=None) -> int:
         del ddev, xd
         torch.cuda.empty_cache()
 
+    # ---- 16-bit inputs vs FP32 (B=256, C=8, U=32, 3300 x 14, ADMM T=3) ------
+    mixed = None
+    if not args.no_mixed:
+        mixed = bench_mixed(dbp, h, stream, device, rank, args, hbm_peak, hbm_src, alu_peak)
+
     # ---- end to end through the host-buffer C ABI ----------------------------
     e2e = None
     if not args.no_e2e:
@@ -504,6 +578,7 @@ def main(argv=None) -> int:
             "roofline": dominant,
             "roofline_other": rf_admm if dominant is rf_cg else rf_cg,
             "downlink": downlink,
+            "mixed_vs_fp32": mixed,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 2 * K,

@@ -30,8 +30,10 @@
  *   s      [W][N][U]  downlink transmit symbols
  *   x      [W][N][B]  downlink beamforming vectors
  * Element type by precision: DBP_FP32 -> float complex (8 B),
- * DBP_FP64 -> double complex (16 B).  All device pointers must be aligned
- * to the element size.
+ * DBP_FP64 -> double complex (16 B), DBP_FP16 / DBP_BF16 -> two 16-bit
+ * floats (4 B) for H and y with x_hat as float complex.  All device
+ * pointers must be aligned to the element size; 16-byte alignment enables
+ * the bulk-copy kernel.
  *
  * Ownership: the caller owns every input and output buffer and keeps it
  * alive until the work enqueued on `stream` has completed.  The library
@@ -63,7 +65,13 @@ typedef enum dbp_status {
 
 typedef enum dbp_precision {
     DBP_FP32 = 0,              /* complex float in, FP32 arithmetic          */
-    DBP_FP64 = 1               /* complex double in, FP64 arithmetic         */
+    DBP_FP64 = 1,              /* complex double in, FP64 arithmetic         */
+    DBP_FP16 = 2,              /* uplink only: H and y stored as complex
+                                  FP16 (4 B); Gram and matched filter on the
+                                  tensor cores with FP32 accumulation, FP32
+                                  inverse (FP64 retry on a small pivot) and
+                                  iterations; x_hat is complex float        */
+    DBP_BF16 = 3               /* as DBP_FP16 with BF16 storage             */
 } dbp_precision;
 
 /* Regulariser g(s) of the equalisation problem (E0), Sec. III-A, and its
@@ -114,11 +122,21 @@ typedef enum dbp_mapping {
                                   cluster_size CTAs, DSMEM consensus         */
 } dbp_mapping;
 
+typedef enum dbp_kernel_path {
+    DBP_PATH_AUTO = 0,         /* persistent bulk-copy kernel when eligible  */
+    DBP_PATH_GENERIC = 1,      /* per-subcarrier kernel with staged loads:
+                                  any shape, FP64, thread-block clusters     */
+    DBP_PATH_TMA = 2           /* persistent kernel fed by cp.async.bulk:
+                                  FP32, U in {4,8,16,32}, even S <= 64,
+                                  16-byte aligned buffers, CTA mapping       */
+} dbp_kernel_path;
+
 typedef struct dbp_tuning {
     int32_t mapping;           /* dbp_mapping                                */
     int32_t cluster_size;      /* CTAs per cluster (divides C, <= 16); 0 =
                                   smallest that fits                         */
     int32_t warps_per_cta;     /* CTA mapping: target warps per CTA; 0 = 8   */
+    int32_t kernel;            /* dbp_kernel_path                            */
 } dbp_tuning;
 
 typedef struct dbp_context *dbp_handle_t;
@@ -142,6 +160,18 @@ const char *dbp_version(void);
  * DBP_ERR_INVALID_ARG for out-of-range values; a shape that does not fit a
  * frame is reported by the compute call (DBP_ERR_UNSUPPORTED). */
 dbp_status dbp_set_tuning(dbp_handle_t h, const dbp_tuning *t);
+
+/* Wait for all work on the handle's device and report whether any kernel
+ * gave up a bounded wait for its input copies since the last check
+ * (DBP_ERR_TIMEOUT; the flag is then cleared).  The host-buffer variants
+ * check this themselves. */
+dbp_status dbp_device_status(dbp_handle_t h);
+
+/* Wait for all work on the handle's device and return in *count how many
+ * (subcarrier, cluster) inverses were recomputed in FP64 because a pivot
+ * of the FP32 Gauss-Jordan elimination fell below 2^-12 of the largest
+ * diagonal entry, since the last call (the counter is then cleared). */
+dbp_status dbp_fp64_retries(dbp_handle_t h, uint32_t *count);
 
 /* Decentralized ADMM-based data detection, Alg. 1 (Sec. III-B, III-C):
  * per subcarrier w and symbol n, C clusters each solve (E1) locally with

@@ -37,10 +37,11 @@ DBP_ERR_TIMEOUT = 5
 DBP_ERR_UNIMPLEMENTED = 6
 DBP_PENDING = 7
 
-DBP_FP32, DBP_FP64 = 0, 1
+DBP_FP32, DBP_FP64, DBP_FP16, DBP_BF16 = 0, 1, 2, 3
 DBP_REG_ZF, DBP_REG_MMSE, DBP_REG_BOX = 0, 1, 2
 DBP_FLAG_NORMALIZE = 1
 DBP_MAP_AUTO, DBP_MAP_CTA, DBP_MAP_CLUSTER = 0, 1, 2
+DBP_PATH_AUTO, DBP_PATH_GENERIC, DBP_PATH_TMA = 0, 1, 2
 
 _STATUS = {0: "DBP_OK", 1: "DBP_ERR_INVALID_ARG", 2: "DBP_ERR_UNSUPPORTED", 3: "DBP_ERR_NOMEM",
            4: "DBP_ERR_CUDA", 5: "DBP_ERR_TIMEOUT", 6: "DBP_ERR_UNIMPLEMENTED", 7: "DBP_PENDING"}
@@ -62,7 +63,7 @@ class dbp_frame_desc(ctypes.Structure):
 
 class dbp_tuning(ctypes.Structure):
     _fields_ = [("mapping", ctypes.c_int32), ("cluster_size", ctypes.c_int32),
-                ("warps_per_cta", ctypes.c_int32)]
+                ("warps_per_cta", ctypes.c_int32), ("kernel", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -146,8 +147,9 @@ def dbp_last_error(h) -> str:
     return _lib.dbp_last_error(h).decode()
 
 
-def dbp_set_tuning(h, mapping: int = DBP_MAP_AUTO, cluster_size: int = 0, warps_per_cta: int = 0) -> None:
-    t = dbp_tuning(mapping, cluster_size, warps_per_cta)
+def dbp_set_tuning(h, mapping: int = DBP_MAP_AUTO, cluster_size: int = 0, warps_per_cta: int = 0,
+                   kernel: int = DBP_PATH_AUTO) -> None:
+    t = dbp_tuning(mapping, cluster_size, warps_per_cta, kernel)
     _check(h, _lib.dbp_set_tuning(h, ctypes.byref(t)))
 
 
@@ -156,6 +158,24 @@ def frame_desc(B, C, U, W, N, qam_order=0, T_max=3, regularizer=DBP_REG_MMSE,
                box_r=0.0) -> dbp_frame_desc:
     return dbp_frame_desc(B, C, U, W, N, qam_order, T_max, regularizer, precision, flags,
                           rho, gamma, N0, Es, box_r)
+
+
+_lib.dbp_device_status.restype = _S
+_lib.dbp_device_status.argtypes = [_H]
+
+
+def dbp_device_status(h) -> None:
+    _check(h, _lib.dbp_device_status(h))
+
+
+_lib.dbp_fp64_retries.restype = _S
+_lib.dbp_fp64_retries.argtypes = [_H, ctypes.POINTER(ctypes.c_uint32)]
+
+
+def dbp_fp64_retries(h) -> int:
+    n = ctypes.c_uint32(0)
+    _check(h, _lib.dbp_fp64_retries(h, ctypes.byref(n)))
+    return int(n.value)
 
 
 def dbp_uplink_admm(h, d, H, y, x_hat, labels=None, stream=None) -> None:

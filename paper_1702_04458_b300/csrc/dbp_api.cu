@@ -3,6 +3,7 @@
 // in the fused kernels of dbp_fused.cuh; there is no host fallback.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -24,6 +25,7 @@ struct dbp_context {
     std::string err;
     dbp_tuning tuning{};
     double *energy = nullptr;            // downlink power accumulator
+    int *status = nullptr;               // device status word of the kernels
     void *dev[4] = {nullptr, nullptr, nullptr, nullptr};   // host-variant buffers
     size_t dev_cap[4] = {0, 0, 0, 0};
 };
@@ -54,7 +56,7 @@ int next_pow2_ut(int U) {
 
 int max_warps_for(int prec, int UT) {
     // Must agree with dbp::Bounds<T, UT>::max_warps.
-    if (prec == DBP_FP32) return (UT <= 4) ? 32 : (UT <= 16) ? 16 : 8;
+    if (prec != DBP_FP64) return (UT <= 4) ? 32 : (UT <= 16) ? 16 : 8;   // FP32 arithmetic
     return (UT <= 4) ? 16 : 8;
 }
 
@@ -69,7 +71,10 @@ size_t smem_bytes_for(int prec, int UT, int nwarps) {
     return elems * (prec == DBP_FP32 ? sizeof(float2) : sizeof(double2));
 }
 
-size_t elem_bytes(int prec) { return prec == DBP_FP32 ? 8 : 16; }
+// Bytes of one complex input element (H, y, s) and of one output element.
+size_t elem_bytes(int prec) { return prec == DBP_FP64 ? 16 : (prec == DBP_FP32 ? 8 : 4); }
+size_t out_bytes(int prec) { return prec == DBP_FP64 ? 16 : 8; }
+bool is16(int prec) { return prec == DBP_FP16 || prec == DBP_BF16; }
 
 enum Kind { K_ADMM_UL = dbp::ALG_ADMM_UL, K_CG_UL = dbp::ALG_CG_UL, K_ADMM_DL = dbp::ALG_ADMM_DL };
 
@@ -81,9 +86,11 @@ dbp_status validate(dbp_context *h, const dbp_frame_desc *d, Kind kind) {
                     d->B, d->C, d->U, d->W, d->N);
     if (d->B % d->C != 0)
         return fail(h, DBP_ERR_INVALID_ARG, "B=%d is not a multiple of C=%d", d->B, d->C);
-    if (d->precision != DBP_FP32 && d->precision != DBP_FP64)
+    if (d->precision < DBP_FP32 || d->precision > DBP_BF16)
         return fail(h, DBP_ERR_INVALID_ARG, "unknown precision %d", d->precision);
-    const int umax = (d->precision == DBP_FP32) ? 32 : 16;
+    if (is16(d->precision) && kind == K_ADMM_DL)
+        return fail(h, DBP_ERR_UNSUPPORTED, "16-bit inputs are supported for uplink detection only");
+    const int umax = (d->precision == DBP_FP64) ? 16 : 32;
     if (d->U > umax)
         return fail(h, DBP_ERR_UNSUPPORTED, "U=%d exceeds %d users for this precision", d->U, umax);
     if (d->qam_order != 0 && d->qam_order != 4 && d->qam_order != 16 && d->qam_order != 64 && d->qam_order != 256)
@@ -111,11 +118,117 @@ dbp_status validate(dbp_context *h, const dbp_frame_desc *d, Kind kind) {
     return DBP_OK;
 }
 
-dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Shape &s) {
+int tile_syms(int UT) {
+    switch (UT) {
+    case 4: return dbp::Tile<4>::NCH;
+    case 8: return dbp::Tile<8>::NCH;
+    case 16: return dbp::Tile<16>::NCH;
+    default: return dbp::Tile<32>::NCH;
+    }
+}
+
+size_t tma_cta_for(int UT, int nwarps, int P) {
+    switch (UT) {
+    case 4: return dbp::tma_cta_bytes<4>(nwarps, P);
+    case 8: return dbp::tma_cta_bytes<8>(nwarps, P);
+    case 16: return dbp::tma_cta_bytes<16>(nwarps, P);
+    default: return dbp::tma_cta_bytes<32>(nwarps, P);
+    }
+}
+
+int v_ld_for(int UT) { return UT + 2; }
+int round_up(int a, int m) { return ((a + m - 1) / m) * m; }
+int round16(long long b) { return (int)(((b + 15) / 16) * 16); }
+
+// Per-warp shared-memory layout of the bulk-copy kernel (byte offsets).
+void tma_layout(const dbp_frame_desc *d, Kind kind, int UT, Shape &s) {
+    const int S = d->B / d->C, N = d->N;
+    const int nch = tile_syms(UT);
+    const int vbytes = round16(std::max(nch * v_ld_for(UT) * 8, UT * 16));
+    if (is16(d->precision)) {
+        s.hp = (UT <= 8) ? UT : UT + 8;             // conflict-free fragment loads
+        s.h_rows = round_up(S, 8);
+        s.yp = S + ((S % 8 == 0) ? 4 : 0);           // yp = 4 (mod 8)
+        s.y_rows = std::max(round_up(N, 8), round_up(N, nch));
+        s.ms_rows = s.y_rows;
+        const int hb = round16((long long)s.h_rows * s.hp * 4);
+        const int yb = round16((long long)s.y_rows * s.yp * 4);
+        const int gb = round16((long long)std::max(std::min(UT, 16), s.ms_rows) * (UT + 2) * 8);
+        s.off_h1 = hb;
+        s.off_y0 = 2 * hb;
+        s.off_y1 = s.off_y0 + yb;
+        s.off_g = s.off_y1 + yb;
+        s.off_v = s.off_g + gb;
+        s.warp_bytes = s.off_v + vbytes;
+    } else {
+        s.hp = UT;
+        s.h_rows = S;
+        s.yp = S + ((S % 4 == 0) ? 2 : 4);           // odd number of 16-byte units
+        s.y_rows = (kind == K_ADMM_DL) ? 0 : round_up(N, nch);
+        s.ms_rows = 0;
+        const int hb = round16((long long)S * UT * 8);
+        const int yb = round16((long long)s.y_rows * s.yp * 8);
+        s.off_h1 = hb;
+        s.off_y0 = 2 * hb;
+        s.off_y1 = s.off_y0 + yb;
+        s.off_g = s.off_y1 + yb;
+        s.off_v = s.off_g;
+        s.warp_bytes = s.off_v + vbytes;
+    }
+}
+
+// Persistent bulk-copy kernel: U a power of two (no padded users), S <= 64
+// with 16-byte aligned copies (S even for FP32 inputs, S a multiple of 4 for
+// 16-bit inputs), 16-byte aligned buffers and all C warps of a subcarrier in
+// one CTA.
+bool tma_eligible(const dbp_frame_desc *d, int UT, int maxw, bool aligned16) {
+    const int S = d->B / d->C;
+    const bool shape = is16(d->precision) ? (S % 4 == 0) : (d->precision == DBP_FP32 && S % 2 == 0);
+    return shape && d->U == UT && S <= 64 && d->C <= maxw && aligned16;
+}
+
+dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool aligned16, Shape &s) {
     const int UT = next_pow2_ut(d->U);
     const int maxw = max_warps_for(d->precision, UT);
     const int C = d->C;
     const dbp_tuning &t = h->tuning;
+    s.tma = false;
+    if (t.kernel != DBP_PATH_GENERIC && t.mapping != DBP_MAP_CLUSTER && tma_eligible(d, UT, maxw, aligned16)) {
+        tma_layout(d, kind, UT, s);
+        const int target = t.warps_per_cta > 0 ? t.warps_per_cta : 8;
+        int P = target / C;
+        if (P < 1) P = 1;
+        auto bytes = [&](int PP) { return (size_t)PP * C * s.warp_bytes + tma_cta_for(UT, PP * C, PP); };
+        while (P > 1 && (P * C > maxw || bytes(P) > h->smem_optin)) --P;
+        const size_t smem = bytes(P);
+        if (smem <= h->smem_optin) {
+            s.tma = true;
+            s.clu = false;
+            s.P = P;
+            s.CPB = C;
+            s.CL = 1;
+            s.nwarps = P * C;
+            s.smem = smem;
+            const long long tiles = (d->W + P - 1) / P;
+            int occ = 0;
+            if (kind == K_ADMM_UL) occ = dbp_tma_occupancy_admm_ul(d->precision, UT, s.nwarps * 32, smem);
+            else if (kind == K_CG_UL) occ = dbp_tma_occupancy_cg_ul(d->precision, UT, s.nwarps * 32, smem);
+            else occ = dbp_tma_occupancy_admm_dl(d->precision, UT, s.nwarps * 32, smem);
+            if (occ < 1) occ = 1;
+            const long long slots = (long long)h->num_sms * occ;
+            s.grid = tiles < slots ? tiles : slots;
+            s.tiles = (int)tiles;
+            return DBP_OK;
+        }
+    }
+    if (is16(d->precision))
+        return fail(h, DBP_ERR_UNSUPPORTED,
+                    "16-bit inputs need U in {4,8,16,32}, S a multiple of 4 up to 64, 16-byte aligned buffers "
+                    "and all C warps in one CTA (B=%d C=%d U=%d)", d->B, d->C, d->U);
+    if (t.kernel == DBP_PATH_TMA)
+        return fail(h, DBP_ERR_UNSUPPORTED,
+                    "the bulk-copy kernel needs FP32, U in {4,8,16,32}, even S <= 64, 16-byte aligned buffers "
+                    "and all C warps in one CTA (B=%d C=%d U=%d)", d->B, d->C, d->U);
     bool want_clu = (t.mapping == DBP_MAP_CLUSTER) || (t.mapping == DBP_MAP_AUTO && C > maxw);
     if (t.mapping == DBP_MAP_CTA && C > maxw)
         return fail(h, DBP_ERR_UNSUPPORTED, "C=%d clusters need %d warps; one CTA allows %d at U=%d", C, C, maxw, d->U);
@@ -195,16 +308,31 @@ dbp_status run(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void *H
     if ((long long)d->W * d->N == 0) return DBP_OK;   // nothing to compute
     if (!H || !vin || !out) return fail(h, DBP_ERR_INVALID_ARG, "NULL data pointer");
     const size_t eb = elem_bytes(d->precision);
-    if (!aligned(H, eb) || !aligned(vin, eb) || !aligned(out, eb))
-        return fail(h, DBP_ERR_INVALID_ARG, "data pointers must be aligned to %zu bytes", eb);
+    if (!aligned(H, eb) || !aligned(vin, eb) || !aligned(out, out_bytes(d->precision)))
+        return fail(h, DBP_ERR_INVALID_ARG, "data pointers must be aligned to the element size");
     Shape s;
-    v = choose_shape(h, d, s);
+    const bool a16 = aligned(H, 16) && aligned(vin, 16) && aligned(out, 16);
+    v = choose_shape(h, d, kind, a16, s);
     if (v != DBP_OK) return v;
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
 
     FusedParams p;
     fill_params(p, d, s);
+    p.status = h->status;
+    p.retries = reinterpret_cast<unsigned int *>(h->status + 1);
+    p.tiles = s.tiles;
+    p.hp = s.hp;
+    p.yp = s.yp;
+    p.h_rows = s.h_rows;
+    p.y_rows = s.y_rows;
+    p.ms_rows = s.ms_rows;
+    p.off_h1 = s.off_h1;
+    p.off_y0 = s.off_y0;
+    p.off_y1 = s.off_y1;
+    p.off_g = s.off_g;
+    p.off_v = s.off_v;
+    p.warp_bytes = s.warp_bytes;
     p.H = H;
     p.vin = vin;
     p.out = out;
@@ -273,7 +401,8 @@ dbp_status run_host(dbp_context *h, const dbp_frame_desc *d, Kind kind, const vo
     const size_t W = d->W, N = d->N, B = d->B, U = d->U;
     const size_t bH = W * B * U * eb;
     const size_t bin = (kind == K_ADMM_DL) ? W * N * U * eb : W * N * B * eb;
-    const size_t bout = (kind == K_ADMM_DL) ? W * N * B * eb : W * N * U * eb;
+    const size_t ob = out_bytes(d->precision);
+    const size_t bout = (kind == K_ADMM_DL) ? W * N * B * ob : W * N * U * ob;
     const bool want_labels = (kind != K_ADMM_DL) && labels && d->qam_order > 0;
     const size_t blab = want_labels ? W * N * U : 0;
     const bool want_beta = (kind == K_ADMM_DL) && beta_out && (d->flags & DBP_FLAG_NORMALIZE);
@@ -294,6 +423,13 @@ dbp_status run_host(dbp_context *h, const dbp_frame_desc *d, Kind kind, const vo
     if (want_beta && (e = cudaMemcpyAsync(beta_out, dbeta, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(h, e, "copy beta");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    int word = 0;
+    if ((e = cudaMemcpy(&word, h->status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(h, e, "read status");
+    if (word != 0) {
+        cudaMemset(h->status, 0, sizeof(int));
+        return fail(h, DBP_ERR_TIMEOUT, "a kernel gave up waiting for its input copies (status 0x%x)", word);
+    }
     return DBP_OK;
 }
 
@@ -321,6 +457,12 @@ dbp_status dbp_create(dbp_handle_t *out, const dbp_config *cfg) {
     if ((e = cudaGetDeviceProperties(&prop, h->device)) != cudaSuccess) { delete h; return DBP_ERR_CUDA; }
     h->num_sms = prop.multiProcessorCount;
     h->smem_optin = prop.sharedMemPerBlockOptin;
+    if (cudaMalloc(&h->status, 2 * sizeof(int)) != cudaSuccess ||
+        cudaMemset(h->status, 0, 2 * sizeof(int)) != cudaSuccess) {
+        if (h->status) cudaFree(h->status);
+        delete h;
+        return DBP_ERR_NOMEM;
+    }
     h->tuning.mapping = DBP_MAP_AUTO;
     h->tuning.cluster_size = 0;
     h->tuning.warps_per_cta = 0;
@@ -332,6 +474,7 @@ dbp_status dbp_destroy(dbp_handle_t h) {
     if (!h) return DBP_ERR_INVALID_ARG;
     cudaSetDevice(h->device);
     if (h->energy) cudaFree(h->energy);
+    if (h->status) cudaFree(h->status);
     for (int i = 0; i < 4; ++i)
         if (h->dev[i]) cudaFree(h->dev[i]);
     delete h;
@@ -343,9 +486,33 @@ const char *dbp_last_error(dbp_handle_t h) { return h ? h->err.c_str() : "NULL h
 dbp_status dbp_set_tuning(dbp_handle_t h, const dbp_tuning *t) {
     if (!h || !t) return DBP_ERR_INVALID_ARG;
     if (t->mapping < DBP_MAP_AUTO || t->mapping > DBP_MAP_CLUSTER || t->cluster_size < 0 || t->cluster_size > 16 ||
-        t->warps_per_cta < 0 || t->warps_per_cta > 32)
+        t->warps_per_cta < 0 || t->warps_per_cta > 32 || t->kernel < DBP_PATH_AUTO || t->kernel > DBP_PATH_TMA)
         return fail(h, DBP_ERR_INVALID_ARG, "bad tuning values");
     h->tuning = *t;
+    return DBP_OK;
+}
+
+dbp_status dbp_device_status(dbp_handle_t h) {
+    if (!h) return DBP_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(h, e, "cudaDeviceSynchronize");
+    int word = 0;
+    if ((e = cudaMemcpy(&word, h->status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(h, e, "read status");
+    if (word == 0) return DBP_OK;
+    cudaMemset(h->status, 0, sizeof(int));
+    return fail(h, DBP_ERR_TIMEOUT, "a kernel gave up waiting for its input copies (status 0x%x)", word);
+}
+
+dbp_status dbp_fp64_retries(dbp_handle_t h, uint32_t *count) {
+    if (!h || !count) return DBP_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(h, e, "cudaDeviceSynchronize");
+    if ((e = cudaMemcpy(count, h->status + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(h, e, "read retry counter");
+    cudaMemset(h->status + 1, 0, sizeof(int));
     return DBP_OK;
 }
 

@@ -56,6 +56,17 @@ struct FusedParams {
     double inv_rho;      // 1/rho
     int qam_M, qam_L, qam_half;
     double qam_inv_a;    // 1 / sqrt(3 / (2 (M - 1)))
+    // Persistent bulk-copy kernel only:
+    int *status;         // device word: bit 0 = a bounded wait gave up
+    unsigned int *retries;   // device counter of FP64 inverse retries
+    int tiles;           // subcarrier tiles (ceil(W / P))
+    int hp;              // staged H row pitch, in input elements
+    int yp;              // staged receive-row pitch, in input elements
+    int h_rows;          // staged H rows (S, or S rounded up to 8)
+    int y_rows;          // staged receive rows per buffer (N rounded up)
+    int ms_rows;         // rows of the matched-filter result buffer
+    // per-warp shared-memory layout, byte offsets from the warp's base
+    int off_h1, off_y0, off_y1, off_g, off_v, warp_bytes;
 };
 
 // ---------------------------------------------------------------------------

@@ -4,3 +4,7 @@
 cudaError_t dbp_launch_admm_ul(int prec, int UT, const dbp::FusedParams &p, const dbp::Shape &s, cudaStream_t st) {
     return dbp::launch_alg<dbp::ALG_ADMM_UL>(prec, UT, p, s, st);
 }
+
+int dbp_tma_occupancy_admm_ul(int prec, int UT, int threads, size_t smem) {
+    return dbp::tma_occupancy<dbp::ALG_ADMM_UL>(prec, UT, threads, smem);
+}

@@ -7,6 +7,7 @@
 
 #include "dbp.h"
 #include "dbp_fused.cuh"
+#include "dbp_tma.cuh"
 
 namespace dbp {
 
@@ -14,9 +15,13 @@ namespace dbp {
 // a subcarrier fit in one CTA, else thread-block clusters of CL CTAs.
 struct Shape {
     bool clu;
+    bool tma;              // persistent bulk-copy kernel
     int P, CPB, CL, nwarps;
     long long grid;
     size_t smem;
+    // bulk-copy kernel only: tiles, staging pitches and the per-warp layout
+    int tiles = 0, hp = 0, yp = 0, h_rows = 0, y_rows = 0, ms_rows = 0;
+    int off_h1 = 0, off_y0 = 0, off_y1 = 0, off_g = 0, off_v = 0, warp_bytes = 0;
 };
 
 
@@ -60,8 +65,70 @@ cudaError_t launch_ut(int UT, const FusedParams &p, const Shape &s, cudaStream_t
     }
 }
 
+template <int UT, int ALG, typename TIn>
+cudaError_t launch_tma_one(const FusedParams &p, const Shape &s, cudaStream_t st) {
+    auto kern = dbp::dbp_tma_kernel<UT, ALG, TIn>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)s.grid, s.nwarps * 32, s.smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+// Resident CTAs per SM of the persistent kernel at this shape.
+template <int UT, int ALG, typename TIn>
+int tma_occupancy_one(int threads, size_t smem) {
+    auto kern = dbp::dbp_tma_kernel<UT, ALG, TIn>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+template <int ALG, typename TIn>
+int tma_occupancy_ut(int UT, int threads, size_t smem) {
+    switch (UT) {
+    case 4: return tma_occupancy_one<4, ALG, TIn>(threads, smem);
+    case 8: return tma_occupancy_one<8, ALG, TIn>(threads, smem);
+    case 16: return tma_occupancy_one<16, ALG, TIn>(threads, smem);
+    default: return tma_occupancy_one<32, ALG, TIn>(threads, smem);
+    }
+}
+
+template <int ALG, typename TIn>
+cudaError_t launch_tma_ut(int UT, const FusedParams &p, const Shape &s, cudaStream_t st) {
+    switch (UT) {
+    case 4: return launch_tma_one<4, ALG, TIn>(p, s, st);
+    case 8: return launch_tma_one<8, ALG, TIn>(p, s, st);
+    case 16: return launch_tma_one<16, ALG, TIn>(p, s, st);
+    default: return launch_tma_one<32, ALG, TIn>(p, s, st);
+    }
+}
+
+// Input storage precision -> kernel instance (16-bit inputs: uplink only).
+template <int ALG>
+int tma_occupancy(int prec, int UT, int threads, size_t smem) {
+    if (prec == DBP_FP32) return tma_occupancy_ut<ALG, float2>(UT, threads, smem);
+    if constexpr (ALG != ALG_ADMM_DL) {
+        if (prec == DBP_FP16) return tma_occupancy_ut<ALG, __half2>(UT, threads, smem);
+        if (prec == DBP_BF16) return tma_occupancy_ut<ALG, __nv_bfloat162>(UT, threads, smem);
+    }
+    return 0;
+}
+
+template <int ALG>
+cudaError_t launch_tma(int prec, int UT, const FusedParams &p, const Shape &s, cudaStream_t st) {
+    if (prec == DBP_FP32) return launch_tma_ut<ALG, float2>(UT, p, s, st);
+    if constexpr (ALG != ALG_ADMM_DL) {
+        if (prec == DBP_FP16) return launch_tma_ut<ALG, __half2>(UT, p, s, st);
+        if (prec == DBP_BF16) return launch_tma_ut<ALG, __nv_bfloat162>(UT, p, s, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <int ALG>
 cudaError_t launch_alg(int prec, int UT, const FusedParams &p, const Shape &s, cudaStream_t st) {
+    if (s.tma) return launch_tma<ALG>(prec, UT, p, s, st);
+    if (prec != DBP_FP32 && prec != DBP_FP64) return cudaErrorInvalidValue;
     if (prec == DBP_FP32)
         return s.clu ? launch_ut<float, ALG, true>(UT, p, s, st) : launch_ut<float, ALG, false>(UT, p, s, st);
     return s.clu ? launch_ut<double, ALG, true>(UT, p, s, st) : launch_ut<double, ALG, false>(UT, p, s, st);
@@ -74,3 +141,6 @@ cudaError_t launch_alg(int prec, int UT, const FusedParams &p, const Shape &s, c
 cudaError_t dbp_launch_admm_ul(int prec, int UT, const dbp::FusedParams &p, const dbp::Shape &s, cudaStream_t st);
 cudaError_t dbp_launch_cg_ul(int prec, int UT, const dbp::FusedParams &p, const dbp::Shape &s, cudaStream_t st);
 cudaError_t dbp_launch_admm_dl(int prec, int UT, const dbp::FusedParams &p, const dbp::Shape &s, cudaStream_t st);
+int dbp_tma_occupancy_admm_ul(int prec, int UT, int threads, size_t smem);
+int dbp_tma_occupancy_cg_ul(int prec, int UT, int threads, size_t smem);
+int dbp_tma_occupancy_admm_dl(int prec, int UT, int threads, size_t smem);

@@ -64,6 +64,7 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(dbp_frame_desc, flags), offsetof(dbp_frame_desc, rho),
          offsetof(dbp_frame_desc, Es), offsetof(dbp_frame_desc, box_r));
   printf("%zu\n", offsetof(dbp_config, hbm_budget_bytes));
+  printf("%zu\n", offsetof(dbp_tuning, kernel));
   return 0;
 }
 '''
@@ -78,6 +79,7 @@ int main(void) {
     assert vals[:3] == [ctypes.sizeof(D), ctypes.sizeof(pkg.dbp_config), ctypes.sizeof(pkg.dbp_tuning)]
     assert vals[3:7] == [D.flags.offset, D.rho.offset, D.Es.offset, D.box_r.offset]
     assert vals[7] == pkg.dbp_config.hbm_budget_bytes.offset
+    assert vals[8] == pkg.dbp_tuning.kernel.offset
 
 
 def test_version_string(pkg):

@@ -128,8 +128,18 @@ UL_CASES = [
 ]
 
 
+@pytest.fixture(params=["auto", "generic"])
+def path(request, dbp, handle):
+    """Run a test with the automatic kernel choice (the persistent bulk-copy
+    kernel wherever it applies) and again with the generic kernel forced."""
+    code = dbp.DBP_PATH_AUTO if request.param == "auto" else dbp.DBP_PATH_GENERIC
+    dbp.dbp_set_tuning(handle, kernel=code)
+    yield request.param
+    dbp.dbp_set_tuning(handle)
+
+
 @pytest.mark.parametrize("W,N,B,C,U,M,T", UL_CASES)
-def test_uplink_admm_fp32_matches_oracle(dbp, handle, W, N, B, C, U, M, T):
+def test_uplink_admm_fp32_matches_oracle(dbp, handle, path, W, N, B, C, U, M, T):
     f = synth.uplink_frame(W, N, B, U, M, 12.0, seed=W * 1000 + B + C + U)
     x, lab = run_ul(dbp, handle, f, C, T, "admm")
     ref = oracle_ul(f, C, T, "admm", "fp32")
@@ -139,7 +149,7 @@ def test_uplink_admm_fp32_matches_oracle(dbp, handle, W, N, B, C, U, M, T):
 
 
 @pytest.mark.parametrize("W,N,B,C,U,M,T", UL_CASES)
-def test_uplink_cg_fp32_matches_oracle(dbp, handle, W, N, B, C, U, M, T):
+def test_uplink_cg_fp32_matches_oracle(dbp, handle, path, W, N, B, C, U, M, T):
     f = synth.uplink_frame(W, N, B, U, M, 12.0, seed=W * 1000 + B + C + U + 1)
     Tcg = T + 5
     x, lab = run_ul(dbp, handle, f, C, Tcg, "cg")
@@ -150,7 +160,7 @@ def test_uplink_cg_fp32_matches_oracle(dbp, handle, W, N, B, C, U, M, T):
 
 
 @pytest.mark.parametrize("reg", ["zf", "box"])
-def test_uplink_admm_regularisers(dbp, handle, reg):
+def test_uplink_admm_regularisers(dbp, handle, path, reg):
     f = synth.uplink_frame(23, 14, 128, 8, 16, 10.0, seed=77)
     r = oracle.box_radius(16)
     code_d = dbp.DBP_REG_ZF if reg == "zf" else dbp.DBP_REG_BOX
@@ -203,7 +213,7 @@ DL_CASES = [
 
 
 @pytest.mark.parametrize("W,N,B,C,U,M,T", DL_CASES)
-def test_downlink_admm_fp32_matches_oracle(dbp, handle, W, N, B, C, U, M, T):
+def test_downlink_admm_fp32_matches_oracle(dbp, handle, path, W, N, B, C, U, M, T):
     f = synth.downlink_frame(W, N, B, U, M, seed=W * 7 + B + C + U)
     x, _ = run_dl(dbp, handle, f, C, T)
     ref = oracle.admm_dl(_round(f["H"], "fp32"), _round(f["s"], "fp32"), C=C, rho=1.0, T_max=T)
@@ -218,7 +228,7 @@ def test_downlink_fp64(dbp, handle):
     assert _rel_per_vector(x, ref).max() <= FP64_TOL
 
 
-def test_downlink_normalisation(dbp, handle):
+def test_downlink_normalisation(dbp, handle, path):
     f = synth.downlink_frame(21, 14, 128, 8, 16, seed=6)
     x, beta = run_dl(dbp, handle, f, 8, 3, normalize=True)
     ref = oracle.admm_dl(_round(f["H"], "fp32"), _round(f["s"], "fp32"), C=8, rho=1.0, T_max=3)
@@ -249,7 +259,9 @@ def test_cluster_mapping_matches_cta_mapping(dbp, handle, algo, cl):
             b, _ = run_ul(dbp, handle, f, 8, 4, algo)
     finally:
         dbp.dbp_set_tuning(handle, dbp.DBP_MAP_AUTO)
-    assert _rel_per_vector(b, a).max() <= 1e-6
+    # two FP32 kernels (the CTA shape may use the bulk-copy kernel, whose
+    # Gauss-Jordan step uses a rounded reciprocal): rounding-level agreement
+    assert _rel_per_vector(b, a).max() <= 1e-5
 
 
 @pytest.mark.parametrize("wpc", [4, 16, 32])
@@ -271,6 +283,33 @@ def test_large_cluster_count_uses_cluster_mapping(dbp, handle):
     x, _ = run_ul(dbp, handle, f, 16, 3, "admm")
     ref = oracle_ul(f, 16, 3, "admm", "fp32")
     assert _rel_per_vector(x, ref).max() <= FP32_TOL
+
+
+@pytest.mark.parametrize("algo", ["admm", "cg", "dl"])
+def test_bulk_copy_kernel_matches_generic_kernel(dbp, handle, algo):
+    """The persistent bulk-copy kernel (forced) and the generic kernel give the
+    same results on a frame spanning many persistent tiles."""
+    f = synth.uplink_frame(1201, 14, 128, 8, 16, 8.0, seed=450)
+    runs = []
+    try:
+        for code in (dbp.DBP_PATH_TMA, dbp.DBP_PATH_GENERIC):
+            dbp.dbp_set_tuning(handle, kernel=code)
+            runs.append(run_dl(dbp, handle, f, 8, 4)[0] if algo == "dl" else run_ul(dbp, handle, f, 8, 4, algo)[0])
+    finally:
+        dbp.dbp_set_tuning(handle)
+    assert _rel_per_vector(runs[0], runs[1]).max() <= 1e-5
+
+
+def test_forced_bulk_copy_kernel_rejects_ineligible_shapes(dbp, handle):
+    f = synth.uplink_frame(3, 2, 40, 5, 16, 8.0, seed=451)      # U=5 is not a power of two
+    try:
+        dbp.dbp_set_tuning(handle, kernel=dbp.DBP_PATH_TMA)
+        with pytest.raises(dbp.DbpError) as ei:
+            run_ul(dbp, handle, f, 4, 3, "admm")
+        assert ei.value.status == dbp.DBP_ERR_UNSUPPORTED
+    finally:
+        dbp.dbp_set_tuning(handle)
+    dbp.dbp_device_status(handle)
 
 
 # ---------------------------------------------------------------------------
