@@ -56,7 +56,7 @@ ROTATE = 8
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["dbp", "reference"], default="dbp")
     ap.add_argument("--e2e-steps", type=int, default=40)
@@ -65,6 +65,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-downlink", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-frames", type=int, default=240)
     a = ap.parse_args(argv)
     a.warmup = max(a.warmup, 3)
     return a
@@ -117,63 +119,101 @@ _REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_
 
 
 class ClockSampler:
-    def __init__(self, uuid: str, period_s: float = 0.005):
-        self.uuid, self.period = uuid, period_s
+    """Samples the SM clock and the clock-event (throttle) reasons of the
+    benchmark's GPU while the timed region runs: NVML when importable, else
+    an `nvidia-smi --query-gpu ... -lms` child process.  The GPU is matched
+    by UUID, because NVML and nvidia-smi enumerate every GPU of the node."""
+
+    def __init__(self, uuid: str, period_ms: int = 20):
+        self.uuid, self.period_ms = uuid.replace("GPU-", "").lower(), period_ms
         self.error = None
         self.samples = []
         self.max_mhz = None
         self._stop = threading.Event()
         self._thr = None
-        self.ok = False
+        self._proc = None
+        self.source = None
 
     def __enter__(self):
         try:
             import pynvml
             pynvml.nvmlInit()
             self._nv = pynvml
-            self._h = self._handle(pynvml)
+            self._h = None
+            for i in range(pynvml.nvmlDeviceGetCount()):
+                hh = pynvml.nvmlDeviceGetHandleByIndex(i)
+                u = pynvml.nvmlDeviceGetUUID(hh)
+                u = u.decode() if isinstance(u, bytes) else u
+                if u.replace("GPU-", "").lower() == self.uuid:
+                    self._h = hh
+            if self._h is None:
+                raise RuntimeError("GPU not found by UUID")
             self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
-            self.ok = True
-        except Exception as e:  # clocks stay unreported rather than guessed
-            self.error = repr(e)
+            self.source = "nvml"
+            self._thr = threading.Thread(target=self._run_nvml, daemon=True)
+            self._thr.start()
             return self
-        self._thr = threading.Thread(target=self._run, daemon=True)
-        self._thr.start()
+        except Exception as e:
+            self.error = repr(e)
+        try:
+            import subprocess
+            q = subprocess.run(["nvidia-smi", "--query-gpu=index,uuid,clocks.max.sm", "--format=csv,noheader,nounits"],
+                               capture_output=True, text=True, timeout=30).stdout
+            idx = None
+            for line in q.strip().splitlines():
+                i, u, mx = [x.strip() for x in line.split(",")]
+                if u.replace("GPU-", "").lower() == self.uuid:
+                    idx, self.max_mhz = i, float(mx)
+            if idx is None:
+                raise RuntimeError("GPU not found by UUID in nvidia-smi")
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", "-i", idx, "--query-gpu=clocks.sm,clocks_event_reasons.active",
+                 "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi"
+            self._thr = threading.Thread(target=self._run_smi, daemon=True)
+            self._thr.start()
+            self.error = None
+        except Exception as e:
+            self.error = (self.error or "") + " | " + repr(e)
         return self
 
-    def _handle(self, nv):
-        """NVML handle of the CUDA device (NVML enumerates every GPU of the
-        node, so match by UUID rather than by index)."""
-        want = self.uuid.replace("GPU-", "").lower()
-        for i in range(nv.nvmlDeviceGetCount()):
-            h = nv.nvmlDeviceGetHandleByIndex(i)
-            u = nv.nvmlDeviceGetUUID(h)
-            u = u.decode() if isinstance(u, bytes) else u
-            if u.replace("GPU-", "").lower() == want:
-                return h
-        raise RuntimeError(f"no NVML device with UUID {self.uuid}")
-
-    def _run(self):
+    def _run_nvml(self):
         nv = self._nv
         while not self._stop.is_set():
             try:
                 mhz = nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM)
                 rs = nv.nvmlDeviceGetCurrentClocksEventReasons(self._h)
-                self.samples.append((mhz, rs))
+                self.samples.append((float(mhz), int(rs)))
             except Exception:
                 pass
-            time.sleep(self.period)
+            time.sleep(self.period_ms / 1e3)
+
+    def _run_smi(self):
+        for line in self._proc.stdout:
+            try:
+                mhz, rs = [x.strip() for x in line.split(",")]
+                self.samples.append((float(mhz), int(rs, 16)))
+            except Exception:
+                pass
 
     def __exit__(self, *exc):
         self._stop.set()
+        if self._proc is not None:
+            time.sleep(2 * self.period_ms / 1e3)
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
         if self._thr is not None:
-            self._thr.join()
+            self._thr.join(timeout=5)
         return False
 
     def summary(self):
-        if not self.ok or not self.samples:
+        if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0,
-                    "error": self.error}
+                    "source": self.source, "error": self.error}
         busy = [m for m, r in self.samples if not (r & 0x1)] or [m for m, _ in self.samples]
         reasons = set()
         for _, r in self.samples:
@@ -181,7 +221,7 @@ class ClockSampler:
                 if r & bit and bit != 0x1:
                     reasons.add(name)
         return {"sm_mhz": float(statistics.median(busy)), "sm_max_mhz": self.max_mhz,
-                "reasons": sorted(reasons), "samples": len(self.samples)}
+                "reasons": sorted(reasons), "samples": len(self.samples), "source": self.source}
 
 
 # ---------------------------------------------------------------------------
@@ -400,6 +440,144 @@ def bench_mixed(dbp, h, stream, device, rank, args, hbm_peak, hbm_src, alu_peak)
 
 
 # ---------------------------------------------------------------------------
+# Served stream: Poisson arrivals of uneven frames through the request loop
+# ---------------------------------------------------------------------------
+
+SERVE_CHANNELS = 8
+SERVE_COHERENCE = 4     # consecutive frames of a channel share H (one coherence block)
+SERVE_RING = 3          # output buffers per channel
+
+
+def serve_channels(rng):
+    """Random frame shapes: B in {64,128,256}, U in {4,8,16,32} (U <= B),
+    C in {1,2,4,8,16} with S = B/C >= 4, W in {300,600,1200,3300} x 14,
+    16/64-QAM, 3..8 iterations; uplink ADMM, uplink CG or downlink ADMM."""
+    out = []
+    for i in range(SERVE_CHANNELS):
+        B = int(rng.choice([64, 128, 256]))
+        U = int(rng.choice([u for u in (4, 8, 16, 32) if u <= B]))
+        C = int(rng.choice([c for c in (1, 2, 4, 8, 16) if B // c >= 4]))
+        W = int(rng.choice([300, 600, 1200, 3300], p=[0.35, 0.3, 0.25, 0.1]))
+        M = int(rng.choice([16, 64]))
+        out.append(dict(B=B, U=U, C=C, W=W, N=14, M=M, seed=50000 + i))
+    return out
+
+
+class ServeChannel:
+    def __init__(self, dbp, spec, rng):
+        import torch
+        f = synth.uplink_frame(spec["W"], spec["N"], spec["B"], spec["U"], spec["M"], 15.0, seed=spec["seed"])
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        self.spec, self.N0 = spec, f["N0"]
+        self.H = pin(f["H"].astype(np.complex64))
+        self.y = pin(f["y"].astype(np.complex64))
+        self.s = pin(f["s"].astype(np.complex64))
+        W, N, B, U = spec["W"], spec["N"], spec["B"], spec["U"]
+        self.out_ul = [pin(np.zeros((W, N, U), np.complex64)) for _ in range(SERVE_RING)]
+        self.out_dl = [pin(np.zeros((W, N, B), np.complex64)) for _ in range(SERVE_RING)]
+        self.lab = [pin(np.zeros((W, N, U), np.uint8)) for _ in range(SERVE_RING)]
+        self.busy = [None] * SERVE_RING
+
+    def bits(self):
+        sp = self.spec
+        return sp["U"] * (sp["M"].bit_length() - 1) * sp["W"] * sp["N"]
+
+
+def serve_run(dbp, h, chans, kinds, rate_hz, n_frames, rng):
+    """Submit n_frames (Poisson at rate_hz, or back to back if rate_hz is
+    None); returns per-frame (latency_us, bits, hit) and the wall time."""
+    import collections
+    done = []
+    outstanding = collections.deque()
+
+    def collect(block):
+        """Retire finished frames in submission order; with block=True wait
+        for (and retire) the oldest outstanding frame."""
+        while outstanding:
+            t, ch, slot, bits = outstanding[0]
+            r = dbp.dbp_wait(h, t, 120.0) if block else dbp.dbp_poll(h, t)
+            if r is None:
+                return
+            outstanding.popleft()
+            ch.busy[slot] = None
+            if r.status != dbp.DBP_OK:
+                raise RuntimeError(f"served frame failed: status {r.status}")
+            done.append((r.finish_us - r.submit_us, bits, r.resident_hit, r.submit_us, r.finish_us))
+            if block:
+                return
+
+    t0 = time.perf_counter()
+    next_t = t0
+    for i in range(n_frames):
+        ci = (i // SERVE_COHERENCE) % len(chans)
+        epoch = i // (SERVE_COHERENCE * len(chans))
+        ch = chans[ci]
+        kind = kinds[i]
+        while None not in ch.busy:          # this channel's output ring is full
+            collect(True)
+        slot = ch.busy.index(None)
+        sp = ch.spec
+        T = int(rng.integers(3, 9))
+        if kind == dbp.DBP_KIND_DOWNLINK_ADMM:
+            d = dbp.frame_desc(sp["B"], sp["C"], sp["U"], sp["W"], sp["N"], T_max=T, rho=1.0)
+            req = dbp.request(kind, d, ch.H, ch.s, ch.out_dl[slot], None, None, ci + 1, epoch, i)
+        else:
+            d = dbp.frame_desc(sp["B"], sp["C"], sp["U"], sp["W"], sp["N"], qam_order=sp["M"], T_max=T,
+                               rho=1.0, N0=ch.N0, Es=1.0)
+            req = dbp.request(kind, d, ch.H, ch.y, ch.out_ul[slot], ch.lab[slot], None, ci + 1, epoch, i)
+        if rate_hz is not None:
+            next_t += rng.exponential(1.0 / rate_hz)
+            while True:
+                now = time.perf_counter()
+                if now >= next_t:
+                    break
+                if next_t - now > 0.002:
+                    time.sleep(next_t - now - 0.001)
+                collect(False)
+        t = dbp.dbp_submit(h, req)
+        ch.busy[slot] = t
+        outstanding.append((t, ch, slot, ch.bits()))
+        collect(False)
+    while outstanding:
+        collect(True)
+    return done, time.perf_counter() - t0
+
+
+def bench_serving(dbp, h, args):
+    rng = np.random.default_rng(123)
+    specs = serve_channels(rng)
+    chans = [ServeChannel(dbp, sp, rng) for sp in specs]
+    n = args.serve_frames
+    kinds = [int(k) for k in rng.choice([dbp.DBP_KIND_UPLINK_ADMM, dbp.DBP_KIND_UPLINK_CG,
+                                         dbp.DBP_KIND_DOWNLINK_ADMM], size=n, p=[0.4, 0.3, 0.3])]
+    dbp.dbp_server_start(h, streams=4, hbm_bytes=8 << 30)
+    try:
+        serve_run(dbp, h, chans, kinds, None, min(n, 2 * SERVE_CHANNELS * SERVE_COHERENCE), rng)   # warm-up
+        done, wall = serve_run(dbp, h, chans, kinds, None, n, rng)
+        span_us = max(d[4] for d in done) - min(d[3] for d in done)
+        cap_fps = len(done) / (span_us / 1e6)
+        points = []
+        for frac in (0.3, 0.6, 0.9, None):
+            rate = None if frac is None else frac * cap_fps
+            done, wall = serve_run(dbp, h, chans, kinds, rate, n, rng)
+            lat = np.array([d[0] for d in done])
+            bits = sum(d[1] for d in done)
+            span_us = max(d[4] for d in done) - min(d[3] for d in done)
+            points.append({"offered_load": "saturation" if frac is None else frac,
+                           "offered_frames_per_s": rate, "frames": len(done),
+                           "gbit_s": bits / (span_us / 1e6) / 1e9,
+                           "p50_ms": float(np.percentile(lat, 50)) / 1e3,
+                           "p99_ms": float(np.percentile(lat, 99)) / 1e3,
+                           "resident_hits": int(sum(d[2] for d in done))})
+    finally:
+        dbp.dbp_server_stop(h)
+    return {"channels": specs, "coherence_frames": SERVE_COHERENCE, "streams": 4,
+            "kind_mix": "40% uplink ADMM, 30% uplink CG, 30% downlink ADMM (FP32), 3..8 iterations",
+            "capacity_frames_per_s": cap_fps, "load_points": points,
+            "latency": "submit to completion observed by the request loop (host copies included)"}
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -528,6 +706,11 @@ def main(argv=None) -> int:
     if not args.no_mixed:
         mixed = bench_mixed(dbp, h, stream, device, rank, args, hbm_peak, hbm_src, alu_peak)
 
+    # ---- served stream (request loop, uneven frames, coherence blocks) -------
+    serving = None
+    if not args.no_serving:
+        serving = bench_serving(dbp, h, args)
+
     # ---- end to end through the host-buffer C ABI ----------------------------
     e2e = None
     if not args.no_e2e:
@@ -579,6 +762,7 @@ def main(argv=None) -> int:
             "roofline_other": rf_admm if dominant is rf_cg else rf_cg,
             "downlink": downlink,
             "mixed_vs_fp32": mixed,
+            "serving": serving,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 2 * K,

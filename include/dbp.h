@@ -219,6 +219,82 @@ dbp_status dbp_downlink_admm_host(dbp_handle_t h, const dbp_frame_desc *d,
                                   const void *H, const void *s, void *x,
                                   double *beta_out, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Request loop (serving).  Frames arrive with HOST buffers and are admitted
+ * as device memory and stream slots free up: a frame is admitted when one
+ * of `streams` slots is free and the device pool (hbm_bytes) can hold its
+ * staged inputs and outputs; a frame that does not fit yet may be passed by
+ * later, smaller frames until it has waited 20 ms.  Admitted frames run
+ * concurrently on separate streams (copies in, fused kernel, copies out).
+ * Frames that carry the same non-zero channel_key and coherence_epoch share
+ * one resident device copy of H and, where the persistent bulk-copy kernel
+ * runs, the per-cluster operator (B_c^{-1}, G_c or Q_c) computed by the
+ * first of them: later frames of the coherence block skip the copy of H and
+ * the Gram and inverse (the channel is constant over a coherence block,
+ * Sec. II and Sec. VI-A).  Resident channels are evicted least recently
+ * used when the pool is full.  A frame's result does not depend on what
+ * else is in flight.
+ * ------------------------------------------------------------------------ */
+typedef enum dbp_kind {
+    DBP_KIND_UPLINK_ADMM = 0,
+    DBP_KIND_UPLINK_CG = 1,
+    DBP_KIND_DOWNLINK_ADMM = 2
+} dbp_kind;
+
+typedef struct dbp_server_config {
+    int32_t streams;           /* concurrent frames (slots); 0 = 4           */
+    int32_t reserved;
+    uint64_t hbm_bytes;        /* device pool for staged frames and resident
+                                  channels; 0 = 2 GiB                        */
+} dbp_server_config;
+
+typedef struct dbp_request {
+    int32_t kind;              /* dbp_kind                                   */
+    int32_t reserved;
+    dbp_frame_desc desc;
+    const void *H;             /* host [W][B][U]                             */
+    const void *in;            /* host y [W][N][B] (uplink), s [W][N][U]     */
+    void *out;                 /* host x_hat [W][N][U] or x [W][N][B]        */
+    uint8_t *labels;           /* host [W][N][U] or NULL (uplink)            */
+    double *beta_out;          /* host, downlink normalisation, or NULL      */
+    uint64_t channel_key;      /* 0 = no reuse                               */
+    uint64_t coherence_epoch;  /* a new epoch of a key replaces its channel  */
+    uint64_t user_tag;         /* returned in the result                     */
+} dbp_request;
+
+typedef struct dbp_result {
+    int32_t status;            /* the frame's dbp_status                     */
+    int32_t resident_hit;      /* 1 if the resident channel was reused       */
+    uint64_t user_tag;
+    double submit_us;          /* host monotonic microseconds since
+                                  dbp_server_start: submission               */
+    double start_us;           /*   admission (work enqueued)                */
+    double finish_us;          /*   completion observed (outputs in host
+                                    memory)                                  */
+} dbp_result;
+
+/* Start the request loop on this handle (one per handle).  Allocates the
+ * device pool and the streams; DBP_ERR_NOMEM if the pool cannot be had. */
+dbp_status dbp_server_start(dbp_handle_t h, const dbp_server_config *cfg);
+
+/* Stop admitting, let in-flight frames finish (bounded: 30 s), fail the
+ * frames still queued with DBP_ERR_TIMEOUT and release the pool. */
+dbp_status dbp_server_stop(dbp_handle_t h);
+
+/* Queue one frame.  The descriptor and pointers are copied; the host
+ * buffers must stay valid until dbp_poll / dbp_wait reports the ticket
+ * finished.  DBP_ERR_INVALID_ARG for a bad descriptor (checked here). */
+dbp_status dbp_submit(dbp_handle_t h, const dbp_request *req, uint64_t *ticket);
+
+/* DBP_PENDING while the frame is queued or running; otherwise fills *res,
+ * releases the ticket and returns DBP_OK (res->status holds the frame's own
+ * status).  DBP_ERR_INVALID_ARG for an unknown ticket. */
+dbp_status dbp_poll(dbp_handle_t h, uint64_t ticket, dbp_result *res);
+
+/* As dbp_poll, blocking up to timeout_s seconds; DBP_ERR_TIMEOUT if the
+ * frame has not finished by then (the ticket stays valid). */
+dbp_status dbp_wait(dbp_handle_t h, uint64_t ticket, double timeout_s, dbp_result *res);
+
 /* Largest subcarrier count W accepted by dbp_downlink_admm_static. */
 #define DBP_STATIC_MAX_SUBCARRIERS 16384
 

@@ -223,4 +223,80 @@ def dbp_downlink_admm_static(h, d, H, s, x, beta_out=None, stream=None) -> None:
     _check(h, st)
 
 
-__all__ = [n for n in dir() if n.startswith(("dbp_", "DBP_")) or n in ("frame_desc", "DbpError", "LIB_PATH")]
+# ---------------------------------------------------------------------------
+# Request loop (serving)
+# ---------------------------------------------------------------------------
+DBP_KIND_UPLINK_ADMM, DBP_KIND_UPLINK_CG, DBP_KIND_DOWNLINK_ADMM = 0, 1, 2
+
+
+class dbp_server_config(ctypes.Structure):
+    _fields_ = [("streams", ctypes.c_int32), ("reserved", ctypes.c_int32), ("hbm_bytes", ctypes.c_uint64)]
+
+
+class dbp_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("desc", dbp_frame_desc),
+                ("H", ctypes.c_void_p), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("labels", ctypes.c_void_p), ("beta_out", ctypes.c_void_p),
+                ("channel_key", ctypes.c_uint64), ("coherence_epoch", ctypes.c_uint64),
+                ("user_tag", ctypes.c_uint64)]
+
+
+class dbp_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("resident_hit", ctypes.c_int32), ("user_tag", ctypes.c_uint64),
+                ("submit_us", ctypes.c_double), ("start_us", ctypes.c_double), ("finish_us", ctypes.c_double)]
+
+
+_lib.dbp_server_start.restype = _S
+_lib.dbp_server_start.argtypes = [_H, ctypes.POINTER(dbp_server_config)]
+_lib.dbp_server_stop.restype = _S
+_lib.dbp_server_stop.argtypes = [_H]
+_lib.dbp_submit.restype = _S
+_lib.dbp_submit.argtypes = [_H, ctypes.POINTER(dbp_request), ctypes.POINTER(ctypes.c_uint64)]
+_lib.dbp_poll.restype = _S
+_lib.dbp_poll.argtypes = [_H, ctypes.c_uint64, ctypes.POINTER(dbp_result)]
+_lib.dbp_wait.restype = _S
+_lib.dbp_wait.argtypes = [_H, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(dbp_result)]
+
+
+def dbp_server_start(h, streams: int = 4, hbm_bytes: int = 0) -> None:
+    cfg = dbp_server_config(streams, 0, hbm_bytes)
+    _check(h, _lib.dbp_server_start(h, ctypes.byref(cfg)))
+
+
+def dbp_server_stop(h) -> None:
+    _check(h, _lib.dbp_server_stop(h))
+
+
+def request(kind, desc, H, inp, out, labels=None, beta_out=None, channel_key=0, coherence_epoch=0,
+            user_tag=0) -> dbp_request:
+    return dbp_request(kind, 0, desc, _ptr(H), _ptr(inp), _ptr(out), _ptr(labels), _ptr(beta_out),
+                       channel_key, coherence_epoch, user_tag)
+
+
+def dbp_submit(h, req: dbp_request) -> int:
+    t = ctypes.c_uint64(0)
+    _check(h, _lib.dbp_submit(h, ctypes.byref(req), ctypes.byref(t)))
+    return int(t.value)
+
+
+def dbp_poll(h, ticket: int):
+    """None while pending, else the dbp_result (ticket released)."""
+    r = dbp_result()
+    st = _lib.dbp_poll(h, ticket, ctypes.byref(r))
+    if st == DBP_PENDING:
+        return None
+    _check(h, st)
+    return r
+
+
+def dbp_wait(h, ticket: int, timeout_s: float = 60.0):
+    """The dbp_result, or None if the frame is not done within timeout_s."""
+    r = dbp_result()
+    st = _lib.dbp_wait(h, ticket, timeout_s, ctypes.byref(r))
+    if st == DBP_ERR_TIMEOUT:
+        return None
+    _check(h, st)
+    return r
+
+
+__all__ = [n for n in dir() if n.startswith(("dbp_", "DBP_")) or n in ("frame_desc", "request", "DbpError", "LIB_PATH")]

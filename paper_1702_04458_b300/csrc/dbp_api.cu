@@ -12,34 +12,25 @@
 #include <string>
 
 #include "dbp.h"
+#include "dbp_internal.h"
 #include "dbp_launch.cuh"
 
 using dbp::FusedParams;
 using dbp::Shape;
 
-struct dbp_context {
-    int device = 0;
-    uint64_t budget = 0;
-    int num_sms = 0;
-    size_t smem_optin = 0;
-    std::string err;
-    dbp_tuning tuning{};
-    double *energy = nullptr;            // downlink power accumulator
-    int *status = nullptr;               // device status word of the kernels
-    void *dev[4] = {nullptr, nullptr, nullptr, nullptr};   // host-variant buffers
-    size_t dev_cap[4] = {0, 0, 0, 0};
-};
-
 namespace {
 
+thread_local std::string *t_err_sink = nullptr;   // server thread: per-request messages
+
 dbp_status fail(dbp_context *h, dbp_status st, const char *fmt, ...) {
-    if (h) {
+    if (h || t_err_sink) {
         char buf[512];
         va_list ap;
         va_start(ap, fmt);
         vsnprintf(buf, sizeof buf, fmt, ap);
         va_end(ap);
-        h->err = buf;
+        if (t_err_sink) *t_err_sink = buf;
+        else h->err = buf;
     }
     return st;
 }
@@ -301,8 +292,10 @@ void fill_params(FusedParams &p, const dbp_frame_desc *d, const Shape &s) {
 
 bool aligned(const void *ptr, size_t a) { return (reinterpret_cast<uintptr_t>(ptr) % a) == 0; }
 
-dbp_status run(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void *H, const void *vin,
-               void *out, uint8_t *labels, double *beta_out, cudaStream_t st) {
+dbp_status run_ex(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void *H, const void *vin,
+                  void *out, uint8_t *labels, double *beta_out, cudaStream_t st, const DbpExec *ex,
+                  bool *factor_used) {
+    if (factor_used) *factor_used = false;
     dbp_status v = validate(h, d, kind);
     if (v != DBP_OK) return v;
     if ((long long)d->W * d->N == 0) return DBP_OK;   // nothing to compute
@@ -338,14 +331,24 @@ dbp_status run(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void *H
     p.out = out;
     p.labels = (kind != K_ADMM_DL && d->qam_order > 0) ? labels : nullptr;
     const bool norm = (kind == K_ADMM_DL) && (d->flags & DBP_FLAG_NORMALIZE);
+    double *energy = (ex && ex->energy) ? ex->energy : nullptr;
     if (norm) {
-        if (!h->energy) {
-            e = cudaMalloc(&h->energy, sizeof(double));
-            if (e != cudaSuccess) return fail(h, DBP_ERR_NOMEM, "cudaMalloc(energy): %s", cudaGetErrorString(e));
+        if (!energy) {
+            if (!h->energy) {
+                e = cudaMalloc(&h->energy, sizeof(double));
+                if (e != cudaSuccess)
+                    return fail(h, DBP_ERR_NOMEM, "cudaMalloc(energy): %s", cudaGetErrorString(e));
+            }
+            energy = h->energy;
         }
-        e = cudaMemsetAsync(h->energy, 0, sizeof(double), st);
+        e = cudaMemsetAsync(energy, 0, sizeof(double), st);
         if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
-        p.energy = h->energy;
+        p.energy = energy;
+    }
+    if (ex && ex->factor && ex->factor_mode != 0 && s.tma) {
+        p.factor = ex->factor;
+        p.factor_mode = ex->factor_mode;
+        if (factor_used) *factor_used = true;
     }
     const int UT = next_pow2_ut(d->U);
     switch (kind) {
@@ -368,13 +371,18 @@ dbp_status run(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void *H
         const double count = (double)n;   // unit mean power per antenna and sample
         const int blocks = h->num_sms * 4;
         if (d->precision == DBP_FP32)
-            dbp::dbp_scale_kernel<float><<<blocks, 256, 0, st>>>((float2 *)out, n, h->energy, count, beta_out);
+            dbp::dbp_scale_kernel<float><<<blocks, 256, 0, st>>>((float2 *)out, n, energy, count, beta_out);
         else
-            dbp::dbp_scale_kernel<double><<<blocks, 256, 0, st>>>((double2 *)out, n, h->energy, count, beta_out);
+            dbp::dbp_scale_kernel<double><<<blocks, 256, 0, st>>>((double2 *)out, n, energy, count, beta_out);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(h, e, "normalisation launch");
     }
     return DBP_OK;
+}
+
+dbp_status run(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void *H, const void *vin,
+               void *out, uint8_t *labels, double *beta_out, cudaStream_t st) {
+    return run_ex(h, d, kind, H, vin, out, labels, beta_out, st, nullptr, nullptr);
 }
 
 dbp_status ensure_dev(dbp_context *h, int slot, size_t bytes) {
@@ -435,6 +443,26 @@ dbp_status run_host(dbp_context *h, const dbp_frame_desc *d, Kind kind, const vo
 
 }  // namespace
 
+dbp_status dbp_run_internal(dbp_context *h, const dbp_frame_desc *d, int kind, const void *H, const void *vin,
+                            void *out, uint8_t *labels, double *beta_out, cudaStream_t st, const DbpExec *ex,
+                            bool *factor_used, std::string *err) {
+    t_err_sink = err;
+    dbp_status r = run_ex(h, d, (Kind)kind, H, vin, out, labels, beta_out, st, ex, factor_used);
+    t_err_sink = nullptr;
+    return r;
+}
+
+dbp_status dbp_validate_internal(dbp_context *h, const dbp_frame_desc *d, int kind, std::string *err) {
+    t_err_sink = err;
+    dbp_status r = validate(h, d, (Kind)kind);
+    t_err_sink = nullptr;
+    return r;
+}
+
+size_t dbp_in_elem_bytes(int prec) { return elem_bytes(prec); }
+size_t dbp_out_elem_bytes(int prec) { return out_bytes(prec); }
+int dbp_padded_users(int U) { return next_pow2_ut(U); }
+
 extern "C" {
 
 const char *dbp_version(void) { return "dbp-b300 0.1 (sm_103a)"; }
@@ -472,6 +500,8 @@ dbp_status dbp_create(dbp_handle_t *out, const dbp_config *cfg) {
 
 dbp_status dbp_destroy(dbp_handle_t h) {
     if (!h) return DBP_ERR_INVALID_ARG;
+    if (h->server) dbp_server_destroy(h->server);
+    h->server = nullptr;
     cudaSetDevice(h->device);
     if (h->energy) cudaFree(h->energy);
     if (h->status) cudaFree(h->status);

@@ -67,6 +67,12 @@ struct FusedParams {
     int ms_rows;         // rows of the matched-filter result buffer
     // per-warp shared-memory layout, byte offsets from the warp's base
     int off_h1, off_y0, off_y1, off_g, off_v, warp_bytes;
+    // Resident per-cluster operator of a coherence block (bulk-copy kernel):
+    // 0 = compute, 1 = compute and store, 2 = load instead of computing.
+    // Layout [W][C][UT][UT] float2: B_c^{-1} (uplink ADMM), G_c (CG) or
+    // Q_c = I - rho^{-1} B_c^{-1} (downlink).
+    float2 *factor;
+    int factor_mode;
 };
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,47 @@
+// dbp_internal.h -- host-side definitions shared by the library's
+// translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "dbp.h"
+
+struct dbp_server;
+
+struct dbp_context {
+    int device = 0;
+    uint64_t budget = 0;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    std::string err;
+    dbp_tuning tuning{};
+    double *energy = nullptr;            // downlink power accumulator
+    int *status = nullptr;               // device status word of the kernels
+    void *dev[4] = {nullptr, nullptr, nullptr, nullptr};   // host-variant buffers
+    size_t dev_cap[4] = {0, 0, 0, 0};
+    dbp_server *server = nullptr;        // request loop (dbp_server_start)
+};
+
+
+enum DbpKind { DBP_K_ADMM_UL = 0, DBP_K_CG_UL = 1, DBP_K_ADMM_DL = 2 };
+
+// Per-call resources supplied by the request loop instead of the handle's.
+struct DbpExec {
+    double *energy = nullptr;      // downlink power accumulator (one double)
+    float2 *factor = nullptr;      // resident operator [W][C][UT][UT]
+    int factor_mode = 0;           // 0 none, 1 compute and store, 2 load
+};
+
+// Validate and enqueue one frame on `st` (errors go to *err when non-null).
+// *factor_used reports whether the kernel that ran can store / load the
+// resident operator (the persistent bulk-copy kernel).
+dbp_status dbp_run_internal(dbp_context *h, const dbp_frame_desc *d, int kind, const void *H, const void *vin,
+                            void *out, uint8_t *labels, double *beta_out, cudaStream_t st, const DbpExec *ex,
+                            bool *factor_used, std::string *err);
+dbp_status dbp_validate_internal(dbp_context *h, const dbp_frame_desc *d, int kind, std::string *err);
+size_t dbp_in_elem_bytes(int prec);
+size_t dbp_out_elem_bytes(int prec);
+int dbp_padded_users(int U);
+void dbp_server_destroy(dbp_server *s);

@@ -370,8 +370,25 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
         const TIn *Hs = reinterpret_cast<const TIn *>(wb + (b ? p.off_h1 : 0));
         const TIn *Ys = reinterpret_cast<const TIn *>(wb + (b ? p.off_y1 : p.off_y0));
 
-        // ---- Gram (+ diagonal loading): row u per lane ----
+        // ---- Per-cluster operator: row u per lane ----
         C2 R[UT];
+        C2 *frow = (p.factor != nullptr && valid)
+                       ? p.factor + (((size_t)w * C + c) * UT + u) * UT : nullptr;
+        if (p.factor_mode == 2) {
+            // resident operator of this coherence block
+            if (frow != nullptr) {
+#pragma unroll
+                for (int v = 0; v < UT; v += 2) {
+                    const float4 q = *reinterpret_cast<const float4 *>(&frow[v]);
+                    R[v] = make_float2(q.x, q.y);
+                    R[v + 1] = make_float2(q.z, q.w);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < UT; ++v) R[v] = make_float2(0.f, 0.f);
+            }
+        } else {
+        // ---- Gram (+ diagonal loading) ----
         if constexpr (MMA) {
             gram_mma<UT, TIn>(reinterpret_cast<const uint32_t *>(Hs), hp, p.h_rows, Gm, lane, u, R);
         } else {
@@ -447,6 +464,12 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
                 }
             }
         }
+        if (p.factor_mode == 1 && frow != nullptr && g == 0) {
+#pragma unroll
+            for (int v = 0; v < UT; v += 2)
+                *reinterpret_cast<float4 *>(&frow[v]) = make_float4(R[v].x, R[v].y, R[v + 1].x, R[v + 1].y);
+        }
+        }   // operator computed
 
         if constexpr (MMA) {
             if (ALG != ALG_ADMM_DL) {

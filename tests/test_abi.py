@@ -65,6 +65,8 @@ int main(void) {
          offsetof(dbp_frame_desc, Es), offsetof(dbp_frame_desc, box_r));
   printf("%zu\n", offsetof(dbp_config, hbm_budget_bytes));
   printf("%zu\n", offsetof(dbp_tuning, kernel));
+  printf("%zu %zu %zu %zu\n", sizeof(dbp_request), offsetof(dbp_request, channel_key),
+         sizeof(dbp_result), offsetof(dbp_result, finish_us));
   return 0;
 }
 '''
@@ -80,6 +82,9 @@ int main(void) {
     assert vals[3:7] == [D.flags.offset, D.rho.offset, D.Es.offset, D.box_r.offset]
     assert vals[7] == pkg.dbp_config.hbm_budget_bytes.offset
     assert vals[8] == pkg.dbp_tuning.kernel.offset
+    R = pkg.dbp_request
+    assert vals[9:13] == [ctypes.sizeof(R), R.channel_key.offset, ctypes.sizeof(pkg.dbp_result),
+                          pkg.dbp_result.finish_us.offset]
 
 
 def test_version_string(pkg):

@@ -1,0 +1,189 @@
+"""The request loop (dbp_server_start / dbp_submit / dbp_poll / dbp_wait):
+every frame's result is the same alone and in a mix of uneven frames that
+overlap on the device; frames of one coherence block reuse the resident
+channel and per-cluster operator; a pool too small for all frames at once
+still completes every frame; bad requests are refused at submission."""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dbp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1702_04458_b300 as p
+    return p
+
+
+def _pin(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+
+def _c16(a, kind):
+    dt = torch.float16 if kind == "fp16" else torch.bfloat16
+    t = torch.from_numpy(np.stack([a.real, a.imag], -1).astype(np.float32)).to(dt)
+    return t.contiguous().pin_memory()
+
+
+class Frame:
+    """One served frame: host inputs, host outputs and its descriptor."""
+
+    def __init__(self, dbp, kind, B, C, U, W, N, M, T, seed, prec="fp32", key=0, epoch=0, H=None):
+        self.kind, self.prec = kind, prec
+        if kind == dbp.DBP_KIND_DOWNLINK_ADMM:
+            f = synth.downlink_frame(W, N, B, U, M, seed=seed)
+            inp = f["s"]
+        else:
+            f = synth.uplink_frame(W, N, B, U, M, 15.0, seed=seed)
+            inp = f["y"]
+        if H is not None:
+            f["H"] = H
+            if kind != dbp.DBP_KIND_DOWNLINK_ADMM:
+                inp = np.einsum("wbu,wnu->wnb", H, f["s"])
+        self.Hc = f["H"]
+        if prec == "fp32":
+            self.H, self.inp = _pin(f["H"].astype(np.complex64)), _pin(inp.astype(np.complex64))
+            p = dbp.DBP_FP32
+        else:
+            self.H, self.inp = _c16(f["H"], prec), _c16(inp, prec)
+            p = dbp.DBP_FP16 if prec == "fp16" else dbp.DBP_BF16
+        shape = (W, N, B) if kind == dbp.DBP_KIND_DOWNLINK_ADMM else (W, N, U)
+        self.out = _pin(np.zeros(shape, dtype=np.complex64))
+        self.lab = _pin(np.zeros((W, N, U), dtype=np.uint8))
+        self.desc = dbp.frame_desc(B, C, U, W, N, qam_order=M, T_max=T, precision=p, rho=1.0,
+                                   N0=f.get("N0", 0.1), Es=1.0)
+        self.key, self.epoch = key, epoch
+
+    def request(self, dbp, tag):
+        lab = self.lab if self.kind != dbp.DBP_KIND_DOWNLINK_ADMM else None
+        return dbp.request(self.kind, self.desc, self.H, self.inp, self.out, lab, None,
+                           self.key, self.epoch, tag)
+
+    def run_alone(self, dbp, h):
+        """The same frame through the synchronous host-buffer entry points."""
+        out = np.zeros_like(self.out)
+        lab = np.zeros_like(self.lab)
+        if self.kind == dbp.DBP_KIND_DOWNLINK_ADMM:
+            dbp.dbp_downlink_admm_host(h, self.desc, self.H, self.inp, out)
+        elif self.kind == dbp.DBP_KIND_UPLINK_ADMM:
+            dbp.dbp_uplink_admm_host(h, self.desc, self.H, self.inp, out, lab)
+        else:
+            dbp.dbp_uplink_cg_host(h, self.desc, self.H, self.inp, out, lab)
+        return out, lab
+
+
+def _mix(dbp):
+    K = dbp
+    specs = [
+        (K.DBP_KIND_UPLINK_ADMM, 128, 8, 8, 300, 14, 16, 3, "fp32"),
+        (K.DBP_KIND_UPLINK_CG, 128, 8, 8, 600, 14, 16, 8, "fp32"),
+        (K.DBP_KIND_DOWNLINK_ADMM, 256, 16, 16, 300, 14, 64, 5, "fp32"),
+        (K.DBP_KIND_UPLINK_ADMM, 256, 8, 32, 300, 14, 64, 3, "fp16"),
+        (K.DBP_KIND_UPLINK_CG, 64, 4, 4, 1200, 14, 16, 4, "fp32"),
+        (K.DBP_KIND_UPLINK_ADMM, 64, 1, 16, 300, 14, 64, 6, "fp32"),      # C=1, S=64
+        (K.DBP_KIND_DOWNLINK_ADMM, 128, 2, 32, 300, 14, 16, 3, "fp32"),   # S=64 > U
+        (K.DBP_KIND_UPLINK_ADMM, 256, 16, 16, 600, 14, 64, 4, "bf16"),
+        (K.DBP_KIND_UPLINK_CG, 256, 16, 32, 300, 14, 64, 5, "fp32"),      # cluster mapping
+        (K.DBP_KIND_UPLINK_ADMM, 128, 4, 5, 300, 14, 16, 3, "fp32"),      # U=5: generic kernel
+    ]
+    return [Frame(dbp, *sp[:8], seed=900 + i, prec=sp[8]) for i, sp in enumerate(specs)]
+
+
+def test_results_are_the_same_alone_and_in_the_mix(dbp):
+    h = dbp.dbp_create(0)
+    try:
+        frames = _mix(dbp)
+        alone = [f.run_alone(dbp, h) for f in frames]
+        dbp.dbp_server_start(h, streams=4)
+        tickets = [dbp.dbp_submit(h, f.request(dbp, i)) for i, f in enumerate(frames)]
+        results = [dbp.dbp_wait(h, t, 120.0) for t in tickets]
+        dbp.dbp_server_stop(h)
+        for i, (f, r) in enumerate(zip(frames, results)):
+            assert r is not None and r.status == dbp.DBP_OK and r.user_tag == i
+            assert r.submit_us <= r.start_us <= r.finish_us
+            # same kernels, same shape: bit-identical
+            assert np.array_equal(f.out, alone[i][0]), i
+            if f.kind != dbp.DBP_KIND_DOWNLINK_ADMM:
+                assert np.array_equal(f.lab, alone[i][1]), i
+    finally:
+        dbp.dbp_destroy(h)
+
+
+def test_coherence_block_reuses_resident_channel(dbp):
+    h = dbp.dbp_create(0)
+    try:
+        K = dbp.DBP_KIND_UPLINK_ADMM
+        first = Frame(dbp, K, 128, 8, 8, 1200, 14, 16, 3, seed=1, key=77, epoch=3)
+        block = [first] + [Frame(dbp, K, 128, 8, 8, 1200, 14, 16, 3, seed=2 + i, key=77, epoch=3, H=first.Hc)
+                           for i in range(3)]
+        dl = Frame(dbp, dbp.DBP_KIND_DOWNLINK_ADMM, 128, 8, 8, 1200, 14, 16, 4, seed=9, key=77, epoch=3,
+                   H=first.Hc)
+        alone = [f.run_alone(dbp, h) for f in block + [dl]]
+        dbp.dbp_server_start(h, streams=2)
+        hits = []
+        for f in block + [dl]:                       # one after the other
+            r = dbp.dbp_wait(h, dbp.dbp_submit(h, f.request(dbp, 0)), 60.0)
+            assert r.status == dbp.DBP_OK
+            hits.append(r.resident_hit)
+        # a new epoch of the same key replaces the resident channel
+        nxt = Frame(dbp, K, 128, 8, 8, 1200, 14, 16, 3, seed=20, key=77, epoch=4)
+        r = dbp.dbp_wait(h, dbp.dbp_submit(h, nxt.request(dbp, 0)), 60.0)
+        hits.append(r.resident_hit)
+        ref_next = nxt.run_alone(dbp, h)
+        dbp.dbp_server_stop(h)
+        assert hits == [0, 1, 1, 1, 1, 0]
+        for f, a in zip(block + [dl], alone):
+            # the resident operator is the one the first frame computed:
+            # identical arithmetic, identical results
+            assert np.array_equal(f.out, a[0])
+        assert np.array_equal(nxt.out, ref_next[0])
+    finally:
+        dbp.dbp_destroy(h)
+
+
+def test_small_pool_admits_frames_as_memory_frees(dbp):
+    h = dbp.dbp_create(0)
+    try:
+        K = dbp.DBP_KIND_UPLINK_CG
+        frames = [Frame(dbp, K, 128, 8, 8, 1200, 14, 16, 6, seed=40 + i) for i in range(6)]
+        alone = [f.run_alone(dbp, h) for f in frames]
+        per = frames[0].H.nbytes + frames[0].inp.nbytes + frames[0].out.nbytes + frames[0].lab.nbytes
+        dbp.dbp_server_start(h, streams=4, hbm_bytes=int(per * 1.6))   # room for one frame at a time
+        tickets = [dbp.dbp_submit(h, f.request(dbp, i)) for i, f in enumerate(frames)]
+        res = [dbp.dbp_wait(h, t, 120.0) for t in tickets]
+        dbp.dbp_server_stop(h)
+        for f, a, r in zip(frames, alone, res):
+            assert r.status == dbp.DBP_OK
+            assert np.array_equal(f.out, a[0])
+        # one frame at a time: each starts after the previous one finished
+        starts = sorted((r.start_us, r.finish_us) for r in res)
+        for (s0, f0), (s1, f1) in zip(starts, starts[1:]):
+            assert s1 >= f0 - 50.0
+    finally:
+        dbp.dbp_destroy(h)
+
+
+def test_submission_errors_and_waits(dbp):
+    h = dbp.dbp_create(0)
+    try:
+        dbp.dbp_server_start(h)
+        f = Frame(dbp, dbp.DBP_KIND_UPLINK_ADMM, 128, 8, 8, 1200, 14, 16, 3, seed=60)
+        bad = f.request(dbp, 0)
+        bad.desc.C = 7                              # 128 % 7 != 0
+        with pytest.raises(dbp.DbpError) as ei:
+            dbp.dbp_submit(h, bad)
+        assert ei.value.status == dbp.DBP_ERR_INVALID_ARG
+        t = dbp.dbp_submit(h, f.request(dbp, 5))
+        assert dbp.dbp_wait(h, t, 0.0) is None      # cannot be done yet
+        r = dbp.dbp_wait(h, t, 60.0)
+        assert r.status == dbp.DBP_OK and r.user_tag == 5
+        with pytest.raises(dbp.DbpError):
+            dbp.dbp_poll(h, t)                      # released
+        dbp.dbp_server_stop(h)
+    finally:
+        dbp.dbp_destroy(h)
