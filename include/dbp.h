@@ -123,12 +123,16 @@ typedef enum dbp_mapping {
 } dbp_mapping;
 
 typedef enum dbp_kernel_path {
-    DBP_PATH_AUTO = 0,         /* persistent bulk-copy kernel when eligible  */
+    DBP_PATH_AUTO = 0,         /* DBP_PATH_MMA, else DBP_PATH_TMA, where
+                                  eligible                                   */
     DBP_PATH_GENERIC = 1,      /* per-subcarrier kernel with staged loads:
                                   any shape, FP64, thread-block clusters     */
-    DBP_PATH_TMA = 2           /* persistent kernel fed by cp.async.bulk:
-                                  FP32, U in {4,8,16,32}, even S <= 64,
-                                  16-byte aligned buffers, CTA mapping       */
+    DBP_PATH_TMA = 2,          /* persistent kernel fed by cp.async.bulk:
+                                  U in {4,8,16,32}, even S <= 64, 16-byte
+                                  aligned buffers, CTA mapping               */
+    DBP_PATH_MMA = 3           /* uplink, FP32, U = 8, even S <= 64: as
+                                  DBP_PATH_TMA with every dense product on
+                                  the tensor cores (3 x TF32 per product)   */
 } dbp_kernel_path;
 
 typedef struct dbp_tuning {

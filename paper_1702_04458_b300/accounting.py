@@ -94,12 +94,12 @@ def algorithmic_mults(alg: str, wl: Workload) -> float:
 
 def algorithmic_bytes(alg: str, wl: Workload) -> float:
     """Minimum HBM bytes per subcarrier."""
-    e = wl.elem_bytes
+    e = wl.elem_bytes                     # input element (complex64, or 2 x 16 bit)
     H = wl.B * wl.U * e
     if alg in ("admm_ul", "cg_ul"):
-        return H + wl.N * wl.B * e + wl.N * wl.U * (e + 1)
+        return H + wl.N * wl.B * e + wl.N * wl.U * (8 + 1)   # x_hat complex64 + label
     if alg == "admm_dl":
-        return H + wl.N * wl.U * e + wl.N * wl.B * e
+        return H + wl.N * wl.U * e + wl.N * wl.B * 8
     raise ValueError(alg)
 
 

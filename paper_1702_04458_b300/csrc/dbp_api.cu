@@ -178,12 +178,76 @@ bool tma_eligible(const dbp_frame_desc *d, int UT, int maxw, bool aligned16) {
     return shape && d->U == UT && S <= 64 && d->C <= maxw && aligned16;
 }
 
+// U = 8 tensor-core kernel: uplink, FP32, exactly 8 users, even S <= 64,
+// all C warps in one CTA, 16-byte aligned buffers.
+bool mma8_eligible(const dbp_frame_desc *d, Kind kind, bool aligned16) {
+    const int S = d->B / d->C;
+    return kind != K_ADMM_DL && d->precision == DBP_FP32 && d->U == 8 && S % 2 == 0 && S <= 64 && d->C <= 16 &&
+           aligned16;
+}
+
+void mma8_layout(const dbp_frame_desc *d, Shape &s) {
+    const int S = d->B / d->C;
+    s.hp = 8;
+    s.h_rows = round_up(S, 4);
+    s.yp = S + ((S % 4 == 0) ? 2 : 4);
+    s.y_rows = round_up(d->N, 16);
+    s.ms_rows = 0;
+    const int hb = round16((long long)s.h_rows * 8 * 8);
+    const int yb = round16((long long)s.y_rows * s.yp * 8);
+    s.off_h1 = hb;
+    s.off_y0 = 2 * hb;
+    s.off_y1 = s.off_y0 + yb;
+    s.off_g = s.off_y1 + yb;
+    s.off_v = s.off_g;
+    s.warp_bytes = s.off_v + 16 * 10 * 8;
+}
+
 dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool aligned16, Shape &s) {
     const int UT = next_pow2_ut(d->U);
     const int maxw = max_warps_for(d->precision, UT);
     const int C = d->C;
     const dbp_tuning &t = h->tuning;
     s.tma = false;
+    s.mma8 = false;
+    // AUTO takes the tensor-core kernel for ADMM only: there the Gram and the
+    // inverse dominate and the MMA shortens them; the CG iteration is a chain
+    // of dependent mat-vecs on which the MMA latency measured slower than the
+    // bulk-copy kernel's FMA path.
+    const bool want_mma = t.kernel == DBP_PATH_MMA || (t.kernel == DBP_PATH_AUTO && kind == K_ADMM_UL);
+    if (want_mma && t.mapping != DBP_MAP_CLUSTER && mma8_eligible(d, kind, aligned16)) {
+        mma8_layout(d, s);
+        const int target = t.warps_per_cta > 0 ? t.warps_per_cta : 8;
+        int P = target / C;
+        if (P < 1) P = 1;
+        auto bytes = [&](int PP) {
+            return (size_t)PP * C * s.warp_bytes + (2 * (size_t)PP * C * 128 + 2 * (size_t)PP * 128) * 8 +
+                   (size_t)PP * C * 16;
+        };
+        while (P > 1 && (P * C > 16 || bytes(P) > h->smem_optin)) --P;
+        if (bytes(P) <= h->smem_optin) {
+            s.mma8 = true;
+            s.tma = true;                      // also a persistent bulk-copy kernel
+            s.clu = false;
+            s.P = P;
+            s.CPB = C;
+            s.CL = 1;
+            s.nwarps = P * C;
+            s.smem = bytes(P);
+            const long long tiles = (d->W + P - 1) / P;
+            int occ = (kind == K_ADMM_UL) ? dbp_mma8_occupancy_admm_ul(s.nwarps * 32, s.smem)
+                                          : dbp_mma8_occupancy_cg_ul(s.nwarps * 32, s.smem);
+            if (occ < 1) occ = 1;
+            const long long slots = (long long)h->num_sms * occ;
+            s.grid = tiles < slots ? tiles : slots;
+            s.tiles = (int)tiles;
+            return DBP_OK;
+        }
+    }
+    if (t.kernel == DBP_PATH_MMA)
+        return fail(h, DBP_ERR_UNSUPPORTED,
+                    "the tensor-core kernel needs uplink, FP32, U = 8, even S <= 64, C <= 16 and 16-byte "
+                    "aligned buffers (B=%d C=%d U=%d)", d->B, d->C, d->U);
     if (t.kernel != DBP_PATH_GENERIC && t.mapping != DBP_MAP_CLUSTER && tma_eligible(d, UT, maxw, aligned16)) {
         tma_layout(d, kind, UT, s);
         const int target = t.warps_per_cta > 0 ? t.warps_per_cta : 8;
@@ -516,7 +580,7 @@ const char *dbp_last_error(dbp_handle_t h) { return h ? h->err.c_str() : "NULL h
 dbp_status dbp_set_tuning(dbp_handle_t h, const dbp_tuning *t) {
     if (!h || !t) return DBP_ERR_INVALID_ARG;
     if (t->mapping < DBP_MAP_AUTO || t->mapping > DBP_MAP_CLUSTER || t->cluster_size < 0 || t->cluster_size > 16 ||
-        t->warps_per_cta < 0 || t->warps_per_cta > 32 || t->kernel < DBP_PATH_AUTO || t->kernel > DBP_PATH_TMA)
+        t->warps_per_cta < 0 || t->warps_per_cta > 32 || t->kernel < DBP_PATH_AUTO || t->kernel > DBP_PATH_MMA)
         return fail(h, DBP_ERR_INVALID_ARG, "bad tuning values");
     h->tuning = *t;
     return DBP_OK;

@@ -8,3 +8,5 @@ cudaError_t dbp_launch_admm_ul(int prec, int UT, const dbp::FusedParams &p, cons
 int dbp_tma_occupancy_admm_ul(int prec, int UT, int threads, size_t smem) {
     return dbp::tma_occupancy<dbp::ALG_ADMM_UL>(prec, UT, threads, smem);
 }
+
+int dbp_mma8_occupancy_admm_ul(int threads, size_t smem) { return dbp::mma8_occupancy<dbp::ALG_ADMM_UL>(threads, smem); }

@@ -8,3 +8,5 @@ cudaError_t dbp_launch_cg_ul(int prec, int UT, const dbp::FusedParams &p, const 
 int dbp_tma_occupancy_cg_ul(int prec, int UT, int threads, size_t smem) {
     return dbp::tma_occupancy<dbp::ALG_CG_UL>(prec, UT, threads, smem);
 }
+
+int dbp_mma8_occupancy_cg_ul(int threads, size_t smem) { return dbp::mma8_occupancy<dbp::ALG_CG_UL>(threads, smem); }

@@ -8,6 +8,7 @@
 #include "dbp.h"
 #include "dbp_fused.cuh"
 #include "dbp_tma.cuh"
+#include "dbp_mma8.cuh"
 
 namespace dbp {
 
@@ -16,6 +17,7 @@ namespace dbp {
 struct Shape {
     bool clu;
     bool tma;              // persistent bulk-copy kernel
+    bool mma8 = false;     // U = 8 tensor-core kernel
     int P, CPB, CL, nwarps;
     long long grid;
     size_t smem;
@@ -126,7 +128,35 @@ cudaError_t launch_tma(int prec, int UT, const FusedParams &p, const Shape &s, c
 }
 
 template <int ALG>
+int mma8_occupancy(int threads, size_t smem) {
+    if constexpr (ALG == ALG_ADMM_DL) {
+        return 0;
+    } else {
+        auto kern = dbp::dbp_mma8_kernel<ALG>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) return 0;
+        return n;
+    }
+}
+
+template <int ALG>
+cudaError_t launch_mma8(const FusedParams &p, const Shape &s, cudaStream_t st) {
+    if constexpr (ALG == ALG_ADMM_DL) {
+        return cudaErrorInvalidValue;
+    } else {
+        auto kern = dbp::dbp_mma8_kernel<ALG>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)s.grid, s.nwarps * 32, s.smem, st>>>(p);
+        return cudaGetLastError();
+    }
+}
+
+template <int ALG>
 cudaError_t launch_alg(int prec, int UT, const FusedParams &p, const Shape &s, cudaStream_t st) {
+    if (s.mma8) return launch_mma8<ALG>(p, s, st);
     if (s.tma) return launch_tma<ALG>(prec, UT, p, s, st);
     if (prec != DBP_FP32 && prec != DBP_FP64) return cudaErrorInvalidValue;
     if (prec == DBP_FP32)
@@ -144,3 +174,5 @@ cudaError_t dbp_launch_admm_dl(int prec, int UT, const dbp::FusedParams &p, cons
 int dbp_tma_occupancy_admm_ul(int prec, int UT, int threads, size_t smem);
 int dbp_tma_occupancy_cg_ul(int prec, int UT, int threads, size_t smem);
 int dbp_tma_occupancy_admm_dl(int prec, int UT, int threads, size_t smem);
+int dbp_mma8_occupancy_admm_ul(int threads, size_t smem);
+int dbp_mma8_occupancy_cg_ul(int threads, size_t smem);

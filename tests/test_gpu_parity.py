@@ -128,11 +128,20 @@ UL_CASES = [
 ]
 
 
-@pytest.fixture(params=["auto", "generic"])
+@pytest.fixture(params=["auto", "generic", "tma"])
 def path(request, dbp, handle):
-    """Run a test with the automatic kernel choice (the persistent bulk-copy
-    kernel wherever it applies) and again with the generic kernel forced."""
-    code = dbp.DBP_PATH_AUTO if request.param == "auto" else dbp.DBP_PATH_GENERIC
+    """Run a test with the automatic kernel choice (the U = 8 tensor-core
+    kernel or the persistent bulk-copy kernel wherever they apply), with the
+    generic kernel forced, and with the bulk-copy kernel preferred."""
+    code = {"auto": dbp.DBP_PATH_AUTO, "generic": dbp.DBP_PATH_GENERIC, "tma": dbp.DBP_PATH_TMA}[request.param]
+    if request.param == "tma":
+        # forcing would reject shapes the bulk-copy kernel cannot take; prefer it
+        # only where it applies (U a power of two, even S <= 64)
+        U, B, C = request.node.callspec.params.get("U", 8), request.node.callspec.params.get("B", 32), \
+            request.node.callspec.params.get("C", 4)
+        S = B // C
+        if U not in (4, 8, 16) or S % 2 or S > 64:   # FP32 at U = 32 does not fit its shared memory
+            code = dbp.DBP_PATH_AUTO
     dbp.dbp_set_tuning(handle, kernel=code)
     yield request.param
     dbp.dbp_set_tuning(handle)
@@ -310,6 +319,82 @@ def test_forced_bulk_copy_kernel_rejects_ineligible_shapes(dbp, handle):
     finally:
         dbp.dbp_set_tuning(handle)
     dbp.dbp_device_status(handle)
+
+
+# ---------------------------------------------------------------------------
+# U = 8 tensor-core kernel (3 x TF32 products)
+# ---------------------------------------------------------------------------
+
+MMA8_CASES = [
+    # (W, N, B, C, M)
+    (37, 14, 128, 8, 16),     # the B=128 / C=8 / U=8 workload, ragged W
+    (9, 20, 48, 8, 16),       # S=6 (padded to a multiple of 4), N > 16 (two symbol passes)
+    (5, 1, 16, 2, 4),         # S=8, N=1
+    (7, 17, 64, 1, 64),       # C=1 (S=64), two symbol passes
+    (11, 14, 128, 16, 16),    # C=16 clusters of 8
+]
+
+
+@pytest.mark.parametrize("algo", ["admm", "cg"])
+@pytest.mark.parametrize("W,N,B,C,M", MMA8_CASES)
+def test_mma8_kernel_matches_oracle(dbp, handle, algo, W, N, B, C, M):
+    f = synth.uplink_frame(W, N, B, 8, M, 10.0, seed=800 + W + N + B + C)
+    T = 3 if algo == "admm" else 8
+    try:
+        dbp.dbp_set_tuning(handle, kernel=dbp.DBP_PATH_MMA)
+        x, lab = run_ul(dbp, handle, f, C, T, algo)
+    finally:
+        dbp.dbp_set_tuning(handle)
+    ref = oracle_ul(f, C, T, algo, "fp32")
+    err = _rel_per_vector(x, ref)
+    assert err.max() <= FP32_TOL, err.max()
+    assert_labels(x, lab, ref, M, np.float32)
+
+
+@pytest.mark.parametrize("reg", ["zf", "box"])
+def test_mma8_kernel_regularisers(dbp, handle, reg):
+    f = synth.uplink_frame(21, 14, 128, 8, 16, 10.0, seed=850)
+    r = oracle.box_radius(16)
+    try:
+        dbp.dbp_set_tuning(handle, kernel=dbp.DBP_PATH_MMA)
+        x, _ = run_ul(dbp, handle, f, 8, 4, "admm", reg=dbp.DBP_REG_ZF if reg == "zf" else dbp.DBP_REG_BOX,
+                      box_r=r)
+    finally:
+        dbp.dbp_set_tuning(handle)
+    ref = oracle_ul(f, 8, 4, "admm", "fp32", reg=oracle.REG_ZF if reg == "zf" else oracle.REG_BOX, box_r=r)
+    assert _rel_per_vector(x, ref).max() <= FP32_TOL
+
+
+def test_mma8_fp64_retry_on_a_near_singular_cluster(dbp, handle):
+    W, N, B, C = 10, 14, 128, 4                   # S = 32 > U = 8
+    f = synth.uplink_frame(W, N, B, 8, 16, 20.0, seed=860)
+    S = B // C
+    u_, s_, vh = np.linalg.svd(f["H"][4, S:2 * S], full_matrices=False)
+    s_[-1] = 1e-4 * s_[0]
+    f["H"][4, S:2 * S] = (u_ * s_) @ vh
+    f["y"] = np.einsum("wbu,wnu->wnb", f["H"], f["s"])
+    dbp.dbp_fp64_retries(handle)
+    try:
+        dbp.dbp_set_tuning(handle, kernel=dbp.DBP_PATH_MMA)
+        x, _ = run_ul(dbp, handle, f, C, 3, "admm", rho=1e-6)
+    finally:
+        dbp.dbp_set_tuning(handle)
+    assert dbp.dbp_fp64_retries(handle) == 1
+    ref = oracle_ul(f, C, 3, "admm", "fp32", rho=1e-6)
+    good = np.arange(W) != 4
+    assert np.all(np.isfinite(x))
+    assert _rel_per_vector(x[good], ref[good]).max() <= FP32_TOL
+
+
+def test_forced_mma8_kernel_rejects_other_shapes(dbp, handle):
+    f = synth.uplink_frame(3, 2, 64, 16, 16, 8.0, seed=870)   # U = 16
+    try:
+        dbp.dbp_set_tuning(handle, kernel=dbp.DBP_PATH_MMA)
+        with pytest.raises(dbp.DbpError) as ei:
+            run_ul(dbp, handle, f, 4, 3, "admm")
+        assert ei.value.status == dbp.DBP_ERR_UNSUPPORTED
+    finally:
+        dbp.dbp_set_tuning(handle)
 
 
 # ---------------------------------------------------------------------------
