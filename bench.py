@@ -67,6 +67,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-frames", type=int, default=240)
+    ap.add_argument("--kernel", choices=["auto", "generic", "tma", "mma"], default="auto",
+                    help="uplink/downlink kernel path (dbp_tuning.kernel); auto picks per shape")
     a = ap.parse_args(argv)
     a.warmup = max(a.warmup, 3)
     return a
@@ -599,6 +601,9 @@ def main(argv=None) -> int:
         dist.init_process_group("nccl", device_id=device)
 
     h = dbp.dbp_create(local)
+    if args.kernel != "auto":
+        dbp.dbp_set_tuning(h, kernel={"generic": dbp.DBP_PATH_GENERIC, "tma": dbp.DBP_PATH_TMA,
+                                      "mma": dbp.DBP_PATH_MMA}[args.kernel])
     stream = torch.cuda.current_stream(device)
     props = torch.cuda.get_device_properties(device)
     sms = props.multi_processor_count
@@ -753,6 +758,7 @@ def main(argv=None) -> int:
                 "bits_per_step": bits_step, "snr_db": "rotating 0..14 dB over 8 resident frames",
                 "l2": "inputs larger than L2: 8 rotating frames, 226 MB resident",
                 "parallelism": f"subcarrier-parallel, {world} independent rank(s)",
+                "kernel_path": args.kernel,
             },
             "per_detector": {
                 "admm_ul": {"ms": admm_avg, "gbit_s": detected_bits(UL) / (admm_avg / 1e3) / 1e9},
