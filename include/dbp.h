@@ -123,16 +123,22 @@ typedef enum dbp_mapping {
 } dbp_mapping;
 
 typedef enum dbp_kernel_path {
-    DBP_PATH_AUTO = 0,         /* DBP_PATH_MMA, else DBP_PATH_TMA, where
-                                  eligible                                   */
+    DBP_PATH_AUTO = 0,         /* ADMM uplink: DBP_PATH_MMA; CG uplink:
+                                  DBP_PATH_BCAST; else DBP_PATH_TMA; each
+                                  where eligible, then DBP_PATH_GENERIC      */
     DBP_PATH_GENERIC = 1,      /* per-subcarrier kernel with staged loads:
                                   any shape, FP64, thread-block clusters     */
     DBP_PATH_TMA = 2,          /* persistent kernel fed by cp.async.bulk:
                                   U in {4,8,16,32}, even S <= 64, 16-byte
                                   aligned buffers, CTA mapping               */
-    DBP_PATH_MMA = 3           /* uplink, FP32, U = 8, even S <= 64: as
+    DBP_PATH_MMA = 3,          /* uplink, FP32, U = 8, even S <= 64: as
                                   DBP_PATH_TMA with every dense product on
                                   the tensor cores (3 x TF32 per product)   */
+    DBP_PATH_BCAST = 4         /* CG uplink, FP32, U in {4,8,16}, even S,
+                                  C <= 16: the consensus w and the updates of
+                                  e, x, r, p run once per subcarrier and p is
+                                  broadcast to the clusters (Sec. III-D, the
+                                  first of its two placements)               */
 } dbp_kernel_path;
 
 typedef struct dbp_tuning {

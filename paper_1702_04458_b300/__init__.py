@@ -41,7 +41,7 @@ DBP_FP32, DBP_FP64, DBP_FP16, DBP_BF16 = 0, 1, 2, 3
 DBP_REG_ZF, DBP_REG_MMSE, DBP_REG_BOX = 0, 1, 2
 DBP_FLAG_NORMALIZE = 1
 DBP_MAP_AUTO, DBP_MAP_CTA, DBP_MAP_CLUSTER = 0, 1, 2
-DBP_PATH_AUTO, DBP_PATH_GENERIC, DBP_PATH_TMA, DBP_PATH_MMA = 0, 1, 2, 3
+DBP_PATH_AUTO, DBP_PATH_GENERIC, DBP_PATH_TMA, DBP_PATH_MMA, DBP_PATH_BCAST = 0, 1, 2, 3, 4
 
 _STATUS = {0: "DBP_OK", 1: "DBP_ERR_INVALID_ARG", 2: "DBP_ERR_UNSUPPORTED", 3: "DBP_ERR_NOMEM",
            4: "DBP_ERR_CUDA", 5: "DBP_ERR_TIMEOUT", 6: "DBP_ERR_UNIMPLEMENTED", 7: "DBP_PENDING"}

@@ -203,6 +203,39 @@ void mma8_layout(const dbp_frame_desc *d, Shape &s) {
     s.warp_bytes = s.off_v + 16 * 10 * 8;
 }
 
+// CG kernel with the centralized update and broadcast of p: FP32, U a power
+// of two in {4, 8, 16}, even S, all C <= 16 warps of a subcarrier in one CTA.
+bool cg_eligible(const dbp_frame_desc *d, Kind kind, int UT, bool aligned16) {
+    const int S = d->B / d->C;
+    return kind == K_CG_UL && d->precision == DBP_FP32 && d->U == UT && UT <= 16 && S % 2 == 0 && d->C <= 16 &&
+           aligned16;
+}
+
+size_t cg_cta_for(int UT, int nwarps, int P) {
+    switch (UT) {
+    case 4: return dbp::cg_cta_bytes<4>(nwarps, P);
+    case 8: return dbp::cg_cta_bytes<8>(nwarps, P);
+    default: return dbp::cg_cta_bytes<16>(nwarps, P);
+    }
+}
+
+// Per-warp staging of the CG kernel: H_c (S x U, dense) then the receive rows
+// (pitch yp, an odd number of 16-byte units), one buffer.
+void cg_layout(const dbp_frame_desc *d, int UT, Shape &s) {
+    const int S = d->B / d->C;
+    s.hp = UT;
+    s.h_rows = S;
+    s.yp = S + ((S % 4 == 0) ? 2 : 4);
+    s.y_rows = round_up(d->N, tile_syms(UT));
+    s.ms_rows = 0;
+    s.off_h1 = 0;
+    s.off_y0 = round16((long long)S * UT * 8);
+    s.off_y1 = s.off_y0;
+    s.off_g = s.off_y0 + round16((long long)s.y_rows * s.yp * 8);
+    s.off_v = s.off_g;
+    s.warp_bytes = s.off_g;
+}
+
 dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool aligned16, Shape &s) {
     const int UT = next_pow2_ut(d->U);
     const int maxw = max_warps_for(d->precision, UT);
@@ -210,6 +243,7 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
     const dbp_tuning &t = h->tuning;
     s.tma = false;
     s.mma8 = false;
+    s.cg = false;
     // AUTO takes the tensor-core kernel for ADMM only: there the Gram and the
     // inverse dominate and the MMA shortens them; the CG iteration is a chain
     // of dependent mat-vecs on which the MMA latency measured slower than the
@@ -244,6 +278,36 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
             return DBP_OK;
         }
     }
+    if ((t.kernel == DBP_PATH_AUTO || t.kernel == DBP_PATH_BCAST) && t.mapping != DBP_MAP_CLUSTER &&
+        cg_eligible(d, kind, UT, aligned16)) {
+        cg_layout(d, UT, s);
+        const int target = t.warps_per_cta > 0 ? t.warps_per_cta : 8;
+        int P = target / C;
+        if (P < 1) P = 1;
+        auto bytes = [&](int PP) { return (size_t)PP * C * s.warp_bytes + cg_cta_for(UT, PP * C, PP); };
+        while (P > 1 && (P * C > 16 || bytes(P) > h->smem_optin)) --P;
+        if (bytes(P) <= h->smem_optin) {
+            s.cg = true;
+            s.tma = true;                      // also a persistent bulk-copy kernel
+            s.clu = false;
+            s.P = P;
+            s.CPB = C;
+            s.CL = 1;
+            s.nwarps = P * C;
+            s.smem = bytes(P);
+            const long long tiles = (d->W + P - 1) / P;
+            int occ = dbp_cg_occupancy(UT, s.nwarps * 32, s.smem);
+            if (occ < 1) occ = 1;
+            const long long slots = (long long)h->num_sms * occ;
+            s.grid = tiles < slots ? tiles : slots;
+            s.tiles = (int)tiles;
+            return DBP_OK;
+        }
+    }
+    if (t.kernel == DBP_PATH_BCAST)
+        return fail(h, DBP_ERR_UNSUPPORTED,
+                    "the broadcast CG kernel needs uplink CG, FP32, U in {4,8,16}, even S, C <= 16, 16-byte "
+                    "aligned buffers and a CTA that fits shared memory (B=%d C=%d U=%d)", d->B, d->C, d->U);
     if (t.kernel == DBP_PATH_MMA)
         return fail(h, DBP_ERR_UNSUPPORTED,
                     "the tensor-core kernel needs uplink, FP32, U = 8, even S <= 64, C <= 16 and 16-byte "
@@ -580,7 +644,7 @@ const char *dbp_last_error(dbp_handle_t h) { return h ? h->err.c_str() : "NULL h
 dbp_status dbp_set_tuning(dbp_handle_t h, const dbp_tuning *t) {
     if (!h || !t) return DBP_ERR_INVALID_ARG;
     if (t->mapping < DBP_MAP_AUTO || t->mapping > DBP_MAP_CLUSTER || t->cluster_size < 0 || t->cluster_size > 16 ||
-        t->warps_per_cta < 0 || t->warps_per_cta > 32 || t->kernel < DBP_PATH_AUTO || t->kernel > DBP_PATH_MMA)
+        t->warps_per_cta < 0 || t->warps_per_cta > 32 || t->kernel < DBP_PATH_AUTO || t->kernel > DBP_PATH_BCAST)
         return fail(h, DBP_ERR_INVALID_ARG, "bad tuning values");
     h->tuning = *t;
     return DBP_OK;

@@ -10,3 +10,12 @@ int dbp_tma_occupancy_cg_ul(int prec, int UT, int threads, size_t smem) {
 }
 
 int dbp_mma8_occupancy_cg_ul(int threads, size_t smem) { return dbp::mma8_occupancy<dbp::ALG_CG_UL>(threads, smem); }
+
+int dbp_cg_occupancy(int UT, int threads, size_t smem) {
+    switch (UT) {
+    case 4: return dbp::cg_occupancy_one<4>(threads, smem);
+    case 8: return dbp::cg_occupancy_one<8>(threads, smem);
+    case 16: return dbp::cg_occupancy_one<16>(threads, smem);
+    default: return 0;
+    }
+}

@@ -9,6 +9,7 @@
 #include "dbp_fused.cuh"
 #include "dbp_tma.cuh"
 #include "dbp_mma8.cuh"
+#include "dbp_cg.cuh"
 
 namespace dbp {
 
@@ -18,6 +19,7 @@ struct Shape {
     bool clu;
     bool tma;              // persistent bulk-copy kernel
     bool mma8 = false;     // U = 8 tensor-core kernel
+    bool cg = false;       // CG with the centralized update and broadcast of p
     int P, CPB, CL, nwarps;
     long long grid;
     size_t smem;
@@ -154,8 +156,36 @@ cudaError_t launch_mma8(const FusedParams &p, const Shape &s, cudaStream_t st) {
     }
 }
 
+template <int UT>
+int cg_occupancy_one(int threads, size_t smem) {
+    auto kern = dbp::dbp_cg_kernel<UT>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+template <int UT>
+cudaError_t launch_cg_one(const FusedParams &p, const Shape &s, cudaStream_t st) {
+    auto kern = dbp::dbp_cg_kernel<UT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)s.grid, s.nwarps * 32, s.smem, st>>>(p);
+    return cudaGetLastError();
+}
+
 template <int ALG>
 cudaError_t launch_alg(int prec, int UT, const FusedParams &p, const Shape &s, cudaStream_t st) {
+    if constexpr (ALG == ALG_CG_UL) {
+        if (s.cg) {
+            switch (UT) {
+            case 4: return launch_cg_one<4>(p, s, st);
+            case 8: return launch_cg_one<8>(p, s, st);
+            case 16: return launch_cg_one<16>(p, s, st);
+            default: return cudaErrorInvalidValue;
+            }
+        }
+    }
     if (s.mma8) return launch_mma8<ALG>(p, s, st);
     if (s.tma) return launch_tma<ALG>(prec, UT, p, s, st);
     if (prec != DBP_FP32 && prec != DBP_FP64) return cudaErrorInvalidValue;
@@ -176,3 +206,4 @@ int dbp_tma_occupancy_cg_ul(int prec, int UT, int threads, size_t smem);
 int dbp_tma_occupancy_admm_dl(int prec, int UT, int threads, size_t smem);
 int dbp_mma8_occupancy_admm_ul(int threads, size_t smem);
 int dbp_mma8_occupancy_cg_ul(int threads, size_t smem);
+int dbp_cg_occupancy(int UT, int threads, size_t smem);

@@ -87,6 +87,21 @@ int main(void) {
                           pkg.dbp_result.finish_us.offset]
 
 
+def test_enum_values_match_the_header(pkg):
+    """Every DBP_* enumerator the binding defines has the header's value."""
+    names = sorted(n for n in dir(pkg) if n.startswith("DBP_") and isinstance(getattr(pkg, n), int))
+    body = "".join(f'  printf("%lld\\n", (long long){n});\n' for n in names)
+    prog = "#include <stdio.h>\n#include \"dbp.h\"\nint main(void) {\n" + body + "  return 0;\n}\n"
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "e.c")
+        exe = os.path.join(d, "e")
+        open(src, "w").write(prog)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals == [getattr(pkg, n) for n in names]
+    assert "DBP_PATH_BCAST" in names
+
+
 def test_version_string(pkg):
     assert "sm_103a" in pkg.dbp_version()
 

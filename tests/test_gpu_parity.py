@@ -398,6 +398,92 @@ def test_forced_mma8_kernel_rejects_other_shapes(dbp, handle):
 
 
 # ---------------------------------------------------------------------------
+# CG with the centralized update and broadcast of p (Sec. III-D, first placement)
+# ---------------------------------------------------------------------------
+
+BCAST_CASES = [
+    # (W, N, B, C, U, M, T)          covers
+    (37, 14, 128, 8, 8, 16, 8),      # the B=128 / C=8 / U=8 workload, ragged W
+    (9, 14, 256, 16, 16, 64, 8),     # C=16 warps per CTA, U=16 (14-symbol chunk)
+    (11, 20, 128, 8, 8, 16, 5),      # N > 16: two symbol chunks, the second ragged
+    (7, 14, 64, 1, 8, 16, 8),        # C=1: one warp updates every symbol (4 passes of 32)
+    (13, 9, 32, 2, 4, 4, 6),         # C=2: four subcarriers per CTA, U=4
+    (6, 17, 64, 4, 4, 16, 3),        # U=4, 16-symbol chunks, ragged second chunk
+    (5, 1, 24, 3, 8, 16, 4),         # N=1: one owner, the other warps idle in the update
+    (8, 14, 96, 6, 16, 64, 16),      # T = U: CG reaches the LMMSE solution
+    (3, 14, 256, 8, 16, 64, 2),      # S=32 rows of H per cluster
+]
+
+
+def _with_path(dbp, handle, code, fn):
+    try:
+        dbp.dbp_set_tuning(handle, kernel=code)
+        return fn()
+    finally:
+        dbp.dbp_set_tuning(handle)
+
+
+@pytest.mark.parametrize("W,N,B,C,U,M,T", BCAST_CASES)
+def test_bcast_cg_kernel_matches_oracle(dbp, handle, W, N, B, C, U, M, T):
+    f = synth.uplink_frame(W, N, B, U, M, 12.0, seed=900 + W + N + B + C + U)
+    x, lab = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, C, T, "cg"))
+    ref = oracle_ul(f, C, T, "cg", "fp32")
+    err = _rel_per_vector(x, ref)
+    assert err.max() <= FP32_TOL, err.max()
+    assert_labels(x, lab, ref, M, np.float32)
+
+
+def test_bcast_cg_kernel_zf_and_T_edges(dbp, handle):
+    f = synth.uplink_frame(19, 14, 64, 8, 16, 15.0, seed=910)
+    x, _ = _with_path(dbp, handle, dbp.DBP_PATH_BCAST,
+                      lambda: run_ul(dbp, handle, f, 4, 6, "cg", reg=dbp.DBP_REG_ZF))
+    assert _rel_per_vector(x, oracle_ul(f, 4, 6, "cg", "fp32", reg=oracle.REG_ZF)).max() <= FP32_TOL
+    x1, _ = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, 4, 1, "cg"))
+    assert _rel_per_vector(x1, oracle_ul(f, 4, 1, "cg", "fp32")).max() <= FP32_TOL
+    x0, _ = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, 4, 0, "cg"))
+    assert np.all(x0 == 0)
+
+
+def test_bcast_cg_kernel_stops_on_a_zero_residual(dbp, handle):
+    """A symbol whose receive vector is zero has r = y_MRC = 0: its iterate
+    stays x = 0 (no 0/0), and the other symbols are unaffected."""
+    f = synth.uplink_frame(6, 14, 128, 8, 16, 10.0, seed=911)
+    f["y"][2, 5] = 0.0
+    f["y"][4] = 0.0
+    x, _ = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, 8, 8, "cg"))
+    assert np.all(np.isfinite(x))
+    assert np.all(x[2, 5] == 0) and np.all(x[4] == 0)
+    ref = oracle_ul(f, 8, 8, "cg", "fp32")
+    keep = np.ones(x.shape[:2], dtype=bool)
+    keep[2, 5] = False
+    keep[4] = False
+    assert _rel_per_vector(x[keep], ref[keep]).max() <= FP32_TOL
+
+
+def test_bcast_cg_kernel_matches_generic_kernel_over_many_tiles(dbp, handle):
+    f = synth.uplink_frame(1201, 14, 128, 8, 16, 8.0, seed=912)
+    a, la = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, 8, 8, "cg"))
+    b, lb = _with_path(dbp, handle, dbp.DBP_PATH_GENERIC, lambda: run_ul(dbp, handle, f, 8, 8, "cg"))
+    # two FP32 kernels with different summation orders: rounding-level agreement
+    assert _rel_per_vector(a, b).max() <= 1e-5
+
+
+def test_auto_path_uses_bcast_for_cg(dbp, handle):
+    f = synth.uplink_frame(17, 14, 128, 8, 16, 10.0, seed=913)
+    a, _ = run_ul(dbp, handle, f, 8, 8, "cg")
+    b, _ = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, 8, 8, "cg"))
+    assert np.array_equal(a, b)
+
+
+def test_forced_bcast_kernel_rejects_other_work(dbp, handle):
+    f = synth.uplink_frame(3, 2, 64, 8, 16, 8.0, seed=914)
+    for algo, ff, C in (("admm", f, 4), ("cg", synth.uplink_frame(3, 2, 64, 32, 16, 8.0, seed=915), 2)):
+        with pytest.raises(dbp.DbpError) as ei:
+            _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, ff, C, 3, algo))
+        assert ei.value.status == dbp.DBP_ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------------------
 # Host-buffer (end-to-end) entry points and argument errors
 # ---------------------------------------------------------------------------
 
