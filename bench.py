@@ -67,7 +67,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-frames", type=int, default=240)
-    ap.add_argument("--kernel", choices=["auto", "generic", "tma", "mma"], default="auto",
+    ap.add_argument("--kernel", choices=["auto", "generic", "tma", "mma", "bcast"], default="auto",
                     help="uplink/downlink kernel path (dbp_tuning.kernel); auto picks per shape")
     a = ap.parse_args(argv)
     a.warmup = max(a.warmup, 3)
@@ -603,7 +603,7 @@ def main(argv=None) -> int:
     h = dbp.dbp_create(local)
     if args.kernel != "auto":
         dbp.dbp_set_tuning(h, kernel={"generic": dbp.DBP_PATH_GENERIC, "tma": dbp.DBP_PATH_TMA,
-                                      "mma": dbp.DBP_PATH_MMA}[args.kernel])
+                                      "mma": dbp.DBP_PATH_MMA, "bcast": dbp.DBP_PATH_BCAST}[args.kernel])
     stream = torch.cuda.current_stream(device)
     props = torch.cuda.get_device_properties(device)
     sms = props.multi_processor_count

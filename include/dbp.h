@@ -123,8 +123,8 @@ typedef enum dbp_mapping {
 } dbp_mapping;
 
 typedef enum dbp_kernel_path {
-    DBP_PATH_AUTO = 0,         /* ADMM uplink: DBP_PATH_MMA; CG uplink:
-                                  DBP_PATH_BCAST; else DBP_PATH_TMA; each
+    DBP_PATH_AUTO = 0,         /* uplink: DBP_PATH_BCAST, else
+                                  DBP_PATH_TMA; downlink: DBP_PATH_TMA; each
                                   where eligible, then DBP_PATH_GENERIC      */
     DBP_PATH_GENERIC = 1,      /* per-subcarrier kernel with staged loads:
                                   any shape, FP64, thread-block clusters     */
@@ -134,11 +134,13 @@ typedef enum dbp_kernel_path {
     DBP_PATH_MMA = 3,          /* uplink, FP32, U = 8, even S <= 64: as
                                   DBP_PATH_TMA with every dense product on
                                   the tensor cores (3 x TF32 per product)   */
-    DBP_PATH_BCAST = 4         /* CG uplink, FP32, U in {4,8,16}, even S,
-                                  C <= 16: the consensus w and the updates of
-                                  e, x, r, p run once per subcarrier and p is
-                                  broadcast to the clusters (Sec. III-D, the
-                                  first of its two placements)               */
+    DBP_PATH_BCAST = 4         /* uplink ADMM and CG, FP32, U in {4,8,16},
+                                  even S, C <= 16: the consensus and the
+                                  centralized step (the (E2) prox of Alg. 1;
+                                  the e, x, r, p updates of Alg. 2, the first
+                                  placement of Sec. III-D) run once per
+                                  symbol and s or p is broadcast to the
+                                  clusters                                   */
 } dbp_kernel_path;
 
 typedef struct dbp_tuning {

@@ -203,25 +203,42 @@ void mma8_layout(const dbp_frame_desc *d, Shape &s) {
     s.warp_bytes = s.off_v + 16 * 10 * 8;
 }
 
-// CG kernel with the centralized update and broadcast of p: FP32, U a power
-// of two in {4, 8, 16}, even S, all C <= 16 warps of a subcarrier in one CTA.
-bool cg_eligible(const dbp_frame_desc *d, Kind kind, int UT, bool aligned16) {
+// Uplink kernels with the consensus step once per symbol and its result
+// broadcast (s for ADMM, p for CG): FP32, U a power of two in {4, 8, 16},
+// even S, all C <= 16 warps of a subcarrier in one CTA.
+bool bcast_eligible(const dbp_frame_desc *d, Kind kind, int UT, bool aligned16) {
     const int S = d->B / d->C;
-    return kind == K_CG_UL && d->precision == DBP_FP32 && d->U == UT && UT <= 16 && S % 2 == 0 && d->C <= 16 &&
-           aligned16;
+    return kind != K_ADMM_DL && d->precision == DBP_FP32 && d->U == UT && UT <= 16 && S % 2 == 0 &&
+           d->C <= 16 && aligned16;
 }
 
-size_t cg_cta_for(int UT, int nwarps, int P) {
+size_t bcast_cta_for(Kind kind, int UT, int nwarps, int P) {
+    if (kind == K_CG_UL) {
+        switch (UT) {
+        case 4: return dbp::cg_cta_bytes<4>(nwarps, P);
+        case 8: return dbp::cg_cta_bytes<8>(nwarps, P);
+        default: return dbp::cg_cta_bytes<16>(nwarps, P);
+        }
+    }
     switch (UT) {
-    case 4: return dbp::cg_cta_bytes<4>(nwarps, P);
-    case 8: return dbp::cg_cta_bytes<8>(nwarps, P);
-    default: return dbp::cg_cta_bytes<16>(nwarps, P);
+    case 4: return dbp::admm_cta_bytes<4>(nwarps, P);
+    case 8: return dbp::admm_cta_bytes<8>(nwarps, P);
+    default: return dbp::admm_cta_bytes<16>(nwarps, P);
     }
 }
 
-// Per-warp staging of the CG kernel: H_c (S x U, dense) then the receive rows
-// (pitch yp, an odd number of 16-byte units), one buffer.
-void cg_layout(const dbp_frame_desc *d, int UT, Shape &s) {
+int admm_scratch_elems(int UT) {
+    switch (UT) {
+    case 4: return dbp::AdmmCfg<4>::VB;
+    case 8: return dbp::AdmmCfg<8>::VB;
+    default: return dbp::AdmmCfg<16>::VB;
+    }
+}
+
+// Per-warp staging of the broadcast kernels: H_c (S x U, dense), the receive
+// rows (pitch yp, an odd number of 16-byte units), one buffer; ADMM adds the
+// mat-vec / inverse scratch.
+void bcast_layout(const dbp_frame_desc *d, Kind kind, int UT, Shape &s) {
     const int S = d->B / d->C;
     s.hp = UT;
     s.h_rows = S;
@@ -231,9 +248,14 @@ void cg_layout(const dbp_frame_desc *d, int UT, Shape &s) {
     s.off_h1 = 0;
     s.off_y0 = round16((long long)S * UT * 8);
     s.off_y1 = s.off_y0;
-    s.off_g = s.off_y0 + round16((long long)s.y_rows * s.yp * 8);
-    s.off_v = s.off_g;
-    s.warp_bytes = s.off_g;
+    s.off_v = s.off_y0 + round16((long long)s.y_rows * s.yp * 8);
+    if (kind == K_ADMM_UL) {
+        s.off_g = s.off_v + round16((long long)admm_scratch_elems(UT) * 8);     // y_c^reg
+        s.warp_bytes = s.off_g + round16((long long)tile_syms(UT) * UT * 8);
+    } else {
+        s.off_g = s.off_v;
+        s.warp_bytes = s.off_v;
+    }
 }
 
 dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool aligned16, Shape &s) {
@@ -243,12 +265,11 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
     const dbp_tuning &t = h->tuning;
     s.tma = false;
     s.mma8 = false;
-    s.cg = false;
-    // AUTO takes the tensor-core kernel for ADMM only: there the Gram and the
-    // inverse dominate and the MMA shortens them; the CG iteration is a chain
-    // of dependent mat-vecs on which the MMA latency measured slower than the
-    // bulk-copy kernel's FMA path.
-    const bool want_mma = t.kernel == DBP_PATH_MMA || (t.kernel == DBP_PATH_AUTO && kind == K_ADMM_UL);
+    s.bcast = false;
+    // AUTO prefers the broadcast kernels for the uplink (measured fastest for
+    // both ADMM and CG on the B=128, C=8, U=8 frame); the tensor-core kernel
+    // runs when it is asked for.
+    const bool want_mma = t.kernel == DBP_PATH_MMA;
     if (want_mma && t.mapping != DBP_MAP_CLUSTER && mma8_eligible(d, kind, aligned16)) {
         mma8_layout(d, s);
         const int target = t.warps_per_cta > 0 ? t.warps_per_cta : 8;
@@ -278,16 +299,16 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
             return DBP_OK;
         }
     }
-    if ((t.kernel == DBP_PATH_AUTO || t.kernel == DBP_PATH_BCAST) && t.mapping != DBP_MAP_CLUSTER &&
-        cg_eligible(d, kind, UT, aligned16)) {
-        cg_layout(d, UT, s);
+    const bool want_bcast = t.kernel == DBP_PATH_BCAST || t.kernel == DBP_PATH_AUTO;
+    if (want_bcast && t.mapping != DBP_MAP_CLUSTER && bcast_eligible(d, kind, UT, aligned16)) {
+        bcast_layout(d, kind, UT, s);
         const int target = t.warps_per_cta > 0 ? t.warps_per_cta : 8;
         int P = target / C;
         if (P < 1) P = 1;
-        auto bytes = [&](int PP) { return (size_t)PP * C * s.warp_bytes + cg_cta_for(UT, PP * C, PP); };
+        auto bytes = [&](int PP) { return (size_t)PP * C * s.warp_bytes + bcast_cta_for(kind, UT, PP * C, PP); };
         while (P > 1 && (P * C > 16 || bytes(P) > h->smem_optin)) --P;
         if (bytes(P) <= h->smem_optin) {
-            s.cg = true;
+            s.bcast = true;
             s.tma = true;                      // also a persistent bulk-copy kernel
             s.clu = false;
             s.P = P;
@@ -296,7 +317,8 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
             s.nwarps = P * C;
             s.smem = bytes(P);
             const long long tiles = (d->W + P - 1) / P;
-            int occ = dbp_cg_occupancy(UT, s.nwarps * 32, s.smem);
+            int occ = (kind == K_CG_UL) ? dbp_cg_occupancy(UT, s.nwarps * 32, s.smem)
+                                        : dbp_bcast_admm_occupancy(UT, s.nwarps * 32, s.smem);
             if (occ < 1) occ = 1;
             const long long slots = (long long)h->num_sms * occ;
             s.grid = tiles < slots ? tiles : slots;
@@ -306,7 +328,7 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
     }
     if (t.kernel == DBP_PATH_BCAST)
         return fail(h, DBP_ERR_UNSUPPORTED,
-                    "the broadcast CG kernel needs uplink CG, FP32, U in {4,8,16}, even S, C <= 16, 16-byte "
+                    "the broadcast kernels need uplink ADMM or CG, FP32, U in {4,8,16}, even S, C <= 16, 16-byte "
                     "aligned buffers and a CTA that fits shared memory (B=%d C=%d U=%d)", d->B, d->C, d->U);
     if (t.kernel == DBP_PATH_MMA)
         return fail(h, DBP_ERR_UNSUPPORTED,

@@ -10,3 +10,12 @@ int dbp_tma_occupancy_admm_ul(int prec, int UT, int threads, size_t smem) {
 }
 
 int dbp_mma8_occupancy_admm_ul(int threads, size_t smem) { return dbp::mma8_occupancy<dbp::ALG_ADMM_UL>(threads, smem); }
+
+int dbp_bcast_admm_occupancy(int UT, int threads, size_t smem) {
+    switch (UT) {
+    case 4: return dbp::admm_occupancy_one<4>(threads, smem);
+    case 8: return dbp::admm_occupancy_one<8>(threads, smem);
+    case 16: return dbp::admm_occupancy_one<16>(threads, smem);
+    default: return 0;
+    }
+}

@@ -10,6 +10,7 @@
 #include "dbp_tma.cuh"
 #include "dbp_mma8.cuh"
 #include "dbp_cg.cuh"
+#include "dbp_admm.cuh"
 
 namespace dbp {
 
@@ -19,7 +20,7 @@ struct Shape {
     bool clu;
     bool tma;              // persistent bulk-copy kernel
     bool mma8 = false;     // U = 8 tensor-core kernel
-    bool cg = false;       // CG with the centralized update and broadcast of p
+    bool bcast = false;    // consensus step once per symbol, result broadcast
     int P, CPB, CL, nwarps;
     long long grid;
     size_t smem;
@@ -174,14 +175,42 @@ cudaError_t launch_cg_one(const FusedParams &p, const Shape &s, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <int UT>
+int admm_occupancy_one(int threads, size_t smem) {
+    auto kern = dbp::dbp_admm_kernel<UT>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+template <int UT>
+cudaError_t launch_admm_one(const FusedParams &p, const Shape &s, cudaStream_t st) {
+    auto kern = dbp::dbp_admm_kernel<UT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)s.grid, s.nwarps * 32, s.smem, st>>>(p);
+    return cudaGetLastError();
+}
+
 template <int ALG>
 cudaError_t launch_alg(int prec, int UT, const FusedParams &p, const Shape &s, cudaStream_t st) {
     if constexpr (ALG == ALG_CG_UL) {
-        if (s.cg) {
+        if (s.bcast) {
             switch (UT) {
             case 4: return launch_cg_one<4>(p, s, st);
             case 8: return launch_cg_one<8>(p, s, st);
             case 16: return launch_cg_one<16>(p, s, st);
+            default: return cudaErrorInvalidValue;
+            }
+        }
+    }
+    if constexpr (ALG == ALG_ADMM_UL) {
+        if (s.bcast) {
+            switch (UT) {
+            case 4: return launch_admm_one<4>(p, s, st);
+            case 8: return launch_admm_one<8>(p, s, st);
+            case 16: return launch_admm_one<16>(p, s, st);
             default: return cudaErrorInvalidValue;
             }
         }
@@ -207,3 +236,4 @@ int dbp_tma_occupancy_admm_dl(int prec, int UT, int threads, size_t smem);
 int dbp_mma8_occupancy_admm_ul(int threads, size_t smem);
 int dbp_mma8_occupancy_cg_ul(int threads, size_t smem);
 int dbp_cg_occupancy(int UT, int threads, size_t smem);
+int dbp_bcast_admm_occupancy(int UT, int threads, size_t smem);

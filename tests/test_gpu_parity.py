@@ -130,9 +130,9 @@ UL_CASES = [
 
 @pytest.fixture(params=["auto", "generic", "tma"])
 def path(request, dbp, handle):
-    """Run a test with the automatic kernel choice (the U = 8 tensor-core
-    kernel or the persistent bulk-copy kernel wherever they apply), with the
-    generic kernel forced, and with the bulk-copy kernel preferred."""
+    """Run a test with the automatic kernel choice (the broadcast kernels or
+    the persistent bulk-copy kernel wherever they apply), with the generic
+    kernel forced, and with the bulk-copy kernel preferred."""
     code = {"auto": dbp.DBP_PATH_AUTO, "generic": dbp.DBP_PATH_GENERIC, "tma": dbp.DBP_PATH_TMA}[request.param]
     if request.param == "tma":
         # forcing would reject shapes the bulk-copy kernel cannot take; prefer it
@@ -398,7 +398,8 @@ def test_forced_mma8_kernel_rejects_other_shapes(dbp, handle):
 
 
 # ---------------------------------------------------------------------------
-# CG with the centralized update and broadcast of p (Sec. III-D, first placement)
+# Broadcast kernels: the consensus step once per symbol, s (Alg. 1) or p
+# (Alg. 2, the first placement of Sec. III-D) broadcast to the clusters
 # ---------------------------------------------------------------------------
 
 BCAST_CASES = [
@@ -412,6 +413,7 @@ BCAST_CASES = [
     (5, 1, 24, 3, 8, 16, 4),         # N=1: one owner, the other warps idle in the update
     (8, 14, 96, 6, 16, 64, 16),      # T = U: CG reaches the LMMSE solution
     (3, 14, 256, 8, 16, 64, 2),      # S=32 rows of H per cluster
+    (4, 14, 32, 8, 8, 16, 3),        # S=4 < U=8 (the Woodbury regime of the paper)
 ]
 
 
@@ -423,14 +425,43 @@ def _with_path(dbp, handle, code, fn):
         dbp.dbp_set_tuning(handle)
 
 
+@pytest.mark.parametrize("algo", ["admm", "cg"])
 @pytest.mark.parametrize("W,N,B,C,U,M,T", BCAST_CASES)
-def test_bcast_cg_kernel_matches_oracle(dbp, handle, W, N, B, C, U, M, T):
+def test_bcast_kernels_match_oracle(dbp, handle, algo, W, N, B, C, U, M, T):
     f = synth.uplink_frame(W, N, B, U, M, 12.0, seed=900 + W + N + B + C + U)
-    x, lab = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, C, T, "cg"))
-    ref = oracle_ul(f, C, T, "cg", "fp32")
+    x, lab = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, C, T, algo))
+    ref = oracle_ul(f, C, T, algo, "fp32")
     err = _rel_per_vector(x, ref)
     assert err.max() <= FP32_TOL, err.max()
     assert_labels(x, lab, ref, M, np.float32)
+
+
+@pytest.mark.parametrize("reg", ["zf", "box"])
+def test_bcast_admm_kernel_regularisers(dbp, handle, reg):
+    f = synth.uplink_frame(21, 14, 128, 8, 16, 10.0, seed=905)
+    r = oracle.box_radius(16)
+    x, _ = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(
+        dbp, handle, f, 8, 4, "admm", reg=dbp.DBP_REG_ZF if reg == "zf" else dbp.DBP_REG_BOX, box_r=r))
+    ref = oracle_ul(f, 8, 4, "admm", "fp32", reg=oracle.REG_ZF if reg == "zf" else oracle.REG_BOX, box_r=r)
+    assert _rel_per_vector(x, ref).max() <= FP32_TOL
+
+
+@pytest.mark.parametrize("U", [4, 8, 16])
+def test_bcast_admm_fp64_retry_on_a_near_singular_cluster(dbp, handle, U):
+    W, N, B, C = 10, 14, 128, 4                   # S = 32 > U
+    f = synth.uplink_frame(W, N, B, U, 16, 20.0, seed=906 + U)
+    S = B // C
+    u_, s_, vh = np.linalg.svd(f["H"][4, S:2 * S], full_matrices=False)
+    s_[-1] = 1e-4 * s_[0]
+    f["H"][4, S:2 * S] = (u_ * s_) @ vh
+    f["y"] = np.einsum("wbu,wnu->wnb", f["H"], f["s"])
+    dbp.dbp_fp64_retries(handle)
+    x, _ = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, C, 3, "admm", rho=1e-6))
+    assert dbp.dbp_fp64_retries(handle) == 1
+    ref = oracle_ul(f, C, 3, "admm", "fp32", rho=1e-6)
+    good = np.arange(W) != 4
+    assert np.all(np.isfinite(x))
+    assert _rel_per_vector(x[good], ref[good]).max() <= FP32_TOL
 
 
 def test_bcast_cg_kernel_zf_and_T_edges(dbp, handle):
@@ -442,6 +473,8 @@ def test_bcast_cg_kernel_zf_and_T_edges(dbp, handle):
     assert _rel_per_vector(x1, oracle_ul(f, 4, 1, "cg", "fp32")).max() <= FP32_TOL
     x0, _ = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, 4, 0, "cg"))
     assert np.all(x0 == 0)
+    a1, _ = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, 4, 1, "admm"))
+    assert _rel_per_vector(a1, oracle_ul(f, 4, 1, "admm", "fp32")).max() <= FP32_TOL
 
 
 def test_bcast_cg_kernel_stops_on_a_zero_residual(dbp, handle):
@@ -460,26 +493,33 @@ def test_bcast_cg_kernel_stops_on_a_zero_residual(dbp, handle):
     assert _rel_per_vector(x[keep], ref[keep]).max() <= FP32_TOL
 
 
-def test_bcast_cg_kernel_matches_generic_kernel_over_many_tiles(dbp, handle):
+@pytest.mark.parametrize("algo", ["admm", "cg"])
+def test_bcast_kernels_match_generic_kernel_over_many_tiles(dbp, handle, algo):
     f = synth.uplink_frame(1201, 14, 128, 8, 16, 8.0, seed=912)
-    a, la = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, 8, 8, "cg"))
-    b, lb = _with_path(dbp, handle, dbp.DBP_PATH_GENERIC, lambda: run_ul(dbp, handle, f, 8, 8, "cg"))
+    T = 3 if algo == "admm" else 8
+    a, la = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, 8, T, algo))
+    b, lb = _with_path(dbp, handle, dbp.DBP_PATH_GENERIC, lambda: run_ul(dbp, handle, f, 8, T, algo))
     # two FP32 kernels with different summation orders: rounding-level agreement
     assert _rel_per_vector(a, b).max() <= 1e-5
 
 
-def test_auto_path_uses_bcast_for_cg(dbp, handle):
+@pytest.mark.parametrize("algo", ["admm", "cg"])
+def test_auto_path_uses_bcast_for_the_uplink(dbp, handle, algo):
     f = synth.uplink_frame(17, 14, 128, 8, 16, 10.0, seed=913)
-    a, _ = run_ul(dbp, handle, f, 8, 8, "cg")
-    b, _ = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, 8, 8, "cg"))
+    a, _ = run_ul(dbp, handle, f, 8, 8, algo)
+    b, _ = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, 8, 8, algo))
     assert np.array_equal(a, b)
 
 
-def test_forced_bcast_kernel_rejects_other_work(dbp, handle):
-    f = synth.uplink_frame(3, 2, 64, 8, 16, 8.0, seed=914)
-    for algo, ff, C in (("admm", f, 4), ("cg", synth.uplink_frame(3, 2, 64, 32, 16, 8.0, seed=915), 2)):
+def test_forced_bcast_kernels_reject_other_work(dbp, handle):
+    fd = synth.downlink_frame(3, 2, 64, 8, 16, seed=914)
+    with pytest.raises(dbp.DbpError) as ei:
+        _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_dl(dbp, handle, fd, 4, 3))
+    assert ei.value.status == dbp.DBP_ERR_UNSUPPORTED
+    f32 = synth.uplink_frame(3, 2, 64, 32, 16, 8.0, seed=915)   # U = 32
+    for algo in ("admm", "cg"):
         with pytest.raises(dbp.DbpError) as ei:
-            _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, ff, C, 3, algo))
+            _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f32, 2, 3, algo))
         assert ei.value.status == dbp.DBP_ERR_UNSUPPORTED
 
 
