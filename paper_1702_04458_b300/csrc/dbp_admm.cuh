@@ -7,8 +7,9 @@
 // iteration lambda_c += gamma (z_c - s), z_c = y_c^reg + rho B_c^{-1}(s -
 // lambda_c).  The consensus w = sum_c (z_c + lambda_c) and the (E2) prox of
 // Lemma 1 run once per symbol: warp c reduces and applies the prox to the
-// symbols [c*per, (c+1)*per) of the chunk and s is broadcast through shared
-// memory (the centralized unit of Fig. 2, spread over the cluster warps).
+// units c, c + C, ... of 32 (symbol, user) entries of the chunk and s is
+// broadcast through shared memory (the centralized unit, spread over the
+// cluster warps).
 //
 // The Gram and the Gauss-Jordan inverse run in a column-split layout: lane
 // (u, g) holds columns [g*CPG, (g+1)*CPG) of row u, so the UT / CPG groups of
@@ -19,6 +20,7 @@
 
 #include "dbp_fused.cuh"
 #include "dbp_tma.cuh"
+#include "dbp_cg.cuh"
 
 namespace dbp {
 
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_admm_kernel(const 
     C2 *contrib = reinterpret_cast<C2 *>(smem_raw + (size_t)nwarps * p.warp_bytes);   // [nwarps][E]
     C2 *sb = contrib + (size_t)nwarps * E + (size_t)pl * E;                             // this subcarrier's s
     uint64_t *bar = reinterpret_cast<uint64_t *>(contrib + (size_t)nwarps * E + (size_t)P * E) + warp;
-    const C2 *grp = contrib + (size_t)pl * C * E;
+    const C2 *grp = contrib + pl * C * E;
 
     for (int i = lane * 16; i < p.warp_bytes; i += 32 * 16)
         *reinterpret_cast<float4 *>(wb + i) = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -226,10 +228,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_admm_kernel(const 
         }
 
         for (int n0 = 0; n0 < N; n0 += K::NCH) {
-            const int nv = min(K::NCH, N - n0);
-            const int per = (nv + C - 1) / C;
-            const int own = per * UT;
-            const int e0 = c * own;
+            const int nvu = min(K::NCH, N - n0) * UT;     // (symbol, user) entries in this chunk
 
             // Matched filter and regularised estimate y_c^reg = B_c^{-1} H_c^H y_c
             // (kept in shared memory; z_c starts from it).
@@ -238,13 +237,15 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_admm_kernel(const 
                 C2 acc[K::NN];
 #pragma unroll
                 for (int j = 0; j < K::NN; ++j) acc[j] = make_float2(0.f, 0.f);
+                const C2 *yr = Ys + (n0 + g) * yp;
+                const int js = K::G * yp;                 // row step between a lane's symbols
                 for (int r = 0; r < S; r += 2) {
                     const C2 h0 = Hs[r * UT + u];
                     const C2 h1 = Hs[(r + 1) * UT + u];
 #pragma unroll
                     for (int j = 0; j < K::NN; ++j) {
                         C2 a, b;
-                        ld2(&Ys[(size_t)(n0 + g + K::G * j) * yp + r], a, b);
+                        ld2(&yr[j * js + r], a, b);
                         cmacc(acc[j], h0, a);
                         cmacc(acc[j], h1, b);
                     }
@@ -262,20 +263,16 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_admm_kernel(const 
             }
 
             // Consensus and (E2) prox for the owned symbols, s broadcast.
-            auto consensus = [&](const C2 (&val)[K::NN], C2 (&s)[K::NN]) {
-                C2 *mine = contrib + (size_t)warp * E;
+            // w_c = z_c + lambda_c is published, s = prox(sum_c w_c) returned.
+            auto consensus = [&](const C2 (&zz)[K::NN], const C2 (&ll)[K::NN], C2 (&s)[K::NN]) {
+                C2 *mine = contrib + warp * E;
 #pragma unroll
-                for (int j = 0; j < K::NN; ++j) mine[(g + K::G * j) * UT + u] = val[j];
+                for (int j = 0; j < K::NN; ++j) mine[(g + K::G * j) * UT + u] = cadd(zz[j], ll[j]);
                 __syncthreads();
-                for (int k0 = 0; k0 < own; k0 += 32) {
-                    const int k = k0 + lane, e = e0 + k;
-                    if (k < own && e < nv * UT) {
-                        C2 a = make_float2(0.f, 0.f);
-                        for (int cc = 0; cc < C; ++cc) {
-                            const C2 t = grp[(size_t)cc * E + e];
-                            a.x += t.x;
-                            a.y += t.y;
-                        }
+                for (int base = c * 32; base < nvu; base += C * 32) {
+                    const int e = base + lane;
+                    if (e < nvu) {
+                        C2 a = consensus_sum<E>(grp, e, C);
                         if (p.reg == 2) {
                             const float r = (float)p.box_r, ic = (float)p.invC;
                             a.x = clip_r(a.x * ic, r);
@@ -294,7 +291,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_admm_kernel(const 
             // Init: lambda_c = 0, z_c = y_c^reg, s = prox(sum_c z_c).
 #pragma unroll
             for (int j = 0; j < K::NN; ++j) lam[j] = make_float2(0.f, 0.f);
-            consensus(z, s);
+            consensus(z, lam, s);
             const float gam = (float)p.gamma, rho = (float)p.rho;
             for (int t = 2; t <= p.T; ++t) {
                 C2 d[K::NN];
@@ -308,21 +305,17 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_admm_kernel(const 
                 __syncwarp();
                 matvec<UT>(R, Vb, g, z);
                 __syncwarp();
-                C2 wv[K::NN];
 #pragma unroll
-                for (int j = 0; j < K::NN; ++j) {
-                    z[j] = cadd(z[j], Yr[(g + K::G * j) * UT + u]);
-                    wv[j] = cadd(z[j], lam[j]);
-                }
-                consensus(wv, s);
+                for (int j = 0; j < K::NN; ++j) z[j] = cadd(z[j], Yr[(g + K::G * j) * UT + u]);
+                consensus(z, lam, s);
             }
 
             // Output s^(T) and its label, written by the warp that formed it.
             if (valid) {
                 C2 *xo = reinterpret_cast<C2 *>(p.out);
-                for (int k0 = 0; k0 < own; k0 += 32) {
-                    const int k = k0 + lane, e = e0 + k;
-                    if (k < own && e < nv * UT) {
+                for (int base = c * 32; base < nvu; base += C * 32) {
+                    const int e = base + lane;
+                    if (e < nvu) {
                         const C2 sv = sb[e];
                         const size_t o = ((size_t)w * N + n0) * UT + e;
                         xo[o] = sv;

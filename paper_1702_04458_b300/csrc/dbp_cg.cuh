@@ -7,9 +7,9 @@
 // of p^(t) to every cluster; or in every cluster on its own copy after a
 // broadcast of w.  The bulk-copy kernel (dbp_tma.cuh) follows the second;
 // this kernel follows the first.  On one GPU the "centralized unit" for a
-// subcarrier is spread over its C cluster warps by symbol: warp c reduces and
-// updates the symbols [c*per, (c+1)*per) of each chunk, so each update runs
-// once instead of C times.  Per (subcarrier, cluster) the local work is what
+// subcarrier is spread over its C cluster warps in units of 32 (symbol, user)
+// entries: warp c reduces and updates the units c, c + C, ... of each chunk,
+// so each update runs once instead of C times and on full warps.  Per (subcarrier, cluster) the local work is what
 // Alg. 2 assigns to cluster c: the matched filter H_c^H y_c and, per
 // iteration, w_c = G_c p with the local Gram G_c = H_c^H H_c (the footnote to
 // Alg. 2).
@@ -34,6 +34,27 @@ template <int UT> struct CgCfg {
     using K = Tile<UT>;
     static constexpr int E = K::NCH * UT;   // entries (symbol, user) per chunk
 };
+
+// Consensus sum over the C cluster contributions of entry e (stride E in
+// shared memory), in cluster order.
+template <int E>
+__device__ __forceinline__ float2 consensus_sum(const float2 *grp, int e, int C) {
+    float2 a = make_float2(0.f, 0.f);
+    const float2 *q = grp + e;
+    int cc = 0;
+    for (; cc + 4 <= C; cc += 4, q += 4 * E) {
+        const float2 t0 = q[0], t1 = q[E], t2 = q[2 * E], t3 = q[3 * E];
+        a.x += t0.x; a.y += t0.y;
+        a.x += t1.x; a.y += t1.y;
+        a.x += t2.x; a.y += t2.y;
+        a.x += t3.x; a.y += t3.y;
+    }
+    for (; cc < C; ++cc, q += E) {
+        a.x += q[0].x;
+        a.y += q[0].y;
+    }
+    return a;
+}
 
 template <int UT> __host__ __device__ constexpr size_t cg_cta_bytes(int nwarps, int P) {
     return (size_t)nwarps * CgCfg<UT>::E * 8 + (size_t)P * CgCfg<UT>::E * (3 * 8 + 4) + (size_t)nwarps * 8;
@@ -64,7 +85,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_cg_kernel(const Fu
     uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<float *>(contrib + (size_t)nwarps * E +
                                                                            3 * (size_t)P * E) +
                                                  (size_t)P * E) + warp;
-    const C2 *grp = contrib + (size_t)pl * C * E;   // the C contributions of this subcarrier
+    const C2 *grp = contrib + pl * C * E;           // the C contributions of this subcarrier
 
     // Zero the staging region (receive rows past N stay zero), set up the
     // mbarrier.
@@ -151,9 +172,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_cg_kernel(const Fu
 
         for (int n0 = 0; n0 < N; n0 += K::NCH) {
             const int nv = min(K::NCH, N - n0);          // symbols in this chunk
-            const int per = (nv + C - 1) / C;             // symbols updated by each warp
-            const int own = per * UT;                     // entries updated by each warp
-            const int e0 = c * own;                       // first entry of this warp
+            const int nvu = nv * UT;                      // (symbol, user) entries in this chunk
 
             // Matched filter m_c = H_c^H y_c for the chunk, published for the
             // consensus y_MRC = sum_c m_c (Alg. 2, preprocessing).
@@ -161,18 +180,21 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_cg_kernel(const Fu
                 C2 acc[K::NN];
 #pragma unroll
                 for (int j = 0; j < K::NN; ++j) acc[j] = make_float2(0.f, 0.f);
+                const C2 *yr = Ys + (n0 + g) * yp;
+                const int js = K::G * yp;                 // row step between a lane's symbols
+#pragma unroll 2
                 for (int r = 0; r < S; r += 2) {
                     const C2 h0 = Hs[r * UT + u];
                     const C2 h1 = Hs[(r + 1) * UT + u];
 #pragma unroll
                     for (int j = 0; j < K::NN; ++j) {
                         C2 a, b;
-                        ld2(&Ys[(size_t)(n0 + g + K::G * j) * yp + r], a, b);
+                        ld2(&yr[j * js + r], a, b);
                         cmacc(acc[j], h0, a);
                         cmacc(acc[j], h1, b);
                     }
                 }
-                C2 *mine = contrib + (size_t)warp * E;
+                C2 *mine = contrib + warp * E;
 #pragma unroll
                 for (int j = 0; j < K::NN; ++j) mine[(g + K::G * j) * UT + u] = acc[j];
             }
@@ -184,17 +206,11 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_cg_kernel(const Fu
             __syncthreads();
 
             // Init (Alg. 2): r = y_MRC, p = r, x = 0.
-            for (int k0 = 0; k0 < own; k0 += 32) {
-                const int k = k0 + lane, e = e0 + k;
-                const bool ok = (k < own) && (e < nv * UT);
+            for (int base = c * 32; base < nvu; base += C * 32) {
+                const int e = base + lane;
+                const bool ok = e < nvu;
                 C2 y = make_float2(0.f, 0.f);
-                if (ok) {
-                    for (int cc = 0; cc < C; ++cc) {
-                        const C2 t = grp[(size_t)cc * E + e];
-                        y.x += t.x;
-                        y.y += t.y;
-                    }
-                }
+                if (ok) y = consensus_sum<E>(grp, e, C);
                 const float rr = group_sum<UT>(y.x * y.x + y.y * y.y);
                 if (ok) {
                     pb[e] = y;
@@ -221,7 +237,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_cg_kernel(const Fu
                             cmac(wc[j], R[v + 1], b);
                         }
                     }
-                    C2 *mine = contrib + (size_t)warp * E;
+                    C2 *mine = contrib + warp * E;
 #pragma unroll
                     for (int j = 0; j < K::NN; ++j) mine[(g + K::G * j) * UT + u] = wc[j];
                 }
@@ -230,17 +246,13 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_cg_kernel(const Fu
                 // updates of e, alpha, x, r, beta and p; p^(t) is broadcast
                 // through shared memory.  A symbol whose ||r||^2 or Re(p^H e)
                 // is zero stops (its iterate is final); rr < 0 marks it.
-                for (int k0 = 0; k0 < own; k0 += 32) {
-                    const int k = k0 + lane, e = e0 + k;
-                    const bool ok = (k < own) && (e < nv * UT);
+                for (int base = c * 32; base < nvu; base += C * 32) {
+                    const int e = base + lane;
+                    const bool ok = e < nvu;
                     C2 ws = make_float2(0.f, 0.f), pv = ws, rv = ws, xv = ws;
                     float rr = -1.f;
                     if (ok) {
-                        for (int cc = 0; cc < C; ++cc) {
-                            const C2 tv = grp[(size_t)cc * E + e];
-                            ws.x += tv.x;
-                            ws.y += tv.y;
-                        }
+                        ws = consensus_sum<E>(grp, e, C);
                         pv = pb[e];
                         rv = rb[e];
                         xv = xb[e];
@@ -279,9 +291,9 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_cg_kernel(const Fu
             // Output x^(T) and its label, written by the updating warp.
             if (valid) {
                 C2 *xo = reinterpret_cast<C2 *>(p.out);
-                for (int k0 = 0; k0 < own; k0 += 32) {
-                    const int k = k0 + lane, e = e0 + k;
-                    if (k < own && e < nv * UT) {
+                for (int base = c * 32; base < nvu; base += C * 32) {
+                    const int e = base + lane;
+                    if (e < nvu) {
                         const C2 xv = xb[e];
                         const size_t o = ((size_t)w * N + n0) * UT + e;
                         xo[o] = xv;
