@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_admm_kernel(const 
                     }
                 }
             }
-            const float delta = (float)p.delta;
+            const float delta = p.f_delta;
             float dmax = 0.f;
 #pragma unroll
             for (int i = 0; i < SP::CPG; ++i)
@@ -274,11 +274,11 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_admm_kernel(const 
                     if (e < nvu) {
                         C2 a = consensus_sum<E>(grp, e, C);
                         if (p.reg == 2) {
-                            const float r = (float)p.box_r, ic = (float)p.invC;
+                            const float r = p.f_box_r, ic = p.f_invC;
                             a.x = clip_r(a.x * ic, r);
                             a.y = clip_r(a.y * ic, r);
                         } else {
-                            a = cscale(a, (float)p.e2_scale);
+                            a = cscale(a, p.f_e2_scale);
                         }
                         sb[e] = a;
                     }
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_admm_kernel(const 
 #pragma unroll
             for (int j = 0; j < K::NN; ++j) lam[j] = make_float2(0.f, 0.f);
             consensus(z, lam, s);
-            const float gam = (float)p.gamma, rho = (float)p.rho;
+            const float gam = p.f_gamma, rho = p.f_rho;
             for (int t = 2; t <= p.T; ++t) {
                 C2 d[K::NN];
 #pragma unroll
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_admm_kernel(const 
                         const size_t o = ((size_t)w * N + n0) * UT + e;
                         xo[o] = sv;
                         if (p.labels != nullptr)
-                            p.labels[o] = qam_label<float>(sv.x, sv.y, (float)p.qam_inv_a, p.qam_L, p.qam_half);
+                            p.labels[o] = qam_label<float>(sv.x, sv.y, p.f_qam_inv_a, p.qam_L, p.qam_half);
                     }
                 }
             }

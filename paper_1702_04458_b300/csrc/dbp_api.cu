@@ -440,6 +440,20 @@ void fill_params(FusedParams &p, const dbp_frame_desc *d, const Shape &s) {
     }
 }
 
+// FP32 copies of the scalars (round to nearest, as the device conversion).
+void fill_float_params(FusedParams &p) {
+    p.f_delta = (float)p.delta;
+    p.f_rho = (float)p.rho;
+    p.f_gamma = (float)p.gamma;
+    p.f_e2_scale = (float)p.e2_scale;
+    p.f_invC = (float)p.invC;
+    p.f_box_r = (float)p.box_r;
+    p.f_rho_cg = (float)p.rho_cg;
+    p.f_kappa = (float)p.kappa;
+    p.f_inv_rho = (float)p.inv_rho;
+    p.f_qam_inv_a = (float)p.qam_inv_a;
+}
+
 bool aligned(const void *ptr, size_t a) { return (reinterpret_cast<uintptr_t>(ptr) % a) == 0; }
 
 dbp_status run_ex(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void *H, const void *vin,
@@ -501,19 +515,14 @@ dbp_status run_ex(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void
         if (factor_used) *factor_used = true;
     }
     const int UT = next_pow2_ut(d->U);
+    if (kind == K_ADMM_UL) p.delta = d->rho;          // B_c = H_c^H H_c + rho I
+    else if (kind == K_CG_UL) p.delta = 0.0;          // G_c = H_c^H H_c
+    else p.delta = 1.0 / d->rho;                      // B_c = H^d_c H^dH_c + rho^{-1} I
+    fill_float_params(p);
     switch (kind) {
-    case K_ADMM_UL:
-        p.delta = d->rho;                 // B_c = H_c^H H_c + rho I
-        e = dbp_launch_admm_ul(d->precision, UT, p, s, st);
-        break;
-    case K_CG_UL:
-        p.delta = 0.0;                    // G_c = H_c^H H_c
-        e = dbp_launch_cg_ul(d->precision, UT, p, s, st);
-        break;
-    default:
-        p.delta = 1.0 / d->rho;           // B_c = H^d_c H^dH_c + rho^{-1} I
-        e = dbp_launch_admm_dl(d->precision, UT, p, s, st);
-        break;
+    case K_ADMM_UL: e = dbp_launch_admm_ul(d->precision, UT, p, s, st); break;
+    case K_CG_UL: e = dbp_launch_cg_ul(d->precision, UT, p, s, st); break;
+    default: e = dbp_launch_admm_dl(d->precision, UT, p, s, st); break;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
     if (norm) {

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_cg_kernel(const Fu
     int tile = blockIdx.x;
     if (tile < p.tiles && tile * P + pl < W) issue(tile * P + pl);
 
-    const float rcg = (float)p.rho_cg;
+    const float rcg = p.f_rho_cg;
     for (; tile < p.tiles; tile += gridDim.x) {
         const int w = tile * P + pl;
         const bool valid = (w < W);
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_cg_kernel(const Fu
                     R[v].y += shfl_x(R[v].y, m);
                 }
             }
-            const float delta = (float)p.delta;
+            const float delta = p.f_delta;
 #pragma unroll
             for (int v = 0; v < UT; ++v)
                 if (v == u) R[v].x += delta;
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_cg_kernel(const Fu
                         const size_t o = ((size_t)w * N + n0) * UT + e;
                         xo[o] = xv;
                         if (p.labels != nullptr)
-                            p.labels[o] = qam_label<float>(xv.x, xv.y, (float)p.qam_inv_a, p.qam_L, p.qam_half);
+                            p.labels[o] = qam_label<float>(xv.x, xv.y, p.f_qam_inv_a, p.qam_L, p.qam_half);
                     }
                 }
             }

@@ -33,6 +33,15 @@ namespace dbp {
 
 enum Alg { ALG_ADMM_UL = 0, ALG_CG_UL = 1, ALG_ADMM_DL = 2 };
 
+struct FusedParams;
+template <typename T> struct ParamSel;
+template <> struct ParamSel<float> {
+    static __device__ __forceinline__ float get(double, float f) { return f; }
+};
+template <> struct ParamSel<double> {
+    static __device__ __forceinline__ double get(double d, float) { return d; }
+};
+
 struct FusedParams {
     const void *H;       // [W][B][U] complex
     const void *vin;     // uplink: y [W][N][B]; downlink: s [W][N][U]
@@ -56,6 +65,9 @@ struct FusedParams {
     double inv_rho;      // 1/rho
     int qam_M, qam_L, qam_half;
     double qam_inv_a;    // 1 / sqrt(3 / (2 (M - 1)))
+    // The same scalars rounded to FP32 on the host, so FP32 kernels read
+    // them from the parameter bank without a double conversion.
+    float f_delta, f_rho, f_gamma, f_e2_scale, f_invC, f_box_r, f_rho_cg, f_kappa, f_inv_rho, f_qam_inv_a;
     // Persistent bulk-copy kernel only:
     int *status;         // device word: bit 0 = a bounded wait gave up
     unsigned int *retries;   // device counter of FP64 inverse retries
@@ -362,7 +374,7 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
             R[v].y += shfl_x(R[v].y, m);
         }
     }
-    const T delta = (T)p.delta;
+    const T delta = ParamSel<T>::get(p.delta, p.f_delta);
 #pragma unroll
     for (int v = 0; v < UT; ++v)
         if (v == u) R[v].x += delta;
@@ -372,7 +384,7 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
     } else if (ALG == ALG_ADMM_DL) {
         gj_invert<UT>(R, Vb, u, lane);                   // row u of B_c^{-1}
         // Q_c = I - rho^{-1} B_c^{-1}: the map (z_c + lambda_c) -> m_c = H_c x_c
-        const T ir = (T)p.inv_rho;
+        const T ir = ParamSel<T>::get(p.inv_rho, p.f_inv_rho);
 #pragma unroll
         for (int v = 0; v < UT; ++v) {
             R[v].x = ((v == u) ? (T)1 : (T)0) - ir * R[v].x;
@@ -467,17 +479,17 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
 #pragma unroll
                 for (int j = 0; j < K::NN; ++j) {
                     if (p.reg == 2) {
-                        const T r = (T)p.box_r, ic = (T)p.invC;
+                        const T r = ParamSel<T>::get(p.box_r, p.f_box_r), ic = ParamSel<T>::get(p.invC, p.f_invC);
                         s_[j].x = clip_r(sum[j].x * ic, r);
                         s_[j].y = clip_r(sum[j].y * ic, r);
                     } else {
-                        s_[j] = cscale(sum[j], (T)p.e2_scale);
+                        s_[j] = cscale(sum[j], ParamSel<T>::get(p.e2_scale, p.f_e2_scale));
                     }
                 }
             };
             consensus(z, acc);
             prox(acc);
-            const T gam = (T)p.gamma, rho = (T)p.rho;
+            const T gam = ParamSel<T>::get(p.gamma, p.f_gamma), rho = ParamSel<T>::get(p.rho, p.f_rho);
             for (int t = 2; t <= p.T; ++t) {
                 C2 d[K::NN];
 #pragma unroll
@@ -512,7 +524,7 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
                 rr[j] = group_sum<UT>(r[j].x * r[j].x + r[j].y * r[j].y);
                 live[j] = true;
             }
-            const T rcg = (T)p.rho_cg;
+            const T rcg = ParamSel<T>::get(p.rho_cg, p.f_rho_cg);
             for (int t = 1; t <= p.T; ++t) {
                 C2 wc[K::NN], e[K::NN];
                 put_vec<UT>(Vb, u, g, pv);
@@ -545,7 +557,7 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
             for (int j = 0; j < K::NN; ++j) s_[j] = x[j];
         } else {  // ALG_ADMM_DL
             C2 sv[K::NN], z[K::NN], lam[K::NN], v[K::NN], m[K::NN];
-            const T kap = (T)p.kappa, gam = (T)p.gamma, ic = (T)p.invC;
+            const T kap = ParamSel<T>::get(p.kappa, p.f_kappa), gam = ParamSel<T>::get(p.gamma, p.f_gamma), ic = ParamSel<T>::get(p.invC, p.f_invC);
 #pragma unroll
             for (int j = 0; j < K::NN; ++j) {
                 const int n = n0 + g + K::G * j;
@@ -579,7 +591,7 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
             __syncwarp();
             matvec<UT>(R, Vb, g, m);
             __syncwarp();
-            const T rho = (T)p.rho;
+            const T rho = ParamSel<T>::get(p.rho, p.f_rho);
 #pragma unroll
             for (int j = 0; j < K::NN; ++j) m[j] = cscale(csub(v[j], m[j]), rho);
             put_vec<UT>(Vb, u, g, m);
@@ -628,7 +640,7 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
                     const size_t o = ((size_t)w * N + n) * U + u;
                     xo[o] = s_[j];
                     if (p.labels != nullptr)
-                        p.labels[o] = qam_label<T>(s_[j].x, s_[j].y, (T)p.qam_inv_a, p.qam_L, p.qam_half);
+                        p.labels[o] = qam_label<T>(s_[j].x, s_[j].y, ParamSel<T>::get(p.qam_inv_a, p.f_qam_inv_a), p.qam_L, p.qam_half);
                 }
             }
         }

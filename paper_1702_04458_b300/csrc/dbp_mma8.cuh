@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(512) dbp_mma8_kernel(const FusedParams p) {
             e0 = make_float2(gacc[0], gacc[2]);
             e1 = make_float2(gacc[1], gacc[3]);
             if (ALG == ALG_ADMM_UL) {
-                const float delta = (float)p.delta;
+                const float delta = p.f_delta;
                 if (2 * t == g) e0.x += delta;
                 if (2 * t + 1 == g) e1.x += delta;
                 float dmax = (2 * t == g) ? e0.x : ((2 * t + 1 == g) ? e1.x : 0.f);
@@ -381,17 +381,17 @@ __global__ void __launch_bounds__(512) dbp_mma8_kernel(const FusedParams p) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         if (p.reg == 2) {
-                            const float r = (float)p.box_r, ic = (float)p.invC;
+                            const float r = p.f_box_r, ic = p.f_invC;
                             s_[q].x = clip_r(sum[q].x * ic, r);
                             s_[q].y = clip_r(sum[q].y * ic, r);
                         } else {
-                            s_[q] = cscale(sum[q], (float)p.e2_scale);
+                            s_[q] = cscale(sum[q], p.f_e2_scale);
                         }
                     }
                 };
                 consensus(z, acc);
                 prox(acc);
-                const float gam = (float)p.gamma, rho = (float)p.rho;
+                const float gam = p.f_gamma, rho = p.f_rho;
                 for (int it2 = 2; it2 <= p.T; ++it2) {
                     C2 d[4], wv[4];
 #pragma unroll
@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(512) dbp_mma8_kernel(const FusedParams p) {
                     x[q] = make_float2(0.f, 0.f);
                     rr[q] = usum(r[q].x * r[q].x + r[q].y * r[q].y);
                 }
-                const float rcg = (float)p.rho_cg;
+                const float rcg = p.f_rho_cg;
                 for (int it2 = 1; it2 <= p.T; ++it2) {
                     C2 wc[4], e[4];
                     apply(pv, wc);                    // w_c = G_c p
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(512) dbp_mma8_kernel(const FusedParams p) {
                         const size_t o = ((size_t)w * N + n) * 8 + g;
                         xo[o] = s_[q];
                         if (p.labels != nullptr)
-                            p.labels[o] = qam_label<float>(s_[q].x, s_[q].y, (float)p.qam_inv_a, p.qam_L, p.qam_half);
+                            p.labels[o] = qam_label<float>(s_[q].x, s_[q].y, p.f_qam_inv_a, p.qam_L, p.qam_half);
                     }
                 }
             }

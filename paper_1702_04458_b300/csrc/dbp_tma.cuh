@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
                 }
             }
         }
-        const float delta = (float)p.delta;
+        const float delta = p.f_delta;
         float dmax = 0.f;
 #pragma unroll
         for (int v = 0; v < UT; ++v)
@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
                 if (lane == 0 && p.retries) atomicAdd(p.retries, 1u);
             }
             if (ALG == ALG_ADMM_DL) {
-                const float ir = (float)p.inv_rho;
+                const float ir = p.f_inv_rho;
 #pragma unroll
                 for (int v = 0; v < UT; ++v) {
                     R[v].x = ((v == u) ? 1.f : 0.f) - ir * R[v].x;
@@ -544,17 +544,17 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
 #pragma unroll
                     for (int j = 0; j < K::NN; ++j) {
                         if (p.reg == 2) {
-                            const float r = (float)p.box_r, ic = (float)p.invC;
+                            const float r = p.f_box_r, ic = p.f_invC;
                             s_[j].x = clip_r(sum[j].x * ic, r);
                             s_[j].y = clip_r(sum[j].y * ic, r);
                         } else {
-                            s_[j] = cscale(sum[j], (float)p.e2_scale);
+                            s_[j] = cscale(sum[j], p.f_e2_scale);
                         }
                     }
                 };
                 consensus(z, acc);
                 prox(acc);
-                const float gam = (float)p.gamma, rho = (float)p.rho;
+                const float gam = p.f_gamma, rho = p.f_rho;
                 for (int t = 2; t <= p.T; ++t) {
                     C2 d[K::NN];
 #pragma unroll
@@ -588,7 +588,7 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
                     rr[j] = group_sum<UT>(r[j].x * r[j].x + r[j].y * r[j].y);
                     live[j] = true;
                 }
-                const float rcg = (float)p.rho_cg;
+                const float rcg = p.f_rho_cg;
                 for (int t = 1; t <= p.T; ++t) {
                     C2 wc[K::NN], e[K::NN];
                     put_vec<UT>(Vb, u, g, pv);
@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
                 for (int j = 0; j < K::NN; ++j) s_[j] = x[j];
             } else {  // ALG_ADMM_DL (FP32 inputs only)
                 C2 sv[K::NN], z[K::NN], lam[K::NN], v[K::NN], m[K::NN];
-                const float kap = (float)p.kappa, gam = (float)p.gamma, ic = (float)p.invC;
+                const float kap = p.f_kappa, gam = p.f_gamma, ic = p.f_invC;
                 const C2 *Sg = reinterpret_cast<const C2 *>(p.vin);
 #pragma unroll
                 for (int j = 0; j < K::NN; ++j) {
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
                 __syncwarp();
                 matvec<UT>(R, Vb, g, m);
                 __syncwarp();
-                const float rho = (float)p.rho;
+                const float rho = p.f_rho;
 #pragma unroll
                 for (int j = 0; j < K::NN; ++j) m[j] = cscale(csub(v[j], m[j]), rho);
                 put_vec<UT>(Vb, u, g, m);
@@ -710,7 +710,7 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
                         const size_t o = ((size_t)w * N + n) * UT + u;
                         xo[o] = s_[j];
                         if (p.labels != nullptr)
-                            p.labels[o] = qam_label<float>(s_[j].x, s_[j].y, (float)p.qam_inv_a, p.qam_L, p.qam_half);
+                            p.labels[o] = qam_label<float>(s_[j].x, s_[j].y, p.f_qam_inv_a, p.qam_L, p.qam_half);
                     }
                 }
             }
