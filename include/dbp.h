@@ -131,9 +131,11 @@ typedef enum dbp_kernel_path {
     DBP_PATH_TMA = 2,          /* persistent kernel fed by cp.async.bulk:
                                   U in {4,8,16,32}, even S <= 64, 16-byte
                                   aligned buffers, CTA mapping               */
-    DBP_PATH_MMA = 3,          /* uplink, FP32, U = 8, even S <= 64: as
-                                  DBP_PATH_TMA with every dense product on
-                                  the tensor cores (3 x TF32 per product)   */
+    DBP_PATH_MMA = 3,          /* uplink ADMM and CG, FP32, U = 8, even S,
+                                  C <= 16: as DBP_PATH_BCAST with every dense
+                                  product (Gram, matched filter, operator x
+                                  state) on the tensor cores, 3 x TF32 per
+                                  product                                    */
     DBP_PATH_BCAST = 4         /* uplink ADMM and CG, FP32, U in {4,8,16},
                                   even S, C <= 16: the consensus and the
                                   centralized step (the (E2) prox of Alg. 1;

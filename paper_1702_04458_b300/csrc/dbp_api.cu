@@ -178,29 +178,34 @@ bool tma_eligible(const dbp_frame_desc *d, int UT, int maxw, bool aligned16) {
     return shape && d->U == UT && S <= 64 && d->C <= maxw && aligned16;
 }
 
-// U = 8 tensor-core kernel: uplink, FP32, exactly 8 users, even S <= 64,
-// all C warps in one CTA, 16-byte aligned buffers.
-bool mma8_eligible(const dbp_frame_desc *d, Kind kind, bool aligned16) {
+// U = 8 tensor-core kernel: uplink, FP32, exactly 8 users, even S, all
+// C <= 16 warps of a subcarrier in one CTA, 16-byte aligned buffers.
+bool tc8_eligible(const dbp_frame_desc *d, Kind kind, bool aligned16) {
     const int S = d->B / d->C;
-    return kind != K_ADMM_DL && d->precision == DBP_FP32 && d->U == 8 && S % 2 == 0 && S <= 64 && d->C <= 16 &&
-           aligned16;
+    return kind != K_ADMM_DL && d->precision == DBP_FP32 && d->U == 8 && S % 2 == 0 && d->C <= 16 && aligned16;
 }
 
-void mma8_layout(const dbp_frame_desc *d, Shape &s) {
+// Per-warp layout of the tensor-core kernel: H_c (rows padded to a multiple
+// of 4), the receive rows (pitch yp, 16-symbol passes), and for ADMM the
+// transpose buffer [16][10] and y_c^reg [4][32].
+void tc8_layout(const dbp_frame_desc *d, Kind kind, Shape &s) {
     const int S = d->B / d->C;
     s.hp = 8;
     s.h_rows = round_up(S, 4);
     s.yp = S + ((S % 4 == 0) ? 2 : 4);
     s.y_rows = round_up(d->N, 16);
     s.ms_rows = 0;
-    const int hb = round16((long long)s.h_rows * 8 * 8);
-    const int yb = round16((long long)s.y_rows * s.yp * 8);
-    s.off_h1 = hb;
-    s.off_y0 = 2 * hb;
-    s.off_y1 = s.off_y0 + yb;
-    s.off_g = s.off_y1 + yb;
-    s.off_v = s.off_g;
-    s.warp_bytes = s.off_v + 16 * 10 * 8;
+    s.off_h1 = 0;
+    s.off_y0 = round16((long long)s.h_rows * 8 * 8);
+    s.off_y1 = s.off_y0;
+    s.off_v = s.off_y0 + round16((long long)s.y_rows * s.yp * 8);
+    if (kind == K_ADMM_UL) {
+        s.off_g = s.off_v + 16 * dbp::Tc8::VP * 8;
+        s.warp_bytes = s.off_g + 4 * 32 * 8;
+    } else {
+        s.off_g = s.off_v;
+        s.warp_bytes = s.off_v;
+    }
 }
 
 // Uplink kernels with the consensus step once per symbol and its result
@@ -264,24 +269,24 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
     const int C = d->C;
     const dbp_tuning &t = h->tuning;
     s.tma = false;
-    s.mma8 = false;
+    s.tc8 = false;
     s.bcast = false;
     // AUTO prefers the broadcast kernels for the uplink (measured fastest for
     // both ADMM and CG on the B=128, C=8, U=8 frame); the tensor-core kernel
     // runs when it is asked for.
     const bool want_mma = t.kernel == DBP_PATH_MMA;
-    if (want_mma && t.mapping != DBP_MAP_CLUSTER && mma8_eligible(d, kind, aligned16)) {
-        mma8_layout(d, s);
+    if (want_mma && t.mapping != DBP_MAP_CLUSTER && tc8_eligible(d, kind, aligned16)) {
+        tc8_layout(d, kind, s);
         const int target = t.warps_per_cta > 0 ? t.warps_per_cta : 8;
         int P = target / C;
         if (P < 1) P = 1;
         auto bytes = [&](int PP) {
-            return (size_t)PP * C * s.warp_bytes + (2 * (size_t)PP * C * 128 + 2 * (size_t)PP * 128) * 8 +
-                   (size_t)PP * C * 16;
+            return (size_t)PP * C * s.warp_bytes + ((kind == K_ADMM_UL) ? dbp::tc8_cta_bytes<dbp::ALG_ADMM_UL>(PP * C, PP)
+                                                                        : dbp::tc8_cta_bytes<dbp::ALG_CG_UL>(PP * C, PP));
         };
         while (P > 1 && (P * C > 16 || bytes(P) > h->smem_optin)) --P;
         if (bytes(P) <= h->smem_optin) {
-            s.mma8 = true;
+            s.tc8 = true;
             s.tma = true;                      // also a persistent bulk-copy kernel
             s.clu = false;
             s.P = P;
@@ -290,8 +295,8 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
             s.nwarps = P * C;
             s.smem = bytes(P);
             const long long tiles = (d->W + P - 1) / P;
-            int occ = (kind == K_ADMM_UL) ? dbp_mma8_occupancy_admm_ul(s.nwarps * 32, s.smem)
-                                          : dbp_mma8_occupancy_cg_ul(s.nwarps * 32, s.smem);
+            int occ = (kind == K_ADMM_UL) ? dbp_tc8_occupancy_admm_ul(s.nwarps * 32, s.smem)
+                                          : dbp_tc8_occupancy_cg_ul(s.nwarps * 32, s.smem);
             if (occ < 1) occ = 1;
             const long long slots = (long long)h->num_sms * occ;
             s.grid = tiles < slots ? tiles : slots;
@@ -332,8 +337,8 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
                     "aligned buffers and a CTA that fits shared memory (B=%d C=%d U=%d)", d->B, d->C, d->U);
     if (t.kernel == DBP_PATH_MMA)
         return fail(h, DBP_ERR_UNSUPPORTED,
-                    "the tensor-core kernel needs uplink, FP32, U = 8, even S <= 64, C <= 16 and 16-byte "
-                    "aligned buffers (B=%d C=%d U=%d)", d->B, d->C, d->U);
+                    "the tensor-core kernel needs uplink, FP32, U = 8, even S, C <= 16, 16-byte aligned "
+                    "buffers and a CTA that fits shared memory (B=%d C=%d U=%d)", d->B, d->C, d->U);
     if (t.kernel != DBP_PATH_GENERIC && t.mapping != DBP_MAP_CLUSTER && tma_eligible(d, UT, maxw, aligned16)) {
         tma_layout(d, kind, UT, s);
         const int target = t.warps_per_cta > 0 ? t.warps_per_cta : 8;

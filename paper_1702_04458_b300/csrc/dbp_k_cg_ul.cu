@@ -9,7 +9,7 @@ int dbp_tma_occupancy_cg_ul(int prec, int UT, int threads, size_t smem) {
     return dbp::tma_occupancy<dbp::ALG_CG_UL>(prec, UT, threads, smem);
 }
 
-int dbp_mma8_occupancy_cg_ul(int threads, size_t smem) { return dbp::mma8_occupancy<dbp::ALG_CG_UL>(threads, smem); }
+int dbp_tc8_occupancy_cg_ul(int threads, size_t smem) { return dbp::tc8_occupancy<dbp::ALG_CG_UL>(threads, smem); }
 
 int dbp_cg_occupancy(int UT, int threads, size_t smem) {
     switch (UT) {

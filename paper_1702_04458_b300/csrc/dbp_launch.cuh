@@ -11,6 +11,7 @@
 #include "dbp_mma8.cuh"
 #include "dbp_cg.cuh"
 #include "dbp_admm.cuh"
+#include "dbp_tc8.cuh"
 
 namespace dbp {
 
@@ -19,7 +20,7 @@ namespace dbp {
 struct Shape {
     bool clu;
     bool tma;              // persistent bulk-copy kernel
-    bool mma8 = false;     // U = 8 tensor-core kernel
+    bool tc8 = false;      // U = 8 tensor-core kernel
     bool bcast = false;    // consensus step once per symbol, result broadcast
     int P, CPB, CL, nwarps;
     long long grid;
@@ -131,11 +132,11 @@ cudaError_t launch_tma(int prec, int UT, const FusedParams &p, const Shape &s, c
 }
 
 template <int ALG>
-int mma8_occupancy(int threads, size_t smem) {
+int tc8_occupancy(int threads, size_t smem) {
     if constexpr (ALG == ALG_ADMM_DL) {
         return 0;
     } else {
-        auto kern = dbp::dbp_mma8_kernel<ALG>;
+        auto kern = dbp::dbp_tc8_kernel<ALG>;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return 0;
         int n = 0;
@@ -145,11 +146,11 @@ int mma8_occupancy(int threads, size_t smem) {
 }
 
 template <int ALG>
-cudaError_t launch_mma8(const FusedParams &p, const Shape &s, cudaStream_t st) {
+cudaError_t launch_tc8(const FusedParams &p, const Shape &s, cudaStream_t st) {
     if constexpr (ALG == ALG_ADMM_DL) {
         return cudaErrorInvalidValue;
     } else {
-        auto kern = dbp::dbp_mma8_kernel<ALG>;
+        auto kern = dbp::dbp_tc8_kernel<ALG>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
         if (e != cudaSuccess) return e;
         kern<<<(unsigned)s.grid, s.nwarps * 32, s.smem, st>>>(p);
@@ -215,7 +216,7 @@ cudaError_t launch_alg(int prec, int UT, const FusedParams &p, const Shape &s, c
             }
         }
     }
-    if (s.mma8) return launch_mma8<ALG>(p, s, st);
+    if (s.tc8) return launch_tc8<ALG>(p, s, st);
     if (s.tma) return launch_tma<ALG>(prec, UT, p, s, st);
     if (prec != DBP_FP32 && prec != DBP_FP64) return cudaErrorInvalidValue;
     if (prec == DBP_FP32)
@@ -233,7 +234,7 @@ cudaError_t dbp_launch_admm_dl(int prec, int UT, const dbp::FusedParams &p, cons
 int dbp_tma_occupancy_admm_ul(int prec, int UT, int threads, size_t smem);
 int dbp_tma_occupancy_cg_ul(int prec, int UT, int threads, size_t smem);
 int dbp_tma_occupancy_admm_dl(int prec, int UT, int threads, size_t smem);
-int dbp_mma8_occupancy_admm_ul(int threads, size_t smem);
-int dbp_mma8_occupancy_cg_ul(int threads, size_t smem);
+int dbp_tc8_occupancy_admm_ul(int threads, size_t smem);
+int dbp_tc8_occupancy_cg_ul(int threads, size_t smem);
 int dbp_cg_occupancy(int UT, int threads, size_t smem);
 int dbp_bcast_admm_occupancy(int UT, int threads, size_t smem);

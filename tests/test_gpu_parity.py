@@ -493,11 +493,13 @@ def test_bcast_cg_kernel_stops_on_a_zero_residual(dbp, handle):
     assert _rel_per_vector(x[keep], ref[keep]).max() <= FP32_TOL
 
 
+@pytest.mark.parametrize("kernel", ["bcast", "mma"])
 @pytest.mark.parametrize("algo", ["admm", "cg"])
-def test_bcast_kernels_match_generic_kernel_over_many_tiles(dbp, handle, algo):
+def test_bcast_kernels_match_generic_kernel_over_many_tiles(dbp, handle, algo, kernel):
     f = synth.uplink_frame(1201, 14, 128, 8, 16, 8.0, seed=912)
     T = 3 if algo == "admm" else 8
-    a, la = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, 8, T, algo))
+    code = dbp.DBP_PATH_BCAST if kernel == "bcast" else dbp.DBP_PATH_MMA
+    a, la = _with_path(dbp, handle, code, lambda: run_ul(dbp, handle, f, 8, T, algo))
     b, lb = _with_path(dbp, handle, dbp.DBP_PATH_GENERIC, lambda: run_ul(dbp, handle, f, 8, T, algo))
     # two FP32 kernels with different summation orders: rounding-level agreement
     assert _rel_per_vector(a, b).max() <= 1e-5
