@@ -123,9 +123,9 @@ typedef enum dbp_mapping {
 } dbp_mapping;
 
 typedef enum dbp_kernel_path {
-    DBP_PATH_AUTO = 0,         /* uplink: DBP_PATH_BCAST, else
-                                  DBP_PATH_TMA; downlink: DBP_PATH_TMA; each
-                                  where eligible, then DBP_PATH_GENERIC      */
+    DBP_PATH_AUTO = 0,         /* uplink: DBP_PATH_MMA, else DBP_PATH_BCAST,
+                                  else DBP_PATH_TMA; downlink: DBP_PATH_TMA;
+                                  each where eligible, then DBP_PATH_GENERIC */
     DBP_PATH_GENERIC = 1,      /* per-subcarrier kernel with staged loads:
                                   any shape, FP64, thread-block clusters     */
     DBP_PATH_TMA = 2,          /* persistent kernel fed by cp.async.bulk:

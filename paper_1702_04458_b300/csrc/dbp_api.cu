@@ -186,8 +186,8 @@ bool tc8_eligible(const dbp_frame_desc *d, Kind kind, bool aligned16) {
 }
 
 // Per-warp layout of the tensor-core kernel: H_c (rows padded to a multiple
-// of 4), the receive rows (pitch yp, 16-symbol passes), and for ADMM the
-// transpose buffer [16][10] and y_c^reg [4][32].
+// of 4), the receive rows (pitch yp, 16-symbol passes), and for ADMM
+// y_c^reg [4][32].
 void tc8_layout(const dbp_frame_desc *d, Kind kind, Shape &s) {
     const int S = d->B / d->C;
     s.hp = 8;
@@ -200,7 +200,7 @@ void tc8_layout(const dbp_frame_desc *d, Kind kind, Shape &s) {
     s.off_y1 = s.off_y0;
     s.off_v = s.off_y0 + round16((long long)s.y_rows * s.yp * 8);
     if (kind == K_ADMM_UL) {
-        s.off_g = s.off_v + 16 * dbp::Tc8::VP * 8;
+        s.off_g = s.off_v;
         s.warp_bytes = s.off_g + 4 * 32 * 8;
     } else {
         s.off_g = s.off_v;
@@ -271,10 +271,9 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
     s.tma = false;
     s.tc8 = false;
     s.bcast = false;
-    // AUTO prefers the broadcast kernels for the uplink (measured fastest for
-    // both ADMM and CG on the B=128, C=8, U=8 frame); the tensor-core kernel
-    // runs when it is asked for.
-    const bool want_mma = t.kernel == DBP_PATH_MMA;
+    // AUTO takes the tensor-core kernel for U = 8 (measured fastest for ADMM
+    // and CG on the B=128, C=8, U=8 frame), else the broadcast kernels.
+    const bool want_mma = t.kernel == DBP_PATH_MMA || t.kernel == DBP_PATH_AUTO;
     if (want_mma && t.mapping != DBP_MAP_CLUSTER && tc8_eligible(d, kind, aligned16)) {
         tc8_layout(d, kind, s);
         const int target = t.warps_per_cta > 0 ? t.warps_per_cta : 8;

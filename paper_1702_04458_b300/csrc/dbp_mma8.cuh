@@ -3,10 +3,11 @@
 // fragment of H_c^H and the shuffle-based Gauss-Jordan inversion used by the
 // tensor-core uplink kernel (dbp_tc8.cuh).
 //
-// FP32 accuracy from TF32 tensor cores: every operand x is split into
-// x_hi = tf32(x) and x_lo = tf32(x - x_hi), and a product is accumulated as
-// a_lo b_hi + a_hi b_lo + a_hi b_hi in FP32 (the a_lo b_lo term, ~2^-22
-// relative, is dropped) -- three mma.sync.m16n8k8.tf32 per product.
+// FP32 accuracy from TF32 tensor cores: every operand x is split into two
+// TF32 values x_hi + x_lo (truncated, |x - x_hi - x_lo| < 2^-20 |x|), and a
+// product is accumulated as a_lo b_hi + a_hi b_lo + a_hi b_hi in FP32 (the
+// a_lo b_lo term, < 2^-20 relative, is dropped) -- three
+// mma.sync.m16n8k8.tf32 per product.
 //
 // Complex products are embedded in real ones with real/imaginary parts
 // interleaved along the contraction, k' = 2k + a:
@@ -27,9 +28,12 @@ __device__ __forceinline__ uint32_t tf32_bits(float x) {
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return r;
 }
+// x = hi + lo + r with hi, lo TF32 values: hi keeps the 10 leading mantissa
+// bits of x (truncation), lo those of the exact remainder x - hi, and
+// |r| < 2^-20 |x|.
 __device__ __forceinline__ void split3(float x, uint32_t &hi, uint32_t &lo) {
-    hi = tf32_bits(x);
-    lo = tf32_bits(x - __uint_as_float(hi));
+    hi = __float_as_uint(x) & 0xffffe000u;
+    lo = __float_as_uint(x - __uint_as_float(hi)) & 0xffffe000u;
 }
 __device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint32_t b0, uint32_t b1) {

@@ -20,9 +20,11 @@
 // read straight from that broadcast buffer.
 //
 // Shared memory per warp: H_c (h_rows x 8), receive rows (y_rows x yp), and
-// for ADMM a transpose buffer [16][VP] and y_c^reg in the accumulator layout.
+// for ADMM y_c^reg in the accumulator layout.
 // After the warps: contrib[nwarps][CE] | ADMM: s[P][CE] | CG: p[P][CE],
-// r[P][E], x[P][E], rr[P][E] | mbarrier[nwarps].
+// r[P][E], x[P][E], rr[P][E] | mbarrier[nwarps].  contrib and s rows have
+// PITCH complex per symbol, p rows VP; the ADMM transpose buffer is the
+// warp's own contrib slot.
 #pragma once
 
 #include "dbp_mma8.cuh"
@@ -32,13 +34,14 @@ namespace dbp {
 
 struct Tc8 {
     static constexpr int E = 128;      // 16 symbol slots x 8 users
-    static constexpr int PITCH = 12;   // complex per symbol row in contrib / s / p
+    static constexpr int PITCH = 12;   // complex per symbol row in contrib and s
     static constexpr int CE = 16 * PITCH;
-    static constexpr int VP = 10;      // transpose buffer pitch (complex)
+    static constexpr int VP = 10;      // transpose buffer and CG p pitch (complex):
+                                       // conflict-free B fragment loads
 };
 
 // entry e = 8 n + u of a 16-symbol pass -> padded shared-memory index
-__device__ __forceinline__ int tc8_idx(int e) { return (e >> 3) * Tc8::PITCH + (e & 7); }
+template <int PITCH> __device__ __forceinline__ int tc8_idx(int e) { return (e >> 3) * PITCH + (e & 7); }
 
 template <int ALG> __host__ __device__ constexpr size_t tc8_cta_bytes(int nwarps, int P) {
     return (size_t)nwarps * Tc8::CE * 8 +
@@ -61,10 +64,12 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
 
     unsigned char *wb = smem_raw + (size_t)warp * p.warp_bytes;
     const C2 *Hs = reinterpret_cast<const C2 *>(wb);
-    const C2 *Ys = reinterpret_cast<const C2 *>(wb + p.off_y0);
-    C2 *Vs = reinterpret_cast<C2 *>(wb + p.off_v);            // ADMM: [16][VP]
+    const float *Yf = reinterpret_cast<const float *>(wb + p.off_y0);
     C2 *Yr = reinterpret_cast<C2 *>(wb + p.off_g);            // ADMM: y_c^reg [4][32]
     C2 *contrib = reinterpret_cast<C2 *>(smem_raw + (size_t)nwarps * p.warp_bytes);   // [nwarps][CE]
+    // ADMM transpose buffer [16][VP]: this warp's contribution slot, free
+    // between the consensus rounds
+    C2 *Vs = contrib + warp * CE;
     C2 *bc = contrib + nwarps * CE + pl * CE;                 // broadcast s or p of this subcarrier
     C2 *rb = contrib + nwarps * CE + P * CE + pl * E;         // CG: r
     C2 *xb = rb + P * E;                                      // CG: x
@@ -130,11 +135,10 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
                 if (npass == 1) {
 #pragma unroll
                     for (int nt = 0; nt < 2; ++nt) {
-                        const float2 y0 = Ys[(8 * nt + g) * yp + s0 + (t >> 1)];
-                        const float2 y1 = Ys[(8 * nt + g) * yp + s0 + 2 + (t >> 1)];
+                        const float *yr = Yf + ((8 * nt + g) * yp + s0 + (t >> 1)) * 2 + (t & 1);
                         uint32_t bh0, bl0, bh1, bl1;
-                        split3((t & 1) ? y0.y : y0.x, bh0, bl0);
-                        split3((t & 1) ? y1.y : y1.x, bh1, bl1);
+                        split3(yr[0], bh0, bl0);
+                        split3(yr[4], bh1, bl1);
                         mma3(macc[nt], ah, al, bh0, bh1, bl0, bl1);
                     }
                 }
@@ -253,11 +257,10 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
                     for (int i = 0; i < 4; ++i) split3(a[i], ah[i], al[i]);
 #pragma unroll
                     for (int nt = 0; nt < 2; ++nt) {
-                        const float2 y0 = Ys[(n0 + 8 * nt + g) * yp + s0 + (t >> 1)];
-                        const float2 y1 = Ys[(n0 + 8 * nt + g) * yp + s0 + 2 + (t >> 1)];
+                        const float *yr = Yf + ((n0 + 8 * nt + g) * yp + s0 + (t >> 1)) * 2 + (t & 1);
                         uint32_t bh0, bl0, bh1, bl1;
-                        split3((t & 1) ? y0.y : y0.x, bh0, bl0);
-                        split3((t & 1) ? y1.y : y1.x, bh1, bl1);
+                        split3(yr[0], bh0, bl0);
+                        split3(yr[4], bh1, bl1);
                         mma3(ma[nt], ah, al, bh0, bh1, bl0, bl1);
                     }
                 }
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
                     lam[q] = make_float2(0.f, 0.f);
                 }
                 // symbol slots past N read s = 0 (the owners write only valid slots)
-                for (int e = nvu + lane; e < E; e += 32) bc[tc8_idx(e)] = make_float2(0.f, 0.f);
+                for (int e = nvu + lane; e < E; e += 32) bc[tc8_idx<PITCH>(e)] = make_float2(0.f, 0.f);
                 // publish w_c = z_c + lambda_c, reduce and prox the owned
                 // entries, read s back
                 auto consensus = [&]() {
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
                     for (int base = c * 32; base < nvu; base += C * 32) {
                         const int e = base + lane;
                         if (e < nvu) {
-                            C2 a = consensus_sum<CE>(grp, tc8_idx(e), C);
+                            C2 a = consensus_sum<CE>(grp, tc8_idx<PITCH>(e), C);
                             if (p.reg == 2) {
                                 const float r = p.f_box_r, ic = p.f_invC;
                                 a.x = clip_r(a.x * ic, r);
@@ -308,7 +311,7 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
                             } else {
                                 a = cscale(a, p.f_e2_scale);
                             }
-                            bc[tc8_idx(e)] = a;
+                            bc[tc8_idx<PITCH>(e)] = a;
                         }
                     }
                     __syncthreads();
@@ -336,7 +339,7 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
                     for (int base = c * 32; base < nvu; base += C * 32) {
                         const int e = base + lane;
                         if (e < nvu) {
-                            const C2 sv = bc[tc8_idx(e)];
+                            const C2 sv = bc[tc8_idx<PITCH>(e)];
                             const size_t o = ((size_t)w * N + n0) * 8 + e;
                             xo[o] = sv;
                             if (p.labels != nullptr)
@@ -353,10 +356,10 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
                     const int e = base + lane;
                     const bool ok = e < nvu;
                     C2 y = make_float2(0.f, 0.f);
-                    if (ok) y = consensus_sum<CE>(grp, tc8_idx(e), C);
+                    if (ok) y = consensus_sum<CE>(grp, tc8_idx<PITCH>(e), C);
                     const float rr = group_sum<8>(y.x * y.x + y.y * y.y);
                     if (ok) {
-                        bc[tc8_idx(e)] = y;
+                        bc[tc8_idx<VP>(e)] = y;
                         rb[e] = y;
                         xb[e] = make_float2(0.f, 0.f);
                         rrb[e] = rr;
@@ -364,13 +367,13 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
                 }
                 if (nvu < E) {
                     // symbol slots past N: p = 0 keeps the products finite
-                    for (int e = nvu + lane; e < E; e += 32) bc[tc8_idx(e)] = make_float2(0.f, 0.f);
+                    for (int e = nvu + lane; e < E; e += 32) bc[tc8_idx<VP>(e)] = make_float2(0.f, 0.f);
                 }
                 __syncthreads();
                 const float rcg = p.f_rho_cg;
                 for (int it = 1; it <= p.T; ++it) {
                     C2 wc[4];
-                    apply_from(bc, PITCH, wc);                 // w_c = G_c p
+                    apply_from(bc, VP, wc);                 // w_c = G_c p
 #pragma unroll
                     for (int q = 0; q < 4; ++q) mine[nof(q) * PITCH + g] = wc[q];
                     __syncthreads();
@@ -380,8 +383,8 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
                         C2 ws = make_float2(0.f, 0.f), pv = ws, rv = ws, xv = ws;
                         float rr = -1.f;
                         if (ok) {
-                            ws = consensus_sum<CE>(grp, tc8_idx(e), C);
-                            pv = bc[tc8_idx(e)];
+                            ws = consensus_sum<CE>(grp, tc8_idx<PITCH>(e), C);
+                            pv = bc[tc8_idx<VP>(e)];
                             rv = rb[e];
                             xv = xb[e];
                             rr = rrb[e];
@@ -404,7 +407,7 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
                                 const float beta = __fdividef(rn, rr);
                                 pv.x = fmaf(beta, pv.x, rv.x);
                                 pv.y = fmaf(beta, pv.y, rv.y);
-                                bc[tc8_idx(e)] = pv;
+                                bc[tc8_idx<VP>(e)] = pv;
                                 rb[e] = rv;
                                 xb[e] = xv;
                                 rrb[e] = rn;

@@ -130,8 +130,8 @@ UL_CASES = [
 
 @pytest.fixture(params=["auto", "generic", "tma"])
 def path(request, dbp, handle):
-    """Run a test with the automatic kernel choice (the broadcast kernels or
-    the persistent bulk-copy kernel wherever they apply), with the generic
+    """Run a test with the automatic kernel choice (the tensor-core, broadcast
+    or persistent bulk-copy kernel wherever they apply), with the generic
     kernel forced, and with the bulk-copy kernel preferred."""
     code = {"auto": dbp.DBP_PATH_AUTO, "generic": dbp.DBP_PATH_GENERIC, "tma": dbp.DBP_PATH_TMA}[request.param]
     if request.param == "tma":
@@ -506,10 +506,14 @@ def test_bcast_kernels_match_generic_kernel_over_many_tiles(dbp, handle, algo, k
 
 
 @pytest.mark.parametrize("algo", ["admm", "cg"])
-def test_auto_path_uses_bcast_for_the_uplink(dbp, handle, algo):
-    f = synth.uplink_frame(17, 14, 128, 8, 16, 10.0, seed=913)
+@pytest.mark.parametrize("U", [4, 8, 16])
+def test_auto_path_for_the_uplink(dbp, handle, algo, U):
+    """AUTO runs the tensor-core kernel at U = 8 and the broadcast kernels at
+    U = 4 and 16 (bit-identical results to forcing them)."""
+    f = synth.uplink_frame(17, 14, 128, U, 16, 10.0, seed=913 + U)
     a, _ = run_ul(dbp, handle, f, 8, 8, algo)
-    b, _ = _with_path(dbp, handle, dbp.DBP_PATH_BCAST, lambda: run_ul(dbp, handle, f, 8, 8, algo))
+    code = dbp.DBP_PATH_MMA if U == 8 else dbp.DBP_PATH_BCAST
+    b, _ = _with_path(dbp, handle, code, lambda: run_ul(dbp, handle, f, 8, 8, algo))
     assert np.array_equal(a, b)
 
 
