@@ -8,7 +8,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 
 #include "dbp.h"
@@ -443,6 +446,53 @@ void fill_params(FusedParams &p, const dbp_frame_desc *d, const Shape &s) {
         p.qam_inv_a = 1.0 / std::sqrt(3.0 / (2.0 * (M - 1)));
     }
 }
+
+}  // namespace
+
+namespace {
+struct LaunchCache {
+    std::mutex mu;
+    std::map<std::pair<const void *, int>, size_t> smem;                       // (kernel, device) -> limit set
+    std::map<std::tuple<const void *, int, int, size_t>, int> occ;             // (kernel, device, threads, smem)
+};
+LaunchCache &launch_cache() {
+    static LaunchCache c;
+    return c;
+}
+}  // namespace
+
+cudaError_t dbp_prepare_kernel(const void *kern, size_t smem) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    LaunchCache &c = launch_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto key = std::make_pair(kern, dev);
+    auto it = c.smem.find(key);
+    if (it != c.smem.end() && it->second >= smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) c.smem[key] = smem;
+    return e;
+}
+
+int dbp_occupancy_cached(const void *kern, int threads, size_t smem) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    LaunchCache &c = launch_cache();
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        auto it = c.occ.find(std::make_tuple(kern, dev, threads, smem));
+        if (it != c.occ.end()) return it->second;
+    }
+    if (dbp_prepare_kernel(kern, smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.occ[std::make_tuple(kern, dev, threads, smem)] = n;
+    return n;
+}
+
+namespace {
 
 // FP32 copies of the scalars (round to nearest, as the device conversion).
 void fill_float_params(FusedParams &p) {

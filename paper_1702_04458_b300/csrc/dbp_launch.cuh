@@ -13,6 +13,13 @@
 #include "dbp_admm.cuh"
 #include "dbp_tc8.cuh"
 
+// Host-side caches (dbp_api.cu): the dynamic shared-memory limit of a kernel
+// is raised once per device and size, and the resident-CTA count of a
+// (kernel, threads, shared memory) shape is queried once, so that a launch
+// costs no driver attribute or occupancy call after the first.
+cudaError_t dbp_prepare_kernel(const void *kern, size_t smem);
+int dbp_occupancy_cached(const void *kern, int threads, size_t smem);
+
 namespace dbp {
 
 // Launch shape: CTA mapping (P whole subcarriers per CTA) when all C warps of
@@ -34,7 +41,7 @@ struct Shape {
 template <typename T, int UT, int ALG, bool CLU>
 cudaError_t launch_one(const FusedParams &p, const Shape &s, cudaStream_t st) {
     auto kern = dbp::dbp_fused_kernel<T, UT, ALG, CLU>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
+    cudaError_t e = dbp_prepare_kernel(reinterpret_cast<const void *>(kern), s.smem);
     if (e != cudaSuccess) return e;
     if (!CLU) {
         kern<<<(unsigned)s.grid, s.nwarps * 32, s.smem, st>>>(p);
@@ -74,7 +81,7 @@ cudaError_t launch_ut(int UT, const FusedParams &p, const Shape &s, cudaStream_t
 template <int UT, int ALG, typename TIn>
 cudaError_t launch_tma_one(const FusedParams &p, const Shape &s, cudaStream_t st) {
     auto kern = dbp::dbp_tma_kernel<UT, ALG, TIn>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
+    cudaError_t e = dbp_prepare_kernel(reinterpret_cast<const void *>(kern), s.smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)s.grid, s.nwarps * 32, s.smem, st>>>(p);
     return cudaGetLastError();
@@ -84,10 +91,7 @@ cudaError_t launch_tma_one(const FusedParams &p, const Shape &s, cudaStream_t st
 template <int UT, int ALG, typename TIn>
 int tma_occupancy_one(int threads, size_t smem) {
     auto kern = dbp::dbp_tma_kernel<UT, ALG, TIn>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) return 0;
-    return n;
+    return dbp_occupancy_cached(reinterpret_cast<const void *>(kern), threads, smem);
 }
 
 template <int ALG, typename TIn>
@@ -137,11 +141,7 @@ int tc8_occupancy(int threads, size_t smem) {
         return 0;
     } else {
         auto kern = dbp::dbp_tc8_kernel<ALG>;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return 0;
-        int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) return 0;
-        return n;
+        return dbp_occupancy_cached(reinterpret_cast<const void *>(kern), threads, smem);
     }
 }
 
@@ -151,7 +151,7 @@ cudaError_t launch_tc8(const FusedParams &p, const Shape &s, cudaStream_t st) {
         return cudaErrorInvalidValue;
     } else {
         auto kern = dbp::dbp_tc8_kernel<ALG>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
+        cudaError_t e = dbp_prepare_kernel(reinterpret_cast<const void *>(kern), s.smem);
         if (e != cudaSuccess) return e;
         kern<<<(unsigned)s.grid, s.nwarps * 32, s.smem, st>>>(p);
         return cudaGetLastError();
@@ -161,16 +161,13 @@ cudaError_t launch_tc8(const FusedParams &p, const Shape &s, cudaStream_t st) {
 template <int UT>
 int cg_occupancy_one(int threads, size_t smem) {
     auto kern = dbp::dbp_cg_kernel<UT>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) return 0;
-    return n;
+    return dbp_occupancy_cached(reinterpret_cast<const void *>(kern), threads, smem);
 }
 
 template <int UT>
 cudaError_t launch_cg_one(const FusedParams &p, const Shape &s, cudaStream_t st) {
     auto kern = dbp::dbp_cg_kernel<UT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
+    cudaError_t e = dbp_prepare_kernel(reinterpret_cast<const void *>(kern), s.smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)s.grid, s.nwarps * 32, s.smem, st>>>(p);
     return cudaGetLastError();
@@ -179,16 +176,13 @@ cudaError_t launch_cg_one(const FusedParams &p, const Shape &s, cudaStream_t st)
 template <int UT>
 int admm_occupancy_one(int threads, size_t smem) {
     auto kern = dbp::dbp_admm_kernel<UT>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) return 0;
-    return n;
+    return dbp_occupancy_cached(reinterpret_cast<const void *>(kern), threads, smem);
 }
 
 template <int UT>
 cudaError_t launch_admm_one(const FusedParams &p, const Shape &s, cudaStream_t st) {
     auto kern = dbp::dbp_admm_kernel<UT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
+    cudaError_t e = dbp_prepare_kernel(reinterpret_cast<const void *>(kern), s.smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)s.grid, s.nwarps * 32, s.smem, st>>>(p);
     return cudaGetLastError();
