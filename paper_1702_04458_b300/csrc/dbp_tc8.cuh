@@ -49,6 +49,50 @@ template <int ALG> __host__ __device__ constexpr size_t tc8_cta_bytes(int nwarps
            (size_t)nwarps * 8;
 }
 
+// Operator (A fragments, hi and lo, for the k-steps of users 0-3 and 4-7)
+// times a state whose complex entry (n, k) sits at src[n * PITCH + k] in
+// shared memory; the result lands in the accumulator layout.
+template <int PITCH>
+__device__ __forceinline__ void tc8_apply(const uint32_t (&oh)[2][4], const uint32_t (&ol)[2][4], const float2 *src,
+                                          int g, int t, float2 (&out)[4]) {
+    const float *sf = reinterpret_cast<const float *>(src) + (g * PITCH + (t >> 1)) * 2 + (t & 1);
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            const float b0 = sf[(8 * nt * PITCH + 4 * ks) * 2];
+            const float b1 = sf[(8 * nt * PITCH + 4 * ks + 2) * 2];
+            uint32_t bh0, bl0, bh1, bl1;
+            split3(b0, bh0, bl0);
+            split3(b1, bh1, bl1);
+            mma3(acc[nt], oh[ks], ol[ks], bh0, bh1, bl0, bl1);
+        }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        out[2 * nt] = make_float2(acc[nt][0], acc[nt][2]);
+        out[2 * nt + 1] = make_float2(acc[nt][1], acc[nt][3]);
+    }
+}
+
+// Sum of the C contributions of one entry (stride CE), in cluster order; C = 8
+// unrolled.
+template <int CE>
+__device__ __forceinline__ float2 tc8_sum(const float2 *grp, int idx, int C) {
+    if (C == 8) {
+        const float2 *q = grp + idx;
+        float2 a = q[0];
+#pragma unroll
+        for (int cc = 1; cc < 8; ++cc) {
+            a.x += q[cc * CE].x;
+            a.y += q[cc * CE].y;
+        }
+        return a;
+    }
+    return consensus_sum<CE>(grp, idx, C);
+}
+
 template <int ALG>
 __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
     using C2 = float2;
@@ -214,29 +258,6 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
 
         // Operator times a state whose complex entry (n, k) sits at
         // src[n * pitch + k] in shared memory -> accumulator layout.
-        auto apply_from = [&](const C2 *src, int pitch, C2 (&out)[4]) {
-            const float *sf = reinterpret_cast<const float *>(src);
-            float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-#pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
-                    const int n = 8 * nt + g;
-                    const float b0 = sf[(n * pitch + 4 * ks + (t >> 1)) * 2 + (t & 1)];
-                    const float b1 = sf[(n * pitch + 4 * ks + 2 + (t >> 1)) * 2 + (t & 1)];
-                    uint32_t bh0, bl0, bh1, bl1;
-                    split3(b0, bh0, bl0);
-                    split3(b1, bh1, bl1);
-                    mma3(acc[nt], oh[ks], ol[ks], bh0, bh1, bl0, bl1);
-                }
-            }
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-                out[2 * nt] = make_float2(acc[nt][0], acc[nt][2]);
-                out[2 * nt + 1] = make_float2(acc[nt][1], acc[nt][3]);
-            }
-        };
-
         for (int pass = 0; pass < npass; ++pass) {
             const int n0 = 16 * pass;
             const int nvu = min(16, N - n0) * 8;            // valid (symbol, user) entries
@@ -283,7 +304,7 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) Vs[nof(q) * VP + g] = x[q];
                     __syncwarp();
-                    apply_from(Vs, VP, out);
+                    tc8_apply<VP>(oh, ol, Vs, g, t, out);
                     __syncwarp();
                 };
                 apply_regs(m, z);
@@ -301,18 +322,16 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
                     for (int q = 0; q < 4; ++q) mine[nof(q) * PITCH + g] = cadd(z[q], lam[q]);
                     __syncthreads();
                     for (int base = c * 32; base < nvu; base += C * 32) {
-                        const int e = base + lane;
-                        if (e < nvu) {
-                            C2 a = consensus_sum<CE>(grp, tc8_idx<PITCH>(e), C);
-                            if (p.reg == 2) {
-                                const float r = p.f_box_r, ic = p.f_invC;
-                                a.x = clip_r(a.x * ic, r);
-                                a.y = clip_r(a.y * ic, r);
-                            } else {
-                                a = cscale(a, p.f_e2_scale);
-                            }
-                            bc[tc8_idx<PITCH>(e)] = a;
+                        const int e = base + lane;            // < E: in the buffers
+                        C2 a = tc8_sum<CE>(grp, tc8_idx<PITCH>(e), C);
+                        if (p.reg == 2) {
+                            const float r = p.f_box_r, ic = p.f_invC;
+                            a.x = clip_r(a.x * ic, r);
+                            a.y = clip_r(a.y * ic, r);
+                        } else {
+                            a = cscale(a, p.f_e2_scale);
                         }
+                        if (e < nvu) bc[tc8_idx<PITCH>(e)] = a;
                     }
                     __syncthreads();
 #pragma unroll
@@ -356,7 +375,7 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
                     const int e = base + lane;
                     const bool ok = e < nvu;
                     C2 y = make_float2(0.f, 0.f);
-                    if (ok) y = consensus_sum<CE>(grp, tc8_idx<PITCH>(e), C);
+                    if (ok) y = tc8_sum<CE>(grp, tc8_idx<PITCH>(e), C);
                     const float rr = group_sum<8>(y.x * y.x + y.y * y.y);
                     if (ok) {
                         bc[tc8_idx<VP>(e)] = y;
@@ -373,47 +392,42 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
                 const float rcg = p.f_rho_cg;
                 for (int it = 1; it <= p.T; ++it) {
                     C2 wc[4];
-                    apply_from(bc, VP, wc);                 // w_c = G_c p
+                    tc8_apply<VP>(oh, ol, bc, g, t, wc);                 // w_c = G_c p
 #pragma unroll
                     for (int q = 0; q < 4; ++q) mine[nof(q) * PITCH + g] = wc[q];
                     __syncthreads();
+                    // e < E always (base < nvu <= E): the loads stay in the
+                    // buffers; entries past N compute on stale values that no
+                    // valid symbol group reads, and only valid entries store.
                     for (int base = c * 32; base < nvu; base += C * 32) {
                         const int e = base + lane;
                         const bool ok = e < nvu;
-                        C2 ws = make_float2(0.f, 0.f), pv = ws, rv = ws, xv = ws;
-                        float rr = -1.f;
-                        if (ok) {
-                            ws = consensus_sum<CE>(grp, tc8_idx<PITCH>(e), C);
-                            pv = bc[tc8_idx<VP>(e)];
-                            rv = rb[e];
-                            xv = xb[e];
-                            rr = rrb[e];
-                        }
+                        const int ie = tc8_idx<VP>(e);
+                        const C2 ws = tc8_sum<CE>(grp, tc8_idx<PITCH>(e), C);
+                        C2 pv = bc[ie], rv = rb[e], xv = xb[e];
+                        const float rr = rrb[e];
                         C2 ev;
                         ev.x = fmaf(rcg, pv.x, ws.x);
                         ev.y = fmaf(rcg, pv.y, ws.y);
                         const float pe = group_sum<8>(pv.x * ev.x + pv.y * ev.y);
                         const bool go = !(rr < 0.f) && rr != 0.f && pe != 0.f;
                         const float alpha = go ? __fdividef(rr, pe) : 0.f;
-                        if (go) {
-                            xv.x = fmaf(alpha, pv.x, xv.x);
-                            xv.y = fmaf(alpha, pv.y, xv.y);
-                            rv.x = fmaf(-alpha, ev.x, rv.x);
-                            rv.y = fmaf(-alpha, ev.y, rv.y);
-                        }
+                        // a stopped symbol (alpha = 0) keeps x and r
+                        xv.x = fmaf(alpha, pv.x, xv.x);
+                        xv.y = fmaf(alpha, pv.y, xv.y);
+                        rv.x = fmaf(-alpha, ev.x, rv.x);
+                        rv.y = fmaf(-alpha, ev.y, rv.y);
                         const float rn = group_sum<8>(rv.x * rv.x + rv.y * rv.y);
+                        const float beta = go ? __fdividef(rn, rr) : 0.f;
+                        if (go) {
+                            pv.x = fmaf(beta, pv.x, rv.x);
+                            pv.y = fmaf(beta, pv.y, rv.y);
+                        }
                         if (ok) {
-                            if (go) {
-                                const float beta = __fdividef(rn, rr);
-                                pv.x = fmaf(beta, pv.x, rv.x);
-                                pv.y = fmaf(beta, pv.y, rv.y);
-                                bc[tc8_idx<VP>(e)] = pv;
-                                rb[e] = rv;
-                                xb[e] = xv;
-                                rrb[e] = rn;
-                            } else {
-                                rrb[e] = -1.f;
-                            }
+                            bc[ie] = pv;
+                            rb[e] = rv;
+                            xb[e] = xv;
+                            rrb[e] = go ? rn : -1.f;
                         }
                     }
                     __syncthreads();
