@@ -716,30 +716,79 @@ def main(argv=None) -> int:
     if not args.no_serving:
         serving = bench_serving(dbp, h, args)
 
-    # ---- end to end through the host-buffer C ABI ----------------------------
+    # ---- end to end: host inputs in, host results out ------------------------
+    # Each step copies the frame's channel and receive vectors (one pinned
+    # host block, one copy) to the device, runs both detectors through the C
+    # ABI and copies both detectors' outputs and labels back.  Two streams
+    # with their own device buffers alternate, so one step's copies overlap
+    # the other's kernels, as in a receiver fed frame by frame.
     e2e = None
     if not args.no_e2e:
         f0 = frames[0]
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
-        Hh = pin(f0["H"].astype(np.complex64))
-        yh = pin(f0["y"].astype(np.complex64))
-        xh = pin(np.zeros((UL.W, UL.N, UL.U), dtype=np.complex64))
-        lh = pin(np.zeros((UL.W, UL.N, UL.U), dtype=np.uint8))
+        Hc = np.ascontiguousarray(f0["H"].astype(np.complex64)).view(np.uint8).reshape(-1)
+        yc = np.ascontiguousarray(f0["y"].astype(np.complex64)).view(np.uint8).reshape(-1)
+        host_in = torch.empty(Hc.size + yc.size, dtype=torch.uint8).pin_memory()
+        host_in[:Hc.size] = torch.from_numpy(Hc)
+        host_in[Hc.size:] = torch.from_numpy(yc)
+        out_shape = (UL.W, UL.N, UL.U)
+        streams = [torch.cuda.Stream(device) for _ in range(2)]
+        sets = []
+        for _ in range(2):
+            din = torch.empty(host_in.numel(), dtype=torch.uint8, device=device)
+            sets.append({
+                "din": din,
+                "H": din[:Hc.size], "y": din[Hc.size:],
+                "xa": torch.empty(out_shape, dtype=torch.complex64, device=device),
+                "la": torch.empty(out_shape, dtype=torch.uint8, device=device),
+                "xc": torch.empty(out_shape, dtype=torch.complex64, device=device),
+                "lc": torch.empty(out_shape, dtype=torch.uint8, device=device),
+                "hxa": torch.empty(out_shape, dtype=torch.complex64).pin_memory(),
+                "hla": torch.empty(out_shape, dtype=torch.uint8).pin_memory(),
+                "hxc": torch.empty(out_shape, dtype=torch.complex64).pin_memory(),
+                "hlc": torch.empty(out_shape, dtype=torch.uint8).pin_memory()})
         da, dc = descs(f0["N0"])
-        for _ in range(3):
-            dbp.dbp_uplink_admm_host(h, da, Hh, yh, xh, lh, sp)
-            dbp.dbp_uplink_cg_host(h, dc, Hh, yh, xh, lh, sp)
+
+        def e2e_step(k):
+            st, b = streams[k % 2], sets[k % 2]
+            with torch.cuda.stream(st):
+                b["din"].copy_(host_in, non_blocking=True)
+                dbp.dbp_uplink_admm(h, da, b["H"], b["y"], b["xa"], b["la"], st.cuda_stream)
+                dbp.dbp_uplink_cg(h, dc, b["H"], b["y"], b["xc"], b["lc"], st.cuda_stream)
+                for src, dst in (("xa", "hxa"), ("la", "hla"), ("xc", "hxc"), ("lc", "hlc")):
+                    b[dst].copy_(b[src], non_blocking=True)
+
+        for k in range(4):
+            e2e_step(k)
+        torch.cuda.synchronize(device)
         KE = args.e2e_steps
         barrier(world, device)
         t0 = time.perf_counter()
-        for _ in range(KE):
+        for k in range(KE):
+            e2e_step(k)
+        torch.cuda.synchronize(device)
+        el = max_over_ranks(time.perf_counter() - t0, world, device)
+        # the host-buffer entry points (each call copies its own inputs)
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        Hh, yh = pin(f0["H"].astype(np.complex64)), pin(f0["y"].astype(np.complex64))
+        xh, lh = pin(np.zeros(out_shape, dtype=np.complex64)), pin(np.zeros(out_shape, dtype=np.uint8))
+        for _ in range(2):
             dbp.dbp_uplink_admm_host(h, da, Hh, yh, xh, lh, sp)
             dbp.dbp_uplink_cg_host(h, dc, Hh, yh, xh, lh, sp)
-        el = max_over_ranks(time.perf_counter() - t0, world, device)
+        KH = max(KE // 4, 4)
+        t1 = time.perf_counter()
+        for _ in range(KH):
+            dbp.dbp_uplink_admm_host(h, da, Hh, yh, xh, lh, sp)
+            dbp.dbp_uplink_cg_host(h, dc, Hh, yh, xh, lh, sp)
+        el_host = max_over_ranks(time.perf_counter() - t1, world, device)
         e2e = {"value": world * bits_step * KE / el / 1e9, "unit": "Gbit/s",
-               "h2d_bytes_per_step": 2 * (Hh.nbytes + yh.nbytes),
-               "d2h_bytes_per_step": 2 * (xh.nbytes + lh.nbytes),
-               "api": "dbp_uplink_admm_host + dbp_uplink_cg_host (pinned host buffers)"}
+               "h2d_bytes_per_step": int(host_in.numel()),
+               "d2h_bytes_per_step": int(2 * (sets[0]["hxa"].numel() * 8 + sets[0]["hla"].numel())),
+               "api": "pinned host frame -> device (one copy), dbp_uplink_admm + dbp_uplink_cg, "
+                      "outputs and labels of both -> pinned host; two streams alternate",
+               "host_api": {"value": world * bits_step * KH / el_host / 1e9, "unit": "Gbit/s",
+                            "h2d_bytes_per_step": 2 * (Hh.nbytes + yh.nbytes),
+                            "d2h_bytes_per_step": 2 * (xh.nbytes + lh.nbytes),
+                            "api": "dbp_uplink_admm_host + dbp_uplink_cg_host (each call copies its inputs)"}}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
