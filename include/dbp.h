@@ -124,18 +124,20 @@ typedef enum dbp_mapping {
 
 typedef enum dbp_kernel_path {
     DBP_PATH_AUTO = 0,         /* uplink: DBP_PATH_MMA, else DBP_PATH_BCAST,
-                                  else DBP_PATH_TMA; downlink: DBP_PATH_TMA;
-                                  each where eligible, then DBP_PATH_GENERIC */
+                                  else DBP_PATH_TMA; downlink: DBP_PATH_MMA,
+                                  else DBP_PATH_TMA; each where eligible,
+                                  then DBP_PATH_GENERIC                      */
     DBP_PATH_GENERIC = 1,      /* per-subcarrier kernel with staged loads:
                                   any shape, FP64, thread-block clusters     */
     DBP_PATH_TMA = 2,          /* persistent kernel fed by cp.async.bulk:
                                   U in {4,8,16,32}, even S <= 64, 16-byte
                                   aligned buffers, CTA mapping               */
-    DBP_PATH_MMA = 3,          /* uplink ADMM and CG, FP32, U = 8, even S,
-                                  C <= 16: as DBP_PATH_BCAST with every dense
-                                  product (Gram, matched filter, operator x
-                                  state) on the tensor cores, 3 x TF32 per
-                                  product                                    */
+    DBP_PATH_MMA = 3,          /* FP32, C <= 16, every dense product (Gram,
+                                  matched filter, operator x state, output)
+                                  on the tensor cores, 3 x TF32 per product,
+                                  consensus as DBP_PATH_BCAST: uplink ADMM and
+                                  CG with U = 8 and even S; downlink ADMM with
+                                  U = 16 and S a multiple of 8               */
     DBP_PATH_BCAST = 4         /* uplink ADMM and CG, FP32, U in {4,8,16},
                                   even S, C <= 16: the consensus and the
                                   centralized step (the (E2) prox of Alg. 1;

@@ -211,6 +211,29 @@ void tc8_layout(const dbp_frame_desc *d, Kind kind, Shape &s) {
     }
 }
 
+// U = 16 tensor-core downlink kernel: FP32, exactly 16 users, S a multiple
+// of 8, all C <= 16 warps of a subcarrier in one CTA, 16-byte aligned buffers.
+bool tcdl_eligible(const dbp_frame_desc *d, Kind kind, bool aligned16) {
+    const int S = d->B / d->C;
+    return kind == K_ADMM_DL && d->precision == DBP_FP32 && d->U == 16 && S % 8 == 0 && d->C <= 16 && aligned16;
+}
+
+// Per-warp layout of the downlink tensor-core kernel: two H_c buffers, the
+// state [16][18] and the operator [16][18].
+void tcdl_layout(const dbp_frame_desc *d, Shape &s) {
+    const int S = d->B / d->C;
+    s.hp = 16;
+    s.h_rows = S;
+    s.yp = 0;
+    s.y_rows = 0;
+    s.ms_rows = 0;
+    s.off_h1 = round16((long long)S * 16 * 8);
+    s.off_y0 = s.off_y1 = 2 * s.off_h1;
+    s.off_v = 2 * s.off_h1;
+    s.off_g = s.off_v + 16 * dbp::TcDl::VPD * 8;
+    s.warp_bytes = s.off_g + 16 * dbp::TcDl::QP * 8;
+}
+
 // Uplink kernels with the consensus step once per symbol and its result
 // broadcast (s for ADMM, p for CG): FP32, U a power of two in {4, 8, 16},
 // even S, all C <= 16 warps of a subcarrier in one CTA.
@@ -273,6 +296,7 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
     const dbp_tuning &t = h->tuning;
     s.tma = false;
     s.tc8 = false;
+    s.tcdl = false;
     s.bcast = false;
     // AUTO takes the tensor-core kernel for U = 8 (measured fastest for ADMM
     // and CG on the B=128, C=8, U=8 frame), else the broadcast kernels.
@@ -299,6 +323,31 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
             const long long tiles = (d->W + P - 1) / P;
             int occ = (kind == K_ADMM_UL) ? dbp_tc8_occupancy_admm_ul(s.nwarps * 32, s.smem)
                                           : dbp_tc8_occupancy_cg_ul(s.nwarps * 32, s.smem);
+            if (occ < 1) occ = 1;
+            const long long slots = (long long)h->num_sms * occ;
+            s.grid = tiles < slots ? tiles : slots;
+            s.tiles = (int)tiles;
+            return DBP_OK;
+        }
+    }
+    if (want_mma && t.mapping != DBP_MAP_CLUSTER && tcdl_eligible(d, kind, aligned16)) {
+        tcdl_layout(d, s);
+        const int target = t.warps_per_cta > 0 ? t.warps_per_cta : 8;
+        int P = target / C;
+        if (P < 1) P = 1;
+        auto bytes = [&](int PP) { return (size_t)PP * C * s.warp_bytes + dbp::tcdl_cta_bytes(PP * C, PP); };
+        while (P > 1 && (P * C > 16 || bytes(P) > h->smem_optin)) --P;
+        if (bytes(P) <= h->smem_optin) {
+            s.tcdl = true;
+            s.tma = true;                      // also a persistent bulk-copy kernel
+            s.clu = false;
+            s.P = P;
+            s.CPB = C;
+            s.CL = 1;
+            s.nwarps = P * C;
+            s.smem = bytes(P);
+            const long long tiles = (d->W + P - 1) / P;
+            int occ = dbp_tcdl_occupancy(s.nwarps * 32, s.smem);
             if (occ < 1) occ = 1;
             const long long slots = (long long)h->num_sms * occ;
             s.grid = tiles < slots ? tiles : slots;
@@ -339,8 +388,9 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
                     "aligned buffers and a CTA that fits shared memory (B=%d C=%d U=%d)", d->B, d->C, d->U);
     if (t.kernel == DBP_PATH_MMA)
         return fail(h, DBP_ERR_UNSUPPORTED,
-                    "the tensor-core kernel needs uplink, FP32, U = 8, even S, C <= 16, 16-byte aligned "
-                    "buffers and a CTA that fits shared memory (B=%d C=%d U=%d)", d->B, d->C, d->U);
+                    "the tensor-core kernels need FP32 and either the uplink with U = 8 and even S or the "
+                    "downlink with U = 16 and S a multiple of 8, C <= 16, 16-byte aligned buffers and a CTA "
+                    "that fits shared memory (B=%d C=%d U=%d)", d->B, d->C, d->U);
     if (t.kernel != DBP_PATH_GENERIC && t.mapping != DBP_MAP_CLUSTER && tma_eligible(d, UT, maxw, aligned16)) {
         tma_layout(d, kind, UT, s);
         const int target = t.warps_per_cta > 0 ? t.warps_per_cta : 8;

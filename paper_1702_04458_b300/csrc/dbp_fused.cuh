@@ -81,8 +81,8 @@ struct FusedParams {
     int off_h1, off_y0, off_y1, off_g, off_v, warp_bytes;
     // Resident per-cluster operator of a coherence block (bulk-copy kernel):
     // 0 = compute, 1 = compute and store, 2 = load instead of computing.
-    // Layout [W][C][UT][UT] float2: B_c^{-1} (uplink ADMM), G_c (CG) or
-    // Q_c = I - rho^{-1} B_c^{-1} (downlink).
+    // Layout [W][C][UT][UT] float2: B_c^{-1} (uplink and downlink ADMM) or
+    // G_c (CG).
     float2 *factor;
     int factor_mode;
 };
@@ -383,13 +383,6 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
         gj_invert<UT>(R, Vb, u, lane);                   // row u of B_c^{-1}
     } else if (ALG == ALG_ADMM_DL) {
         gj_invert<UT>(R, Vb, u, lane);                   // row u of B_c^{-1}
-        // Q_c = I - rho^{-1} B_c^{-1}: the map (z_c + lambda_c) -> m_c = H_c x_c
-        const T ir = ParamSel<T>::get(p.inv_rho, p.f_inv_rho);
-#pragma unroll
-        for (int v = 0; v < UT; ++v) {
-            R[v].x = ((v == u) ? (T)1 : (T)0) - ir * R[v].x;
-            R[v].y = -ir * R[v].y;
-        }
     }
     // (CG keeps G_c = H_c^H H_c in R.)
 
@@ -566,11 +559,18 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
                 lam[j] = cz(C2());
                 v[j] = z[j];
             }
+            const T ir = ParamSel<T>::get(p.inv_rho, p.f_inv_rho);
             for (int t = 2; t <= p.T; ++t) {
                 put_vec<UT>(Vb, u, g, v);
                 __syncwarp();
-                matvec<UT>(R, Vb, g, m);          // m_c = H_c x_c = Q_c (z_c + lambda_c)
+                matvec<UT>(R, Vb, g, m);          // B_c^{-1} v_c
                 __syncwarp();
+                // m_c = H_c x_c = v_c - rho^{-1} B_c^{-1} v_c  (v_c = z_c + lambda_c)
+#pragma unroll
+                for (int j = 0; j < K::NN; ++j) {
+                    m[j].x = fma(-ir, m[j].x, v[j].x);
+                    m[j].y = fma(-ir, m[j].y, v[j].y);
+                }
                 C2 wc[K::NN], wsum[K::NN];
 #pragma unroll
                 for (int j = 0; j < K::NN; ++j) wc[j] = csub(m[j], lam[j]);   // w_c
@@ -586,14 +586,11 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
                     v[j] = cadd(z[j], lam[j]);
                 }
             }
-            // (P1) output: x_c = H^dH_c B_c^{-1} v, with B_c^{-1} v = rho (v - Q_c v)
+            // (P1) output: x_c = H^dH_c B_c^{-1} v
             put_vec<UT>(Vb, u, g, v);
             __syncwarp();
             matvec<UT>(R, Vb, g, m);
             __syncwarp();
-            const T rho = ParamSel<T>::get(p.rho, p.f_rho);
-#pragma unroll
-            for (int j = 0; j < K::NN; ++j) m[j] = cscale(csub(v[j], m[j]), rho);
             put_vec<UT>(Vb, u, g, m);
             __syncwarp();
             // x_c[s'][n] = sum_u conj(H_c[s'][u]) t[u][n]; lanes run over s'.

@@ -8,3 +8,5 @@ cudaError_t dbp_launch_admm_dl(int prec, int UT, const dbp::FusedParams &p, cons
 int dbp_tma_occupancy_admm_dl(int prec, int UT, int threads, size_t smem) {
     return dbp::tma_occupancy<dbp::ALG_ADMM_DL>(prec, UT, threads, smem);
 }
+
+int dbp_tcdl_occupancy(int threads, size_t smem) { return dbp::tcdl_occupancy(threads, smem); }

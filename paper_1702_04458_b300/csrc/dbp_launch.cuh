@@ -12,6 +12,7 @@
 #include "dbp_cg.cuh"
 #include "dbp_admm.cuh"
 #include "dbp_tc8.cuh"
+#include "dbp_tcdl.cuh"
 
 // Host-side caches (dbp_api.cu): the dynamic shared-memory limit of a kernel
 // is raised once per device and size, and the resident-CTA count of a
@@ -27,7 +28,8 @@ namespace dbp {
 struct Shape {
     bool clu;
     bool tma;              // persistent bulk-copy kernel
-    bool tc8 = false;      // U = 8 tensor-core kernel
+    bool tc8 = false;      // U = 8 tensor-core uplink kernel
+    bool tcdl = false;     // U = 16 tensor-core downlink kernel
     bool bcast = false;    // consensus step once per symbol, result broadcast
     int P, CPB, CL, nwarps;
     long long grid;
@@ -188,8 +190,22 @@ cudaError_t launch_admm_one(const FusedParams &p, const Shape &s, cudaStream_t s
     return cudaGetLastError();
 }
 
+inline int tcdl_occupancy(int threads, size_t smem) {
+    return dbp_occupancy_cached(reinterpret_cast<const void *>(dbp::dbp_tcdl_kernel<16>), threads, smem);
+}
+
+inline cudaError_t launch_tcdl(const FusedParams &p, const Shape &s, cudaStream_t st) {
+    cudaError_t e = dbp_prepare_kernel(reinterpret_cast<const void *>(dbp::dbp_tcdl_kernel<16>), s.smem);
+    if (e != cudaSuccess) return e;
+    dbp::dbp_tcdl_kernel<16><<<(unsigned)s.grid, s.nwarps * 32, s.smem, st>>>(p);
+    return cudaGetLastError();
+}
+
 template <int ALG>
 cudaError_t launch_alg(int prec, int UT, const FusedParams &p, const Shape &s, cudaStream_t st) {
+    if constexpr (ALG == ALG_ADMM_DL) {
+        if (s.tcdl) return launch_tcdl(p, s, st);
+    }
     if constexpr (ALG == ALG_CG_UL) {
         if (s.bcast) {
             switch (UT) {
@@ -232,3 +248,4 @@ int dbp_tc8_occupancy_admm_ul(int threads, size_t smem);
 int dbp_tc8_occupancy_cg_ul(int threads, size_t smem);
 int dbp_cg_occupancy(int UT, int threads, size_t smem);
 int dbp_bcast_admm_occupancy(int UT, int threads, size_t smem);
+int dbp_tcdl_occupancy(int threads, size_t smem);

@@ -1,0 +1,408 @@
+// dbp_tcdl.cuh -- decentralized ADMM downlink beamforming (Alg. 3) for U = 16
+// users with FP32 inputs, every dense complex product on the tensor cores.
+//
+// Per (subcarrier, cluster) warp, in the U x U form of Alg. 3 with
+// H^d_c = (H_c)^T (reciprocity):
+//   * B_c = H^d_c H^{dH}_c + rho^{-1} I = conj(H_c^H H_c) + rho^{-1} I: the
+//     Gram on the tensor cores, its inverse by the column-split Gauss-Jordan
+//     of dbp_admm.cuh (lane (u, g) holds columns 8g..8g+7 of row u);
+//   * per iteration m_c = H^d_c x_c = v_c - rho^{-1} B_c^{-1} v_c with
+//     v_c = z_c + lambda_c (x_c = H^{dH}_c B_c^{-1} v_c, push-through), the
+//     product B_c^{-1} v_c for 16 symbol slots being a 32 x 32 x 16 real
+//     product (2 m-tiles of 8 users, real parts over imaginary parts, 4
+//     k-steps, 2 n-tiles of 8 symbols), three mma.sync.m16n8k8 TF32 products
+//     per k-step with the operands split into TF32 parts (dbp_mma8.cuh);
+//   * the output x_c = H^{dH}_c B_c^{-1} v_c, an (S x 16) x (16 x 16) product.
+// The consensus w = sum_c (m_c - lambda_c) and (s - w)/C run once per symbol:
+// warp c reduces the units c, c + C, ... of 32 (symbol, user) entries and
+// broadcasts d = (s - w)/C; every cluster then forms z_c = w_c + d and its
+// dual update (Alg. 3, the consensus step of Sec. IV-B).
+//
+// Lane (g, t) = (lane / 4, lane % 4) holds, for m-tile mt and n-tile nt, user
+// 8 mt + g of symbols 8 nt + 2t and 8 nt + 2t + 1 (8 complex state entries).
+//
+// Shared memory per warp: two H_c buffers (S x 16, double-buffered bulk
+// copies), the state v [16][VPD] and B_c^{-1} [16][QP].  After the warps:
+// contrib[nwarps][CE] | d[P][CE] | s[P][CE] | mbarrier[nwarps][2].
+#pragma once
+
+#include "dbp_mma8.cuh"
+#include "dbp_admm.cuh"
+
+namespace dbp {
+
+struct TcDl {
+    static constexpr int U = 16;
+    static constexpr int NS = 16;            // symbol slots per pass
+    static constexpr int VPD = 18;           // state pitch (complex): conflict-free B fragment loads
+    static constexpr int QP = 18;            // operator pitch (complex)
+    static constexpr int CP = 20;            // contrib / broadcast pitch (complex)
+    static constexpr int CE = NS * CP;
+};
+
+__host__ __device__ constexpr size_t tcdl_cta_bytes(int nwarps, int P) {
+    return (size_t)nwarps * TcDl::CE * 8 + 2 * (size_t)P * TcDl::CE * 8 + (size_t)nwarps * 16;
+}
+
+// A fragment values (before splitting) of H_c^H for the k-step of antenna
+// rows s0..s0+3, rows u (real parts) and u (imaginary parts); H_c has 16
+// users per row.
+__device__ __forceinline__ void hh16_frag(const float2 *Hs, int s0, int u, int t, float (&a)[4]) {
+    const float2 h0 = Hs[(s0 + (t >> 1)) * 16 + u];
+    const float2 h1 = Hs[(s0 + 2 + (t >> 1)) * 16 + u];
+    const bool odd = t & 1;
+    a[0] = odd ? h0.y : h0.x;
+    a[1] = odd ? h0.x : -h0.y;
+    a[2] = odd ? h1.y : h1.x;
+    a[3] = odd ? h1.x : -h1.y;
+}
+
+// m = Q v: Q (B_c^{-1}) as A fragments (hi, lo) [m-tile][k-step][4], v [16 symbols][VPD]
+// in shared memory; result in the accumulator layout m[mt][nt][q].
+__device__ __forceinline__ void tcdl_apply(const uint32_t (&qh)[2][4][4], const uint32_t (&ql)[2][4][4],
+                                           const float2 *Vb, int g, int t, float2 (&m)[2][2][2]) {
+    const float *sf = reinterpret_cast<const float *>(Vb) + (g * TcDl::VPD + (t >> 1)) * 2 + (t & 1);
+    float acc[2][2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            uint32_t bh0, bl0, bh1, bl1;
+            split3(sf[(8 * nt * TcDl::VPD + 4 * ks) * 2], bh0, bl0);
+            split3(sf[(8 * nt * TcDl::VPD + 4 * ks + 2) * 2], bh1, bl1);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) mma3(acc[mt][nt], qh[mt][ks], ql[mt][ks], bh0, bh1, bl0, bl1);
+        }
+    }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            m[mt][nt][0] = make_float2(acc[mt][nt][0], acc[mt][nt][2]);
+            m[mt][nt][1] = make_float2(acc[mt][nt][1], acc[mt][nt][3]);
+        }
+}
+
+// (a template only so that every translation unit may include it)
+template <int UT>
+__global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
+    static_assert(UT == TcDl::U, "the downlink tensor-core kernel is for 16 users");
+    using C2 = float2;
+    constexpr int U = TcDl::U, VPD = TcDl::VPD, QP = TcDl::QP, CP = TcDl::CP, CE = TcDl::CE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const int C = p.C, P = p.P, S = p.S, N = p.N, B = p.B, W = p.W;
+    const int pl = warp / C, c = warp - pl * C;
+    const int g = lane >> 2, t = lane & 3;          // MMA layout
+    const int ur = lane & 15, gc = lane >> 4;       // column-split layout: row ur, columns 8 gc + i
+
+    unsigned char *wb = smem_raw + (size_t)warp * p.warp_bytes;
+    C2 *Vb = reinterpret_cast<C2 *>(wb + p.off_v);
+    C2 *Qs = reinterpret_cast<C2 *>(wb + p.off_g);
+    C2 *contrib = reinterpret_cast<C2 *>(smem_raw + (size_t)nwarps * p.warp_bytes);   // [nwarps][CE]
+    C2 *db = contrib + nwarps * CE + pl * CE;                 // d = (s - w) / C of this subcarrier
+    C2 *ss = contrib + nwarps * CE + P * CE + pl * CE;        // s of this subcarrier, this pass
+    uint64_t *bars = reinterpret_cast<uint64_t *>(contrib + nwarps * CE + 2 * P * CE) + 2 * warp;
+    const C2 *grp = contrib + pl * C * CE;
+    C2 *mine = contrib + warp * CE;
+
+    for (int i = lane * 16; i < p.warp_bytes; i += 32 * 16)
+        *reinterpret_cast<float4 *>(wb + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    fence_proxy_async();
+
+    const C2 *Hg = reinterpret_cast<const C2 *>(p.H);
+    const C2 *Sg = reinterpret_cast<const C2 *>(p.vin);
+    auto issue = [&](int w, int b) {
+        const uint32_t hbytes = (uint32_t)(S * U * 8);
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive_expect_tx(&bars[b], hbytes);
+            bulk_g2s(wb + (b ? p.off_h1 : 0), Hg + ((size_t)w * B + (size_t)c * S) * U, hbytes, &bars[b]);
+        }
+    };
+
+    const float kap = p.f_kappa, gam = p.f_gamma, ic = p.f_invC, ir = p.f_inv_rho;
+    float energy = 0.f;
+    uint32_t parity = 0u;
+    int tile = blockIdx.x;
+    if (tile < p.tiles && tile * P + pl < W) issue(tile * P + pl, 0);
+
+    for (int it = 0; tile < p.tiles; ++it, tile += gridDim.x) {
+        const int b = it & 1;
+        const int w = tile * P + pl;
+        const bool valid = (w < W);
+        const int ntile = tile + gridDim.x;
+        if (ntile < p.tiles && ntile * P + pl < W) issue(ntile * P + pl, b ^ 1);
+        if (valid) {
+            mbar_wait_bounded(&bars[b], (parity >> b) & 1u, p.status);
+            parity ^= (1u << b);
+        }
+        const C2 *Hs = reinterpret_cast<const C2 *>(wb + (b ? p.off_h1 : 0));
+
+        // ---- B_c^{-1} into Qs ----
+        C2 *frow = (p.factor != nullptr && valid) ? p.factor + (((size_t)w * C + c) * U + ur) * U + 8 * gc : nullptr;
+        if (p.factor_mode == 2) {
+#pragma unroll
+            for (int i = 0; i < 8; i += 2) {
+                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (frow != nullptr) q = *reinterpret_cast<const float4 *>(&frow[i]);
+                Qs[ur * QP + 8 * gc + i] = make_float2(q.x, q.y);
+                Qs[ur * QP + 8 * gc + i + 1] = make_float2(q.z, q.w);
+            }
+        } else {
+            // Gram G = H_c^H H_c on the tensor cores: m-tile mt = users
+            // 8 mt .. 8 mt + 7 (rows), n-tile nt = users 8 nt .. (columns).
+            float gacc[2][2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) gacc[mt][nt][i] = 0.f;
+            for (int s0 = 0; s0 < S; s0 += 4) {
+                uint32_t ah[2][4], al[2][4];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    float a[4];
+                    hh16_frag(Hs, s0, 8 * mt + g, t, a);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) split3(a[i], ah[mt][i], al[mt][i]);
+                }
+                // the B fragment of H_c for n-tile nt holds the values a[0], a[2]
+                // of m-tile nt
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt)
+                        mma3(gacc[mt][nt], ah[mt], al[mt], ah[nt][0], ah[nt][2], al[nt][0], al[nt][2]);
+            }
+            // B_c = conj(G) + rho^{-1} I, row-major into Qs
+            const float delta = p.f_delta;
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int row = 8 * mt + g, col = 8 * nt + 2 * t + q;
+                        C2 v = make_float2(gacc[mt][nt][q], -gacc[mt][nt][2 + q]);
+                        if (row == col) v.x += delta;
+                        Qs[row * QP + col] = v;
+                    }
+            __syncwarp();
+            C2 A[8];
+#pragma unroll
+            for (int i = 0; i < 8; i += 2) ld2(&Qs[ur * QP + 8 * gc + i], A[i], A[i + 1]);
+            float dmax = 0.f;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (8 * gc + i == ur) dmax = A[i].x;
+#pragma unroll
+            for (int m2 = 16; m2 > 0; m2 >>= 1) dmax = fmaxf(dmax, shfl_x(dmax, m2));
+            const float min_piv = gj_split<16>(A, ur, gc);
+            __syncwarp();
+            if (!(min_piv >= 0x1p-12f * dmax) && valid) {
+                // FP64 retry: B_c and its inverse again in FP64 (row ur per lane)
+                double2 D[16];
+#pragma unroll
+                for (int v = 0; v < 16; ++v) D[v] = make_double2(0.0, 0.0);
+                for (int r = 0; r < S; ++r) {
+                    const C2 hu = Hs[r * 16 + ur];
+                    const double2 hd = make_double2(hu.x, hu.y);
+#pragma unroll
+                    for (int v = 0; v < 16; ++v) {
+                        const C2 hv = Hs[r * 16 + v];
+                        cmacc(D[v], make_double2(hv.x, hv.y), hd);      // conj(H[r][v]) H[r][ur]
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < 16; ++v)
+                    if (v == ur) D[v].x += p.delta;
+                gj_invert<16>(D, reinterpret_cast<double2 *>(Vb), ur, lane);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const double2 dv = gc ? D[8 + i] : D[i];
+                    A[i] = make_float2((float)dv.x, (float)dv.y);
+                }
+                if (lane == 0 && p.retries) atomicAdd(p.retries, 1u);
+                __syncwarp();
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) Qs[ur * QP + 8 * gc + i] = A[i];
+            if (p.factor_mode == 1 && frow != nullptr) {
+#pragma unroll
+                for (int i = 0; i < 8; i += 2)
+                    *reinterpret_cast<float4 *>(&frow[i]) = make_float4(A[i].x, A[i].y, A[i + 1].x, A[i + 1].y);
+            }
+        }
+        __syncwarp();
+
+        // A fragments (hi, lo) of B_c^{-1}: lane (g, t) needs entries
+        // [8 mt + g][4 ks + t/2] and [8 mt + g][4 ks + 2 + t/2] with the
+        // general complex embedding.
+        uint32_t qh[2][4][4], ql[2][4][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                const C2 o0 = Qs[(8 * mt + g) * QP + 4 * ks + (t >> 1)];
+                const C2 o1 = Qs[(8 * mt + g) * QP + 4 * ks + 2 + (t >> 1)];
+                const bool odd = t & 1;
+                split3(odd ? -o0.y : o0.x, qh[mt][ks][0], ql[mt][ks][0]);
+                split3(odd ? o0.x : o0.y, qh[mt][ks][1], ql[mt][ks][1]);
+                split3(odd ? -o1.y : o1.x, qh[mt][ks][2], ql[mt][ks][2]);
+                split3(odd ? o1.x : o1.y, qh[mt][ks][3], ql[mt][ks][3]);
+            }
+
+        for (int n0 = 0; n0 < N; n0 += TcDl::NS) {
+            const int nv = min(TcDl::NS, N - n0);
+            const int nvu = nv * U;
+            // stage s of this pass (zero past N) for every warp of the subcarrier
+            __syncthreads();
+            for (int e = c * 32 + lane; e < TcDl::NS * U; e += C * 32) {
+                const int n = e >> 4, u = e & 15;
+                ss[n * CP + u] = (valid && n < nv) ? Sg[((size_t)w * N + n0 + n) * U + u] : make_float2(0.f, 0.f);
+                db[n * CP + u] = make_float2(0.f, 0.f);   // slots past N keep d = 0
+            }
+            __syncthreads();
+
+            // Init: z_c = kappa s, lambda_c = 0, v_c = z_c
+            C2 lam[2][2][2];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int u = 8 * mt + g, n = 8 * nt + 2 * t + q;
+                        Vb[n * VPD + u] = cscale(ss[n * CP + u], kap);
+                        lam[mt][nt][q] = make_float2(0.f, 0.f);
+                    }
+            __syncwarp();
+
+            for (int iter = 2; iter <= p.T; ++iter) {
+                C2 m[2][2][2];
+                tcdl_apply(qh, ql, Vb, g, t, m);                  // B_c^{-1} v_c
+                // m_c = H_c x_c = v_c - rho^{-1} B_c^{-1} v_c
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const C2 v = Vb[(8 * nt + 2 * t + q) * VPD + 8 * mt + g];
+                            m[mt][nt][q].x = fmaf(-ir, m[mt][nt][q].x, v.x);
+                            m[mt][nt][q].y = fmaf(-ir, m[mt][nt][q].y, v.y);
+                        }
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const int u = 8 * mt + g, n = 8 * nt + 2 * t + q;
+                            mine[n * CP + u] = csub(m[mt][nt][q], lam[mt][nt][q]);   // w_c
+                        }
+                __syncthreads();
+                for (int base = c * 32; base < nvu; base += C * 32) {
+                    const int e = base + lane;                    // < NS U: in the buffers
+                    const int idx = (e >> 4) * CP + (e & 15);
+                    const C2 ws = consensus_sum<CE>(grp, idx, C);
+                    const C2 sv = ss[idx];
+                    if (e < nvu) db[idx] = make_float2((sv.x - ws.x) * ic, (sv.y - ws.y) * ic);
+                }
+                __syncthreads();
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const int u = 8 * mt + g, n = 8 * nt + 2 * t + q;
+                            const C2 wc = csub(m[mt][nt][q], lam[mt][nt][q]);
+                            const C2 d = db[n * CP + u];
+                            C2 z = cadd(wc, d);                   // z_c = w_c + (s - w) / C
+                            C2 &l = lam[mt][nt][q];
+                            l.x = fmaf(-gam, m[mt][nt][q].x - z.x, l.x);
+                            l.y = fmaf(-gam, m[mt][nt][q].y - z.y, l.y);
+                            Vb[n * VPD + u] = cadd(z, l);         // v_c = z_c + lambda_c
+                        }
+                __syncwarp();
+            }
+
+            // Output x_c = H^{dH}_c B_c^{-1} v_c
+            {
+                C2 tt[2][2][2];
+                tcdl_apply(qh, ql, Vb, g, t, tt);
+                __syncwarp();
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) Vb[(8 * nt + 2 * t + q) * VPD + 8 * mt + g] = tt[mt][nt][q];
+                __syncwarp();
+            }
+            C2 *xo = reinterpret_cast<C2 *>(p.out);
+            const float *tf = reinterpret_cast<const float *>(Vb) + (g * VPD + (t >> 1)) * 2 + (t & 1);
+            for (int sa = 0; sa < S; sa += 8) {
+                // m-tile of antennas sa .. sa+7: A = H^{dH}_c, A[s'][u] = conj(H_c[s'][u])
+                float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {
+                    const C2 h0 = Hs[(sa + g) * U + 4 * ks + (t >> 1)];
+                    const C2 h1 = Hs[(sa + g) * U + 4 * ks + 2 + (t >> 1)];
+                    const bool odd = t & 1;
+                    uint32_t ah[4], al[4];
+                    split3(odd ? h0.y : h0.x, ah[0], al[0]);      // Re block: (Re H, Im H)
+                    split3(odd ? h0.x : -h0.y, ah[1], al[1]);     // Im block: (-Im H, Re H)
+                    split3(odd ? h1.y : h1.x, ah[2], al[2]);
+                    split3(odd ? h1.x : -h1.y, ah[3], al[3]);
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt) {
+                        uint32_t bh0, bl0, bh1, bl1;
+                        split3(tf[(8 * nt * VPD + 4 * ks) * 2], bh0, bl0);
+                        split3(tf[(8 * nt * VPD + 4 * ks + 2) * 2], bh1, bl1);
+                        mma3(acc[nt], ah, al, bh0, bh1, bl0, bl1);
+                    }
+                }
+                if (valid) {
+#pragma unroll
+                    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const int n = 8 * nt + 2 * t + q;
+                            if (n < nv) {
+                                const C2 xv = make_float2(acc[nt][q], acc[nt][2 + q]);
+                                xo[((size_t)w * N + n0 + n) * B + (size_t)c * S + sa + g] = xv;
+                                energy += xv.x * xv.x + xv.y * xv.y;
+                            }
+                        }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (p.energy != nullptr) {
+#pragma unroll
+        for (int m2 = 16; m2 > 0; m2 >>= 1) energy += shfl_x(energy, m2);
+        if (lane == 0) atomicAdd(p.energy, (double)energy);
+    }
+}
+
+}  // namespace dbp

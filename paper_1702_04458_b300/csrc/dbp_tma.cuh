@@ -455,14 +455,6 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
                 for (int v = 0; v < UT; ++v) R[v] = make_float2((float)D[v].x, (float)D[v].y);
                 if (lane == 0 && p.retries) atomicAdd(p.retries, 1u);
             }
-            if (ALG == ALG_ADMM_DL) {
-                const float ir = p.f_inv_rho;
-#pragma unroll
-                for (int v = 0; v < UT; ++v) {
-                    R[v].x = ((v == u) ? 1.f : 0.f) - ir * R[v].x;
-                    R[v].y = -ir * R[v].y;
-                }
-            }
         }
         if (p.factor_mode == 1 && frow != nullptr && g == 0) {
 #pragma unroll
@@ -631,11 +623,18 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
                     lam[j] = make_float2(0.f, 0.f);
                     v[j] = z[j];
                 }
+                const float ir = p.f_inv_rho;
                 for (int t = 2; t <= p.T; ++t) {
                     put_vec<UT>(Vb, u, g, v);
                     __syncwarp();
                     matvec<UT>(R, Vb, g, m);
                     __syncwarp();
+                    // m_c = H_c x_c = v_c - rho^{-1} B_c^{-1} v_c
+#pragma unroll
+                    for (int j = 0; j < K::NN; ++j) {
+                        m[j].x = fmaf(-ir, m[j].x, v[j].x);
+                        m[j].y = fmaf(-ir, m[j].y, v[j].y);
+                    }
                     C2 wc[K::NN], ws[K::NN];
 #pragma unroll
                     for (int j = 0; j < K::NN; ++j) wc[j] = csub(m[j], lam[j]);
@@ -651,11 +650,8 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
                 }
                 put_vec<UT>(Vb, u, g, v);
                 __syncwarp();
-                matvec<UT>(R, Vb, g, m);
+                matvec<UT>(R, Vb, g, m);          // B_c^{-1} v_c
                 __syncwarp();
-                const float rho = p.f_rho;
-#pragma unroll
-                for (int j = 0; j < K::NN; ++j) m[j] = cscale(csub(v[j], m[j]), rho);
                 put_vec<UT>(Vb, u, g, m);
                 __syncwarp();
                 C2 *xo = reinterpret_cast<C2 *>(p.out);

@@ -530,6 +530,75 @@ def test_forced_bcast_kernels_reject_other_work(dbp, handle):
 
 
 # ---------------------------------------------------------------------------
+# Downlink tensor-core kernel (U = 16)
+# ---------------------------------------------------------------------------
+
+TCDL_CASES = [
+    # (W, N, B, C, T)             covers
+    (19, 14, 256, 16, 5),         # the B=256 / C=16 / U=16 workload, ragged W
+    (9, 14, 256, 8, 5),           # S=32: four antenna m-tiles in the output product
+    (11, 20, 64, 4, 3),           # two subcarriers per CTA, N > 16 (two symbol passes)
+    (7, 5, 16, 2, 4),             # S=8, four subcarriers per CTA, ragged N
+    (5, 1, 32, 1, 2),             # C=1 (no consensus partner), N=1
+    (6, 14, 256, 16, 1),          # T=1: init and output only
+]
+
+
+@pytest.mark.parametrize("W,N,B,C,T", TCDL_CASES)
+def test_tcdl_kernel_matches_oracle(dbp, handle, W, N, B, C, T):
+    f = synth.downlink_frame(W, N, B, 16, 64, seed=950 + W + N + B + C + T)
+    x, _ = _with_path(dbp, handle, dbp.DBP_PATH_MMA, lambda: run_dl(dbp, handle, f, C, T))
+    ref = oracle.admm_dl(_round(f["H"], "fp32"), _round(f["s"], "fp32"), C=C, rho=1.0, T_max=T)
+    err = _rel_per_vector(x, ref)
+    assert err.max() <= FP32_TOL, err.max()
+
+
+def test_tcdl_kernel_rho_and_normalisation(dbp, handle):
+    f = synth.downlink_frame(21, 14, 128, 16, 64, seed=960)
+    x, _ = _with_path(dbp, handle, dbp.DBP_PATH_MMA, lambda: run_dl(dbp, handle, f, 8, 4, rho=0.6))
+    ref = oracle.admm_dl(_round(f["H"], "fp32"), _round(f["s"], "fp32"), C=8, rho=0.6, T_max=4)
+    assert _rel_per_vector(x, ref).max() <= FP32_TOL
+    xn, beta = _with_path(dbp, handle, dbp.DBP_PATH_MMA, lambda: run_dl(dbp, handle, f, 8, 4, rho=0.6, normalize=True))
+    beta_ref = math.sqrt(ref.size / np.sum(np.abs(ref) ** 2))
+    assert abs(beta - beta_ref) / beta_ref < 1e-5
+    assert _rel_per_vector(xn, beta_ref * ref).max() <= FP32_TOL
+
+
+def test_tcdl_fp64_retry_on_a_near_singular_cluster(dbp, handle):
+    W, N, B, C = 10, 14, 128, 4                   # S = 32 > U = 16
+    f = synth.downlink_frame(W, N, B, 16, 64, seed=961)
+    S = B // C
+    u_, s_, vh = np.linalg.svd(f["H"][4, S:2 * S], full_matrices=False)
+    s_[-1] = 1e-4 * s_[0]
+    f["H"][4, S:2 * S] = (u_ * s_) @ vh
+    dbp.dbp_fp64_retries(handle)
+    x, _ = _with_path(dbp, handle, dbp.DBP_PATH_MMA, lambda: run_dl(dbp, handle, f, C, 3, rho=1e6))
+    assert dbp.dbp_fp64_retries(handle) == 1
+    ref = oracle.admm_dl(_round(f["H"], "fp32"), _round(f["s"], "fp32"), C=C, rho=1e6, T_max=3)
+    good = np.arange(W) != 4
+    assert np.all(np.isfinite(x))
+    assert _rel_per_vector(x[good], ref[good]).max() <= FP32_TOL
+
+
+def test_tcdl_kernel_matches_bulk_copy_kernel_over_many_tiles(dbp, handle):
+    f = synth.downlink_frame(1201, 14, 256, 16, 64, seed=962)
+    a, _ = _with_path(dbp, handle, dbp.DBP_PATH_MMA, lambda: run_dl(dbp, handle, f, 16, 5))
+    b, _ = _with_path(dbp, handle, dbp.DBP_PATH_TMA, lambda: run_dl(dbp, handle, f, 16, 5))
+    assert _rel_per_vector(a, b).max() <= 1e-5
+
+
+def test_auto_path_uses_tcdl_for_the_downlink(dbp, handle):
+    f = synth.downlink_frame(17, 14, 256, 16, 64, seed=963)
+    a, _ = run_dl(dbp, handle, f, 16, 5)
+    b, _ = _with_path(dbp, handle, dbp.DBP_PATH_MMA, lambda: run_dl(dbp, handle, f, 16, 5))
+    assert np.array_equal(a, b)
+    f8 = synth.downlink_frame(5, 3, 64, 8, 16, seed=964)       # U = 8: no downlink tensor-core kernel
+    with pytest.raises(dbp.DbpError) as ei:
+        _with_path(dbp, handle, dbp.DBP_PATH_MMA, lambda: run_dl(dbp, handle, f8, 4, 3))
+    assert ei.value.status == dbp.DBP_ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------------------
 # Host-buffer (end-to-end) entry points and argument errors
 # ---------------------------------------------------------------------------
 
