@@ -109,6 +109,11 @@ typedef struct dbp_frame_desc {
     double N0;                 /* noise variance per complex entry           */
     double Es;                 /* symbol energy E[|s_u|^2] > 0               */
     double box_r;              /* box radius r for DBP_REG_BOX               */
+    double eps;                /* downlink: residual-interference bound
+                                  epsilon >= 0 of (P0); the consensus step
+                                  scales (s - w)/C by max{0, 1 - eps /
+                                  ||s - w||} (Lemma 2).  0 = Alg. 3 as
+                                  printed; must be 0 for the uplink          */
 } dbp_frame_desc;
 
 /* Launch-shape tuning (the autotuner's knobs; results do not depend on them

@@ -58,7 +58,7 @@ class dbp_frame_desc(ctypes.Structure):
                 ("T_max", ctypes.c_int32), ("regularizer", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("rho", ctypes.c_double), ("gamma", ctypes.c_double), ("N0", ctypes.c_double),
-                ("Es", ctypes.c_double), ("box_r", ctypes.c_double)]
+                ("Es", ctypes.c_double), ("box_r", ctypes.c_double), ("eps", ctypes.c_double)]
 
 
 class dbp_tuning(ctypes.Structure):
@@ -155,9 +155,9 @@ def dbp_set_tuning(h, mapping: int = DBP_MAP_AUTO, cluster_size: int = 0, warps_
 
 def frame_desc(B, C, U, W, N, qam_order=0, T_max=3, regularizer=DBP_REG_MMSE,
                precision=DBP_FP32, flags=0, rho=1.0, gamma=1.0, N0=0.0, Es=1.0,
-               box_r=0.0) -> dbp_frame_desc:
+               box_r=0.0, eps=0.0) -> dbp_frame_desc:
     return dbp_frame_desc(B, C, U, W, N, qam_order, T_max, regularizer, precision, flags,
-                          rho, gamma, N0, Es, box_r)
+                          rho, gamma, N0, Es, box_r, eps)
 
 
 _lib.dbp_device_status.restype = _S

@@ -99,6 +99,10 @@ dbp_status validate(dbp_context *h, const dbp_frame_desc *d, Kind kind) {
             return fail(h, DBP_ERR_INVALID_ARG, "ADMM needs a finite rho > 0");
         if (!std::isfinite(d->gamma)) return fail(h, DBP_ERR_INVALID_ARG, "gamma must be finite");
     }
+    if (!(d->eps >= 0.0) || !std::isfinite(d->eps))
+        return fail(h, DBP_ERR_INVALID_ARG, "eps must be finite and >= 0");
+    if (kind != K_ADMM_DL && d->eps != 0.0)
+        return fail(h, DBP_ERR_INVALID_ARG, "eps (the downlink residual bound of Lemma 2) must be 0 for the uplink");
     if (kind == K_ADMM_UL) {
         if (d->regularizer < DBP_REG_ZF || d->regularizer > DBP_REG_BOX)
             return fail(h, DBP_ERR_INVALID_ARG, "unknown regulariser %d", d->regularizer);
@@ -477,6 +481,7 @@ void fill_params(FusedParams &p, const dbp_frame_desc *d, const Shape &s) {
     p.gamma = d->gamma;
     p.invC = 1.0 / d->C;
     p.box_r = d->box_r;
+    p.eps = d->eps;
     if (d->regularizer == DBP_REG_MMSE && d->rho > 0.0)
         p.e2_scale = 1.0 / (d->N0 / (d->rho * d->Es) + d->C);    // Alg. 1 scaling
     else
@@ -552,6 +557,7 @@ void fill_float_params(FusedParams &p) {
     p.f_e2_scale = (float)p.e2_scale;
     p.f_invC = (float)p.invC;
     p.f_box_r = (float)p.box_r;
+    p.f_eps = (float)p.eps;
     p.f_rho_cg = (float)p.rho_cg;
     p.f_kappa = (float)p.kappa;
     p.f_inv_rho = (float)p.inv_rho;

@@ -60,6 +60,7 @@ struct FusedParams {
     double e2_scale;     // (E2): 1/C (ZF) or 1/(N0/(rho Es) + C) (MMSE)
     double invC;         // 1/C
     double box_r;        // (E2-BOX) radius
+    double eps;          // downlink residual bound (Lemma 2); 0 = Alg. 3 as printed
     double rho_cg;       // CG regulariser N0/Es or 0
     double kappa;        // DL init max{U/B, 1/C}
     double inv_rho;      // 1/rho
@@ -67,7 +68,7 @@ struct FusedParams {
     double qam_inv_a;    // 1 / sqrt(3 / (2 (M - 1)))
     // The same scalars rounded to FP32 on the host, so FP32 kernels read
     // them from the parameter bank without a double conversion.
-    float f_delta, f_rho, f_gamma, f_e2_scale, f_invC, f_box_r, f_rho_cg, f_kappa, f_inv_rho, f_qam_inv_a;
+    float f_delta, f_rho, f_gamma, f_e2_scale, f_invC, f_box_r, f_rho_cg, f_kappa, f_inv_rho, f_qam_inv_a, f_eps;
     // Persistent bulk-copy kernel only:
     int *status;         // device word: bit 0 = a bounded wait gave up
     unsigned int *retries;   // device counter of FP64 inverse retries
@@ -575,9 +576,20 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
 #pragma unroll
                 for (int j = 0; j < K::NN; ++j) wc[j] = csub(m[j], lam[j]);   // w_c
                 consensus(wc, wsum);              // w = sum_c w_c
+                if (p.eps > 0.0) {
+                    // (P2) by Lemma 2: s - w scaled by max{0, 1 - eps / ||s - w||}
+                    const T eps = ParamSel<T>::get(p.eps, p.f_eps);
+#pragma unroll
+                    for (int j = 0; j < K::NN; ++j) {
+                        const C2 dl = csub(sv[j], wsum[j]);
+                        const T nrm = sqrt(group_sum<UT>(dl.x * dl.x + dl.y * dl.y));
+                        const T k = (nrm > (T)0) ? fmax((T)0, (T)1 - eps / nrm) : (T)0;
+                        wsum[j] = csub(sv[j], cscale(dl, k));
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < K::NN; ++j) {
-                    // (P2), eps = 0: z_c = w_c + (s - w) / C
+                    // (P2): z_c = w_c + k (s - w) / C (k = 1 for eps = 0)
                     z[j].x = fma(sv[j].x - wsum[j].x, ic, wc[j].x);
                     z[j].y = fma(sv[j].y - wsum[j].y, ic, wc[j].y);
                     // (P3): lambda_c -= gamma (m_c - z_c)

@@ -15,8 +15,9 @@
 //   * the output x_c = H^{dH}_c B_c^{-1} v_c, an (S x 16) x (16 x 16) product.
 // The consensus w = sum_c (m_c - lambda_c) and (s - w)/C run once per symbol:
 // warp c reduces the units c, c + C, ... of 32 (symbol, user) entries and
-// broadcasts d = (s - w)/C; every cluster then forms z_c = w_c + d and its
-// dual update (Alg. 3, the consensus step of Sec. IV-B).
+// broadcasts d = (s - w)/C, scaled by max{0, 1 - eps/||s - w||} for eps > 0
+// (Lemma 2); every cluster then forms z_c = w_c + d and its dual update
+// (Alg. 3, the consensus step of Sec. IV-B).
 //
 // Lane (g, t) = (lane / 4, lane % 4) holds, for m-tile mt and n-tile nt, user
 // 8 mt + g of symbols 8 nt + 2t and 8 nt + 2t + 1 (8 complex state entries).
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
         }
     };
 
-    const float kap = p.f_kappa, gam = p.f_gamma, ic = p.f_invC, ir = p.f_inv_rho;
+    const float kap = p.f_kappa, gam = p.f_gamma, ic = p.f_invC, ir = p.f_inv_rho, eps = p.f_eps;
     float energy = 0.f;
     uint32_t parity = 0u;
     int tile = blockIdx.x;
@@ -324,7 +325,15 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
                     const int idx = (e >> 4) * CP + (e & 15);
                     const C2 ws = consensus_sum<CE>(grp, idx, C);
                     const C2 sv = ss[idx];
-                    if (e < nvu) db[idx] = make_float2((sv.x - ws.x) * ic, (sv.y - ws.y) * ic);
+                    C2 dl = csub(sv, ws);
+                    if (eps > 0.f) {
+                        // Lemma 2: (s - w)/C scaled by max{0, 1 - eps / ||s - w||}
+                        // (the 16 users of a symbol are 16 aligned lanes)
+                        const float nrm = sqrtf(group_sum<16>(dl.x * dl.x + dl.y * dl.y));
+                        const float k = (nrm > 0.f) ? fmaxf(0.f, 1.f - eps / nrm) : 0.f;
+                        dl = cscale(dl, k);
+                    }
+                    if (e < nvu) db[idx] = make_float2(dl.x * ic, dl.y * ic);
                 }
                 __syncthreads();
 #pragma unroll

@@ -639,6 +639,16 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
 #pragma unroll
                     for (int j = 0; j < K::NN; ++j) wc[j] = csub(m[j], lam[j]);
                     consensus(wc, ws);
+                    if (p.f_eps > 0.f) {
+                        // Lemma 2: s - w scaled by max{0, 1 - eps / ||s - w||}
+#pragma unroll
+                        for (int j = 0; j < K::NN; ++j) {
+                            const C2 dl = csub(sv[j], ws[j]);
+                            const float nrm = sqrtf(group_sum<UT>(dl.x * dl.x + dl.y * dl.y));
+                            const float k = (nrm > 0.f) ? fmaxf(0.f, 1.f - p.f_eps / nrm) : 0.f;
+                            ws[j] = csub(sv[j], cscale(dl, k));
+                        }
+                    }
 #pragma unroll
                     for (int j = 0; j < K::NN; ++j) {
                         z[j].x = fmaf(sv[j].x - ws[j].x, ic, wc[j].x);

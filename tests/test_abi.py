@@ -61,8 +61,8 @@ def test_struct_layouts_match_header(pkg):
 #include "dbp.h"
 int main(void) {
   printf("%zu %zu %zu\n", sizeof(dbp_frame_desc), sizeof(dbp_config), sizeof(dbp_tuning));
-  printf("%zu %zu %zu %zu\n", offsetof(dbp_frame_desc, flags), offsetof(dbp_frame_desc, rho),
-         offsetof(dbp_frame_desc, Es), offsetof(dbp_frame_desc, box_r));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(dbp_frame_desc, flags), offsetof(dbp_frame_desc, rho),
+         offsetof(dbp_frame_desc, Es), offsetof(dbp_frame_desc, box_r), offsetof(dbp_frame_desc, eps));
   printf("%zu\n", offsetof(dbp_config, hbm_budget_bytes));
   printf("%zu\n", offsetof(dbp_tuning, kernel));
   printf("%zu %zu %zu %zu\n", sizeof(dbp_request), offsetof(dbp_request, channel_key),
@@ -79,11 +79,11 @@ int main(void) {
     vals = [int(v) for v in vals]
     D = pkg.dbp_frame_desc
     assert vals[:3] == [ctypes.sizeof(D), ctypes.sizeof(pkg.dbp_config), ctypes.sizeof(pkg.dbp_tuning)]
-    assert vals[3:7] == [D.flags.offset, D.rho.offset, D.Es.offset, D.box_r.offset]
-    assert vals[7] == pkg.dbp_config.hbm_budget_bytes.offset
-    assert vals[8] == pkg.dbp_tuning.kernel.offset
+    assert vals[3:8] == [D.flags.offset, D.rho.offset, D.Es.offset, D.box_r.offset, D.eps.offset]
+    assert vals[8] == pkg.dbp_config.hbm_budget_bytes.offset
+    assert vals[9] == pkg.dbp_tuning.kernel.offset
     R = pkg.dbp_request
-    assert vals[9:13] == [ctypes.sizeof(R), R.channel_key.offset, ctypes.sizeof(pkg.dbp_result),
+    assert vals[10:14] == [ctypes.sizeof(R), R.channel_key.offset, ctypes.sizeof(pkg.dbp_result),
                           pkg.dbp_result.finish_us.offset]
 
 

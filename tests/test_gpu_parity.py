@@ -71,14 +71,14 @@ def run_ul(dbp, h, f, C, T, algo, prec="fp32", reg=None, rho=1.0, M=None, box_r=
     return xd.cpu().numpy().astype(np.complex128), ld.cpu().numpy()
 
 
-def run_dl(dbp, h, f, C, T, prec="fp32", rho=1.0, normalize=False):
+def run_dl(dbp, h, f, C, T, prec="fp32", rho=1.0, normalize=False, eps=0.0):
     W, N, B, U = f["W"], f["N"], f["B"], f["U"]
     ct = np.complex64 if prec == "fp32" else np.complex128
     Hd, sd = _dev(f["H"], ct), _dev(f["s"], ct)
     xd = torch.zeros((W, N, B), dtype=torch.complex64 if prec == "fp32" else torch.complex128, device="cuda")
     beta = torch.zeros(1, dtype=torch.float64, device="cuda")
     d = dbp.frame_desc(B, C, U, W, N, T_max=T, precision=dbp.DBP_FP32 if prec == "fp32" else dbp.DBP_FP64,
-                       rho=rho, flags=dbp.DBP_FLAG_NORMALIZE if normalize else 0)
+                       rho=rho, flags=dbp.DBP_FLAG_NORMALIZE if normalize else 0, eps=eps)
     dbp.dbp_downlink_admm(h, d, Hd, sd, xd, beta if normalize else None)
     torch.cuda.synchronize()
     return xd.cpu().numpy().astype(np.complex128), float(beta.cpu()[0])
@@ -228,6 +228,47 @@ def test_downlink_admm_fp32_matches_oracle(dbp, handle, path, W, N, B, C, U, M, 
     ref = oracle.admm_dl(_round(f["H"], "fp32"), _round(f["s"], "fp32"), C=C, rho=1.0, T_max=T)
     err = _rel_per_vector(x, ref)
     assert err.max() <= FP32_TOL, err.max()
+
+
+DL_EPS_CASES = [
+    # (W, N, B, C, U, T, eps)
+    (19, 14, 256, 16, 16, 5, 0.3),     # the B=256 / C=16 / U=16 workload
+    (13, 14, 128, 8, 8, 4, 0.2),
+    (7, 5, 80, 2, 5, 3, 0.1),          # U=5 padded to 8
+    (9, 3, 64, 4, 16, 6, 3.0),         # eps large enough that k = 0 for some symbols
+]
+
+
+@pytest.mark.parametrize("W,N,B,C,U,T,eps", DL_EPS_CASES)
+def test_downlink_eps_projection_matches_oracle(dbp, handle, path, W, N, B, C, U, T, eps):
+    """Lemma 2 with eps > 0: (s - w)/C scaled by max{0, 1 - eps/||s - w||}."""
+    f = synth.downlink_frame(W, N, B, U, 64, seed=970 + W + B + C + U)
+    x, _ = run_dl(dbp, handle, f, C, T, eps=eps)
+    ref = oracle.admm_dl(_round(f["H"], "fp32"), _round(f["s"], "fp32"), C=C, rho=1.0, T_max=T, eps=eps)
+    assert _rel_per_vector(x, ref).max() <= FP32_TOL
+    ref0 = oracle.admm_dl(_round(f["H"], "fp32"), _round(f["s"], "fp32"), C=C, rho=1.0, T_max=T)
+    assert _rel_per_vector(ref, ref0).max() > 1e-3        # the projection is active
+
+
+def test_downlink_eps_fp64(dbp, handle):
+    f = synth.downlink_frame(11, 4, 64, 8, 16, seed=975)
+    x, _ = run_dl(dbp, handle, f, 4, 5, prec="fp64", eps=0.5)
+    ref = oracle.admm_dl(f["H"], f["s"], C=4, rho=1.0, T_max=5, eps=0.5)
+    assert _rel_per_vector(x, ref).max() <= FP64_TOL
+
+
+def test_eps_is_validated(dbp, handle):
+    buf = torch.zeros(4096, dtype=torch.complex64, device="cuda")
+    for bad in (-0.1, float("nan"), float("inf")):
+        d = dbp.frame_desc(32, 4, 4, 3, 2, T_max=2, eps=bad)
+        with pytest.raises(dbp.DbpError) as ei:
+            dbp.dbp_downlink_admm(handle, d, buf, buf, buf)
+        assert ei.value.status == dbp.DBP_ERR_INVALID_ARG
+    d = dbp.frame_desc(32, 4, 4, 3, 2, qam_order=4, T_max=2, N0=0.1, eps=0.5)
+    for fn in (dbp.dbp_uplink_admm, dbp.dbp_uplink_cg):
+        with pytest.raises(dbp.DbpError) as ei:
+            fn(handle, d, buf, buf, buf, None)
+        assert ei.value.status == dbp.DBP_ERR_INVALID_ARG
 
 
 def test_downlink_fp64(dbp, handle):
