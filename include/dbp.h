@@ -249,7 +249,7 @@ dbp_status dbp_downlink_admm_host(dbp_handle_t h, const dbp_frame_desc *d,
  * concurrently on separate streams (copies in, fused kernel, copies out).
  * Frames that carry the same non-zero channel_key and coherence_epoch share
  * one resident device copy of H and, where the persistent bulk-copy kernel
- * runs, the per-cluster operator (B_c^{-1}, G_c or Q_c) computed by the
+ * runs, the per-cluster operator (B_c^{-1} or G_c) computed by the
  * first of them: later frames of the coherence block skip the copy of H and
  * the Gram and inverse (the channel is constant over a coherence block,
  * Sec. II and Sec. VI-A).  Resident channels are evicted least recently
@@ -315,6 +315,44 @@ dbp_status dbp_poll(dbp_handle_t h, uint64_t ticket, dbp_result *res);
 /* As dbp_poll, blocking up to timeout_s seconds; DBP_ERR_TIMEOUT if the
  * frame has not finished by then (the ticket stays valid). */
 dbp_status dbp_wait(dbp_handle_t h, uint64_t ticket, double timeout_s, dbp_result *res);
+
+/* ------------------------------------------------------------------------
+ * Graphs: a batch of frames of any kinds and shapes (device buffers)
+ * captured once into one CUDA graph and then run by a single launch.  The
+ * frames are spread over `branches` independent branches of the graph, so
+ * frames of different shapes run concurrently on the device, each with the
+ * kernel its shape selects.  Descriptors and pointers are fixed when the
+ * graph is made; every launch recomputes all frames from whatever their
+ * input buffers hold at that point of `stream`.  Results equal those of
+ * the same frames issued one by one.
+ * ------------------------------------------------------------------------ */
+typedef struct dbp_graph *dbp_graph_t;
+
+typedef struct dbp_graph_item {
+    int32_t kind;              /* dbp_kind                                   */
+    int32_t reserved;
+    dbp_frame_desc desc;
+    const void *H;             /* device [W][B][U]                           */
+    const void *in;            /* device y [W][N][B] (uplink), s [W][N][U]   */
+    void *out;                 /* device x_hat [W][N][U] or x [W][N][B]      */
+    uint8_t *labels;           /* device [W][N][U] or NULL (uplink)          */
+    double *beta_out;          /* device, downlink normalisation, or NULL    */
+} dbp_graph_item;
+
+/* Capture items[0..n-1] into a graph (branches: 0 = 4, at most 16).
+ * Validates every item first (DBP_ERR_INVALID_ARG / UNSUPPORTED name the
+ * first bad item in dbp_last_error); DBP_ERR_NOMEM if its scratch cannot be
+ * allocated; DBP_ERR_CUDA if capture or instantiation fails.  The graph
+ * holds the handle: destroy graphs before the handle. */
+dbp_status dbp_graph_create(dbp_handle_t h, const dbp_graph_item *items, int32_t n, int32_t branches,
+                            dbp_graph_t *out);
+
+/* Enqueue one run of every frame of the graph on `stream` (NULL: the
+ * default stream).  Stream-ordered like the single-frame calls. */
+dbp_status dbp_graph_launch(dbp_graph_t g, void *stream);
+
+/* Release the graph (waits for its launches to finish). */
+dbp_status dbp_graph_destroy(dbp_graph_t g);
 
 /* Largest subcarrier count W accepted by dbp_downlink_admm_static. */
 #define DBP_STATIC_MAX_SUBCARRIERS 16384

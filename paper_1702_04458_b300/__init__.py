@@ -61,6 +61,12 @@ class dbp_frame_desc(ctypes.Structure):
                 ("Es", ctypes.c_double), ("box_r", ctypes.c_double), ("eps", ctypes.c_double)]
 
 
+class dbp_graph_item(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("desc", dbp_frame_desc),
+                ("H", ctypes.c_void_p), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("labels", ctypes.c_void_p), ("beta_out", ctypes.c_void_p)]
+
+
 class dbp_tuning(ctypes.Structure):
     _fields_ = [("mapping", ctypes.c_int32), ("cluster_size", ctypes.c_int32),
                 ("warps_per_cta", ctypes.c_int32), ("kernel", ctypes.c_int32)]
@@ -299,4 +305,54 @@ def dbp_wait(h, ticket: int, timeout_s: float = 60.0):
     return r
 
 
-__all__ = [n for n in dir() if n.startswith(("dbp_", "DBP_")) or n in ("frame_desc", "request", "DbpError", "LIB_PATH")]
+_lib.dbp_graph_create.restype = _S
+_lib.dbp_graph_create.argtypes = [_H, ctypes.POINTER(dbp_graph_item), ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.POINTER(ctypes.c_void_p)]
+_lib.dbp_graph_launch.restype = _S
+_lib.dbp_graph_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+_lib.dbp_graph_destroy.restype = _S
+_lib.dbp_graph_destroy.argtypes = [ctypes.c_void_p]
+
+
+def graph_item(kind, desc, H, inp, out, labels=None, beta_out=None) -> dbp_graph_item:
+    return dbp_graph_item(kind, 0, desc, _ptr(H), _ptr(inp), _ptr(out), _ptr(labels), _ptr(beta_out))
+
+
+class DbpGraph:
+    """A captured batch of frames (dbp_graph_create); launch() runs them all."""
+
+    def __init__(self, h, items, branches: int = 0):
+        arr = (dbp_graph_item * len(items))(*items)
+        g = ctypes.c_void_p(None)
+        _check(h, _lib.dbp_graph_create(h, arr, len(items), branches, ctypes.byref(g)))
+        self._h, self._g = h, g
+
+    def launch(self, stream=None) -> None:
+        _check(self._h, _lib.dbp_graph_launch(self._g, _stream(stream)))
+
+    def close(self) -> None:
+        if self._g:
+            _check(self._h, _lib.dbp_graph_destroy(self._g))
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dbp_graph_create(h, items, branches: int = 0) -> DbpGraph:
+    return DbpGraph(h, items, branches)
+
+
+def dbp_graph_launch(g: DbpGraph, stream=None) -> None:
+    g.launch(stream)
+
+
+def dbp_graph_destroy(g: DbpGraph) -> None:
+    g.close()
+
+
+__all__ = [n for n in dir() if n.startswith(("dbp_", "DBP_")) or n in ("frame_desc", "request", "graph_item",
+                                                                      "DbpGraph", "DbpError", "LIB_PATH")]

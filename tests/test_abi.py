@@ -67,6 +67,7 @@ int main(void) {
   printf("%zu\n", offsetof(dbp_tuning, kernel));
   printf("%zu %zu %zu %zu\n", sizeof(dbp_request), offsetof(dbp_request, channel_key),
          sizeof(dbp_result), offsetof(dbp_result, finish_us));
+  printf("%zu %zu %zu\n", sizeof(dbp_graph_item), offsetof(dbp_graph_item, H), offsetof(dbp_graph_item, beta_out));
   return 0;
 }
 '''
@@ -85,6 +86,8 @@ int main(void) {
     R = pkg.dbp_request
     assert vals[10:14] == [ctypes.sizeof(R), R.channel_key.offset, ctypes.sizeof(pkg.dbp_result),
                           pkg.dbp_result.finish_us.offset]
+    G = pkg.dbp_graph_item
+    assert vals[14:17] == [ctypes.sizeof(G), G.H.offset, G.beta_out.offset]
 
 
 def test_enum_values_match_the_header(pkg):
