@@ -583,6 +583,71 @@ def bench_serving(dbp, h, args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def bench_graph(dbp, h, stream, device, args):
+    """The served-stream shapes as one batch of device-resident frames (uplink
+    ADMM, uplink CG and downlink ADMM in turn), captured into one CUDA graph
+    with four branches (dbp_graph_create): one graph launch per batch against
+    the same frames issued one by one on one stream."""
+    import torch
+    specs = serve_channels(np.random.default_rng(123))   # the served stream's shapes
+    kinds = [dbp.DBP_KIND_UPLINK_ADMM, dbp.DBP_KIND_UPLINK_CG, dbp.DBP_KIND_DOWNLINK_ADMM]
+    frames, items, bits = [], [], 0.0
+    for i, sp in enumerate(specs):
+        kind = kinds[i % 3]
+        W, N, B, U, C, M = sp["W"], sp["N"], sp["B"], sp["U"], sp["C"], sp["M"]
+        f = synth.uplink_frame(W, N, B, U, M, 15.0, seed=sp["seed"])
+        Hd = torch.from_numpy(f["H"].astype(np.complex64)).to(device)
+        T = 3 + (i % 6)
+        if kind == dbp.DBP_KIND_DOWNLINK_ADMM:
+            inp = torch.from_numpy(f["s"].astype(np.complex64)).to(device)
+            out = torch.empty((W, N, B), dtype=torch.complex64, device=device)
+            lab = None
+            d = dbp.frame_desc(B, C, U, W, N, T_max=T)
+        else:
+            inp = torch.from_numpy(f["y"].astype(np.complex64)).to(device)
+            out = torch.empty((W, N, U), dtype=torch.complex64, device=device)
+            lab = torch.empty((W, N, U), dtype=torch.uint8, device=device)
+            d = dbp.frame_desc(B, C, U, W, N, qam_order=M, T_max=T, N0=f["N0"])
+        frames.append((kind, d, Hd, inp, out, lab))
+        items.append(dbp.graph_item(kind, d, Hd, inp, out, lab))
+        bits += U * (M.bit_length() - 1) * W * N
+    sp_ = stream.cuda_stream
+
+    def one_by_one():
+        for kind, d, Hd, inp, out, lab in frames:
+            if kind == dbp.DBP_KIND_DOWNLINK_ADMM:
+                dbp.dbp_downlink_admm(h, d, Hd, inp, out, None, sp_)
+            elif kind == dbp.DBP_KIND_UPLINK_ADMM:
+                dbp.dbp_uplink_admm(h, d, Hd, inp, out, lab, sp_)
+            else:
+                dbp.dbp_uplink_cg(h, d, Hd, inp, out, lab, sp_)
+
+    g = dbp.dbp_graph_create(h, items, 4)
+    K = 20
+    res = {}
+    for name, fn in (("sequential", one_by_one), ("graph", lambda: g.launch(sp_))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        res[name] = e0.elapsed_time(e1) / K
+    g.close()
+    del frames, items
+    torch.cuda.empty_cache()
+    return {"frames": len(specs), "branches": 4,
+            "shapes": [dict(sp, kind=["uplink_admm", "uplink_cg", "downlink_admm"][i % 3], T=3 + (i % 6))
+                       for i, sp in enumerate(specs)],
+            "bits_per_batch": bits,
+            "graph_ms_per_batch": res["graph"], "sequential_ms_per_batch": res["sequential"],
+            "graph_gbit_s": bits / (res["graph"] / 1e3) / 1e9,
+            "speedup_vs_sequential": res["sequential"] / res["graph"]}
+
+
 def main(argv=None) -> int:
     args = parse_args(argv)
     if args.impl == "reference":
@@ -715,6 +780,9 @@ def main(argv=None) -> int:
     serving = None
     if not args.no_serving:
         serving = bench_serving(dbp, h, args)
+    graph = None
+    if not args.no_serving:
+        graph = bench_graph(dbp, h, stream, device, args)
 
     # ---- end to end: host inputs in, host results out ------------------------
     # Each step copies the frame's channel and receive vectors (one pinned
@@ -817,6 +885,7 @@ def main(argv=None) -> int:
             "roofline_other": rf_admm if dominant is rf_cg else rf_cg,
             "downlink": downlink,
             "mixed_vs_fp32": mixed,
+            "graph_batch": graph,
             "serving": serving,
             "cpu_baseline": cpu,
             "e2e": e2e,
