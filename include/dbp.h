@@ -317,6 +317,34 @@ dbp_status dbp_poll(dbp_handle_t h, uint64_t ticket, dbp_result *res);
 dbp_status dbp_wait(dbp_handle_t h, uint64_t ticket, double timeout_s, dbp_result *res);
 
 /* ------------------------------------------------------------------------
+ * Autotuner.  Launch choices (kernel path, CTA size, thread-block cluster
+ * size) are timed on a representative frame and the fastest is remembered
+ * per frame shape (kind, B, C, U, N, precision) on the handle; calls whose
+ * tuning is fully automatic (dbp_set_tuning defaults) then use it for every
+ * frame of that shape, whatever W.  Results depend on the choice only
+ * through floating-point rounding.
+ * ------------------------------------------------------------------------ */
+
+/* Time every launch choice that accepts the frame (device buffers; `out`
+ * and `labels` are overwritten) with `reps` runs each (0 = 10) on `stream`,
+ * remember the fastest for this shape and return it in *best (may be
+ * NULL).  Not to be called while other calls on the handle are in flight.
+ * DBP_ERR_INVALID_ARG for a bad descriptor. */
+dbp_status dbp_autotune(dbp_handle_t h, int32_t kind, const dbp_frame_desc *d, const void *H,
+                        const void *in, void *out, uint8_t *labels, void *stream, int32_t reps,
+                        dbp_tuning *best);
+
+/* Forget every tuned shape. */
+dbp_status dbp_autotune_clear(dbp_handle_t h);
+
+/* Write / read the tuned shapes as text, one shape per line
+ * ("kind B C U N precision mapping cluster_size warps_per_cta kernel").
+ * Loading adds to (and overrides) the handle's table; DBP_ERR_INVALID_ARG
+ * for an unreadable file or a malformed line (nothing is loaded then). */
+dbp_status dbp_autotune_save(dbp_handle_t h, const char *path);
+dbp_status dbp_autotune_load(dbp_handle_t h, const char *path);
+
+/* ------------------------------------------------------------------------
  * Graphs: a batch of frames of any kinds and shapes (device buffers)
  * captured once into one CUDA graph and then run by a single launch.  The
  * frames are spread over `branches` independent branches of the graph, so

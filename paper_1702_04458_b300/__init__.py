@@ -314,6 +314,39 @@ _lib.dbp_graph_destroy.restype = _S
 _lib.dbp_graph_destroy.argtypes = [ctypes.c_void_p]
 
 
+_lib.dbp_autotune.restype = _S
+_lib.dbp_autotune.argtypes = [_H, ctypes.c_int32, ctypes.POINTER(dbp_frame_desc), ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                              ctypes.POINTER(dbp_tuning)]
+_lib.dbp_autotune_clear.restype = _S
+_lib.dbp_autotune_clear.argtypes = [_H]
+_lib.dbp_autotune_save.restype = _S
+_lib.dbp_autotune_save.argtypes = [_H, ctypes.c_char_p]
+_lib.dbp_autotune_load.restype = _S
+_lib.dbp_autotune_load.argtypes = [_H, ctypes.c_char_p]
+
+
+def dbp_autotune(h, kind, d, H, inp, out, labels=None, stream=None, reps: int = 0) -> dbp_tuning:
+    """Time the launch choices for this frame shape; the fastest is used by
+    later fully automatic calls and returned."""
+    t = dbp_tuning()
+    _check(h, _lib.dbp_autotune(h, kind, ctypes.byref(d), _ptr(H), _ptr(inp), _ptr(out), _ptr(labels),
+                                _stream(stream), reps, ctypes.byref(t)))
+    return t
+
+
+def dbp_autotune_clear(h) -> None:
+    _check(h, _lib.dbp_autotune_clear(h))
+
+
+def dbp_autotune_save(h, path: str) -> None:
+    _check(h, _lib.dbp_autotune_save(h, path.encode()))
+
+
+def dbp_autotune_load(h, path: str) -> None:
+    _check(h, _lib.dbp_autotune_load(h, path.encode()))
+
+
 def graph_item(kind, desc, H, inp, out, labels=None, beta_out=None) -> dbp_graph_item:
     return dbp_graph_item(kind, 0, desc, _ptr(H), _ptr(inp), _ptr(out), _ptr(labels), _ptr(beta_out))
 

@@ -293,11 +293,11 @@ void bcast_layout(const dbp_frame_desc *d, Kind kind, int UT, Shape &s) {
     }
 }
 
-dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool aligned16, Shape &s) {
+dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool aligned16, Shape &s,
+                        const dbp_tuning &t) {
     const int UT = next_pow2_ut(d->U);
     const int maxw = max_warps_for(d->precision, UT);
     const int C = d->C;
-    const dbp_tuning &t = h->tuning;
     s.tma = false;
     s.tc8 = false;
     s.tcdl = false;
@@ -579,7 +579,16 @@ dbp_status run_ex(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void
         return fail(h, DBP_ERR_INVALID_ARG, "data pointers must be aligned to the element size");
     Shape s;
     const bool a16 = aligned(H, 16) && aligned(vin, 16) && aligned(out, 16);
-    v = choose_shape(h, d, kind, a16, s);
+    // the handle's tuning; when fully automatic, an autotuned choice for
+    // this frame shape (dbp_autotune) if there is one
+    dbp_tuning tune = h->tuning;
+    if (tune.kernel == DBP_PATH_AUTO && tune.mapping == DBP_MAP_AUTO && tune.warps_per_cta == 0 &&
+        tune.cluster_size == 0) {
+        std::lock_guard<std::mutex> lk(h->tune_mu);
+        auto it = h->tuned.find(dbp_tune_key(d, kind));
+        if (it != h->tuned.end()) tune = it->second;
+    }
+    v = choose_shape(h, d, kind, a16, s, tune);
     if (v != DBP_OK) return v;
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");

@@ -4,7 +4,10 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 
 #include "dbp.h"
 
@@ -22,7 +25,14 @@ struct dbp_context {
     void *dev[4] = {nullptr, nullptr, nullptr, nullptr};   // host-variant buffers
     size_t dev_cap[4] = {0, 0, 0, 0};
     dbp_server *server = nullptr;        // request loop (dbp_server_start)
+    // autotuned launch choices per frame shape (kind, B, C, U, N, precision)
+    std::mutex tune_mu;
+    std::map<std::tuple<int, int, int, int, int, int>, dbp_tuning> tuned;
 };
+
+inline std::tuple<int, int, int, int, int, int> dbp_tune_key(const dbp_frame_desc *d, int kind) {
+    return std::make_tuple(kind, d->B, d->C, d->U, d->N, d->precision);
+}
 
 
 enum DbpKind { DBP_K_ADMM_UL = 0, DBP_K_CG_UL = 1, DBP_K_ADMM_DL = 2 };
