@@ -67,6 +67,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-frames", type=int, default=240)
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--kernel", choices=["auto", "generic", "tma", "mma", "bcast"], default="auto",
                     help="uplink/downlink kernel path (dbp_tuning.kernel); auto picks per shape")
     a = ap.parse_args(argv)
@@ -711,6 +712,20 @@ def main(argv=None) -> int:
         if ev is not None:
             ev[2].record(stream)
 
+    # autotune the launch choice of both detectors on this frame shape
+    # (outside the timed region; --kernel other than auto skips it)
+    tuned = {}
+    if args.kernel == "auto" and not args.no_autotune:
+        d0 = dev[0]
+        da0, dc0 = D[0]
+        names = {dbp.DBP_PATH_MMA: "mma", dbp.DBP_PATH_BCAST: "bcast", dbp.DBP_PATH_TMA: "tma",
+                 dbp.DBP_PATH_GENERIC: "generic"}
+        for key, kind, dd in (("admm_ul", dbp.DBP_KIND_UPLINK_ADMM, da0), ("cg_ul", dbp.DBP_KIND_UPLINK_CG, dc0)):
+            t = dbp.dbp_autotune(h, kind, dd, d0["H"], d0["y"], xa, la, sp, 5)
+            tuned[key] = {"kernel": names.get(t.kernel, t.kernel), "mapping": t.mapping,
+                          "cluster_size": t.cluster_size, "warps_per_cta": t.warps_per_cta}
+        torch.cuda.synchronize(device)
+
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize(device)
@@ -753,6 +768,11 @@ def main(argv=None) -> int:
                  "s": torch.from_numpy(f["s"].astype(np.complex64)).to(device)} for f in dfr]
         xd = torch.empty((DL.W, DL.N, DL.B), dtype=torch.complex64, device=device)
         ddesc = dbp.frame_desc(DL.B, DL.C, DL.U, DL.W, DL.N, T_max=DL.T, rho=1.0)
+        dl_tuned = None
+        if args.kernel == "auto" and not args.no_autotune:
+            t = dbp.dbp_autotune(h, dbp.DBP_KIND_DOWNLINK_ADMM, ddesc, ddev[0]["H"], ddev[0]["s"], xd, None, sp, 3)
+            dl_tuned = {"kernel": t.kernel, "mapping": t.mapping, "cluster_size": t.cluster_size,
+                        "warps_per_cta": t.warps_per_cta}
         for k in range(args.warmup):
             dbp.dbp_downlink_admm(h, ddesc, ddev[k % ROTATE]["H"], ddev[k % ROTATE]["s"], xd, None, sp)
         torch.cuda.synchronize(device)
@@ -766,7 +786,7 @@ def main(argv=None) -> int:
         dl_ms = statistics.fmean(e[0].elapsed_time(e[1]) for e in devs)
         downlink = {"workload": workload_name(DL, "downlink ADMM T=5"),
                     "value": detected_bits(DL) / (dl_ms / 1e3) / 1e9, "unit": "Gbit/s (precoded)",
-                    "ms_per_frame": dl_ms, "launches": KD,
+                    "ms_per_frame": dl_ms, "launches": KD, "autotuned": dl_tuned,
                     "roofline": roofline("admm_dl", "admm_dl", DL, dl_ms, hbm_peak, hbm_src, alu_peak)}
         del ddev, xd
         torch.cuda.empty_cache()
@@ -876,6 +896,7 @@ def main(argv=None) -> int:
                 "l2": "inputs larger than L2: 8 rotating frames, 226 MB resident",
                 "parallelism": f"subcarrier-parallel, {world} independent rank(s)",
                 "kernel_path": args.kernel,
+                "autotuned": tuned or None,
             },
             "per_detector": {
                 "admm_ul": {"ms": admm_avg, "gbit_s": detected_bits(UL) / (admm_avg / 1e3) / 1e9},
