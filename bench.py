@@ -68,6 +68,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-frames", type=int, default=240)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tradeoff", action="store_true",
+                    help="instead of the benchmark: minimum SNR for a target uncoded BER against the "
+                         "iteration count (and its Table I complexity) for ADMM and CG")
     ap.add_argument("--kernel", choices=["auto", "generic", "tma", "mma", "bcast"], default="auto",
                     help="uplink/downlink kernel path (dbp_tuning.kernel); auto picks per shape")
     a = ap.parse_args(argv)
@@ -649,6 +652,51 @@ def bench_graph(dbp, h, stream, device, args):
             "speedup_vs_sequential": res["sequential"] / res["graph"]}
 
 
+def run_tradeoff(dbp, h, device, target=0.01):
+    """Uncoded analogue of the paper's performance / complexity trade-off
+    (Sec. VI-B): on the B=128 / C=8 / U=8 / 16-QAM / 1200 x 14 frame, the
+    smallest SNR at which each detector reaches the target uncoded BER,
+    against its iteration count and its real multiplications per symbol
+    (Table I accounting, preprocessing spread over the 14 symbols).  SNR is
+    swept in 1 dB steps and the crossing interpolated in log BER.  Converged
+    ADMM (T = 50, the LMMSE solution) is the reference."""
+    import torch
+    snrs = [float(x) for x in range(0, 21)]
+    runs = [("admm", T) for T in range(1, 6)] + [("cg", T) for T in range(1, 9)] + [("admm", 50)]
+    ber = {r: [] for r in runs}
+    W, N, B, C, U, M = UL.W, UL.N, UL.B, UL.C, UL.U, UL.M
+    x = torch.empty((W, N, U), dtype=torch.complex64, device=device)
+    lab = torch.empty((W, N, U), dtype=torch.uint8, device=device)
+    nbits = W * N * U * (M.bit_length() - 1)
+    for i, snr in enumerate(snrs):
+        f = synth.uplink_frame(W, N, B, U, M, snr, seed=synth.frame_seed(2, 100 + i))
+        H = torch.from_numpy(f["H"].astype(np.complex64)).to(device)
+        y = torch.from_numpy(f["y"].astype(np.complex64)).to(device)
+        for algo, T in runs:
+            d = dbp.frame_desc(B, C, U, W, N, qam_order=M, T_max=T, N0=f["N0"])
+            (dbp.dbp_uplink_admm if algo == "admm" else dbp.dbp_uplink_cg)(h, d, H, y, x, lab)
+            errs = int(np.unpackbits(np.bitwise_xor(lab.cpu().numpy(), f["labels"]).reshape(-1, 1), axis=1).sum())
+            ber[(algo, T)].append(errs / nbits)
+
+    def crossing(bs):
+        """First SNR with BER <= target, interpolated in log BER; None if never."""
+        k = next((i for i, b in enumerate(bs) if b <= target), None)
+        if k is None or k == 0:
+            return None if k is None else snrs[0]
+        lo, hi = math.log(bs[k - 1]), math.log(max(bs[k], 1e-12))
+        return snrs[k - 1] + (math.log(target) - lo) / (hi - lo) * (snrs[k] - snrs[k - 1])
+
+    out = {"workload": workload_name(UL, "uplink detection trade-off"), "target_ber": target,
+           "snr_db": snrs, "bits_per_point": nbits, "detectors": []}
+    for algo, T in runs:
+        wl = Workload(B, C, U, W, N, M, T)
+        alg = "admm_ul" if algo == "admm" else "cg_ul"
+        out["detectors"].append({"algorithm": algo, "T": T, "min_snr_db": crossing(ber[(algo, T)]),
+                                 "mults_per_symbol": algorithmic_mults(alg, wl) / N,
+                                 "ber": ber[(algo, T)]})
+    return out
+
+
 def main(argv=None) -> int:
     args = parse_args(argv)
     if args.impl == "reference":
@@ -667,6 +715,11 @@ def main(argv=None) -> int:
         dist.init_process_group("nccl", device_id=device)
 
     h = dbp.dbp_create(local)
+    if args.tradeoff:
+        if rank == 0:
+            print(json.dumps({"tradeoff": run_tradeoff(dbp, h, device)}))
+        dbp.dbp_destroy(h)
+        return 0
     if args.kernel != "auto":
         dbp.dbp_set_tuning(h, kernel={"generic": dbp.DBP_PATH_GENERIC, "tma": dbp.DBP_PATH_TMA,
                                       "mma": dbp.DBP_PATH_MMA, "bcast": dbp.DBP_PATH_BCAST}[args.kernel])

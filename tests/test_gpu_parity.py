@@ -122,6 +122,7 @@ UL_CASES = [
     (11, 14, 256, 8, 32, 64, 3),       # U=32: two symbol chunks, S=32 staged twice
     (9, 14, 256, 16, 16, 64, 5),       # C=16, U=16
     (13, 5, 24, 6, 8, 16, 4),          # S=4 < U=8 (Woodbury regime), ragged N
+    (9, 14, 64, 8, 16, 16, 4),         # S=8 < U=16 (the paper's S < U configuration)
     (7, 15, 80, 2, 5, 16, 3),          # S=40 > stage rows, U=5 padded to 8
     (5, 1, 12, 1, 3, 4, 2),            # C=1 (centralized ADMM), N=1
     (6, 17, 64, 4, 4, 4, 6),           # U=4, two symbol chunks
@@ -216,6 +217,7 @@ DL_CASES = [
     (13, 14, 128, 8, 8, 16, 3),
     (7, 5, 256, 8, 32, 64, 3),         # U=32
     (11, 3, 24, 6, 8, 16, 4),          # S=4 < U
+    (9, 14, 64, 8, 16, 16, 4),         # S=8 < U=16 (tensor-core kernel under AUTO)
     (5, 9, 80, 2, 5, 16, 2),           # S=40, U=5
     (4, 1, 16, 1, 4, 4, 1),            # C=1, T=1 (no consensus)
 ]
