@@ -10,8 +10,8 @@ follows Alg. 1 (decentralized ADMM detection), Alg. 2 (decentralized CG
 detection) and Alg. 3 (decentralized ADMM beamforming) step by step, plus
 the centralized MMSE/ZF equaliser (Sec. III-A) and ZF beamformer (Sec. IV-A).
 This module adds the detection stage (hard slicing to the QAM alphabet, Sec.
-III-A), bit-error counting and an exhaustive maximum-likelihood search for tiny
-problems.
+III-A), max-log soft outputs (LLRs) of the linear estimate, bit-error counting
+and an exhaustive maximum-likelihood search for tiny problems.
 
 Parity status: every routine here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, library routines, brute force, invariants); none is
@@ -216,6 +216,58 @@ def label_points(labels, M: int) -> np.ndarray:
     kI = ungray(lab >> half)
     kQ = ungray(lab & ((1 << half) - 1))
     return (2 * kI - (L - 1)) * a + 1j * (2 * kQ - (L - 1)) * a
+
+
+def llr_stats(H, N0: float, Es: float = 1.0, reg: int = REG_MMSE):
+    """Per-user bias mu and effective noise variance nu^2 of the linear
+    estimate x = A H^H y with A = (G + delta I)^{-1}, G = H^H H, so that
+    x_u = mu_u s_u + e_u with E|e_u|^2 = nu_u^2 (soft outputs, Sec. III-A):
+
+      MMSE (delta = N0 / Es):  mu_u = 1 - delta A_uu,  nu_u^2 = Es mu_u (1 - mu_u)
+      ZF   (delta = 0):        mu_u = 1,               nu_u^2 = N0 A_uu
+
+    H is [W][B][U]; returns (mu, nu2), each [W][U] float64.  The inverse is a
+    library routine (numpy.linalg.inv)."""
+    H = _c128(H)
+    W, B, U = H.shape
+    G = np.einsum("wbu,wbv->wuv", H.conj(), H)
+    if reg == REG_MMSE:
+        delta = N0 / Es
+    elif reg == REG_ZF:
+        delta = 0.0
+    else:
+        raise ValueError("soft outputs are defined for the ZF and MMSE estimates")
+    A = np.linalg.inv(G + delta * np.eye(U))
+    Ad = np.real(np.diagonal(A, axis1=1, axis2=2))
+    if reg == REG_MMSE:
+        mu = 1.0 - delta * Ad
+        nu2 = Es * mu * (1.0 - mu)
+    else:
+        mu = np.ones_like(Ad)
+        nu2 = N0 * Ad
+    return mu, nu2
+
+
+def llr_maxlog(x, mu, nu2, M: int, Es: float = 1.0) -> np.ndarray:
+    """Max-log LLR of every label bit, most significant bit first, positive
+    when the bit is more likely 0:
+
+      L_j = (min_{s: bit_j(s) = 1} |x - mu s|^2 - min_{s: bit_j(s) = 0} |x - mu s|^2) / nu^2
+
+    by exhaustive search over the M alphabet points (scaled to energy Es).
+    x is [W][N][U], mu and nu2 are [W][U]; returns [W][N][U][log2 M]."""
+    x = _c128(x)
+    m = int(round(math.log2(M)))
+    pts = label_points(np.arange(M), M) * math.sqrt(Es)
+    mu = np.asarray(mu, dtype=np.float64)[:, None, :, None]
+    nu2 = np.asarray(nu2, dtype=np.float64)[:, None, :, None]
+    d2 = np.abs(x[..., None] - mu * pts) ** 2                      # [W][N][U][M]
+    out = np.empty(x.shape + (m,), dtype=np.float64)
+    labels = np.arange(M)
+    for j in range(m):
+        bit = (labels >> (m - 1 - j)) & 1
+        out[..., j] = (d2[..., bit == 1].min(axis=-1) - d2[..., bit == 0].min(axis=-1)) / nu2[..., 0]
+    return out
 
 
 def bit_errors(labels_a, labels_b) -> int:

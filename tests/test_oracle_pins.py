@@ -442,3 +442,83 @@ def test_oracle_rejects_bad_arguments():
         oracle.admm_ul(f["H"], f["y"], C=2, rho=1.0, N0=f["N0"], T_max=0)
     with pytest.raises(ValueError):
         oracle.admm_dl(f["H"], f["s"], C=2, rho=1.0, eps=-1.0)
+
+
+# ---------------------------------------------------------------------------
+# Soft outputs: LLR statistics of the linear estimate and max-log LLRs
+# ---------------------------------------------------------------------------
+
+def test_llr_qpsk_closed_form():
+    """QPSK: per axis the two points are +-a (a = 1/sqrt 2) with Gray bit 1 on
+    the positive point, so L = ((x - mu a)^2 - (x + mu a)^2) / nu^2 = -4 mu a x / nu^2."""
+    rng = np.random.default_rng(11)
+    x = rng.normal(size=(3, 5, 2)) + 1j * rng.normal(size=(3, 5, 2))
+    mu = rng.uniform(0.3, 1.0, size=(3, 2))
+    nu2 = rng.uniform(0.05, 2.0, size=(3, 2))
+    L = oracle.llr_maxlog(x, mu, nu2, 4)
+    a = 1.0 / math.sqrt(2.0)
+    np.testing.assert_allclose(L[..., 0], -4 * mu[:, None, :] * a * x.real / nu2[:, None, :], rtol=1e-12)
+    np.testing.assert_allclose(L[..., 1], -4 * mu[:, None, :] * a * x.imag / nu2[:, None, :], rtol=1e-12)
+
+
+@pytest.mark.parametrize("M", [4, 16, 64, 256])
+def test_llr_signs_are_the_hard_decisions(M):
+    """The max-log decision of each bit (L < 0: bit 1) is the bit of the
+    nearest point to x / mu, i.e. the slicer's label of x / mu."""
+    rng = np.random.default_rng(M)
+    x = 1.3 * (rng.normal(size=(4, 6, 3)) + 1j * rng.normal(size=(4, 6, 3)))
+    mu = rng.uniform(0.5, 1.0, size=(4, 3))
+    nu2 = rng.uniform(0.1, 1.0, size=(4, 3))
+    L = oracle.llr_maxlog(x, mu, nu2, M)
+    lab = oracle.slice_labels(x / mu[:, None, :], M).astype(np.int64)
+    m = L.shape[-1]
+    for j in range(m):
+        bit = (lab >> (m - 1 - j)) & 1
+        clear = np.abs(L[..., j]) > 1e-9
+        assert np.array_equal((L[..., j] < 0)[clear], (bit == 1)[clear])
+
+
+@pytest.mark.parametrize("M", [16, 64])
+def test_llr_reflection_flips_only_the_axis_msb(M):
+    """Binary-reflected Gray code: reflecting a PAM index flips only its top
+    bit, so x -> -conj(x) (real axis reflected) negates the first LLR and
+    leaves the other real-axis LLRs unchanged."""
+    rng = np.random.default_rng(7)
+    x = rng.normal(size=(2, 3, 4)) + 1j * rng.normal(size=(2, 3, 4))
+    mu = rng.uniform(0.5, 1.0, size=(2, 4))
+    nu2 = rng.uniform(0.1, 1.0, size=(2, 4))
+    L = oracle.llr_maxlog(x, mu, nu2, M)
+    Lr = oracle.llr_maxlog(-np.conj(x), mu, nu2, M)
+    half = L.shape[-1] // 2
+    np.testing.assert_allclose(Lr[..., 0], -L[..., 0], atol=1e-12)
+    np.testing.assert_allclose(Lr[..., 1:half], L[..., 1:half], atol=1e-12)
+    np.testing.assert_allclose(Lr[..., half:], L[..., half:], atol=1e-12)
+
+
+def test_llr_stats_zf_orthogonal_columns():
+    """ZF with orthogonal columns of norm^2 b: A = I / b, mu = 1, nu^2 = N0 / b."""
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.normal(size=(16, 4)) + 1j * rng.normal(size=(16, 4)))
+    H = (math.sqrt(5.0) * Q)[None]
+    mu, nu2 = oracle.llr_stats(H, N0=0.3, reg=oracle.REG_ZF)
+    np.testing.assert_allclose(mu, 1.0, rtol=1e-13)
+    np.testing.assert_allclose(nu2, 0.3 / 5.0, rtol=1e-12)
+
+
+def test_llr_stats_mmse_monte_carlo():
+    """The LMMSE estimate of a fixed channel: over many symbol and noise draws,
+    E[x_u conj(s_u)] / Es -> mu_u and E|x_u - mu_u s_u|^2 -> nu_u^2."""
+    rng = np.random.default_rng(5)
+    B, U, M, N0 = 12, 4, 16, 0.8
+    H = (rng.normal(size=(B, U)) + 1j * rng.normal(size=(B, U))) / math.sqrt(2.0)
+    mu, nu2 = oracle.llr_stats(H[None], N0=N0, Es=1.0, reg=oracle.REG_MMSE)
+    K = 200000
+    s = oracle.label_points(rng.integers(0, M, size=(K, U)), M)
+    n = math.sqrt(N0 / 2) * (rng.normal(size=(K, B)) + 1j * rng.normal(size=(K, B)))
+    y = s @ H.T + n
+    A = np.linalg.inv(H.conj().T @ H + N0 * np.eye(U))
+    x = y @ (A @ H.conj().T).T
+    mu_emp = np.mean(x * s.conj(), axis=0).real
+    nu2_emp = np.mean(np.abs(x - mu[0] * s) ** 2, axis=0)
+    np.testing.assert_allclose(mu_emp, mu[0], rtol=0.01)
+    np.testing.assert_allclose(nu2_emp, nu2[0], rtol=0.03)
