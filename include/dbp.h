@@ -225,6 +225,22 @@ dbp_status dbp_downlink_admm(dbp_handle_t h, const dbp_frame_desc *d,
                              const void *H, const void *s, void *x,
                              double *beta_out, void *stream);
 
+/* Soft outputs (max-log LLRs) of an uplink estimate x_hat [W][N][U]
+ * (complex64, e.g. the output of dbp_uplink_admm or dbp_uplink_cg) for the
+ * frame whose channel H [W][B][U] (complex64) is given.  With the
+ * subcarrier's Gram G = H^H H and A = (G + delta I)^{-1}, the estimate is
+ * modelled as x_u = mu_u s_u + e_u:
+ *   DBP_REG_MMSE (delta = N0/Es): mu_u = 1 - delta A_uu, E|e_u|^2 = Es mu_u (1 - mu_u)
+ *   DBP_REG_ZF   (delta = 0):     mu_u = 1,              E|e_u|^2 = N0 A_uu
+ * (the statistics of the estimate the detectors converge to, Sec. III-A).
+ * llr [W][N][U][log2 M] (float32) receives, most significant label bit
+ * first (labels as in the slicer: Gray I bits over Gray Q bits),
+ *   L = (min_{s: bit = 1} |x - mu s|^2 - min_{s: bit = 0} |x - mu s|^2) / E|e|^2,
+ * positive when the bit is more likely 0.  Needs qam_order > 0, N0 > 0,
+ * Es > 0, precision DBP_FP32 and, for ZF, U <= B.  Stream-ordered. */
+dbp_status dbp_uplink_llr(dbp_handle_t h, const dbp_frame_desc *d, const void *H,
+                          const void *x_hat, float *llr, void *stream);
+
 /* Host-memory variants (end-to-end path): the same computations with every
  * buffer in host memory.  The call copies the inputs to library-owned
  * device buffers on `stream`, runs the kernels, copies the outputs back

@@ -314,6 +314,16 @@ _lib.dbp_graph_destroy.restype = _S
 _lib.dbp_graph_destroy.argtypes = [ctypes.c_void_p]
 
 
+_lib.dbp_uplink_llr.restype = _S
+_lib.dbp_uplink_llr.argtypes = [_H, ctypes.POINTER(dbp_frame_desc), ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_void_p]
+
+
+def dbp_uplink_llr(h, d, H, x_hat, llr, stream=None) -> None:
+    """Max-log LLRs [W][N][U][log2 M] (float32) of an uplink estimate."""
+    _check(h, _lib.dbp_uplink_llr(h, ctypes.byref(d), _ptr(H), _ptr(x_hat), _ptr(llr), _stream(stream)))
+
+
 _lib.dbp_autotune.restype = _S
 _lib.dbp_autotune.argtypes = [_H, ctypes.c_int32, ctypes.POINTER(dbp_frame_desc), ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,

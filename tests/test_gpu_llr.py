@@ -1,0 +1,76 @@
+"""Soft outputs (dbp_uplink_llr) against the oracle: the LMMSE / ZF bias and
+noise statistics from the subcarrier's Gram and the max-log LLRs of the
+detector's own estimate, on the same FP32 inputs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dbp():
+    import paper_1702_04458_b300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def handle(dbp):
+    h = dbp.dbp_create(0)
+    yield h
+    dbp.dbp_destroy(h)
+
+
+LLR_CASES = [
+    # (W, N, B, C, U, M, snr_db, reg, detector)
+    (37, 14, 128, 8, 8, 16, 8.0, "mmse", "admm"),      # the B=128 / C=8 / U=8 workload
+    (21, 14, 128, 8, 8, 16, 8.0, "mmse", "cg"),
+    (13, 5, 64, 4, 16, 64, 18.0, "mmse", "cg"),
+    (9, 7, 80, 2, 5, 4, 4.0, "zf", "cg"),              # U=5 padded to 8, QPSK, ZF
+    (6, 3, 256, 8, 32, 256, 25.0, "mmse", "admm"),     # U=32, 256-QAM
+]
+
+
+@pytest.mark.parametrize("W,N,B,C,U,M,snr,reg,det", LLR_CASES)
+def test_llr_matches_oracle(dbp, handle, W, N, B, C, U, M, snr, reg, det):
+    f = synth.uplink_frame(W, N, B, U, M, snr, seed=2100 + W + U + M)
+    H32 = f["H"].astype(np.complex64)
+    Hd = torch.from_numpy(H32).cuda()
+    yd = torch.from_numpy(f["y"].astype(np.complex64)).cuda()
+    code = dbp.DBP_REG_MMSE if reg == "mmse" else dbp.DBP_REG_ZF
+    d = dbp.frame_desc(B, C, U, W, N, qam_order=M, T_max=3 if det == "admm" else 8, regularizer=code,
+                       N0=f["N0"], Es=1.0)
+    x = torch.zeros((W, N, U), dtype=torch.complex64, device="cuda")
+    (dbp.dbp_uplink_admm if det == "admm" else dbp.dbp_uplink_cg)(handle, d, Hd, yd, x, None)
+    m = int(np.log2(M))
+    llr = torch.zeros((W, N, U, m), dtype=torch.float32, device="cuda")
+    dbp.dbp_uplink_llr(handle, d, Hd, x, llr)
+    torch.cuda.synchronize()
+    mu, nu2 = oracle.llr_stats(H32.astype(np.complex128), f["N0"], 1.0,
+                               oracle.REG_MMSE if reg == "mmse" else oracle.REG_ZF)
+    ref = oracle.llr_maxlog(x.cpu().numpy().astype(np.complex128), mu, nu2, M)
+    got = llr.cpu().numpy().astype(np.float64)
+    err = np.abs(got - ref) / (1.0 + np.abs(ref))
+    assert err.max() <= 1e-3, err.max()
+    # hard decisions from the LLRs agree with the oracle's wherever they are not ties
+    clear = np.abs(ref) > 1e-2
+    assert np.array_equal((got < 0)[clear], (ref < 0)[clear])
+
+
+def test_llr_rejects_unsupported_requests(dbp, handle):
+    buf = torch.zeros(4096, dtype=torch.complex64, device="cuda")
+    out = torch.zeros(4096, dtype=torch.float32, device="cuda")
+    base = dict(B=32, C=4, U=4, W=3, N=2, qam_order=16, T_max=3, N0=0.1)
+    for bad, status in ((dict(qam_order=0), dbp.DBP_ERR_INVALID_ARG),
+                        (dict(regularizer=dbp.DBP_REG_BOX, box_r=1.0), dbp.DBP_ERR_INVALID_ARG),
+                        (dict(precision=dbp.DBP_FP64), dbp.DBP_ERR_UNSUPPORTED),
+                        (dict(N0=0.0), dbp.DBP_ERR_INVALID_ARG),
+                        (dict(regularizer=dbp.DBP_REG_ZF, U=8, B=4, C=1), dbp.DBP_ERR_INVALID_ARG)):
+        kw = dict(base)
+        kw.update(bad)
+        with pytest.raises(dbp.DbpError) as ei:
+            dbp.dbp_uplink_llr(handle, dbp.frame_desc(**kw), buf, buf, out)
+        assert ei.value.status == status
