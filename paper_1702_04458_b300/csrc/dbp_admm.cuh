@@ -129,6 +129,8 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_admm_kernel(const 
             bulk_g2s(wb + p.off_y0 + (size_t)n * yp * 8, Yg + ((size_t)w * N + n) * B + (size_t)c * S, ybytes, bar);
     };
 
+    grid_dependency_wait();
+    grid_dependents_launch();
     uint32_t phase = 0u;
     int tile = blockIdx.x;
     if (tile < p.tiles && tile * P + pl < W) issue(tile * P + pl);

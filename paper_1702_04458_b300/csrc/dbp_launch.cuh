@@ -23,6 +23,25 @@ int dbp_occupancy_cached(const void *kern, int threads, size_t smem);
 
 namespace dbp {
 
+// Persistent kernels are launched with programmatic stream serialisation:
+// their set-up (shared-memory zeroing, mbarrier initialisation) may overlap
+// the end of the previous kernel in the stream, and they wait for it in
+// grid_dependency_wait() before their first global access.
+template <typename K, typename... Args>
+cudaError_t launch_pdl(K kern, unsigned grid, unsigned block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(block, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Launch shape: CTA mapping (P whole subcarriers per CTA) when all C warps of
 // a subcarrier fit in one CTA, else thread-block clusters of CL CTAs.
 struct Shape {
@@ -85,8 +104,7 @@ cudaError_t launch_tma_one(const FusedParams &p, const Shape &s, cudaStream_t st
     auto kern = dbp::dbp_tma_kernel<UT, ALG, TIn>;
     cudaError_t e = dbp_prepare_kernel(reinterpret_cast<const void *>(kern), s.smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)s.grid, s.nwarps * 32, s.smem, st>>>(p);
-    return cudaGetLastError();
+        return launch_pdl(kern, (unsigned)s.grid, (unsigned)s.nwarps * 32, s.smem, st, p);
 }
 
 // Resident CTAs per SM of the persistent kernel at this shape.
@@ -155,8 +173,7 @@ cudaError_t launch_tc8(const FusedParams &p, const Shape &s, cudaStream_t st) {
         auto kern = dbp::dbp_tc8_kernel<ALG>;
         cudaError_t e = dbp_prepare_kernel(reinterpret_cast<const void *>(kern), s.smem);
         if (e != cudaSuccess) return e;
-        kern<<<(unsigned)s.grid, s.nwarps * 32, s.smem, st>>>(p);
-        return cudaGetLastError();
+                return launch_pdl(kern, (unsigned)s.grid, (unsigned)s.nwarps * 32, s.smem, st, p);
     }
 }
 
@@ -171,8 +188,7 @@ cudaError_t launch_cg_one(const FusedParams &p, const Shape &s, cudaStream_t st)
     auto kern = dbp::dbp_cg_kernel<UT>;
     cudaError_t e = dbp_prepare_kernel(reinterpret_cast<const void *>(kern), s.smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)s.grid, s.nwarps * 32, s.smem, st>>>(p);
-    return cudaGetLastError();
+        return launch_pdl(kern, (unsigned)s.grid, (unsigned)s.nwarps * 32, s.smem, st, p);
 }
 
 template <int UT>
@@ -186,8 +202,7 @@ cudaError_t launch_admm_one(const FusedParams &p, const Shape &s, cudaStream_t s
     auto kern = dbp::dbp_admm_kernel<UT>;
     cudaError_t e = dbp_prepare_kernel(reinterpret_cast<const void *>(kern), s.smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)s.grid, s.nwarps * 32, s.smem, st>>>(p);
-    return cudaGetLastError();
+        return launch_pdl(kern, (unsigned)s.grid, (unsigned)s.nwarps * 32, s.smem, st, p);
 }
 
 inline int tcdl_occupancy(int threads, size_t smem) {
@@ -197,8 +212,7 @@ inline int tcdl_occupancy(int threads, size_t smem) {
 inline cudaError_t launch_tcdl(const FusedParams &p, const Shape &s, cudaStream_t st) {
     cudaError_t e = dbp_prepare_kernel(reinterpret_cast<const void *>(dbp::dbp_tcdl_kernel<16>), s.smem);
     if (e != cudaSuccess) return e;
-    dbp::dbp_tcdl_kernel<16><<<(unsigned)s.grid, s.nwarps * 32, s.smem, st>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(dbp::dbp_tcdl_kernel<16>, (unsigned)s.grid, (unsigned)s.nwarps * 32, s.smem, st, p);
 }
 
 template <int ALG>

@@ -149,6 +149,8 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
     // symbol of accumulator entry q of this lane (within a 16-symbol pass)
     auto nof = [&](int q) { return 8 * (q >> 1) + 2 * t + (q & 1); };
 
+    grid_dependency_wait();
+    grid_dependents_launch();
     uint32_t phase = 0u;
     int tile = blockIdx.x;
     if (tile < p.tiles && tile * P + pl < W) issue(tile * P + pl);

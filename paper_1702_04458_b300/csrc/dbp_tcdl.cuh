@@ -138,6 +138,8 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
     };
 
     const float kap = p.f_kappa, gam = p.f_gamma, ic = p.f_invC, ir = p.f_inv_rho, eps = p.f_eps;
+    grid_dependency_wait();
+    grid_dependents_launch();
     float energy = 0.f;
     uint32_t parity = 0u;
     int tile = blockIdx.x;

@@ -62,6 +62,14 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the previous kernel of its stream is still
+// running; grid_dependency_wait() blocks until that kernel has completed and
+// its memory is visible (a no-op for an ordinary launch), so every global
+// access of the kernels comes after it and only the set-up overlaps.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -352,6 +360,8 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
         }
     };
 
+    grid_dependency_wait();
+    grid_dependents_launch();
     uint32_t parity = 0u;   // bit b: phase parity of buffer b's mbarrier
     int tile = blockIdx.x;
     if (tile < p.tiles && tile * P + pl < W) issue(tile * P + pl, 0);
