@@ -138,8 +138,9 @@ int v_ld_for(int UT) { return UT + 2; }
 int round_up(int a, int m) { return ((a + m - 1) / m) * m; }
 int round16(long long b) { return (int)(((b + 15) / 16) * 16); }
 
-// Per-warp shared-memory layout of the bulk-copy kernel (byte offsets).
-void tma_layout(const dbp_frame_desc *d, Kind kind, int UT, Shape &s) {
+// Per-warp shared-memory layout of the bulk-copy kernel (byte offsets): two
+// staging buffers, or one (single, uplink only) when two do not fit.
+void tma_layout(const dbp_frame_desc *d, Kind kind, int UT, Shape &s, bool single = false) {
     const int S = d->B / d->C, N = d->N;
     const int nch = tile_syms(UT);
     const int vbytes = round16(std::max(nch * v_ld_for(UT) * 8, UT * 16));
@@ -152,9 +153,9 @@ void tma_layout(const dbp_frame_desc *d, Kind kind, int UT, Shape &s) {
         const int hb = round16((long long)s.h_rows * s.hp * 4);
         const int yb = round16((long long)s.y_rows * s.yp * 4);
         const int gb = round16((long long)std::max(std::min(UT, 16), s.ms_rows) * (UT + 2) * 8);
-        s.off_h1 = hb;
-        s.off_y0 = 2 * hb;
-        s.off_y1 = s.off_y0 + yb;
+        s.off_h1 = single ? 0 : hb;
+        s.off_y0 = (single ? 1 : 2) * hb;
+        s.off_y1 = single ? s.off_y0 : s.off_y0 + yb;
         s.off_g = s.off_y1 + yb;
         s.off_v = s.off_g + gb;
         s.warp_bytes = s.off_v + vbytes;
@@ -166,9 +167,9 @@ void tma_layout(const dbp_frame_desc *d, Kind kind, int UT, Shape &s) {
         s.ms_rows = 0;
         const int hb = round16((long long)S * UT * 8);
         const int yb = round16((long long)s.y_rows * s.yp * 8);
-        s.off_h1 = hb;
-        s.off_y0 = 2 * hb;
-        s.off_y1 = s.off_y0 + yb;
+        s.off_h1 = single ? 0 : hb;
+        s.off_y0 = (single ? 1 : 2) * hb;
+        s.off_y1 = single ? s.off_y0 : s.off_y0 + yb;
         s.off_g = s.off_y1 + yb;
         s.off_v = s.off_g;
         s.warp_bytes = s.off_v + vbytes;
@@ -302,6 +303,7 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
     s.tc8 = false;
     s.tcdl = false;
     s.bcast = false;
+    s.single = false;
     // AUTO takes the tensor-core kernel for U = 8 (measured fastest for ADMM
     // and CG on the B=128, C=8, U=8 frame), else the broadcast kernels.
     const bool want_mma = t.kernel == DBP_PATH_MMA || t.kernel == DBP_PATH_AUTO;
@@ -402,6 +404,11 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
         if (P < 1) P = 1;
         auto bytes = [&](int PP) { return (size_t)PP * C * s.warp_bytes + tma_cta_for(UT, PP * C, PP); };
         while (P > 1 && (P * C > maxw || bytes(P) > h->smem_optin)) --P;
+        if (bytes(P) > h->smem_optin && kind != K_ADMM_DL) {
+            // two staging buffers do not fit: one, refilled after the matched filter
+            tma_layout(d, kind, UT, s, true);
+            s.single = true;
+        }
         const size_t smem = bytes(P);
         if (smem <= h->smem_optin) {
             s.tma = true;
@@ -598,6 +605,7 @@ dbp_status run_ex(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void
     p.status = h->status;
     p.retries = reinterpret_cast<unsigned int *>(h->status + 1);
     p.tiles = s.tiles;
+    p.single_buf = s.single ? 1 : 0;
     p.hp = s.hp;
     p.yp = s.yp;
     p.h_rows = s.h_rows;

@@ -73,6 +73,8 @@ struct FusedParams {
     int *status;         // device word: bit 0 = a bounded wait gave up
     unsigned int *retries;   // device counter of FP64 inverse retries
     int tiles;           // subcarrier tiles (ceil(W / P))
+    int single_buf;      // 1: one staging buffer (uplink), the next subcarrier
+                         // is fetched after the matched filter has read it
     int hp;              // staged H row pitch, in input elements
     int yp;              // staged receive-row pitch, in input elements
     int h_rows;          // staged H rows (S, or S rounded up to 8)

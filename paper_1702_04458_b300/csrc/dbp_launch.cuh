@@ -49,6 +49,7 @@ struct Shape {
     bool tma;              // persistent bulk-copy kernel
     bool tc8 = false;      // U = 8 tensor-core uplink kernel
     bool tcdl = false;     // U = 16 tensor-core downlink kernel
+    bool single = false;   // bulk-copy kernel with one staging buffer (uplink)
     bool bcast = false;    // consensus step once per symbol, result broadcast
     int P, CPB, CL, nwarps;
     long long grid;

@@ -367,12 +367,14 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
     if (tile < p.tiles && tile * P + pl < W) issue(tile * P + pl, 0);
 
     int buf = 0;   // consensus double buffer
+    const bool dbl = (p.single_buf == 0);
     for (int it = 0; tile < p.tiles; ++it, tile += gridDim.x) {
-        const int b = it & 1;
+        const int b = dbl ? (it & 1) : 0;
         const int w = tile * P + pl;
         const bool valid = (w < W);
         const int ntile = tile + gridDim.x;
-        if (ntile < p.tiles && ntile * P + pl < W) issue(ntile * P + pl, b ^ 1);
+        const bool has_next = ntile < p.tiles && ntile * P + pl < W;
+        if (dbl && has_next) issue(ntile * P + pl, b ^ 1);
         if (valid) {
             mbar_wait_bounded(&bars[b], (parity >> b) & 1u, p.status);
             parity ^= (1u << b);
@@ -478,6 +480,8 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
                 mf_mma<UT, TIn>(reinterpret_cast<const uint32_t *>(Hs), hp, p.h_rows,
                                 reinterpret_cast<const uint32_t *>(Ys), yp, (N + 7) / 8, Gm, lane);
                 __syncwarp();
+                // one staging buffer: H_c and y_c are no longer read
+                if (!dbl && has_next) issue(ntile * P + pl, 0);
             }
         }
 
@@ -527,6 +531,12 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
                             cmacc(acc[j], h0, a);
                             cmacc(acc[j], h1, bb);
                         }
+                    }
+                    // one staging buffer: the last chunk's matched filter was
+                    // the last read of H_c and y_c
+                    if (!dbl && n0 + K::NCH >= N) {
+                        __syncwarp();
+                        if (has_next) issue(ntile * P + pl, 0);
                     }
                 }
             }

@@ -352,6 +352,22 @@ def test_bulk_copy_kernel_matches_generic_kernel(dbp, handle, algo):
     assert _rel_per_vector(runs[0], runs[1]).max() <= 1e-5
 
 
+@pytest.mark.parametrize("algo", ["admm", "cg"])
+def test_bulk_copy_kernel_single_staging_buffer(dbp, handle, algo):
+    """FP32, U=32, S=32: two staging buffers do not fit in shared memory, so the
+    forced bulk-copy kernel refills one buffer after the matched filter.  301
+    subcarriers take several persistent tiles per CTA (every refill path)."""
+    f = synth.uplink_frame(301, 14, 256, 32, 64, 20.0, seed=452)
+    try:
+        dbp.dbp_set_tuning(handle, kernel=dbp.DBP_PATH_TMA)
+        x, lab = run_ul(dbp, handle, f, 8, 3, algo)
+    finally:
+        dbp.dbp_set_tuning(handle)
+    ref = oracle_ul(f, 8, 3, algo, "fp32")
+    assert _rel_per_vector(x, ref).max() <= FP32_TOL
+    assert_labels(x, lab, ref, 64, np.float32)
+
+
 def test_forced_bulk_copy_kernel_rejects_ineligible_shapes(dbp, handle):
     f = synth.uplink_frame(3, 2, 40, 5, 16, 8.0, seed=451)      # U=5 is not a power of two
     try:
