@@ -489,7 +489,34 @@ class ServeChannel:
         return sp["U"] * (sp["M"].bit_length() - 1) * sp["W"] * sp["N"]
 
 
-def serve_run(dbp, h, chans, kinds, rate_hz, n_frames, rng):
+class MixServeChannel:
+    """One channel of the served mixed-precision comparison: the B=256, C=8,
+    U=32, 3300 x 14, 64-QAM frame with its host inputs in one precision
+    (pinned) and a ring of host output slots."""
+
+    def __init__(self, f, prec_name, seed):
+        import torch
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+        self.spec = dict(B=MIX.B, C=MIX.C, U=MIX.U, W=MIX.W, N=MIX.N, M=MIX.M, seed=seed)
+        self.N0 = f["N0"]
+        self.labels_true = f["labels"]
+        if prec_name == "fp32":
+            self.H, self.y = pin(f["H"].astype(np.complex64)), pin(f["y"].astype(np.complex64))
+        else:
+            dt = torch.float16 if prec_name == "fp16" else torch.bfloat16
+            c16 = lambda a: torch.from_numpy(  # noqa: E731
+                np.stack([a.real, a.imag], -1).astype(np.float32)).to(dt).contiguous().pin_memory()
+            self.H, self.y = c16(f["H"]), c16(f["y"])
+        shape = (MIX.W, MIX.N, MIX.U)
+        self.out_ul = [pin(np.zeros(shape, np.complex64)) for _ in range(SERVE_RING)]
+        self.lab = [pin(np.zeros(shape, np.uint8)) for _ in range(SERVE_RING)]
+        self.busy = [None] * SERVE_RING
+
+    def bits(self):
+        return detected_bits(MIX)
+
+
+def serve_run(dbp, h, chans, kinds, rate_hz, n_frames, rng, precision=None, fixed_T=None):
     """Submit n_frames (Poisson at rate_hz, or back to back if rate_hz is
     None); returns per-frame (latency_us, bits, hit) and the wall time."""
     import collections
@@ -523,13 +550,14 @@ def serve_run(dbp, h, chans, kinds, rate_hz, n_frames, rng):
             collect(True)
         slot = ch.busy.index(None)
         sp = ch.spec
-        T = int(rng.integers(3, 9))
+        T = int(rng.integers(3, 9)) if fixed_T is None else fixed_T
         if kind == dbp.DBP_KIND_DOWNLINK_ADMM:
             d = dbp.frame_desc(sp["B"], sp["C"], sp["U"], sp["W"], sp["N"], T_max=T, rho=1.0)
             req = dbp.request(kind, d, ch.H, ch.s, ch.out_dl[slot], None, None, ci + 1, epoch, i)
         else:
             d = dbp.frame_desc(sp["B"], sp["C"], sp["U"], sp["W"], sp["N"], qam_order=sp["M"], T_max=T,
-                               rho=1.0, N0=ch.N0, Es=1.0)
+                               rho=1.0, N0=ch.N0, Es=1.0,
+                               precision=dbp.DBP_FP32 if precision is None else precision)
             req = dbp.request(kind, d, ch.H, ch.y, ch.out_ul[slot], ch.lab[slot], None, ci + 1, epoch, i)
         if rate_hz is not None:
             next_t += rng.exponential(1.0 / rate_hz)
@@ -581,6 +609,70 @@ def bench_serving(dbp, h, args):
             "kind_mix": "40% uplink ADMM, 30% uplink CG, 30% downlink ADMM (FP32), 3..8 iterations",
             "capacity_frames_per_s": cap_fps, "load_points": points,
             "latency": "submit to completion observed by the request loop (host copies included)"}
+
+
+MIX_SERVE_CHANNELS = 2
+
+
+def bench_served_precision(dbp, h, args):
+    """The served path with 16-bit against FP32 inputs: uplink ADMM (T=3)
+    frames of the B=256, C=8, U=32, 3300 x 14, 64-QAM workload at 20 dB from
+    pinned host memory through the request loop (channels resident per
+    coherence block of 4 frames).  Per precision: saturation throughput, then
+    Poisson arrivals at one offered load (0.7 of the FP32 capacity, the same
+    for every precision) with p50/p99 latency, and the BER of the served
+    labels with its 95% interval."""
+    rng = np.random.default_rng(321)
+    seeds = [synth.frame_seed(4, 5) + 7000 + i for i in range(MIX_SERVE_CHANNELS)]
+    frames = [synth.uplink_frame(MIX.W, MIX.N, MIX.B, MIX.U, MIX.M, MIX_SNR_DB, seed=sd) for sd in seeds]
+    n = max(args.serve_frames // 5, 24)
+    kinds = [dbp.DBP_KIND_UPLINK_ADMM] * n
+    precs = (("fp32", dbp.DBP_FP32), ("fp16", dbp.DBP_FP16), ("bf16", dbp.DBP_BF16))
+    out = {"workload": workload_name(MIX, f"served uplink ADMM T={MIX.T} at {MIX_SNR_DB:g} dB").replace(
+               ", fp32 complex", ""),
+           "channels": MIX_SERVE_CHANNELS, "coherence_frames": SERVE_COHERENCE, "frames_per_run": n,
+           "latency": "submit to completion observed by the request loop (host copies included)",
+           "per_precision": {}}
+    rate = None
+    for name, prec in precs:
+        chans = [MixServeChannel(f, name, sd) for f, sd in zip(frames, seeds)]
+        dbp.dbp_server_start(h, streams=4, hbm_bytes=8 << 30)
+        try:
+            serve_run(dbp, h, chans, kinds, None, 2 * MIX_SERVE_CHANNELS, rng, prec, MIX.T)   # warm-up
+            done, _ = serve_run(dbp, h, chans, kinds, None, n, rng, prec, MIX.T)
+            span = max(d[4] for d in done) - min(d[3] for d in done)
+            cap = len(done) / (span / 1e6)
+            sat_gbit = sum(d[1] for d in done) / (span / 1e6) / 1e9
+            if rate is None:
+                rate = 0.7 * cap        # offered load of every precision's loaded run
+            done, _ = serve_run(dbp, h, chans, kinds, rate, n, rng, prec, MIX.T)
+            lat = np.array([d[0] for d in done])
+            span = max(d[4] for d in done) - min(d[3] for d in done)
+        finally:
+            dbp.dbp_server_stop(h)
+        errs = nbits = 0
+        for ch in chans:
+            # every frame of a channel detects the same (H, y); slot 0 is the
+            # first one every channel fills
+            lab = ch.lab[0].numpy()
+            errs += int(np.unpackbits(np.bitwise_xor(lab, ch.labels_true).reshape(-1, 1), axis=1).sum())
+            nbits += MIX.W * MIX.N * MIX.U * (MIX.M.bit_length() - 1)
+        out["per_precision"][name] = {
+            "saturation_gbit_s": sat_gbit, "capacity_frames_per_s": cap,
+            "loaded": {"offered_frames_per_s": rate, "gbit_s": sum(d[1] for d in done) / (span / 1e6) / 1e9,
+                       "p50_ms": float(np.percentile(lat, 50)) / 1e3,
+                       "p99_ms": float(np.percentile(lat, 99)) / 1e3,
+                       "resident_hits": int(sum(d[2] for d in done))},
+            "ber": errs / nbits, "ber_ci95": _binom_ci(errs, nbits),
+            "h2d_bytes_per_frame_y": int(chans[0].y.numel() * chans[0].y.element_size()),
+            "h2d_bytes_per_channel_H": int(chans[0].H.numel() * chans[0].H.element_size())}
+        del chans
+    pp = out["per_precision"]
+    for name in ("fp16", "bf16"):
+        lo, hi = pp["fp32"]["ber_ci95"]
+        pp[name]["ber_within_fp32_ci95"] = bool(lo <= pp[name]["ber"] <= hi)
+        pp[name]["saturation_speedup_vs_fp32"] = pp[name]["saturation_gbit_s"] / pp["fp32"]["saturation_gbit_s"]
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -883,8 +975,10 @@ def main(argv=None) -> int:
     if not args.no_serving:
         serving = bench_serving(dbp, h, args)
     graph = None
+    served_mixed = None
     if not args.no_serving:
         graph = bench_graph(dbp, h, stream, device, args)
+        served_mixed = bench_served_precision(dbp, h, args)
 
     # ---- end to end: host inputs in, host results out ------------------------
     # Each step copies the frame's channel and receive vectors (one pinned
@@ -992,6 +1086,7 @@ def main(argv=None) -> int:
             "mixed_vs_fp32": mixed,
             "graph_batch": graph,
             "serving": serving,
+            "served_mixed_vs_fp32": served_mixed,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 2 * K,
