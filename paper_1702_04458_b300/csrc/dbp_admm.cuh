@@ -46,6 +46,12 @@ template <int UT> __host__ __device__ constexpr size_t admm_cta_bytes(int nwarps
 // an HPD matrix) in the column-split layout.  A[i] = entry (u, g*CPG + i) on
 // entry and of the inverse on exit; returns the smallest pivot's real part
 // (identical on every lane).
+//
+// Step k with pivot p = A[k][k] and f_u = A[u][k]: every column j != k takes
+// the same multiply-add A[u][j] -= m_u A[k][j] with m_u = f_u / p for the
+// other rows and m_k = 1 - 1/p for the pivot row (A[k][j] - (1 - 1/p) A[k][j]
+// = A[k][j] / p), so only the lanes holding column k take a different value
+// there (1/p on the pivot row, -f_u / p elsewhere).
 template <int UT>
 __device__ __forceinline__ float gj_split(float2 (&A)[Split<UT>::CPG], int u, int g) {
     using SP = Split<UT>;
@@ -64,20 +70,15 @@ __device__ __forceinline__ float gj_split(float2 (&A)[Split<UT>::CPG], int u, in
             rk[i].y = __shfl_sync(0xffffffffu, A[i].y, k + UT * g);
         }
         min_piv = fminf(min_piv, piv.x);
-        const float2 inv = crcp(piv);
+        const float dd = __frcp_rn(fmaf(piv.x, piv.x, piv.y * piv.y));
+        const float2 inv = make_float2(piv.x * dd, -piv.y * dd);
         const bool me = (u == k);
-        const float2 fk = cmul(f, inv);                 // multiplier of row u
+        const float2 fi = cmul(f, inv);                  // f_u / p
+        const float2 m = me ? make_float2(1.f - inv.x, -inv.y) : fi;
+        const float2 nm = make_float2(-m.x, -m.y);
 #pragma unroll
-        for (int i = 0; i < SP::CPG; ++i) {
-            const int col = (g % SP::NG) * SP::CPG + i;
-            if (col == k) {
-                A[i] = me ? inv : make_float2(-fk.x, -fk.y);
-            } else if (me) {
-                A[i] = cmul(rk[i], inv);
-            } else {
-                cmac(A[i], make_float2(-fk.x, -fk.y), rk[i]);
-            }
-        }
+        for (int i = 0; i < SP::CPG; ++i) cmac(A[i], nm, rk[i]);
+        if (g % SP::NG == gk) A[ik] = me ? inv : make_float2(-fi.x, -fi.y);
     }
     return min_piv;
 }
