@@ -152,12 +152,30 @@ typedef enum dbp_kernel_path {
                                   clusters                                   */
 } dbp_kernel_path;
 
+typedef enum dbp_prefactor {
+    DBP_PREFACTOR_AUTO = 0,    /* off (measured slower on every shape where
+                                  it is available); the autotuner times both */
+    DBP_PREFACTOR_OFF = 1,     /* the fused kernel forms B_c^{-1} itself     */
+    DBP_PREFACTOR_ON = 2       /* where available: B_c^{-1} of every
+                                  (subcarrier, cluster) first, by a kernel
+                                  with independent warps (many per SM), into
+                                  a stream-ordered buffer of W*C*U*U complex
+                                  FP32 taken from a pool of the handle; the
+                                  fused kernel then loads it.  Available for
+                                  ADMM (Alg. 1, Alg. 3) on the persistent
+                                  bulk-copy kernel with U in {16, 32} and on
+                                  the U = 16 tensor-core downlink kernel,
+                                  outside stream capture and the request
+                                  loop.  Same results bit for bit            */
+} dbp_prefactor;
+
 typedef struct dbp_tuning {
     int32_t mapping;           /* dbp_mapping                                */
     int32_t cluster_size;      /* CTAs per cluster (divides C, <= 16); 0 =
                                   smallest that fits                         */
     int32_t warps_per_cta;     /* CTA mapping: target warps per CTA; 0 = 8   */
     int32_t kernel;            /* dbp_kernel_path                            */
+    int32_t prefactor;         /* dbp_prefactor                              */
 } dbp_tuning;
 
 typedef struct dbp_context *dbp_handle_t;
@@ -334,7 +352,7 @@ dbp_status dbp_wait(dbp_handle_t h, uint64_t ticket, double timeout_s, dbp_resul
 
 /* ------------------------------------------------------------------------
  * Autotuner.  Launch choices (kernel path, CTA size, thread-block cluster
- * size) are timed on a representative frame and the fastest is remembered
+ * size, separate operator kernel) are timed on a representative frame and the fastest is remembered
  * per frame shape (kind, B, C, U, N, precision) on the handle; calls whose
  * tuning is fully automatic (dbp_set_tuning defaults) then use it for every
  * frame of that shape, whatever W.  Results depend on the choice only
@@ -354,7 +372,7 @@ dbp_status dbp_autotune(dbp_handle_t h, int32_t kind, const dbp_frame_desc *d, c
 dbp_status dbp_autotune_clear(dbp_handle_t h);
 
 /* Write / read the tuned shapes as text, one shape per line
- * ("kind B C U N precision mapping cluster_size warps_per_cta kernel").
+ * ("kind B C U N precision mapping cluster_size warps_per_cta kernel prefactor").
  * Loading adds to (and overrides) the handle's table; DBP_ERR_INVALID_ARG
  * for an unreadable file or a malformed line (nothing is loaded then). */
 dbp_status dbp_autotune_save(dbp_handle_t h, const char *path);

@@ -42,6 +42,7 @@ DBP_REG_ZF, DBP_REG_MMSE, DBP_REG_BOX = 0, 1, 2
 DBP_FLAG_NORMALIZE = 1
 DBP_MAP_AUTO, DBP_MAP_CTA, DBP_MAP_CLUSTER = 0, 1, 2
 DBP_PATH_AUTO, DBP_PATH_GENERIC, DBP_PATH_TMA, DBP_PATH_MMA, DBP_PATH_BCAST = 0, 1, 2, 3, 4
+DBP_PREFACTOR_AUTO, DBP_PREFACTOR_OFF, DBP_PREFACTOR_ON = 0, 1, 2
 
 _STATUS = {0: "DBP_OK", 1: "DBP_ERR_INVALID_ARG", 2: "DBP_ERR_UNSUPPORTED", 3: "DBP_ERR_NOMEM",
            4: "DBP_ERR_CUDA", 5: "DBP_ERR_TIMEOUT", 6: "DBP_ERR_UNIMPLEMENTED", 7: "DBP_PENDING"}
@@ -69,7 +70,8 @@ class dbp_graph_item(ctypes.Structure):
 
 class dbp_tuning(ctypes.Structure):
     _fields_ = [("mapping", ctypes.c_int32), ("cluster_size", ctypes.c_int32),
-                ("warps_per_cta", ctypes.c_int32), ("kernel", ctypes.c_int32)]
+                ("warps_per_cta", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("prefactor", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -154,8 +156,8 @@ def dbp_last_error(h) -> str:
 
 
 def dbp_set_tuning(h, mapping: int = DBP_MAP_AUTO, cluster_size: int = 0, warps_per_cta: int = 0,
-                   kernel: int = DBP_PATH_AUTO) -> None:
-    t = dbp_tuning(mapping, cluster_size, warps_per_cta, kernel)
+                   kernel: int = DBP_PATH_AUTO, prefactor: int = 0) -> None:
+    t = dbp_tuning(mapping, cluster_size, warps_per_cta, kernel, prefactor)
     _check(h, _lib.dbp_set_tuning(h, ctypes.byref(t)))
 
 

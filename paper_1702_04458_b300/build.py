@@ -22,7 +22,7 @@ LIB = os.path.join(PKG, "libdbp.so")
 
 SOURCES = ["dbp_api.cu", "dbp_k_admm_ul.cu", "dbp_k_cg_ul.cu", "dbp_k_admm_dl.cu",
            "dbp_static.cu", "dbp_serve.cu", "dbp_graph.cu", "dbp_tune.cu",
-           "dbp_llr.cu"]
+           "dbp_llr.cu", "dbp_factor.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

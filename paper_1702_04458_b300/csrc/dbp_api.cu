@@ -17,6 +17,7 @@
 #include "dbp.h"
 #include "dbp_internal.h"
 #include "dbp_launch.cuh"
+#include "dbp_factor.cuh"
 
 using dbp::FusedParams;
 using dbp::Shape;
@@ -573,6 +574,77 @@ void fill_float_params(FusedParams &p) {
 
 bool aligned(const void *ptr, size_t a) { return (reinterpret_cast<uintptr_t>(ptr) % a) == 0; }
 
+// The separate operator kernel (dbp_factor.cuh) exists for ADMM on the
+// bulk-copy kernel with U in {16, 32} and on the U = 16 tensor-core downlink
+// kernel.
+bool prefactor_available(const dbp_frame_desc *d, Kind kind, const Shape &s, int UT) {
+    if (!s.tma || s.tc8 || s.bcast || kind == K_CG_UL || d->U != UT) return false;
+    if (s.tcdl) return true;
+    if (UT != 16 && UT != 32) return false;
+    return kind == K_ADMM_UL || d->precision == DBP_FP32;
+}
+
+// Per-warp layout of the operator kernel: the staged H_c as the fused kernel
+// stages it, the Gram row buffer (16-bit inputs) or B_c (downlink tensor-core
+// kernel), and the Gauss-Jordan / FP64-retry scratch.
+size_t factor_layout(const dbp_frame_desc *d, int UT, const Shape &s, dbp::FactorParams &fp) {
+    const int S = d->B / d->C;
+    fp.S = S;
+    if (s.tcdl) {
+        fp.hp = 16;
+        fp.h_rows = S;
+        fp.off_g = round16((long long)S * 16 * 8);
+        fp.off_v = fp.off_g + round16((long long)16 * dbp::TcDl::QP * 8);
+        fp.warp_bytes = fp.off_v + 16 * 16;
+    } else {
+        const int eb = (int)elem_bytes(d->precision);
+        const bool h16 = is16(d->precision);
+        fp.hp = h16 ? UT + 8 : UT;
+        fp.h_rows = h16 ? round_up(S, 8) : S;
+        fp.off_g = round16((long long)fp.h_rows * fp.hp * eb);
+        fp.off_v = fp.off_g + (h16 ? round16((long long)16 * (UT + 2) * 8) : 0);
+        fp.warp_bytes = fp.off_v + UT * 16;
+    }
+    return (size_t)dbp::kFactorWarps * fp.warp_bytes;
+}
+
+// The handle's pool of operator buffers: memory stays in the pool between
+// calls, and a buffer freed on one stream is not handed to another stream
+// before that free has completed (no reuse through inserted dependencies),
+// so calls on different streams keep running concurrently.
+dbp_status factor_pool(dbp_context *h, cudaMemPool_t *out) {
+    std::lock_guard<std::mutex> lk(h->pool_mu);
+    if (!h->factor_pool) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = h->device;
+        cudaMemPool_t pool = nullptr;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemPoolCreate");
+        uint64_t keep = ~0ull;
+        int off = 0;
+        if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess ||
+            (e = cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowOpportunistic, &off)) != cudaSuccess ||
+            (e = cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &off)) != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return cuda_fail(h, e, "cudaMemPoolSetAttribute");
+        }
+        h->factor_pool = pool;
+    }
+    *out = h->factor_pool;
+    return DBP_OK;
+}
+
+bool stream_capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return true;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
 dbp_status run_ex(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void *H, const void *vin,
                   void *out, uint8_t *labels, double *beta_out, cudaStream_t st, const DbpExec *ex,
                   bool *factor_used) {
@@ -590,7 +662,7 @@ dbp_status run_ex(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void
     // this frame shape (dbp_autotune) if there is one
     dbp_tuning tune = h->tuning;
     if (tune.kernel == DBP_PATH_AUTO && tune.mapping == DBP_MAP_AUTO && tune.warps_per_cta == 0 &&
-        tune.cluster_size == 0) {
+        tune.cluster_size == 0 && tune.prefactor == DBP_PREFACTOR_AUTO) {
         std::lock_guard<std::mutex> lk(h->tune_mu);
         auto it = h->tuned.find(dbp_tune_key(d, kind));
         if (it != h->tuned.end()) tune = it->second;
@@ -646,10 +718,44 @@ dbp_status run_ex(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void
     else if (kind == K_CG_UL) p.delta = 0.0;          // G_c = H_c^H H_c
     else p.delta = 1.0 / d->rho;                      // B_c = H^d_c H^dH_c + rho^{-1} I
     fill_float_params(p);
+    // B_c^{-1} by the operator kernel first, where available and wanted; the
+    // fused kernel then loads it (factor_mode 2) from a stream-ordered buffer
+    // that is returned to the pool after it.
+    void *ws = nullptr;
+    const bool pre_wanted = tune.prefactor == DBP_PREFACTOR_ON && !ex && prefactor_available(d, kind, s, UT);
+    if (pre_wanted && !stream_capturing(st)) {
+        cudaMemPool_t pool = nullptr;
+        v = factor_pool(h, &pool);
+        if (v != DBP_OK) return v;
+        const size_t bytes = (size_t)d->W * d->C * UT * UT * sizeof(float2);
+        e = cudaMallocFromPoolAsync(&ws, bytes, pool, st);
+        if (e != cudaSuccess) return fail(h, DBP_ERR_NOMEM, "operator buffer (%zu bytes): %s", bytes, cudaGetErrorString(e));
+        dbp::FactorParams fp{};
+        const size_t fsmem = factor_layout(d, UT, s, fp);
+        fp.H = H;
+        fp.factor = static_cast<float2 *>(ws);
+        fp.W = d->W;
+        fp.B = d->B;
+        fp.C = d->C;
+        fp.f_delta = p.f_delta;
+        fp.delta = p.delta;
+        fp.retries = p.retries;
+        e = dbp_launch_factor(d->precision, UT, kind == K_ADMM_DL, s.tcdl, fp, fsmem, h->num_sms, st);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(ws, st);
+            return cuda_fail(h, e, "operator kernel launch");
+        }
+        p.factor = static_cast<float2 *>(ws);
+        p.factor_mode = 2;
+    }
     switch (kind) {
     case K_ADMM_UL: e = dbp_launch_admm_ul(d->precision, UT, p, s, st); break;
     case K_CG_UL: e = dbp_launch_cg_ul(d->precision, UT, p, s, st); break;
     default: e = dbp_launch_admm_dl(d->precision, UT, p, s, st); break;
+    }
+    if (ws) {
+        const cudaError_t ef = cudaFreeAsync(ws, st);
+        if (e == cudaSuccess) e = ef;
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
     if (norm) {
@@ -793,6 +899,8 @@ dbp_status dbp_destroy(dbp_handle_t h) {
     if (h->status) cudaFree(h->status);
     for (int i = 0; i < 4; ++i)
         if (h->dev[i]) cudaFree(h->dev[i]);
+    // buffers still in flight go back when their frees complete
+    if (h->factor_pool) cudaMemPoolDestroy(h->factor_pool);
     delete h;
     return DBP_OK;
 }
@@ -802,7 +910,8 @@ const char *dbp_last_error(dbp_handle_t h) { return h ? h->err.c_str() : "NULL h
 dbp_status dbp_set_tuning(dbp_handle_t h, const dbp_tuning *t) {
     if (!h || !t) return DBP_ERR_INVALID_ARG;
     if (t->mapping < DBP_MAP_AUTO || t->mapping > DBP_MAP_CLUSTER || t->cluster_size < 0 || t->cluster_size > 16 ||
-        t->warps_per_cta < 0 || t->warps_per_cta > 32 || t->kernel < DBP_PATH_AUTO || t->kernel > DBP_PATH_BCAST)
+        t->warps_per_cta < 0 || t->warps_per_cta > 32 || t->kernel < DBP_PATH_AUTO || t->kernel > DBP_PATH_BCAST ||
+        t->prefactor < DBP_PREFACTOR_AUTO || t->prefactor > DBP_PREFACTOR_ON)
         return fail(h, DBP_ERR_INVALID_ARG, "bad tuning values");
     h->tuning = *t;
     return DBP_OK;

@@ -28,6 +28,9 @@ struct dbp_context {
     // autotuned launch choices per frame shape (kind, B, C, U, N, precision)
     std::mutex tune_mu;
     std::map<std::tuple<int, int, int, int, int, int>, dbp_tuning> tuned;
+    // stream-ordered pool of the per-call operator buffers (dbp_factor.cuh)
+    std::mutex pool_mu;
+    cudaMemPool_t factor_pool = nullptr;
 };
 
 inline std::tuple<int, int, int, int, int, int> dbp_tune_key(const dbp_frame_desc *d, int kind) {
@@ -42,6 +45,7 @@ struct DbpExec {
     double *energy = nullptr;      // downlink power accumulator (one double)
     float2 *factor = nullptr;      // resident operator [W][C][UT][UT]
     int factor_mode = 0;           // 0 none, 1 compute and store, 2 load
+    bool no_workspace = false;     // allocate nothing (no separate operator kernel)
 };
 
 // Validate and enqueue one frame on `st` (errors go to *err when non-null).

@@ -105,7 +105,7 @@ cudaError_t launch_tma_one(const FusedParams &p, const Shape &s, cudaStream_t st
     auto kern = dbp::dbp_tma_kernel<UT, ALG, TIn>;
     cudaError_t e = dbp_prepare_kernel(reinterpret_cast<const void *>(kern), s.smem);
     if (e != cudaSuccess) return e;
-        return launch_pdl(kern, (unsigned)s.grid, (unsigned)s.nwarps * 32, s.smem, st, p);
+    return launch_pdl(kern, (unsigned)s.grid, (unsigned)s.nwarps * 32, s.smem, st, p);
 }
 
 // Resident CTAs per SM of the persistent kernel at this shape.
@@ -189,7 +189,7 @@ cudaError_t launch_cg_one(const FusedParams &p, const Shape &s, cudaStream_t st)
     auto kern = dbp::dbp_cg_kernel<UT>;
     cudaError_t e = dbp_prepare_kernel(reinterpret_cast<const void *>(kern), s.smem);
     if (e != cudaSuccess) return e;
-        return launch_pdl(kern, (unsigned)s.grid, (unsigned)s.nwarps * 32, s.smem, st, p);
+    return launch_pdl(kern, (unsigned)s.grid, (unsigned)s.nwarps * 32, s.smem, st, p);
 }
 
 template <int UT>
@@ -203,7 +203,7 @@ cudaError_t launch_admm_one(const FusedParams &p, const Shape &s, cudaStream_t s
     auto kern = dbp::dbp_admm_kernel<UT>;
     cudaError_t e = dbp_prepare_kernel(reinterpret_cast<const void *>(kern), s.smem);
     if (e != cudaSuccess) return e;
-        return launch_pdl(kern, (unsigned)s.grid, (unsigned)s.nwarps * 32, s.smem, st, p);
+    return launch_pdl(kern, (unsigned)s.grid, (unsigned)s.nwarps * 32, s.smem, st, p);
 }
 
 inline int tcdl_occupancy(int threads, size_t smem) {
@@ -264,3 +264,12 @@ int dbp_tc8_occupancy_cg_ul(int threads, size_t smem);
 int dbp_cg_occupancy(int UT, int threads, size_t smem);
 int dbp_bcast_admm_occupancy(int UT, int threads, size_t smem);
 int dbp_tcdl_occupancy(int threads, size_t smem);
+
+// The per-cluster operator kernels (dbp_factor.cu): B_c^{-1} of every
+// (subcarrier, cluster) of the frame into p.factor, for the bulk-copy kernel's
+// layout (tcdl = false; 16-bit or FP32 inputs, U in {16, 32}) or the U = 16
+// tensor-core downlink kernel's (tcdl = true).  Returns cudaErrorInvalidValue
+// for a combination that has no instance.
+namespace dbp { struct FactorParams; }
+cudaError_t dbp_launch_factor(int prec, int UT, bool downlink, bool tcdl, const dbp::FactorParams &p, size_t smem,
+                              int num_sms, cudaStream_t st);

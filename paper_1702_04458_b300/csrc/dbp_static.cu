@@ -16,6 +16,7 @@
 
 #include "dbp.h"
 #include "dbp_fused.cuh"
+#include "dbp_internal.h"
 
 namespace {
 
@@ -104,7 +105,10 @@ extern "C" dbp_status dbp_downlink_admm_static(dbp_handle_t h, const dbp_frame_d
     // allocating normalisation.  It also makes the handle's device current.
     dbp_frame_desc dd = *d;
     dd.flags &= ~DBP_FLAG_NORMALIZE;
-    dbp_status st = dbp_downlink_admm(h, &dd, H, s, x, nullptr, stream);
+    DbpExec ex;
+    ex.no_workspace = true;     // no operator buffer either
+    dbp_status st = dbp_run_internal(h, &dd, DBP_K_ADMM_DL, H, s, x, nullptr, nullptr, (cudaStream_t)stream, &ex,
+                                     nullptr, nullptr);
     if (st != DBP_OK) return st;
     if (!(d->flags & DBP_FLAG_NORMALIZE) || (long long)d->W * d->N == 0) return DBP_OK;
 

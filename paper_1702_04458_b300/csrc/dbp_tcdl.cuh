@@ -90,6 +90,96 @@ __device__ __forceinline__ void tcdl_apply(const uint32_t (&qh)[2][4][4], const 
         }
 }
 
+// B_c^{-1} of Alg. 3 for one cluster from the staged H_c (S x 16, row pitch
+// 16): the Gram conj(H_c^H H_c) on the tensor cores (3 x TF32), plus delta on
+// the diagonal, row-major into Qs (pitch QP), then the column-split
+// Gauss-Jordan; lane (ur, gc) returns entries (ur, 8 gc + i) of the inverse in
+// A.  An FP32 pivot below 2^-12 of the largest diagonal entry recomputes this
+// cluster's B_c and its inverse in FP64 (counted in *retries; Vb is scratch).
+// Shared by the downlink kernel and the operator kernel (dbp_factor.cuh).
+__device__ __forceinline__ void tcdl_operator(const float2 *Hs, int S, float2 *Qs, float2 *Vb, int lane, float f_delta,
+                                              double delta, bool valid, unsigned int *retries, float2 (&A)[8]) {
+    using C2 = float2;
+    constexpr int QP = TcDl::QP;
+    const int g = lane >> 2, t = lane & 3;
+    const int ur = lane & 15, gc = lane >> 4;
+    // Gram G = H_c^H H_c on the tensor cores: m-tile mt = users
+    // 8 mt .. 8 mt + 7 (rows), n-tile nt = users 8 nt .. (columns).
+    float gacc[2][2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) gacc[mt][nt][i] = 0.f;
+    for (int s0 = 0; s0 < S; s0 += 4) {
+        uint32_t ah[2][4], al[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            float a[4];
+            hh16_frag(Hs, s0, 8 * mt + g, t, a);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) split3(a[i], ah[mt][i], al[mt][i]);
+        }
+        // the B fragment of H_c for n-tile nt holds the values a[0], a[2]
+        // of m-tile nt
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+                mma3(gacc[mt][nt], ah[mt], al[mt], ah[nt][0], ah[nt][2], al[nt][0], al[nt][2]);
+    }
+    // B_c = conj(G) + delta I, row-major into Qs
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int row = 8 * mt + g, col = 8 * nt + 2 * t + q;
+                C2 v = make_float2(gacc[mt][nt][q], -gacc[mt][nt][2 + q]);
+                if (row == col) v.x += f_delta;
+                Qs[row * QP + col] = v;
+            }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) ld2(&Qs[ur * QP + 8 * gc + i], A[i], A[i + 1]);
+    float dmax = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        if (8 * gc + i == ur) dmax = A[i].x;
+#pragma unroll
+    for (int m2 = 16; m2 > 0; m2 >>= 1) dmax = fmaxf(dmax, shfl_x(dmax, m2));
+    const float min_piv = gj_split<16>(A, ur, gc);
+    __syncwarp();
+    if (!(min_piv >= 0x1p-12f * dmax) && valid) {
+        // FP64 retry: B_c and its inverse again in FP64 (row ur per lane)
+        double2 D[16];
+#pragma unroll
+        for (int v = 0; v < 16; ++v) D[v] = make_double2(0.0, 0.0);
+        for (int r = 0; r < S; ++r) {
+            const C2 hu = Hs[r * 16 + ur];
+            const double2 hd = make_double2(hu.x, hu.y);
+#pragma unroll
+            for (int v = 0; v < 16; ++v) {
+                const C2 hv = Hs[r * 16 + v];
+                cmacc(D[v], make_double2(hv.x, hv.y), hd);      // conj(H[r][v]) H[r][ur]
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 16; ++v)
+            if (v == ur) D[v].x += delta;
+        gj_invert<16>(D, reinterpret_cast<double2 *>(Vb), ur, lane);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const double2 dv = gc ? D[8 + i] : D[i];
+            A[i] = make_float2((float)dv.x, (float)dv.y);
+        }
+        if (lane == 0 && retries) atomicAdd(retries, 1u);
+        __syncwarp();
+    }
+}
+
 // (a template only so that every translation unit may include it)
 template <int UT>
 __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
@@ -168,83 +258,8 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
                 Qs[ur * QP + 8 * gc + i + 1] = make_float2(q.z, q.w);
             }
         } else {
-            // Gram G = H_c^H H_c on the tensor cores: m-tile mt = users
-            // 8 mt .. 8 mt + 7 (rows), n-tile nt = users 8 nt .. (columns).
-            float gacc[2][2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) gacc[mt][nt][i] = 0.f;
-            for (int s0 = 0; s0 < S; s0 += 4) {
-                uint32_t ah[2][4], al[2][4];
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    float a[4];
-                    hh16_frag(Hs, s0, 8 * mt + g, t, a);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) split3(a[i], ah[mt][i], al[mt][i]);
-                }
-                // the B fragment of H_c for n-tile nt holds the values a[0], a[2]
-                // of m-tile nt
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                    for (int nt = 0; nt < 2; ++nt)
-                        mma3(gacc[mt][nt], ah[mt], al[mt], ah[nt][0], ah[nt][2], al[nt][0], al[nt][2]);
-            }
-            // B_c = conj(G) + rho^{-1} I, row-major into Qs
-            const float delta = p.f_delta;
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const int row = 8 * mt + g, col = 8 * nt + 2 * t + q;
-                        C2 v = make_float2(gacc[mt][nt][q], -gacc[mt][nt][2 + q]);
-                        if (row == col) v.x += delta;
-                        Qs[row * QP + col] = v;
-                    }
-            __syncwarp();
             C2 A[8];
-#pragma unroll
-            for (int i = 0; i < 8; i += 2) ld2(&Qs[ur * QP + 8 * gc + i], A[i], A[i + 1]);
-            float dmax = 0.f;
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                if (8 * gc + i == ur) dmax = A[i].x;
-#pragma unroll
-            for (int m2 = 16; m2 > 0; m2 >>= 1) dmax = fmaxf(dmax, shfl_x(dmax, m2));
-            const float min_piv = gj_split<16>(A, ur, gc);
-            __syncwarp();
-            if (!(min_piv >= 0x1p-12f * dmax) && valid) {
-                // FP64 retry: B_c and its inverse again in FP64 (row ur per lane)
-                double2 D[16];
-#pragma unroll
-                for (int v = 0; v < 16; ++v) D[v] = make_double2(0.0, 0.0);
-                for (int r = 0; r < S; ++r) {
-                    const C2 hu = Hs[r * 16 + ur];
-                    const double2 hd = make_double2(hu.x, hu.y);
-#pragma unroll
-                    for (int v = 0; v < 16; ++v) {
-                        const C2 hv = Hs[r * 16 + v];
-                        cmacc(D[v], make_double2(hv.x, hv.y), hd);      // conj(H[r][v]) H[r][ur]
-                    }
-                }
-#pragma unroll
-                for (int v = 0; v < 16; ++v)
-                    if (v == ur) D[v].x += p.delta;
-                gj_invert<16>(D, reinterpret_cast<double2 *>(Vb), ur, lane);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const double2 dv = gc ? D[8 + i] : D[i];
-                    A[i] = make_float2((float)dv.x, (float)dv.y);
-                }
-                if (lane == 0 && p.retries) atomicAdd(p.retries, 1u);
-                __syncwarp();
-            }
+            tcdl_operator(Hs, S, Qs, Vb, lane, p.f_delta, p.delta, valid, p.retries, A);
 #pragma unroll
             for (int i = 0; i < 8; ++i) Qs[ur * QP + 8 * gc + i] = A[i];
             if (p.factor_mode == 1 && frow != nullptr) {

@@ -251,10 +251,18 @@ __device__ __forceinline__ void mf_mma(const uint32_t *Hs, int hp, int h_rows, c
 // multiply-add as every other lane.  FP32 reciprocal via __frcp_rn.  Returns
 // the smallest pivot's real part (all pivots are real and positive for a
 // Hermitian positive definite matrix).
+//
+// Every row is kept rotated so that step k's pivot column sits in R[0]: at
+// the start of step k, R[j] holds column (k + j) mod UT.  The step writes the
+// updated column k + j + 1 into R[j] and the new column k into R[UT - 1],
+// which is the rotation for step k + 1; after UT steps the columns are back
+// in order.  Every step is then the same code with fixed register indices,
+// so the step loop stays rolled (a fully unrolled UT = 32 elimination is
+// several thousand instructions and thrashes the instruction cache).
 template <int UT>
 __device__ __forceinline__ float gj_invert_f(float2 (&R)[UT], float2 *scratch, int u, int lane) {
     float min_piv = 3.0e38f;
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < UT; ++k) {
         if (lane == k) {
 #pragma unroll
@@ -262,7 +270,7 @@ __device__ __forceinline__ float gj_invert_f(float2 (&R)[UT], float2 *scratch, i
                 *reinterpret_cast<float4 *>(&scratch[j]) = make_float4(R[j].x, R[j].y, R[j + 1].x, R[j + 1].y);
         }
         __syncwarp();
-        const float2 pk = scratch[k];
+        const float2 pk = scratch[0];
         min_piv = fminf(min_piv, pk.x);
         const float d = __frcp_rn(fmaf(pk.x, pk.x, pk.y * pk.y));
         const float2 inv = make_float2(pk.x * d, -pk.y * d);
@@ -271,19 +279,107 @@ __device__ __forceinline__ float gj_invert_f(float2 (&R)[UT], float2 *scratch, i
         if (me) {
             f = make_float2(1.f - inv.x, -inv.y);
         } else {
-            f = make_float2(R[k].x * inv.x - R[k].y * inv.y, R[k].x * inv.y + R[k].y * inv.x);
+            f = make_float2(R[0].x * inv.x - R[0].y * inv.y, R[0].x * inv.y + R[0].y * inv.x);
         }
+        const float2 nf = make_float2(-f.x, -f.y);
 #pragma unroll
         for (int j = 0; j < UT; j += 2) {
             float2 a, b;
             ld2(&scratch[j], a, b);
-            if (j != k) cmac(R[j], make_float2(-f.x, -f.y), a);
-            if (j + 1 != k) cmac(R[j + 1], make_float2(-f.x, -f.y), b);
+            if (j > 0) {
+                cmac(R[j], nf, a);
+                R[j - 1] = R[j];
+            }
+            cmac(R[j + 1], nf, b);
+            R[j] = R[j + 1];
         }
-        R[k] = me ? inv : make_float2(-f.x, -f.y);
+        R[UT - 1] = me ? inv : nf;
         __syncwarp();
     }
     return min_piv;
+}
+
+// The per-cluster operator from the staged block H_c (row pitch hp, h_rows
+// rows with zero padding past S), row u per lane (every lane group g holds a
+// copy): B_c^{-1} for Alg. 1 (B_c = H_c^H H_c + delta I) and Alg. 3 (B_c =
+// conj(H_c^H H_c) + delta I), G_c = H_c^H H_c for Alg. 2.  The Gram runs on
+// the tensor cores for 16-bit inputs.  An FP32 pivot below 2^-12 of the
+// largest diagonal entry recomputes this cluster's Gram and inverse in FP64
+// (counted in *retries).  Shared by the fused kernel and the operator kernel
+// (dbp_factor.cuh), so both give the same bits.
+template <int UT, typename TIn, int ALG>
+__device__ __forceinline__ void cluster_operator(const TIn *Hs, int hp, int h_rows, int S, float2 *Gm, float2 *Vb,
+                                                 int lane, int u, int g, float f_delta, double delta, bool valid,
+                                                 unsigned int *retries, float2 (&R)[UT]) {
+    using C2 = float2;
+    constexpr bool MMA = InTraits<TIn>::mma;
+    // ---- Gram (+ diagonal loading) ----
+    if constexpr (MMA) {
+        gram_mma<UT, TIn>(reinterpret_cast<const uint32_t *>(Hs), hp, h_rows, Gm, lane, u, R);
+    } else {
+#pragma unroll
+        for (int v = 0; v < UT; ++v) R[v] = make_float2(0.f, 0.f);
+        for (int r = g; r < S; r += Tile<UT>::G) {
+            const C2 hu = to_f2(Hs[r * hp + u]);
+#pragma unroll
+            for (int v = 0; v < UT; v += 2) {
+                C2 a, bb;
+                ld2(reinterpret_cast<const C2 *>(&Hs[r * hp + v]), a, bb);
+                if (ALG == ALG_ADMM_DL) {
+                    cmacc(R[v], a, hu);
+                    cmacc(R[v + 1], bb, hu);
+                } else {
+                    cmacc(R[v], hu, a);
+                    cmacc(R[v + 1], hu, bb);
+                }
+            }
+        }
+#pragma unroll
+        for (int m = UT; m < 32; m <<= 1) {
+#pragma unroll
+            for (int v = 0; v < UT; ++v) {
+                R[v].x += shfl_x(R[v].x, m);
+                R[v].y += shfl_x(R[v].y, m);
+            }
+        }
+    }
+    float dmax = 0.f;
+#pragma unroll
+    for (int v = 0; v < UT; ++v)
+        if (v == u) {
+            R[v].x += f_delta;
+            dmax = R[v].x;
+        }
+    if (ALG == ALG_ADMM_UL || ALG == ALG_ADMM_DL) {
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) dmax = fmaxf(dmax, shfl_x(dmax, m));
+        const float min_piv = gj_invert_f<UT>(R, Vb, u, lane);
+        if (valid && !(min_piv >= 0x1p-12f * dmax)) {
+            // FP64 retry: recompute this cluster's Gram and inverse in FP64.
+            double2 D[UT];
+#pragma unroll
+            for (int v = 0; v < UT; ++v) D[v] = make_double2(0.0, 0.0);
+            for (int r = 0; r < S; ++r) {
+                const float2 hu = to_f2(Hs[r * hp + u]);
+                const double2 hd = make_double2(hu.x, hu.y);
+#pragma unroll
+                for (int v = 0; v < UT; ++v) {
+                    const float2 hv = to_f2(Hs[r * hp + v]);
+                    const double2 vd = make_double2(hv.x, hv.y);
+                    if (ALG == ALG_ADMM_DL) cmacc(D[v], vd, hd);
+                    else cmacc(D[v], hd, vd);
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < UT; ++v)
+                if (v == u) D[v].x += delta;
+            __syncwarp();
+            gj_invert<UT>(D, reinterpret_cast<double2 *>(Vb), u, lane);
+#pragma unroll
+            for (int v = 0; v < UT; ++v) R[v] = make_float2((float)D[v].x, (float)D[v].y);
+            if (lane == 0 && retries) atomicAdd(retries, 1u);
+        }
+    }
 }
 
 template <int UT> struct TmaCfg {
@@ -400,74 +496,8 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
                 for (int v = 0; v < UT; ++v) R[v] = make_float2(0.f, 0.f);
             }
         } else {
-        // ---- Gram (+ diagonal loading) ----
-        if constexpr (MMA) {
-            gram_mma<UT, TIn>(reinterpret_cast<const uint32_t *>(Hs), hp, p.h_rows, Gm, lane, u, R);
-        } else {
-#pragma unroll
-            for (int v = 0; v < UT; ++v) R[v] = make_float2(0.f, 0.f);
-            for (int r = g; r < S; r += K::G) {
-                const C2 hu = to_f2(Hs[r * hp + u]);
-#pragma unroll
-                for (int v = 0; v < UT; v += 2) {
-                    C2 a, bb;
-                    ld2(reinterpret_cast<const C2 *>(&Hs[r * hp + v]), a, bb);
-                    if (ALG == ALG_ADMM_DL) {
-                        cmacc(R[v], a, hu);
-                        cmacc(R[v + 1], bb, hu);
-                    } else {
-                        cmacc(R[v], hu, a);
-                        cmacc(R[v + 1], hu, bb);
-                    }
-                }
-            }
-#pragma unroll
-            for (int m = UT; m < 32; m <<= 1) {
-#pragma unroll
-                for (int v = 0; v < UT; ++v) {
-                    R[v].x += shfl_x(R[v].x, m);
-                    R[v].y += shfl_x(R[v].y, m);
-                }
-            }
-        }
-        const float delta = p.f_delta;
-        float dmax = 0.f;
-#pragma unroll
-        for (int v = 0; v < UT; ++v)
-            if (v == u) {
-                R[v].x += delta;
-                dmax = R[v].x;
-            }
-        if (ALG == ALG_ADMM_UL || ALG == ALG_ADMM_DL) {
-#pragma unroll
-            for (int m = 16; m > 0; m >>= 1) dmax = fmaxf(dmax, shfl_x(dmax, m));
-            const float min_piv = gj_invert_f<UT>(R, Vb, u, lane);
-            if (valid && !(min_piv >= 0x1p-12f * dmax)) {
-                // FP64 retry: recompute this cluster's Gram and inverse in FP64.
-                double2 D[UT];
-#pragma unroll
-                for (int v = 0; v < UT; ++v) D[v] = make_double2(0.0, 0.0);
-                for (int r = 0; r < S; ++r) {
-                    const float2 hu = to_f2(Hs[r * hp + u]);
-                    const double2 hd = make_double2(hu.x, hu.y);
-#pragma unroll
-                    for (int v = 0; v < UT; ++v) {
-                        const float2 hv = to_f2(Hs[r * hp + v]);
-                        const double2 vd = make_double2(hv.x, hv.y);
-                        if (ALG == ALG_ADMM_DL) cmacc(D[v], vd, hd);
-                        else cmacc(D[v], hd, vd);
-                    }
-                }
-#pragma unroll
-                for (int v = 0; v < UT; ++v)
-                    if (v == u) D[v].x += p.delta;
-                __syncwarp();
-                gj_invert<UT>(D, reinterpret_cast<double2 *>(Vb), u, lane);
-#pragma unroll
-                for (int v = 0; v < UT; ++v) R[v] = make_float2((float)D[v].x, (float)D[v].y);
-                if (lane == 0 && p.retries) atomicAdd(p.retries, 1u);
-            }
-        }
+        cluster_operator<UT, TIn, ALG>(Hs, hp, p.h_rows, S, Gm, Vb, lane, u, g, p.f_delta, p.delta, valid,
+                                       p.retries, R);
         if (p.factor_mode == 1 && frow != nullptr && g == 0) {
 #pragma unroll
             for (int v = 0; v < UT; v += 2)

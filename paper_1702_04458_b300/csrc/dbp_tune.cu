@@ -2,9 +2,11 @@
 // remember the fastest per frame shape on the handle.
 //
 // The candidates are every kernel path (tensor-core, broadcast, persistent
-// bulk-copy, generic) with 4, 8 and 16 warps per CTA, and for the generic
-// kernel also thread-block clusters of 2, 4, 8 and 16 CTAs.  A candidate
-// that does not accept the shape is skipped.  Each is run twice untimed and
+// bulk-copy, generic) with 4, 8 and 16 warps per CTA, the tensor-core and
+// bulk-copy paths with and without the separate operator kernel, and for the
+// generic kernel also thread-block clusters of 2, 4, 8 and 16 CTAs.  A
+// candidate that does not accept the shape is skipped (one whose operator
+// kernel is not available runs as the same choice without it).  Each is run twice untimed and
 // then `reps` times between two CUDA events on the caller's stream.
 #include <cuda_runtime.h>
 
@@ -24,16 +26,21 @@ std::vector<dbp_tuning> candidates(int C) {
     const int paths[] = {DBP_PATH_MMA, DBP_PATH_BCAST, DBP_PATH_TMA, DBP_PATH_GENERIC};
     const int wpcs[] = {0, 4, 16};
     for (int k : paths)
-        for (int w : wpcs) out.push_back(dbp_tuning{DBP_MAP_CTA, 0, w, k});
+        for (int w : wpcs) {
+            out.push_back(dbp_tuning{DBP_MAP_CTA, 0, w, k, DBP_PREFACTOR_OFF});
+            if (k == DBP_PATH_MMA || k == DBP_PATH_TMA)
+                out.push_back(dbp_tuning{DBP_MAP_CTA, 0, w, k, DBP_PREFACTOR_ON});
+        }
     for (int cl = 2; cl <= 16; cl *= 2)
-        if (C % cl == 0) out.push_back(dbp_tuning{DBP_MAP_CLUSTER, cl, 0, DBP_PATH_GENERIC});
+        if (C % cl == 0) out.push_back(dbp_tuning{DBP_MAP_CLUSTER, cl, 0, DBP_PATH_GENERIC, DBP_PREFACTOR_OFF});
     return out;
 }
 
 bool valid_tuning(const dbp_tuning &t) {
     return t.mapping >= DBP_MAP_AUTO && t.mapping <= DBP_MAP_CLUSTER && t.cluster_size >= 0 &&
            t.cluster_size <= 16 && t.warps_per_cta >= 0 && t.warps_per_cta <= 32 &&
-           t.kernel >= DBP_PATH_AUTO && t.kernel <= DBP_PATH_BCAST;
+           t.kernel >= DBP_PATH_AUTO && t.kernel <= DBP_PATH_BCAST && t.prefactor >= DBP_PREFACTOR_AUTO &&
+           t.prefactor <= DBP_PREFACTOR_ON;
 }
 
 }  // namespace
@@ -142,7 +149,7 @@ dbp_status dbp_autotune_save(dbp_handle_t h, const char *path) {
         const dbp_tuning &t = kv.second;
         f << std::get<0>(k) << ' ' << std::get<1>(k) << ' ' << std::get<2>(k) << ' ' << std::get<3>(k) << ' '
           << std::get<4>(k) << ' ' << std::get<5>(k) << ' ' << t.mapping << ' ' << t.cluster_size << ' '
-          << t.warps_per_cta << ' ' << t.kernel << '\n';
+          << t.warps_per_cta << ' ' << t.kernel << ' ' << t.prefactor << '\n';
     }
     return f ? DBP_OK : DBP_ERR_INVALID_ARG;
 }
@@ -168,7 +175,8 @@ dbp_status dbp_autotune_load(dbp_handle_t h, const char *path) {
         int kind, B, C, U, N, prec;
         dbp_tuning t{};
         std::string extra;
-        if (!(is >> kind >> B >> C >> U >> N >> prec >> t.mapping >> t.cluster_size >> t.warps_per_cta >> t.kernel) ||
+        if (!(is >> kind >> B >> C >> U >> N >> prec >> t.mapping >> t.cluster_size >> t.warps_per_cta >> t.kernel >>
+              t.prefactor) ||
             (is >> extra) || kind < 0 || kind > 2 || !valid_tuning(t)) {
             h->err = std::string("dbp_autotune_load: malformed line ") + std::to_string(lineno) + " of " + path;
             return DBP_ERR_INVALID_ARG;

@@ -64,7 +64,7 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu\n", offsetof(dbp_frame_desc, flags), offsetof(dbp_frame_desc, rho),
          offsetof(dbp_frame_desc, Es), offsetof(dbp_frame_desc, box_r), offsetof(dbp_frame_desc, eps));
   printf("%zu\n", offsetof(dbp_config, hbm_budget_bytes));
-  printf("%zu\n", offsetof(dbp_tuning, kernel));
+  printf("%zu %zu\n", offsetof(dbp_tuning, kernel), offsetof(dbp_tuning, prefactor));
   printf("%zu %zu %zu %zu\n", sizeof(dbp_request), offsetof(dbp_request, channel_key),
          sizeof(dbp_result), offsetof(dbp_result, finish_us));
   printf("%zu %zu %zu\n", sizeof(dbp_graph_item), offsetof(dbp_graph_item, H), offsetof(dbp_graph_item, beta_out));
@@ -82,12 +82,12 @@ int main(void) {
     assert vals[:3] == [ctypes.sizeof(D), ctypes.sizeof(pkg.dbp_config), ctypes.sizeof(pkg.dbp_tuning)]
     assert vals[3:8] == [D.flags.offset, D.rho.offset, D.Es.offset, D.box_r.offset, D.eps.offset]
     assert vals[8] == pkg.dbp_config.hbm_budget_bytes.offset
-    assert vals[9] == pkg.dbp_tuning.kernel.offset
+    assert vals[9:11] == [pkg.dbp_tuning.kernel.offset, pkg.dbp_tuning.prefactor.offset]
     R = pkg.dbp_request
-    assert vals[10:14] == [ctypes.sizeof(R), R.channel_key.offset, ctypes.sizeof(pkg.dbp_result),
+    assert vals[11:15] == [ctypes.sizeof(R), R.channel_key.offset, ctypes.sizeof(pkg.dbp_result),
                           pkg.dbp_result.finish_us.offset]
     G = pkg.dbp_graph_item
-    assert vals[14:17] == [ctypes.sizeof(G), G.H.offset, G.beta_out.offset]
+    assert vals[15:18] == [ctypes.sizeof(G), G.H.offset, G.beta_out.offset]
 
 
 def test_enum_values_match_the_header(pkg):

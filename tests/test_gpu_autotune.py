@@ -53,7 +53,7 @@ def test_autotune_choice_is_used_by_auto_calls(dbp, handle, kind, U, C):
     # a different W of the same shape uses the tuned choice
     d2, H2, y2 = _ul(dbp, 77, 14, 128, C, U, 16, d.T_max, seed=1600 + U)
     auto = _run(dbp, handle, fn, d2, H2, y2, U)
-    dbp.dbp_set_tuning(handle, best.mapping, best.cluster_size, best.warps_per_cta, best.kernel)
+    dbp.dbp_set_tuning(handle, best.mapping, best.cluster_size, best.warps_per_cta, best.kernel, best.prefactor)
     forced = _run(dbp, handle, fn, d2, H2, y2, U)
     dbp.dbp_set_tuning(handle)
     assert torch.equal(auto[0], forced[0]) and torch.equal(auto[1], forced[1])
@@ -68,13 +68,13 @@ def test_autotune_table_round_trip(dbp, handle):
         dbp.dbp_autotune_save(handle, path)
         line = open(path).read().split()
         assert [int(v) for v in line] == [dbp.DBP_KIND_UPLINK_ADMM, 128, 8, 8, 14, dbp.DBP_FP32, best.mapping,
-                                          best.cluster_size, best.warps_per_cta, best.kernel]
+                                          best.cluster_size, best.warps_per_cta, best.kernel, best.prefactor]
         dbp.dbp_autotune_clear(handle)
         dbp.dbp_autotune_load(handle, path)
         dbp.dbp_autotune_save(handle, path + "2")
         assert open(path + "2").read() == open(path).read()
         bad = os.path.join(tmp, "bad.txt")
-        open(bad, "w").write("0 128 8 8 14 0 0 0 0\n")          # nine fields
+        open(bad, "w").write("0 128 8 8 14 0 0 0 0 0\n")        # ten fields
         with pytest.raises(dbp.DbpError) as ei:
             dbp.dbp_autotune_load(handle, bad)
         assert ei.value.status == dbp.DBP_ERR_INVALID_ARG
