@@ -93,6 +93,19 @@ def uplink_frame(W: int, N: int, B: int, U: int, M: int, snr_db: float,
             "W": W, "N": N, "B": B, "U": U, "M": M, "snr_db": snr_db}
 
 
+def at_snr(f: dict, snr_db: float, seed: int) -> dict:
+    """The same uplink frame (channel and transmitted symbols) at another
+    SNR: y = H s + n with fresh seeded noise of the variance snr_db gives."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    N0 = noise_variance(snr_db, f["U"], f["Es"])
+    clean = np.matmul(f["H"], np.swapaxes(f["s"], 1, 2)).swapaxes(1, 2)   # [W][N][B]
+    out = dict(f)
+    out["y"] = clean + _cn(rng, clean.shape, N0)
+    out["N0"] = N0
+    out["snr_db"] = snr_db
+    return out
+
+
 def downlink_frame(W: int, N: int, B: int, U: int, M: int, seed: int,
                    Es: float = 1.0) -> dict:
     """One downlink frame: uplink-layout channel H (H^d = H^T) and symbols s."""

@@ -87,3 +87,34 @@ def test_fp16_ber_within_fp32_interval(dbp, handle):
     nbits = W * N * U * 6
     lo, hi = _wilson(errs["fp32"], nbits)
     assert lo <= errs["fp16"] / nbits <= hi, errs
+
+
+@pytest.mark.parametrize("snr", [10.0, 14.0, 18.0, 22.0])
+def test_16bit_ber_within_fp32_interval_over_snr(dbp, handle, snr):
+    """B=256, C=8, U=32, 64-QAM on one channel at several SNRs (fresh noise
+    each): FP16 and BF16 inputs give BERs inside the FP32 path's 95 %
+    interval."""
+    W, N, B, C, U, M = 400, 14, 256, 8, 32, 64
+    base = synth.uplink_frame(W, N, B, U, M, 20.0, seed=3200)
+    f = synth.at_snr(base, snr, seed=3201 + int(snr))
+    errs = {}
+    for prec in ("fp32", "fp16", "bf16"):
+        if prec == "fp32":
+            Hd = torch.from_numpy(f["H"].astype(np.complex64)).cuda()
+            yd = torch.from_numpy(f["y"].astype(np.complex64)).cuda()
+            code = dbp.DBP_FP32
+        else:
+            dt = torch.float16 if prec == "fp16" else torch.bfloat16
+            Hd = torch.from_numpy(np.stack([f["H"].real, f["H"].imag], -1).astype(np.float32)).to(dt).cuda()
+            yd = torch.from_numpy(np.stack([f["y"].real, f["y"].imag], -1).astype(np.float32)).to(dt).cuda()
+            code = dbp.DBP_FP16 if prec == "fp16" else dbp.DBP_BF16
+        x = torch.zeros((W, N, U), dtype=torch.complex64, device="cuda")
+        lab = torch.zeros((W, N, U), dtype=torch.uint8, device="cuda")
+        d = dbp.frame_desc(B, C, U, W, N, qam_order=M, T_max=3, N0=f["N0"], precision=code)
+        dbp.dbp_uplink_admm(handle, d, Hd, yd, x, lab)
+        torch.cuda.synchronize()
+        errs[prec] = oracle.bit_errors(lab.cpu().numpy(), f["labels"])
+    nbits = W * N * U * 6
+    lo, hi = _wilson(errs["fp32"], nbits)
+    for prec in ("fp16", "bf16"):
+        assert lo <= errs[prec] / nbits <= hi, (snr, errs)

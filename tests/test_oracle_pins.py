@@ -522,3 +522,15 @@ def test_llr_stats_mmse_monte_carlo():
     nu2_emp = np.mean(np.abs(x - mu[0] * s) ** 2, axis=0)
     np.testing.assert_allclose(mu_emp, mu[0], rtol=0.01)
     np.testing.assert_allclose(nu2_emp, nu2[0], rtol=0.03)
+
+
+def test_synth_at_snr_keeps_channel_and_symbols():
+    """synth.at_snr: same H and transmitted symbols, y - H s has the noise
+    variance of the requested SNR (N0 = U Es / SNR)."""
+    f = synth.uplink_frame(80, 14, 16, 4, 16, 10.0, seed=11)
+    g = synth.at_snr(f, 25.0, seed=12)
+    assert np.array_equal(g["H"], f["H"]) and np.array_equal(g["labels"], f["labels"])
+    n = g["y"] - np.einsum("wbu,wnu->wnb", f["H"], f["s"])
+    N0 = 4 * 1.0 / 10 ** 2.5
+    assert abs(g["N0"] - N0) < 1e-15
+    assert abs(np.mean(np.abs(n) ** 2) / N0 - 1.0) < 0.02
