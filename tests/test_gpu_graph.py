@@ -130,3 +130,28 @@ def test_graph_rejects_a_bad_item(dbp, handle):
     assert "item 2" in dbp.dbp_last_error(handle)
     with pytest.raises(dbp.DbpError):
         dbp.dbp_graph_create(handle, items[:1], branches=17)
+
+
+def test_graph_with_operator_kernel_tuning(dbp, handle):
+    """With DBP_PREFACTOR_ON on the handle, frames captured into a graph run
+    without the separate operator kernel (no stream-ordered buffer inside a
+    capture) and still equal the single calls, which do use it."""
+    frames = _frames(dbp, 1500)
+    f = synth.downlink_frame(64, 14, 256, 16, 64, seed=1510)          # tensor-core downlink
+    frames.append(dict(kind=dbp.DBP_KIND_DOWNLINK_ADMM, desc=dbp.frame_desc(256, 16, 16, 64, 14, T_max=4),
+                       H=_dev(f["H"]), inp=_dev(f["s"]),
+                       out=torch.zeros((64, 14, 256), dtype=torch.complex64, device="cuda"),
+                       labels=None, beta=None))
+    dbp.dbp_set_tuning(handle, prefactor=dbp.DBP_PREFACTOR_ON)
+    try:
+        ref = _one_by_one(dbp, handle, frames)
+        g = dbp.dbp_graph_create(handle, _items(dbp, frames), 2)
+        try:
+            g.launch()
+            torch.cuda.synchronize()
+            for fr, (o, lab, beta) in zip(frames, ref):
+                assert torch.equal(fr["out"], o)
+        finally:
+            g.close()
+    finally:
+        dbp.dbp_set_tuning(handle)
