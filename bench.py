@@ -50,6 +50,7 @@ DL = Workload(B=256, C=16, U=16, W=1200, N=14, M=64, T=5)
 MIX = Workload(B=256, C=8, U=32, W=3300, N=14, M=64, T=3)
 MIX_SNR_DB = 20.0
 MIX_SWEEP_DB = (10.0, 14.0, 18.0, 22.0, 26.0, 30.0)
+MIX_SWEEP_MAX_FRAMES = 12      # 12 x 8.87 Mbit = 1.06e8 bits
 SNRS_DB = [float(2 * i) for i in range(11)]
 ROTATE = 8
 
@@ -443,32 +444,48 @@ def bench_mixed(dbp, h, stream, device, rank, args, hbm_peak, hbm_src, alu_peak)
         pp[name]["ber_within_fp32_ci95"] = bool(lo <= pp[name]["ber"] <= hi)
         pp[name]["speedup_vs_fp32"] = pp["fp32"]["ms_per_frame"] / pp[name]["ms_per_frame"]
     # BER over the 10-30 dB range of this workload: the same channel and
-    # symbols with fresh noise per SNR, every precision on the same frame
+    # symbols with fresh noise, every precision on the same noise; each point
+    # runs frames until the FP32 path has 200 bit errors or 1e8 bits
     sweep = []
+    precs = (("fp32", dbp.DBP_FP32), ("fp16", dbp.DBP_FP16), ("bf16", dbp.DBP_BF16))
+    dev_H = {}
+    for name, prec in precs:
+        if prec == dbp.DBP_FP32:
+            dev_H[name] = torch.from_numpy(f["H"].astype(np.complex64)).to(device)
+        else:
+            dt = torch.float16 if name == "fp16" else torch.bfloat16
+            dev_H[name] = torch.from_numpy(np.stack([f["H"].real, f["H"].imag], -1).astype(np.float32)).to(dt).to(device)
     for i, snr in enumerate(MIX_SWEEP_DB):
-        fs = synth.at_snr(f, snr, seed=synth.frame_seed(4, i) + 100000 * rank)
-        point = {"snr_db": snr}
-        for name, prec in (("fp32", dbp.DBP_FP32), ("fp16", dbp.DBP_FP16), ("bf16", dbp.DBP_BF16)):
-            if prec == dbp.DBP_FP32:
-                H = torch.from_numpy(fs["H"].astype(np.complex64)).to(device)
-                y = torch.from_numpy(fs["y"].astype(np.complex64)).to(device)
-            else:
-                dt = torch.float16 if name == "fp16" else torch.bfloat16
-                H = torch.from_numpy(np.stack([fs["H"].real, fs["H"].imag], -1).astype(np.float32)).to(dt).to(device)
-                y = torch.from_numpy(np.stack([fs["y"].real, fs["y"].imag], -1).astype(np.float32)).to(dt).to(device)
-            d = dbp.frame_desc(MIX.B, MIX.C, MIX.U, MIX.W, MIX.N, qam_order=MIX.M, T_max=MIX.T,
-                               precision=prec, rho=1.0, N0=fs["N0"], Es=1.0)
-            dbp.dbp_uplink_admm(h, d, H, y, x, lab, sp)
-            torch.cuda.synchronize(device)
-            errs = int(np.unpackbits(np.bitwise_xor(lab.cpu().numpy(), fs["labels"]).reshape(-1, 1), axis=1).sum())
-            point[name] = {"ber": errs / nbits, "bit_errors": errs}
-            del H, y
-        lo, hi = _binom_ci(point["fp32"]["bit_errors"], nbits)
+        errs = {name: 0 for name, _ in precs}
+        frames_run = 0
+        while frames_run < MIX_SWEEP_MAX_FRAMES and (errs["fp32"] < 200 or frames_run == 0):
+            fs = synth.at_snr(f, snr, seed=synth.frame_seed(4, i) + 1000 * frames_run + 100000 * rank)
+            for name, prec in precs:
+                if prec == dbp.DBP_FP32:
+                    y = torch.from_numpy(fs["y"].astype(np.complex64)).to(device)
+                else:
+                    dt = torch.float16 if name == "fp16" else torch.bfloat16
+                    y = torch.from_numpy(np.stack([fs["y"].real, fs["y"].imag], -1).astype(np.float32)).to(dt).to(device)
+                d = dbp.frame_desc(MIX.B, MIX.C, MIX.U, MIX.W, MIX.N, qam_order=MIX.M, T_max=MIX.T,
+                                   precision=prec, rho=1.0, N0=fs["N0"], Es=1.0)
+                dbp.dbp_uplink_admm(h, d, dev_H[name], y, x, lab, sp)
+                torch.cuda.synchronize(device)
+                errs[name] += int(np.unpackbits(np.bitwise_xor(lab.cpu().numpy(), fs["labels"]).reshape(-1, 1),
+                                                axis=1).sum())
+                del y
+            frames_run += 1
+        bits = frames_run * nbits
+        point = {"snr_db": snr, "frames": frames_run, "bits": bits}
+        for name, _ in precs:
+            point[name] = {"ber": errs[name] / bits, "bit_errors": errs[name]}
+        lo, hi = _binom_ci(errs["fp32"], bits)
         point["fp32"]["ber_ci95"] = [lo, hi]
         for name in ("fp16", "bf16"):
             point[name]["within_fp32_ci95"] = bool(lo <= point[name]["ber"] <= hi)
         sweep.append(point)
-    out["ber_sweep"] = {"bits_per_point": nbits, "points": sweep,
+    del dev_H
+    out["ber_sweep"] = {"bits_per_frame": nbits, "rule": "frames until 200 FP32 bit errors or "
+                        f"{MIX_SWEEP_MAX_FRAMES} frames ({MIX_SWEEP_MAX_FRAMES * nbits:.2e} bits)", "points": sweep,
                         "all_within_fp32_ci95": all(p[n]["within_fp32_ci95"] for p in sweep
                                                     for n in ("fp16", "bf16"))}
     out["fp64_retries"] = dbp.dbp_fp64_retries(h)
