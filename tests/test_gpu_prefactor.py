@@ -177,3 +177,24 @@ def test_tuning_rejects_bad_prefactor(dbp, handle):
         dbp.dbp_set_tuning(handle, prefactor=3)
     assert ei.value.status == dbp.DBP_ERR_INVALID_ARG
     dbp.dbp_set_tuning(handle)
+
+
+def test_operator_kernel_with_power_normalisation(dbp, handle):
+    """The downlink with the per-frame power normalisation: x and beta are
+    the same bits with and without the operator kernel."""
+    f = synth.downlink_frame(120, 14, 256, 16, 64, seed=2500)
+    H, s = _dev(f["H"], "fp32"), _dev(f["s"], "fp32")
+    d = dbp.frame_desc(256, 16, 16, 120, 14, T_max=4, rho=1.0, flags=dbp.DBP_FLAG_NORMALIZE)
+    outs = []
+    for pf in (dbp.DBP_PREFACTOR_OFF, dbp.DBP_PREFACTOR_ON):
+        x = torch.zeros((120, 14, 256), dtype=torch.complex64, device="cuda")
+        beta = torch.zeros(1, dtype=torch.float64, device="cuda")
+        try:
+            dbp.dbp_set_tuning(handle, prefactor=pf)
+            dbp.dbp_downlink_admm(handle, d, H, s, x, beta)
+            torch.cuda.synchronize()
+        finally:
+            dbp.dbp_set_tuning(handle)
+        outs.append((x, beta))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    assert abs(float((outs[1][0].abs() ** 2).mean()) - 1.0) < 1e-4
