@@ -927,7 +927,8 @@ def main(argv=None) -> int:
         for key, kind, dd in (("admm_ul", dbp.DBP_KIND_UPLINK_ADMM, da0), ("cg_ul", dbp.DBP_KIND_UPLINK_CG, dc0)):
             t = dbp.dbp_autotune(h, kind, dd, d0["H"], d0["y"], xa, la, sp, 5)
             tuned[key] = {"kernel": names.get(t.kernel, t.kernel), "mapping": t.mapping,
-                          "cluster_size": t.cluster_size, "warps_per_cta": t.warps_per_cta}
+                          "cluster_size": t.cluster_size, "warps_per_cta": t.warps_per_cta,
+                          "prefactor": t.prefactor}
         torch.cuda.synchronize(device)
 
     for k in range(args.warmup):
@@ -993,7 +994,7 @@ def main(argv=None) -> int:
         if args.kernel == "auto" and not args.no_autotune:
             t = dbp.dbp_autotune(h, dbp.DBP_KIND_DOWNLINK_ADMM, ddesc, ddev[0]["H"], ddev[0]["s"], xd, None, sp, 3)
             dl_tuned = {"kernel": t.kernel, "mapping": t.mapping, "cluster_size": t.cluster_size,
-                        "warps_per_cta": t.warps_per_cta}
+                        "warps_per_cta": t.warps_per_cta, "prefactor": t.prefactor}
         for k in range(args.warmup):
             dbp.dbp_downlink_admm(h, ddesc, ddev[k % ROTATE]["H"], ddev[k % ROTATE]["s"], xd, None, sp)
         torch.cuda.synchronize(device)
@@ -1005,11 +1006,27 @@ def main(argv=None) -> int:
         e1.record(stream)
         torch.cuda.synchronize(device)
         dl_ms = e0.elapsed_time(e1) / KD
+        # throughput: consecutive frames alternating over two streams (own
+        # output buffers), as in the uplink step
+        xd2 = torch.empty_like(xd)
+        e0.record(stream)
+        side.wait_event(e0)
+        for k in range(KD):
+            st_k = stream if k % 2 == 0 else side
+            dbp.dbp_downlink_admm(h, ddesc, ddev[k % ROTATE]["H"], ddev[k % ROTATE]["s"],
+                                  xd if k % 2 == 0 else xd2, None, st_k.cuda_stream)
+        stream.wait_stream(side)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        dl_ms2 = e0.elapsed_time(e1) / KD
         downlink = {"workload": workload_name(DL, "downlink ADMM T=5"),
-                    "value": detected_bits(DL) / (dl_ms / 1e3) / 1e9, "unit": "Gbit/s (precoded)",
-                    "ms_per_frame": dl_ms, "launches": KD, "autotuned": dl_tuned,
+                    "value": detected_bits(DL) / (dl_ms2 / 1e3) / 1e9, "unit": "Gbit/s (precoded)",
+                    "ms_per_frame": dl_ms2, "ms_per_frame_one_stream": dl_ms,
+                    "timing": f"{KD} frames alternating over two streams (value); {KD} back-to-back "
+                              "launches on one stream (ms_per_frame_one_stream, the roofline's duration)",
+                    "launches": KD, "autotuned": dl_tuned,
                     "roofline": roofline("admm_dl", "admm_dl", DL, dl_ms, hbm_peak, hbm_src, alu_peak)}
-        del ddev, xd
+        del ddev, xd, xd2
         torch.cuda.empty_cache()
 
     # ---- 16-bit inputs vs FP32 (B=256, C=8, U=32, 3300 x 14, ADMM T=3) ------

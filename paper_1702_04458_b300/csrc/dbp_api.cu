@@ -835,6 +835,18 @@ dbp_status run_host(dbp_context *h, const dbp_frame_desc *d, Kind kind, const vo
 
 }  // namespace
 
+bool dbp_prefactor_applies(dbp_context *h, const dbp_frame_desc *d, int kind, const dbp_tuning &t, const void *H,
+                           const void *vin, const void *out) {
+    std::string sink;
+    t_err_sink = &sink;
+    Shape s;
+    const bool a16 = aligned(H, 16) && aligned(vin, 16) && aligned(out, 16);
+    const bool ok = validate(h, d, (Kind)kind) == DBP_OK && choose_shape(h, d, (Kind)kind, a16, s, t) == DBP_OK &&
+                    prefactor_available(d, (Kind)kind, s, next_pow2_ut(d->U));
+    t_err_sink = nullptr;
+    return ok;
+}
+
 dbp_status dbp_run_internal(dbp_context *h, const dbp_frame_desc *d, int kind, const void *H, const void *vin,
                             void *out, uint8_t *labels, double *beta_out, cudaStream_t st, const DbpExec *ex,
                             bool *factor_used, std::string *err) {

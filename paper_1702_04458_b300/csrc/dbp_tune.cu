@@ -5,9 +5,10 @@
 // bulk-copy, generic) with 4, 8 and 16 warps per CTA, the tensor-core and
 // bulk-copy paths with and without the separate operator kernel, and for the
 // generic kernel also thread-block clusters of 2, 4, 8 and 16 CTAs.  A
-// candidate that does not accept the shape is skipped (one whose operator
-// kernel is not available runs as the same choice without it).  Each is run twice untimed and
-// then `reps` times between two CUDA events on the caller's stream.
+// candidate that does not accept the shape is skipped, and so is an
+// operator-kernel candidate where that kernel does not apply.  Each is run
+// twice untimed and then `reps` times between two CUDA events on the
+// caller's stream.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -82,6 +83,9 @@ dbp_status dbp_autotune(dbp_handle_t h, int32_t kind, const dbp_frame_desc *d, c
     float best_ms = -1.f;
     dbp_status st_out = DBP_OK;
     for (const dbp_tuning &t : candidates(d->C)) {
+        // an operator-kernel candidate where that kernel does not apply is
+        // the same launch as its DBP_PREFACTOR_OFF twin
+        if (t.prefactor == DBP_PREFACTOR_ON && !dbp_prefactor_applies(h, d, kind, t, H, in, out)) continue;
         h->tuning = t;
         std::string e2;
         dbp_status r = DBP_OK;
