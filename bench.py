@@ -246,10 +246,13 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the kernels' device code (the .cuh headers that define them;
+    the .cu files hold host code and instantiations), the key of the ncu
+    traffic records."""
     csrc = os.path.join(ROOT, "paper_1702_04458_b300", "csrc")
     h = hashlib.sha256()
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
+        if name.endswith(".cuh"):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(name.encode())
                 h.update(f.read())
