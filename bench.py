@@ -664,6 +664,38 @@ def bench_serving(dbp, h, args):
 MIX_SERVE_CHANNELS = 2
 
 
+def bench_frame_latency(dbp, h, frame, n=40):
+    """Latency of one frame of the headline workload through the request
+    loop when the GPU is otherwise idle: the frame's H and y in pinned host
+    memory, submitted after the previous one completed, detected by ADMM
+    (T=3) or CG (T=8), x_hat and labels back in pinned host memory;
+    submit-to-completion times as the request loop records them."""
+    import torch
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+    H, y = pin(frame["H"].astype(np.complex64)), pin(frame["y"].astype(np.complex64))
+    x = pin(np.zeros((UL.W, UL.N, UL.U), np.complex64))
+    lab = pin(np.zeros((UL.W, UL.N, UL.U), np.uint8))
+    out = {"workload": workload_name(UL, "one uplink frame per request, idle GPU"),
+           "latency": "dbp_submit to completion (host copies of H, y in and x_hat, labels out included)"}
+    dbp.dbp_server_start(h, streams=2, hbm_bytes=1 << 30)
+    try:
+        for name, kind, T in (("admm_ul", dbp.DBP_KIND_UPLINK_ADMM, UL.T), ("cg_ul", dbp.DBP_KIND_UPLINK_CG, UL_T_CG)):
+            d = dbp.frame_desc(UL.B, UL.C, UL.U, UL.W, UL.N, qam_order=UL.M, T_max=T, rho=1.0,
+                               N0=frame["N0"], Es=1.0)
+            lat = []
+            for i in range(n + 4):
+                r = dbp.dbp_wait(h, dbp.dbp_submit(h, dbp.request(kind, d, H, y, x, lab, None, 0, 0, i)), 60.0)
+                if r is None or r.status != dbp.DBP_OK:
+                    raise RuntimeError("frame latency request failed")
+                if i >= 4:
+                    lat.append(r.finish_us - r.submit_us)
+            out[name] = {"p50_ms": float(np.percentile(lat, 50)) / 1e3, "p99_ms": float(np.percentile(lat, 99)) / 1e3,
+                         "requests": n}
+    finally:
+        dbp.dbp_server_stop(h)
+    return out
+
+
 def bench_served_precision(dbp, h, args):
     """The served path with 16-bit against FP32 inputs: uplink ADMM (T=3)
     frames of the B=256, C=8, U=32, 3300 x 14, 64-QAM workload at 20 dB from
@@ -1043,9 +1075,11 @@ def main(argv=None) -> int:
         serving = bench_serving(dbp, h, args)
     graph = None
     served_mixed = None
+    frame_latency = None
     if not args.no_serving:
         graph = bench_graph(dbp, h, stream, device, args)
         served_mixed = bench_served_precision(dbp, h, args)
+        frame_latency = bench_frame_latency(dbp, h, frames[0])
 
     # ---- end to end: host inputs in, host results out ------------------------
     # Each step copies the frame's channel and receive vectors (one pinned
@@ -1153,6 +1187,7 @@ def main(argv=None) -> int:
             "mixed_vs_fp32": mixed,
             "graph_batch": graph,
             "serving": serving,
+            "frame_latency": frame_latency,
             "served_mixed_vs_fp32": served_mixed,
             "cpu_baseline": cpu,
             "e2e": e2e,
