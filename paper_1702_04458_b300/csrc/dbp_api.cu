@@ -161,18 +161,22 @@ void tma_layout(const dbp_frame_desc *d, Kind kind, int UT, Shape &s, bool singl
         s.off_v = s.off_g + gb;
         s.warp_bytes = s.off_v + vbytes;
     } else {
+        // FP32 at U = 32: Gram and matched filter on the tensor cores (k-steps
+        // of 4 rows, 8-symbol tiles), results through the row buffer at off_g
+        const bool mma3 = (UT == 32);
         s.hp = UT;
-        s.h_rows = S;
+        s.h_rows = mma3 ? round_up(S, 4) : S;
         s.yp = S + ((S % 4 == 0) ? 2 : 4);           // odd number of 16-byte units
-        s.y_rows = (kind == K_ADMM_DL) ? 0 : round_up(N, nch);
-        s.ms_rows = 0;
-        const int hb = round16((long long)S * UT * 8);
+        s.y_rows = (kind == K_ADMM_DL) ? 0 : (mma3 ? std::max(round_up(N, nch), round_up(N, 8)) : round_up(N, nch));
+        s.ms_rows = (mma3 && kind != K_ADMM_DL) ? round_up(N, 8) : 0;
+        const int hb = round16((long long)s.h_rows * UT * 8);
         const int yb = round16((long long)s.y_rows * s.yp * 8);
+        const int gb = mma3 ? round16((long long)std::max(16, s.ms_rows) * (UT + 2) * 8) : 0;
         s.off_h1 = single ? 0 : hb;
         s.off_y0 = (single ? 1 : 2) * hb;
         s.off_y1 = single ? s.off_y0 : s.off_y0 + yb;
         s.off_g = s.off_y1 + yb;
-        s.off_v = s.off_g;
+        s.off_v = s.off_g + gb;
         s.warp_bytes = s.off_v + vbytes;
     }
 }
@@ -597,12 +601,16 @@ size_t factor_layout(const dbp_frame_desc *d, int UT, const Shape &s, dbp::Facto
         fp.off_v = fp.off_g + round16((long long)16 * dbp::TcDl::QP * 8);
         fp.warp_bytes = fp.off_v + 16 * 16;
     } else {
+        // the staging and Gram row buffer of the bulk-copy kernel's operator
+        // (cluster_operator): 16-bit inputs and FP32 at U = 32 go through
+        // the tensor cores and the row buffer
         const int eb = (int)elem_bytes(d->precision);
         const bool h16 = is16(d->precision);
+        const bool mma3 = !h16 && UT == 32;
         fp.hp = h16 ? UT + 8 : UT;
-        fp.h_rows = h16 ? round_up(S, 8) : S;
+        fp.h_rows = h16 ? round_up(S, 8) : (mma3 ? round_up(S, 4) : S);
         fp.off_g = round16((long long)fp.h_rows * fp.hp * eb);
-        fp.off_v = fp.off_g + (h16 ? round16((long long)16 * (UT + 2) * 8) : 0);
+        fp.off_v = fp.off_g + ((h16 || mma3) ? round16((long long)16 * (UT + 2) * 8) : 0);
         fp.warp_bytes = fp.off_v + UT * 16;
     }
     return (size_t)dbp::kFactorWarps * fp.warp_bytes;

@@ -1,13 +1,8 @@
 // dbp_mma8.cuh -- tensor-core building blocks for U = 8 users with FP32
-// inputs: TF32 operand splitting, the three-product m16n8k8 step, the A
-// fragment of H_c^H and the shuffle-based Gauss-Jordan inversion used by the
-// tensor-core uplink kernel (dbp_tc8.cuh).
-//
-// FP32 accuracy from TF32 tensor cores: every operand x is split into two
-// TF32 values x_hi + x_lo (truncated, |x - x_hi - x_lo| < 2^-20 |x|), and a
-// product is accumulated as a_lo b_hi + a_hi b_lo + a_hi b_hi in FP32 (the
-// a_lo b_lo term, < 2^-20 relative, is dropped) -- three
-// mma.sync.m16n8k8.tf32 per product.
+// inputs: the A fragment of H_c^H and the shuffle-based Gauss-Jordan
+// inversion used by the tensor-core uplink kernel (dbp_tc8.cuh).  The TF32
+// operand split and the three-product m16n8k8 step (FP32 accuracy from TF32
+// tensor cores) are in dbp_tma.cuh.
 //
 // Complex products are embedded in real ones with real/imaginary parts
 // interleaved along the contraction, k' = 2k + a:
@@ -23,33 +18,7 @@
 
 namespace dbp {
 
-__device__ __forceinline__ uint32_t tf32_bits(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-// x = hi + lo + r with hi, lo TF32 values: hi keeps the 10 leading mantissa
-// bits of x (truncation), lo those of the exact remainder x - hi, and
-// |r| < 2^-20 |x|.
-__device__ __forceinline__ void split3(float x, uint32_t &hi, uint32_t &lo) {
-    hi = __float_as_uint(x) & 0xffffe000u;
-    lo = __float_as_uint(x - __uint_as_float(hi)) & 0xffffe000u;
-}
-__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-// d += A B with A = ah + al and B = bh + bl (three TF32 products).
-__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4], uint32_t bh0,
-                                     uint32_t bh1, uint32_t bl0, uint32_t bl1) {
-    mma_tf32(d, al[0], al[1], al[2], al[3], bh0, bh1);
-    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bl0, bl1);
-    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
-}
+// tf32_bits, split3, mma_tf32 and mma3 are in dbp_tma.cuh.
 
 // A fragment of H_c^H for one k-step (complex rows s0..s0+3 of H_c):
 // lane (g, t) takes H[s0 + t/2][g] and H[s0 + 2 + t/2][g], component t & 1

@@ -129,6 +129,54 @@ __device__ __forceinline__ void mma_k16<__nv_bfloat162>(float (&d)[4], uint32_t 
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
+// FP32 accuracy from TF32 tensor cores (the U = 8 tensor-core kernel and the
+// FP32 Gram / matched filter here): every operand x is split into two TF32
+// values x_hi + x_lo (truncated, |x - x_hi - x_lo| < 2^-20 |x|) and a product
+// is accumulated as a_lo b_hi + a_hi b_lo + a_hi b_hi in FP32 (the a_lo b_lo
+// term, < 2^-20 relative, is dropped): three mma.sync.m16n8k8.tf32 per
+// product.
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+// x = hi + lo + r with hi, lo TF32 values: hi keeps the 10 leading mantissa
+// bits of x (truncation), lo those of the exact remainder x - hi, and
+// |r| < 2^-20 |x|.
+__device__ __forceinline__ void split3(float x, uint32_t &hi, uint32_t &lo) {
+    hi = __float_as_uint(x) & 0xffffe000u;
+    lo = __float_as_uint(x - __uint_as_float(hi)) & 0xffffe000u;
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+// d += A B with A = ah + al and B = bh + bl (three TF32 products).
+__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4], uint32_t bh0,
+                                     uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+    mma_tf32(d, al[0], al[1], al[2], al[3], bh0, bh1);
+    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+    mma_tf32(d, ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+}
+
+// A fragment of H_c^H for one k-step of the complex embedding (complex rows
+// s0..s0+3 of H_c, row pitch hp): lane (g, t) takes H[s0 + t/2][user] and
+// H[s0 + 2 + t/2][user], component t & 1 for the real rows and the matching
+// component of the rotation (-Im, Re) for the imaginary rows.
+__device__ __forceinline__ void hh_frag_p(const float2 *Hs, int hp, int s0, int user, int t, float (&a)[4]) {
+    const float2 h0 = Hs[(s0 + (t >> 1)) * hp + user];
+    const float2 h1 = Hs[(s0 + 2 + (t >> 1)) * hp + user];
+    const bool odd = t & 1;
+    a[0] = odd ? h0.y : h0.x;
+    a[1] = odd ? h0.x : -h0.y;
+    a[2] = odd ? h1.y : h1.x;
+    a[3] = odd ? h1.x : -h1.y;
+}
+
 // (re, im) -> (-im, re) for a packed pair of 16-bit values (sign bit 15 of
 // the low half; the same layout for FP16 and BF16).
 __device__ __forceinline__ uint32_t rot16(uint32_t h) { return __byte_perm(h, 0, 0x1032) ^ 0x8000u; }
@@ -245,6 +293,131 @@ __device__ __forceinline__ void mf_mma(const uint32_t *Hs, int hp, int h_rows, c
     }
 }
 
+// FP32 inputs at U = 32: the Gram and the matched filter run on the tensor
+// cores (three TF32 products per k-step) instead of the CUDA cores.
+template <int UT, typename TIn> struct FP32Mma {
+    static constexpr bool value = (UT == 32) && !InTraits<TIn>::mma;
+};
+
+// The same two products from FP32 inputs, on the tensor cores with three
+// TF32 products per k-step (dbp_mma8.cuh's embedding: A_re[u][2s:2s+2] =
+// H[s][u] as stored, A_im = (-Im, Re) of it, B'[2s:2s+2][n] = B[s][n] as
+// stored; m16n8k8, four complex rows per k-step).  Output paths as gram_mma
+// and mf_mma.
+template <int UT>
+__device__ __forceinline__ void gram_mma3(const float2 *Hs, int hp, int h_rows, float2 *G, int lane, int u,
+                                          float2 (&R)[UT]) {
+    constexpr int MT = UT / 8;
+    constexpr int LD = UT + 2;
+    constexpr int PASSES = (UT > 16) ? UT / 16 : 1;
+    constexpr int MPP = MT / PASSES;
+    const int g = lane >> 2, t = lane & 3;
+    float acc[MT][MT][4];
+#pragma unroll
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < MT; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+    for (int s0 = 0; s0 < h_rows; s0 += 4) {
+        uint32_t ah[MT][4], al[MT][4];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            float a[4];
+            hh_frag_p(Hs, hp, s0, 8 * mt + g, t, a);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) split3(a[i], ah[mt][i], al[mt][i]);
+        }
+        // the B fragment of H_c for n-tile nt holds the values a[0], a[2] of
+        // m-tile nt; only the blocks on and above the diagonal (the Gram is
+        // Hermitian)
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = mt; nt < MT; ++nt)
+                mma3(acc[mt][nt], ah[mt], al[mt], ah[nt][0], ah[nt][2], al[nt][0], al[nt][2]);
+    }
+#pragma unroll
+    for (int pass = 0; pass < PASSES; ++pass) {
+#pragma unroll
+        for (int m = 0; m < MPP; ++m) {
+            const int mt = pass * MPP + m;
+            const int row = 8 * m + g;
+#pragma unroll
+            for (int nt = 0; nt < MT; ++nt) {
+                if (nt >= mt) {
+                    *reinterpret_cast<float4 *>(&G[row * LD + 8 * nt + 2 * t]) =
+                        make_float4(acc[mt][nt][0], acc[mt][nt][2], acc[mt][nt][1], acc[mt][nt][3]);
+                } else {
+                    // block (mt, nt) = conjugate transpose of block (nt, mt): this
+                    // lane holds G[8 nt + g][8 mt + 2t + q]
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+                        G[(8 * m + 2 * t + q) * LD + 8 * nt + g] = make_float2(acc[nt][mt][q], -acc[nt][mt][2 + q]);
+                }
+            }
+        }
+        __syncwarp();
+        if (u / 16 == pass) {
+#pragma unroll
+            for (int v = 0; v < UT; v += 2) ld2(&G[(u - 16 * pass) * LD + v], R[v], R[v + 1]);
+        }
+        __syncwarp();
+    }
+}
+
+template <int UT>
+__device__ __forceinline__ void mf_mma3(const float2 *Hs, int hp, int h_rows, const float2 *Ys, int yp, int n_tiles,
+                                        float2 *M, int lane) {
+    constexpr int MT = UT / 8;
+    constexpr int LD = UT + 2;
+    const int g = lane >> 2, t = lane & 3;
+    const float *Yf = reinterpret_cast<const float *>(Ys);
+    for (int nb = 0; nb < n_tiles; nb += 2) {
+        const bool two = (nb + 1 < n_tiles);
+        float acc[MT][2][4];
+#pragma unroll
+        for (int i = 0; i < MT; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+        for (int s0 = 0; s0 < h_rows; s0 += 4) {
+            uint32_t bh0[2], bl0[2], bh1[2], bl1[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                // B'[k' = t][n] and B'[t + 4][n]: component t & 1 of y[n][s0 + t/2], y[n][s0 + 2 + t/2]
+                const float *yr = Yf + ((8 * (nb + q) + g) * yp + s0 + (t >> 1)) * 2 + (t & 1);
+                const float b0 = (q == 0 || two) ? yr[0] : 0.f;
+                const float b1 = (q == 0 || two) ? yr[4] : 0.f;
+                split3(b0, bh0[q], bl0[q]);
+                split3(b1, bh1[q], bl1[q]);
+            }
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                float a[4];
+                hh_frag_p(Hs, hp, s0, 8 * mt + g, t, a);
+                uint32_t ah[4], al[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) split3(a[i], ah[i], al[i]);
+                mma3(acc[mt][0], ah, al, bh0[0], bh1[0], bl0[0], bl1[0]);
+                if (two) mma3(acc[mt][1], ah, al, bh0[1], bh1[1], bl0[1], bl1[1]);
+            }
+        }
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            const int uu = 8 * mt + g;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (q == 1 && !two) continue;
+                const int n = 8 * (nb + q) + 2 * t;
+                M[n * LD + uu] = make_float2(acc[mt][q][0], acc[mt][q][2]);
+                M[(n + 1) * LD + uu] = make_float2(acc[mt][q][1], acc[mt][q][3]);
+            }
+        }
+    }
+}
+
 // Gauss-Jordan inversion as in gj_invert, with the pivot lane's row update
 // written uniformly: the pivot lane holds the pivot row itself, so
 // R[j] - (1 - 1/p) P[j] = P[j] / p gives the normalised row with the same
@@ -313,9 +486,16 @@ __device__ __forceinline__ void cluster_operator(const TIn *Hs, int hp, int h_ro
                                                  unsigned int *retries, float2 (&R)[UT]) {
     using C2 = float2;
     constexpr bool MMA = InTraits<TIn>::mma;
+    constexpr bool MMA3 = FP32Mma<UT, TIn>::value;
     // ---- Gram (+ diagonal loading) ----
     if constexpr (MMA) {
         gram_mma<UT, TIn>(reinterpret_cast<const uint32_t *>(Hs), hp, h_rows, Gm, lane, u, R);
+    } else if constexpr (MMA3) {
+        gram_mma3<UT>(reinterpret_cast<const float2 *>(Hs), hp, h_rows, Gm, lane, u, R);
+        if (ALG == ALG_ADMM_DL) {
+#pragma unroll
+            for (int v = 0; v < UT; ++v) R[v].y = -R[v].y;       // conj(H_c^H H_c)
+        }
     } else {
 #pragma unroll
         for (int v = 0; v < UT; ++v) R[v] = make_float2(0.f, 0.f);
@@ -401,6 +581,7 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
     constexpr int E = TmaCfg<UT>::E;
     constexpr int EB = InTraits<TIn>::bytes;
     constexpr bool MMA = InTraits<TIn>::mma;
+    constexpr bool MMA3 = FP32Mma<UT, TIn>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -513,6 +694,13 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
                 // one staging buffer: H_c and y_c are no longer read
                 if (!dbl && has_next) issue(ntile * P + pl, 0);
             }
+        } else if constexpr (MMA3) {
+            if (ALG != ALG_ADMM_DL) {
+                mf_mma3<UT>(reinterpret_cast<const float2 *>(Hs), hp, p.h_rows, reinterpret_cast<const float2 *>(Ys),
+                            yp, (N + 7) / 8, Gm, lane);
+                __syncwarp();
+                if (!dbl && has_next) issue(ntile * P + pl, 0);
+            }
         }
 
         for (int n0 = 0; n0 < N; n0 += K::NCH) {
@@ -545,7 +733,7 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
 
             if (ALG == ALG_ADMM_UL || ALG == ALG_CG_UL) {
                 // Matched filter m_c = H_c^H y_c.
-                if constexpr (MMA) {
+                if constexpr (MMA || MMA3) {
 #pragma unroll
                     for (int j = 0; j < K::NN; ++j) acc[j] = Gm[(n0 + g + K::G * j) * (UT + 2) + u];
                 } else {
