@@ -213,11 +213,12 @@ __device__ __forceinline__ void gram_mma(const uint32_t *Hs, int hp, int h_rows,
             h0[mt] = (uu < UT) ? Hs[(s0 + t) * hp + uu] : 0u;
             h1[mt] = (uu < UT) ? Hs[(s0 + t + 4) * hp + uu] : 0u;
         }
+        // only the blocks on and above the diagonal (the Gram is Hermitian)
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt) {
             const uint32_t r0 = rot16(h0[mt]), r1 = rot16(h1[mt]);
 #pragma unroll
-            for (int nt = 0; nt < MT; ++nt) mma_k16<TIn>(acc[mt][nt], h0[mt], r0, h1[mt], r1, h0[nt], h1[nt]);
+            for (int nt = mt; nt < MT; ++nt) mma_k16<TIn>(acc[mt][nt], h0[mt], r0, h1[mt], r1, h0[nt], h1[nt]);
         }
     }
 #pragma unroll
@@ -229,9 +230,19 @@ __device__ __forceinline__ void gram_mma(const uint32_t *Hs, int hp, int h_rows,
 #pragma unroll
             for (int nt = 0; nt < MT; ++nt) {
                 const int v = 8 * nt + 2 * t;
-                if (8 * mt + g < UT && v < UT)
-                    *reinterpret_cast<float4 *>(&G[row * LD + v]) =
-                        make_float4(acc[mt][nt][0], acc[mt][nt][2], acc[mt][nt][1], acc[mt][nt][3]);
+                if (nt >= mt) {
+                    if (8 * mt + g < UT && v < UT)
+                        *reinterpret_cast<float4 *>(&G[row * LD + v]) =
+                            make_float4(acc[mt][nt][0], acc[mt][nt][2], acc[mt][nt][1], acc[mt][nt][3]);
+                } else {
+                    // block (mt, nt) = conjugate transpose of block (nt, mt): this
+                    // lane holds G[8 nt + g][8 mt + 2t + q]
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+                        if (8 * mt + 2 * t + q < UT && 8 * nt + g < UT)
+                            G[(8 * m + 2 * t + q) * LD + 8 * nt + g] =
+                                make_float2(acc[nt][mt][q], -acc[nt][mt][2 + q]);
+                }
             }
         }
         __syncwarp();
