@@ -122,24 +122,27 @@ __device__ __forceinline__ void tcdl_operator(const float2 *Hs, int S, float2 *Q
             for (int i = 0; i < 4; ++i) split3(a[i], ah[mt][i], al[mt][i]);
         }
         // the B fragment of H_c for n-tile nt holds the values a[0], a[2]
-        // of m-tile nt
+        // of m-tile nt; block (1, 0) is the conjugate transpose of block
+        // (0, 1) (the Gram is Hermitian) and is not multiplied
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < 2; ++nt)
+            for (int nt = mt; nt < 2; ++nt)
                 mma3(gacc[mt][nt], ah[mt], al[mt], ah[nt][0], ah[nt][2], al[nt][0], al[nt][2]);
     }
     // B_c = conj(G) + delta I, row-major into Qs
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int nt = 0; nt < 2; ++nt)
+        for (int nt = mt; nt < 2; ++nt)
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int row = 8 * mt + g, col = 8 * nt + 2 * t + q;
                 C2 v = make_float2(gacc[mt][nt][q], -gacc[mt][nt][2 + q]);
                 if (row == col) v.x += f_delta;
                 Qs[row * QP + col] = v;
+                // conj(G)[col][row] = G[row][col]
+                if (nt != mt) Qs[col * QP + row] = make_float2(gacc[mt][nt][q], gacc[mt][nt][2 + q]);
             }
     __syncwarp();
 #pragma unroll
