@@ -247,15 +247,20 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     """Hash of the kernels' device code (the .cuh headers that define them;
-    the .cu files hold host code and instantiations), the key of the ncu
-    traffic records."""
+    the .cu files hold host code and instantiations) with comments and
+    blank space removed, the key of the ncu traffic records."""
+    import re
     csrc = os.path.join(ROOT, "paper_1702_04458_b300", "csrc")
     h = hashlib.sha256()
     for name in sorted(os.listdir(csrc)):
         if name.endswith(".cuh"):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode())
-                h.update(f.read())
+            with open(os.path.join(csrc, name), encoding="utf-8") as f:
+                code = f.read()
+            code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+            code = re.sub(r"//[^\n]*", " ", code)
+            code = " ".join(code.split())
+            h.update(name.encode())
+            h.update(code.encode())
     return h.hexdigest()[:16]
 
 

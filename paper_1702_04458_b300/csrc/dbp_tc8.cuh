@@ -9,7 +9,7 @@
 // cluster's 8 x 16 state.  Each is a 16 x 16 real product (rows: the real
 // parts of the 8 outputs over their imaginary parts) computed as three
 // mma.sync.m16n8k8 TF32 products per k-step (split operands, FP32 accuracy;
-// the helpers and the real embedding are those of dbp_mma8.cuh).  Lane
+// the split is in dbp_tma.cuh, the real embedding in dbp_mma8.cuh).  Lane
 // (g, t) = (lane / 4, lane % 4) holds user g of symbols
 // n = 8 (q >> 1) + 2t + (q & 1), q = 0..3, of the accumulator.
 //

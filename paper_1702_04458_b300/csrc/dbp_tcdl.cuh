@@ -11,7 +11,7 @@
 //     product B_c^{-1} v_c for 16 symbol slots being a 32 x 32 x 16 real
 //     product (2 m-tiles of 8 users, real parts over imaginary parts, 4
 //     k-steps, 2 n-tiles of 8 symbols), three mma.sync.m16n8k8 TF32 products
-//     per k-step with the operands split into TF32 parts (dbp_mma8.cuh);
+//     per k-step with the operands split into TF32 parts (dbp_tma.cuh);
 //   * the output x_c = H^{dH}_c B_c^{-1} v_c, an (S x 16) x (16 x 16) product.
 // The consensus w = sum_c (m_c - lambda_c) and (s - w)/C run once per symbol:
 // warp c reduces the units c, c + C, ... of 32 (symbol, user) entries and
