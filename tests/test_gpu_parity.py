@@ -368,6 +368,30 @@ def test_bulk_copy_kernel_single_staging_buffer(dbp, handle, algo):
     assert_labels(x, lab, ref, 64, np.float32)
 
 
+@pytest.mark.parametrize("algo", ["admm", "cg", "dl"])
+@pytest.mark.parametrize("W,N,B,C", [(23, 5, 240, 8), (19, 20, 240, 8), (17, 14, 128, 4)])
+def test_bulk_copy_kernel_fp32_u32_tensor_core_products(dbp, handle, algo, W, N, B, C):
+    """FP32 inputs at U = 32 (Gram and matched filter as 3 x TF32 tensor-core
+    products): S = 30 (rows padded to a multiple of 4), N = 5 (one partial
+    8-symbol tile), N = 20 (three tiles, two chunks) and S = 32, against the
+    oracle."""
+    U, M, T = 32, 16, 3
+    try:
+        dbp.dbp_set_tuning(handle, kernel=dbp.DBP_PATH_TMA)
+        if algo == "dl":
+            f = synth.downlink_frame(W, N, B, U, M, seed=470 + W + N + B)
+            x, _ = run_dl(dbp, handle, f, C, T)
+            ref = oracle.admm_dl(_round(f["H"], "fp32"), _round(f["s"], "fp32"), C=C, rho=1.0, T_max=T)
+        else:
+            f = synth.uplink_frame(W, N, B, U, M, 20.0, seed=470 + W + N + B)
+            x, lab = run_ul(dbp, handle, f, C, T, algo)
+            ref = oracle_ul(f, C, T, algo, "fp32")
+            assert_labels(x, lab, ref, M, np.float32)
+    finally:
+        dbp.dbp_set_tuning(handle)
+    assert _rel_per_vector(x, ref).max() <= FP32_TOL
+
+
 def test_forced_bulk_copy_kernel_rejects_ineligible_shapes(dbp, handle):
     f = synth.uplink_frame(3, 2, 40, 5, 16, 8.0, seed=451)      # U=5 is not a power of two
     try:
