@@ -668,12 +668,15 @@ dbp_status run_ex(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void
     const bool a16 = aligned(H, 16) && aligned(vin, 16) && aligned(out, 16);
     // the handle's tuning; when fully automatic, an autotuned choice for
     // this frame shape (dbp_autotune) if there is one
-    dbp_tuning tune = h->tuning;
-    if (tune.kernel == DBP_PATH_AUTO && tune.mapping == DBP_MAP_AUTO && tune.warps_per_cta == 0 &&
-        tune.cluster_size == 0 && tune.prefactor == DBP_PREFACTOR_AUTO) {
+    dbp_tuning tune;
+    {
         std::lock_guard<std::mutex> lk(h->tune_mu);
-        auto it = h->tuned.find(dbp_tune_key(d, kind));
-        if (it != h->tuned.end()) tune = it->second;
+        tune = h->tuning;
+        if (tune.kernel == DBP_PATH_AUTO && tune.mapping == DBP_MAP_AUTO && tune.warps_per_cta == 0 &&
+            tune.cluster_size == 0 && tune.prefactor == DBP_PREFACTOR_AUTO) {
+            auto it = h->tuned.find(dbp_tune_key(d, kind));
+            if (it != h->tuned.end()) tune = it->second;
+        }
     }
     v = choose_shape(h, d, kind, a16, s, tune);
     if (v != DBP_OK) return v;
@@ -933,6 +936,7 @@ dbp_status dbp_set_tuning(dbp_handle_t h, const dbp_tuning *t) {
         t->warps_per_cta < 0 || t->warps_per_cta > 32 || t->kernel < DBP_PATH_AUTO || t->kernel > DBP_PATH_BCAST ||
         t->prefactor < DBP_PREFACTOR_AUTO || t->prefactor > DBP_PREFACTOR_ON)
         return fail(h, DBP_ERR_INVALID_ARG, "bad tuning values");
+    std::lock_guard<std::mutex> lk(h->tune_mu);
     h->tuning = *t;
     return DBP_OK;
 }

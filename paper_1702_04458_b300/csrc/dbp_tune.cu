@@ -78,7 +78,11 @@ dbp_status dbp_autotune(dbp_handle_t h, int32_t kind, const dbp_frame_desc *d, c
         h->err = "dbp_autotune: cudaEventCreate failed";
         return DBP_ERR_CUDA;
     }
-    const dbp_tuning saved = h->tuning;
+    dbp_tuning saved;
+    {
+        std::lock_guard<std::mutex> lk(h->tune_mu);
+        saved = h->tuning;
+    }
     dbp_tuning chosen{};
     float best_ms = -1.f;
     dbp_status st_out = DBP_OK;
@@ -86,7 +90,10 @@ dbp_status dbp_autotune(dbp_handle_t h, int32_t kind, const dbp_frame_desc *d, c
         // an operator-kernel candidate where that kernel does not apply is
         // the same launch as its DBP_PREFACTOR_OFF twin
         if (t.prefactor == DBP_PREFACTOR_ON && !dbp_prefactor_applies(h, d, kind, t, H, in, out)) continue;
-        h->tuning = t;
+        {
+            std::lock_guard<std::mutex> lk(h->tune_mu);
+            h->tuning = t;
+        }
         std::string e2;
         dbp_status r = DBP_OK;
         for (int i = 0; i < 2 && r == DBP_OK; ++i)
@@ -113,7 +120,10 @@ dbp_status dbp_autotune(dbp_handle_t h, int32_t kind, const dbp_frame_desc *d, c
             chosen = t;
         }
     }
-    h->tuning = saved;
+    {
+        std::lock_guard<std::mutex> lk(h->tune_mu);
+        h->tuning = saved;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st_out != DBP_OK) return st_out;
