@@ -53,3 +53,24 @@ def test_reference_arm_only_rank0_prints(capsys, monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "2")
     assert bench.run_reference(bench.parse_args(["--impl", "reference", "--steps", "1"])) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_json_line(capsys, monkeypatch):
+    """Rank 0 of the reference arm prints one JSON line with the contract's
+    keys: the oracle timed on host cores, its own e2e object with no copies."""
+    import json
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    assert bench.run_reference(bench.parse_args(["--impl", "reference", "--steps", "1", "--warmup", "3"])) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["value"] > 0
+    assert d["warmup"] >= 3 and d["higher_is_better"] is True and "workload" in d["config"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
