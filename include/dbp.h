@@ -59,7 +59,7 @@ typedef enum dbp_status {
     DBP_ERR_NOMEM = 3,         /* device or host allocation failed           */
     DBP_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed       */
     DBP_ERR_TIMEOUT = 5,       /* a bounded wait ran out                     */
-    DBP_ERR_UNIMPLEMENTED = 6, /* entry point not available in this build    */
+    DBP_ERR_UNIMPLEMENTED = 6, /* entry point not provided by this library   */
     DBP_PENDING = 7            /* submitted work has not completed yet       */
 } dbp_status;
 
