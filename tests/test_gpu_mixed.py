@@ -146,3 +146,17 @@ def test_16bit_downlink_is_rejected(dbp, handle):
     with pytest.raises(dbp.DbpError) as ei:
         dbp.dbp_downlink_admm(handle, d, buf, buf, buf)
     assert ei.value.status == dbp.DBP_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("kind", ["fp16", "bf16"])
+def test_full_size_16bit_sampled(dbp, handle, kind):
+    """The bench's mixed workload at full size (B=256, C=8, U=32, 64-QAM,
+    3300 x 14, ADMM T=3, 20 dB) in its launch configuration: the oracle on
+    the dequantised inputs recomputes 16 sampled subcarriers."""
+    W, N, B, C, U, M, T = 3300, 14, 256, 8, 32, 64, 3
+    f = synth.uplink_frame(W, N, B, U, M, 20.0, seed=synth.frame_seed(4, 5) + 11)
+    x, lab, Hq, yq = run16(dbp, handle, f, C, T, "admm", kind)
+    idx = np.sort(np.random.default_rng(7).choice(W, size=16, replace=False))
+    sub = dict(f, W=len(idx))
+    ref = oracle_run(sub, C, T, "admm", Hq[idx], yq[idx])
+    assert _rel(x[idx], ref).max() <= ARITH_TOL
