@@ -632,10 +632,39 @@ def serve_run(dbp, h, chans, kinds, rate_hz, n_frames, rng, precision=None, fixe
     return done, time.perf_counter() - t0
 
 
+def autotune_served_shapes(dbp, h, chans):
+    """Time the launch choices of every (shape, kind) of the served stream
+    once (dbp_autotune) so that the request loop's AUTO calls use the
+    fastest; returns the choices."""
+    import torch
+    out = []
+    kinds = ((dbp.DBP_KIND_UPLINK_ADMM, "uplink_admm"), (dbp.DBP_KIND_UPLINK_CG, "uplink_cg"),
+             (dbp.DBP_KIND_DOWNLINK_ADMM, "downlink_admm"))
+    for ch in chans:
+        sp = ch.spec
+        W, N, B, U = sp["W"], sp["N"], sp["B"], sp["U"]
+        H = torch.from_numpy(ch.H).cuda()
+        for kind, name in kinds:
+            dl = kind == dbp.DBP_KIND_DOWNLINK_ADMM
+            inp = torch.from_numpy(ch.s if dl else ch.y).cuda()
+            x = torch.empty((W, N, B if dl else U), dtype=torch.complex64, device="cuda")
+            d = dbp.frame_desc(B, sp["C"], U, W, N, qam_order=0 if dl else sp["M"], T_max=5, rho=1.0,
+                               N0=ch.N0, Es=1.0)
+            t = dbp.dbp_autotune(h, kind, d, H, inp, x, None, None, 3)
+            out.append({"B": B, "C": sp["C"], "U": U, "kind": name, "kernel": t.kernel, "mapping": t.mapping,
+                        "cluster_size": t.cluster_size, "warps_per_cta": t.warps_per_cta,
+                        "prefactor": t.prefactor})
+            del inp, x
+        del H
+    torch.cuda.synchronize()
+    return out
+
+
 def bench_serving(dbp, h, args):
     rng = np.random.default_rng(123)
     specs = serve_channels(rng)
     chans = [ServeChannel(dbp, sp, rng) for sp in specs]
+    tuned = None if args.no_autotune else autotune_served_shapes(dbp, h, chans)
     n = args.serve_frames
     kinds = [int(k) for k in rng.choice([dbp.DBP_KIND_UPLINK_ADMM, dbp.DBP_KIND_UPLINK_CG,
                                          dbp.DBP_KIND_DOWNLINK_ADMM], size=n, p=[0.4, 0.3, 0.3])]
@@ -660,7 +689,7 @@ def bench_serving(dbp, h, args):
                            "resident_hits": int(sum(d[2] for d in done))})
     finally:
         dbp.dbp_server_stop(h)
-    return {"channels": specs, "coherence_frames": SERVE_COHERENCE, "streams": 4,
+    return {"channels": specs, "coherence_frames": SERVE_COHERENCE, "streams": 4, "autotuned": tuned,
             "kind_mix": "40% uplink ADMM, 30% uplink CG, 30% downlink ADMM (FP32), 3..8 iterations",
             "capacity_frames_per_s": cap_fps, "load_points": points,
             "latency": "submit to completion observed by the request loop (host copies included)"}
