@@ -439,12 +439,22 @@ def bench_mixed(dbp, h, stream, device, rank, args, hbm_peak, hbm_src, alu_peak)
         torch.cuda.synchronize(device)
         ms = e0.elapsed_time(e1) / K
         errs = int(np.unpackbits(np.bitwise_xor(lab.cpu().numpy(), f["labels"]).reshape(-1, 1), axis=1).sum())
+        xh = x.cpu().numpy().astype(np.complex128)
+        if name == "fp32":
+            x32 = xh
         wl = Workload(MIX.B, MIX.C, MIX.U, MIX.W, MIX.N, MIX.M, MIX.T, elem_bytes=eb)
         rf = roofline(f"admm_ul_{name}", "admm_ul", wl, ms, hbm_peak, hbm_src, alu_peak)
         out["per_precision"][name] = {
             "gbit_s": detected_bits(MIX) / (ms / 1e3) / 1e9, "ms_per_frame": ms, "launches": K,
             "ber": errs / nbits, "ber_ci95": _binom_ci(errs, nbits), "bit_errors": errs, "bits": nbits,
             "hbm_gbs": rf["hbm_view"]["achieved_gbs"], "alu_tflops": rf["alu_view"]["achieved_tflops"]}
+        if name != "fp32":
+            # input quantisation: relative error per (subcarrier, symbol) vector
+            # against the FP32 path on the original inputs (which matches the
+            # FP64 oracle to 1e-4)
+            rel = np.linalg.norm(xh - x32, axis=-1) / np.maximum(np.linalg.norm(x32, axis=-1), 1e-30)
+            out["per_precision"][name]["rel_err_vs_fp32"] = {"max": float(rel.max()),
+                                                             "median": float(np.median(rel))}
         del H, y
     pp = out["per_precision"]
     for name in ("fp16", "bf16"):
