@@ -49,6 +49,7 @@ UL_T_CG = 8
 DL = Workload(B=256, C=16, U=16, W=1200, N=14, M=64, T=5)
 MIX = Workload(B=256, C=8, U=32, W=3300, N=14, M=64, T=3)
 MIX_SNR_DB = 20.0
+DL_EPS = 0.05                  # Lemma 2 relaxation of the downlink extension line
 MIX_SWEEP_DB = (10.0, 14.0, 18.0, 22.0, 26.0, 30.0)
 MIX_SWEEP_MAX_FRAMES = 12      # 12 x 8.87 Mbit = 1.06e8 bits
 SNRS_DB = [float(2 * i) for i in range(11)]
@@ -1059,6 +1060,42 @@ def main(argv=None) -> int:
                      cg_avg, hbm_peak, hbm_src, alu_peak)
     dominant = rf_cg if cg_avg >= admm_avg else rf_admm
 
+    # ---- the extensions of the hot path on the same frame: ADMM with the
+    # BOX prox (Lemma 1 with a hypercube), and max-log soft outputs --------
+    def back_to_back(fn, n):
+        for k in range(3):
+            fn(k)
+        torch.cuda.synchronize(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(n):
+            fn(k)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        return e0.elapsed_time(e1) / n
+
+    KX = max(min(K, 500), 10)
+    box_r = (math.isqrt(UL.M) - 1) * math.sqrt(3.0 / (2.0 * (UL.M - 1)))
+    dbox = [dbp.frame_desc(UL.B, UL.C, UL.U, UL.W, UL.N, qam_order=UL.M, T_max=UL.T, regularizer=dbp.DBP_REG_BOX,
+                           rho=1.0, N0=d["N0"], Es=1.0, box_r=box_r) for d in dev]
+    box_ms = back_to_back(lambda k: dbp.dbp_uplink_admm(h, dbox[k % ROTATE], dev[k % ROTATE]["H"],
+                                                        dev[k % ROTATE]["y"], xa, la, sp), KX)
+    llr = torch.empty((UL.W, UL.N, UL.U, UL.M.bit_length() - 1), dtype=torch.float32, device=device)
+    llr_ms = back_to_back(lambda k: dbp.dbp_uplink_llr(h, D[k % ROTATE][0], dev[k % ROTATE]["H"], xa, llr, sp), KX)
+    llr_bytes = UL.W * (UL.B * UL.U * 8 + UL.N * UL.U * 8 + UL.N * UL.U * llr.shape[-1] * 4)
+    extensions = {
+        "box_prox": {"workload": workload_name(UL, f"uplink ADMM T={UL.T}, BOX prox r={box_r:.4f}"),
+                     "ms_per_frame": box_ms, "gbit_s": detected_bits(UL) / (box_ms / 1e3) / 1e9,
+                     "launches": KX,
+                     "roofline": roofline("admm_ul_box", "admm_ul", UL, box_ms, hbm_peak, hbm_src, alu_peak)},
+        "soft_outputs": {"workload": workload_name(UL, "max-log LLRs of the ADMM estimate (MMSE statistics)"),
+                         "ms_per_frame": llr_ms, "llr_gbit_s": detected_bits(UL) / (llr_ms / 1e3) / 1e9,
+                         "launches": KX, "bytes_per_frame": llr_bytes,
+                         "hbm_gbs": llr_bytes / (llr_ms / 1e3) / 1e9,
+                         "hbm_frac": llr_bytes / (llr_ms / 1e3) / 1e9 / hbm_peak},
+    }
+    del llr
+
     # ---- downlink precoder (B=256, C=16, U=16) -------------------------------
     downlink = None
     if not args.no_downlink:
@@ -1098,6 +1135,20 @@ def main(argv=None) -> int:
         e1.record(stream)
         torch.cuda.synchronize(device)
         dl_ms2 = e0.elapsed_time(e1) / KD
+        # Lemma 2 with eps > 0 (the precoder's l2 relaxation), one stream
+        deps = dbp.frame_desc(DL.B, DL.C, DL.U, DL.W, DL.N, T_max=DL.T, rho=1.0, eps=DL_EPS)
+        for k in range(3):
+            dbp.dbp_downlink_admm(h, deps, ddev[k % ROTATE]["H"], ddev[k % ROTATE]["s"], xd, None, sp)
+        e0.record(stream)
+        for k in range(KD):
+            dbp.dbp_downlink_admm(h, deps, ddev[k % ROTATE]["H"], ddev[k % ROTATE]["s"], xd, None, sp)
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        eps_ms = e0.elapsed_time(e1) / KD
+        extensions["downlink_eps"] = {
+            "workload": workload_name(DL, f"downlink ADMM T={DL.T}, eps={DL_EPS}"), "ms_per_frame": eps_ms,
+            "gbit_s": detected_bits(DL) / (eps_ms / 1e3) / 1e9, "launches": KD,
+            "roofline": roofline("admm_dl_eps", "admm_dl", DL, eps_ms, hbm_peak, hbm_src, alu_peak)}
         downlink = {"workload": workload_name(DL, "downlink ADMM T=5"),
                     "value": detected_bits(DL) / (dl_ms2 / 1e3) / 1e9, "unit": "Gbit/s (precoded)",
                     "ms_per_frame": dl_ms2, "ms_per_frame_one_stream": dl_ms,
@@ -1227,6 +1278,7 @@ def main(argv=None) -> int:
             },
             "roofline": dominant,
             "roofline_other": rf_admm if dominant is rf_cg else rf_cg,
+            "extensions": extensions,
             "downlink": downlink,
             "mixed_vs_fp32": mixed,
             "graph_batch": graph,
