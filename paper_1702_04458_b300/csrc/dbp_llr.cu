@@ -13,17 +13,23 @@
 // |x - mu s|^2 separates into the two axes, and each axis's bits depend on
 // its PAM level only, so every bit takes a minimum over L = sqrt(M) levels.
 //
-// One warp per subcarrier: lane (u, g) accumulates row u of G over the rows
-// s = g, g + G, ... of H, the groups are summed by shuffles, the Gram is
-// inverted in registers (Gauss-Jordan, HPD, no pivoting) for A_uu, and the
-// lanes then run over the (symbol, user) entries of the subcarrier.
+// One CTA of four warps per subcarrier.  The CTA stages the B rows of H_w
+// into shared memory with asynchronous copies (every load of a chunk issued
+// before the first wait, so a subcarrier costs one memory round trip per
+// chunk, not one per row), thread (u, g) accumulates row u of G over the
+// rows g, g + G, ... of the chunk, the row groups are summed by shuffles
+// within a warp and through shared memory across warps, one warp inverts
+// the Gram in registers (Gauss-Jordan, HPD, no pivoting) for A_uu, and the
+// CTA's threads then run over the (symbol, user) entries of the subcarrier.
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <string>
 
 #include "dbp.h"
 #include "dbp_fused.cuh"
+#include "dbp_mma8.cuh"
 #include "dbp_internal.h"
 
 namespace dbp {
@@ -33,109 +39,238 @@ struct LlrParams {
     const float2 *x;     // [W][N][U]
     float *llr;          // [W][N][U][m]
     int W, N, B, U;
-    int L, m, half;      // PAM levels per axis, bits per symbol, bits per axis
+    int m, half;         // bits per symbol, bits per axis (the kernel's template argument)
+    int llr_align;       // largest power of two (up to 16) dividing the llr address
     int zf;              // 1: ZF statistics, 0: MMSE
     float delta, N0, Es;
     float a;             // PAM half-spacing: levels (2k - L + 1) a
 };
 
-constexpr int kLlrWarps = 8;
+constexpr int kLlrThreads = 128;
 
-template <int UT>
-__global__ void __launch_bounds__(32 * kLlrWarps) dbp_llr_kernel(const LlrParams p) {
-    constexpr int G = 32 / UT;
-    __shared__ __align__(16) float2 scratch[kLlrWarps][UT];
-    __shared__ float mus[kLlrWarps][UT], nus[kLlrWarps][UT];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int u = lane % UT, g = lane / UT;
-    const int w = blockIdx.x * kLlrWarps + warp;
-    if (w >= p.W) return;                       // whole warp: no block-level sync below
-    const int U = p.U, B = p.B;
+// Rows of H_w staged per chunk (pitch UT, padded columns zero).  The buffer
+// also holds the three other warps' partial Grams after the last chunk.
+template <int UT> struct LlrCfg {
+    static constexpr int kChunkBytes = UT == 32 ? 24576 : 8192;
+    static constexpr int kRows = kChunkBytes / (UT * 8);
+    static_assert((kLlrThreads / 32 - 1) * UT * UT * 8 <= kChunkBytes, "partial Grams fit the staging buffer");
+};
 
-    // Row u of G = H^H H (zero for padded users)
+__device__ __forceinline__ void llr_cp16(void *dst, const void *src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void llr_cp8(void *dst, const void *src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void llr_cp_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Bias and inverse noise variance of user u from A_uu = ((G + delta I)^{-1})_uu.
+__device__ __forceinline__ void llr_stats_store(const LlrParams &p, float Auu, int u, float *mus, float *inv_nus) {
+    float mu, nu2;
+    if (p.zf) {
+        mu = 1.f;
+        nu2 = p.N0 * Auu;
+    } else {
+        mu = 1.f - p.delta * Auu;
+        nu2 = p.Es * mu * (1.f - mu);
+    }
+    mus[u] = mu;
+    inv_nus[u] = 1.f / nu2;
+}
+
+template <int UT, int HALF>
+__global__ void __launch_bounds__(kLlrThreads) dbp_llr_kernel(const LlrParams p) {
+    using Cfg = LlrCfg<UT>;
+    constexpr int NW = kLlrThreads / 32;   // warps per CTA
+    constexpr int G = kLlrThreads / UT;    // row groups per CTA
+    __shared__ __align__(16) float2 Hs[Cfg::kRows * UT];
+    __shared__ __align__(16) float2 scratch[UT];
+    __shared__ float mus[UT], inv_nus[UT];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int u = tid % UT, g = tid / UT;
+    const int w = blockIdx.x;
+    const int U = p.U, B = p.B, NU = p.N * U;
+    const float2 *xw = p.x + (size_t)w * NU;
+
+    // this thread's first estimate entry, in flight while the Gram is formed
+    float2 x0 = make_float2(0.f, 0.f);
+    if (tid < NU) x0 = __ldg(&xw[tid]);
+    if (U != UT) {   // padded columns stay zero through every chunk
+        for (int i = tid; i < Cfg::kRows * UT; i += kLlrThreads) Hs[i] = make_float2(0.f, 0.f);
+        __syncthreads();
+    }
+
+    // G = H^H H.  UT = 8: 3xTF32 m16n8k8 products (FP32 accuracy) over
+    // k-steps of 4 rows, lane (gq, t) of each warp accumulating entries
+    // (gq, 2t), (gq, 2t + 1) of its k-steps.  Otherwise thread (u, g) sums
+    // row u over its rows on the CUDA cores.  Padded users give zero rows.
+    constexpr bool kTc = (UT == 8);
+    const int gq = lane >> 2, t = lane & 3;
+    float gacc[4] = {0.f, 0.f, 0.f, 0.f};
     float2 R[UT];
 #pragma unroll
     for (int v = 0; v < UT; ++v) R[v] = make_float2(0.f, 0.f);
-    if (u < U) {
-        const float2 *Hw = p.H + (size_t)w * B * U;
-        for (int s = g; s < B; s += G) {
-            const float2 hu = __ldg(&Hw[(size_t)s * U + u]);
-#pragma unroll
-            for (int v = 0; v < UT; ++v)
-                if (v < U) cmacc(R[v], hu, __ldg(&Hw[(size_t)s * U + v]));
-        }
-    }
-#pragma unroll
-    for (int msk = UT; msk < 32; msk <<= 1) {
-#pragma unroll
-        for (int v = 0; v < UT; ++v) {
-            R[v].x += shfl_x(R[v].x, msk);
-            R[v].y += shfl_x(R[v].y, msk);
-        }
-    }
-#pragma unroll
-    for (int v = 0; v < UT; ++v)
-        if (v == u) R[v].x += (u < U) ? p.delta : 1.f;   // padded users: identity rows
-    gj_invert<UT>(R, &scratch[warp][0], u, lane);
-    float Auu = 0.f;
-#pragma unroll
-    for (int v = 0; v < UT; ++v)
-        if (v == u) Auu = R[v].x;
-    if (g == 0) {
-        float mu, nu2;
-        if (p.zf) {
-            mu = 1.f;
-            nu2 = p.N0 * Auu;
+    const float2 *Hw = p.H + (size_t)w * B * U;
+    const bool vec = (U == UT) && ((reinterpret_cast<uintptr_t>(Hw) & 15) == 0);
+    for (int s0 = 0; s0 < B; s0 += Cfg::kRows) {
+        const int rows = min(Cfg::kRows, B - s0);
+        if (s0 > 0) __syncthreads();   // the previous chunk's reads are done
+        const float2 *src = Hw + (size_t)s0 * U;
+        if (vec) {                      // contiguous rows, U even: 16-byte pieces
+            for (int i = tid; i < rows * UT / 2; i += kLlrThreads) llr_cp16(&Hs[2 * i], src + 2 * i);
         } else {
-            mu = 1.f - p.delta * Auu;
-            nu2 = p.Es * mu * (1.f - mu);
+            for (int i = tid; i < rows * U; i += kLlrThreads) {
+                const int r = i / U;
+                llr_cp8(&Hs[r * UT + (i - r * U)], src + i);
+            }
         }
-        mus[warp][u] = mu;
-        nus[warp][u] = nu2;
+        const int rows4 = (rows + 3) & ~3;
+        if (kTc) {   // a k-step reads four rows: the ones past B are zero
+            for (int i = rows * UT + tid; i < rows4 * UT; i += kLlrThreads) Hs[i] = make_float2(0.f, 0.f);
+        }
+        llr_cp_wait();
+        __syncthreads();
+        if constexpr (kTc) {
+            for (int ks = warp; 4 * ks < rows4; ks += NW) {
+                float a[4];
+                hh_frag(Hs, 4 * ks, gq, t, a);
+                uint32_t ah[4], al[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) split3(a[i], ah[i], al[i]);
+                mma3(gacc, ah, al, ah[0], ah[2], al[0], al[2]);   // B operand = H: the same values
+            }
+        } else {
+            for (int s = g; s < rows; s += G) {
+                const float2 hu = Hs[s * UT + u];
+#pragma unroll
+                for (int v = 0; v < UT; v += 2) {
+                    const float4 q = *reinterpret_cast<const float4 *>(&Hs[s * UT + v]);
+                    cmacc(R[v], hu, make_float2(q.x, q.y));
+                    cmacc(R[v + 1], hu, make_float2(q.z, q.w));
+                }
+            }
+        }
     }
-    __syncwarp();
-
-    // LLRs of the (symbol, user) entries of this subcarrier
-    for (int e = lane; e < p.N * U; e += 32) {
-        const int n = e / U, uu = e - n * U;
-        const float2 xv = p.x[((size_t)w * p.N + n) * U + uu];
-        const float mu = mus[warp][uu];
-        const float inv_nu2 = 1.f / nus[warp][uu];
-        float *out = p.llr + (((size_t)w * p.N + n) * U + uu) * p.m;
+    if constexpr (!kTc) {
 #pragma unroll
-        for (int axis = 0; axis < 2; ++axis) {
-            const float v = axis ? xv.y : xv.x;
-            float mn0[4], mn1[4];
+        for (int msk = UT; msk < 32; msk <<= 1) {   // the warp's row groups
 #pragma unroll
-            for (int j = 0; j < 4; ++j) mn0[j] = mn1[j] = INFINITY;
-            for (int k = 0; k < p.L; ++k) {
-                const float d = v - mu * (float)(2 * k - p.L + 1) * p.a;
-                const float d2 = d * d;
-                const int gray = k ^ (k >> 1);
+            for (int v = 0; v < UT; ++v) {
+                R[v].x += shfl_x(R[v].x, msk);
+                R[v].y += shfl_x(R[v].y, msk);
+            }
+        }
+    }
+    __syncthreads();   // every read of the staged rows is done: the buffer takes the partial Grams
+    if constexpr (kTc) {
+        float *part = reinterpret_cast<float *>(Hs);   // part[((k 4) + i) 32 + lane]: warp k + 1's gacc[i]
+        if (warp > 0) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (j < p.half) {
-                        if ((gray >> (p.half - 1 - j)) & 1) mn1[j] = fminf(mn1[j], d2);
-                        else mn0[j] = fminf(mn0[j], d2);
-                    }
+            for (int i = 0; i < 4; ++i) part[((warp - 1) * 4 + i) * 32 + lane] = gacc[i];
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int k = 0; k < NW - 1; ++k) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) gacc[i] += part[(k * 4 + i) * 32 + lane];
+            }
+            float2 e0 = make_float2(gacc[0], gacc[2]), e1 = make_float2(gacc[1], gacc[3]);
+            const float dl = (gq < U) ? p.delta : 1.f;   // padded users: identity rows
+            if (2 * t == gq) e0.x += dl;
+            if (2 * t + 1 == gq) e1.x += dl;
+            gj8<float2, float>(e0, e1, gq, t);
+            if (gq < U && (gq >> 1) == t) llr_stats_store(p, (gq & 1) ? e1.x : e0.x, gq, mus, inv_nus);
+        }
+    } else {
+        float2 *part = Hs;  // part[(k UT + v) UT + u]: warp k + 1's entry (u, v)
+        if (warp > 0 && lane < UT) {
+#pragma unroll
+            for (int v = 0; v < UT; ++v) part[((warp - 1) * UT + v) * UT + u] = R[v];
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int k = 0; k < NW - 1; ++k) {
+#pragma unroll
+                for (int v = 0; v < UT; ++v) {
+                    const float2 q = part[(k * UT + v) * UT + u];
+                    R[v].x += q.x;
+                    R[v].y += q.y;
                 }
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (j < p.half) out[axis * p.half + j] = (mn1[j] - mn0[j]) * inv_nu2;
+            for (int v = 0; v < UT; ++v)
+                if (v == u) R[v].x += (u < U) ? p.delta : 1.f;   // padded users: identity rows
+            gj_invert<UT>(R, scratch, u, lane);
+            float Auu = 0.f;
+#pragma unroll
+            for (int v = 0; v < UT; ++v)
+                if (v == u) Auu = R[v].x;
+            if (lane < UT) llr_stats_store(p, Auu, u, mus, inv_nus);
+        }
+    }
+    __syncthreads();
+
+    // LLRs of the (symbol, user) entries of this subcarrier: per axis the
+    // minima of |v - mu l a|^2 over the PAM levels l = 2k - L + 1 whose Gray
+    // label has bit j = 0 / 1.
+    constexpr int L = 1 << HALF;
+    for (int e = tid; e < NU; e += kLlrThreads) {
+        const float2 xv = (e == tid) ? x0 : __ldg(&xw[e]);
+        const int uu = e % U;
+        const float mua = mus[uu] * p.a;
+        const float inv_nu2 = inv_nus[uu];
+        float out[2 * HALF];
+#pragma unroll
+        for (int axis = 0; axis < 2; ++axis) {
+            const float v = axis ? xv.y : xv.x;
+            float mn0[HALF], mn1[HALF];
+#pragma unroll
+            for (int j = 0; j < HALF; ++j) mn0[j] = mn1[j] = INFINITY;
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                const float d = v - (float)(2 * k - L + 1) * mua;
+                const float d2 = d * d;
+                const int gray = k ^ (k >> 1);
+#pragma unroll
+                for (int j = 0; j < HALF; ++j) {
+                    if ((gray >> (HALF - 1 - j)) & 1) mn1[j] = fminf(mn1[j], d2);
+                    else mn0[j] = fminf(mn0[j], d2);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < HALF; ++j) out[axis * HALF + j] = (mn1[j] - mn0[j]) * inv_nu2;
+        }
+        float *dst = p.llr + ((size_t)w * NU + e) * (2 * HALF);
+        if (p.llr_align >= 16 && (HALF % 2) == 0) {
+#pragma unroll
+            for (int j = 0; j < 2 * HALF; j += 4)
+                *reinterpret_cast<float4 *>(dst + j) = make_float4(out[j], out[j + 1], out[j + 2], out[j + 3]);
+        } else if (p.llr_align >= 8) {
+#pragma unroll
+            for (int j = 0; j < 2 * HALF; j += 2) *reinterpret_cast<float2 *>(dst + j) = make_float2(out[j], out[j + 1]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 2 * HALF; ++j) dst[j] = out[j];
         }
     }
 }
 
 template <int UT>
 cudaError_t launch_llr(const LlrParams &p, cudaStream_t st) {
-    const int blocks = (p.W + kLlrWarps - 1) / kLlrWarps;
-    dbp_llr_kernel<UT><<<blocks, 32 * kLlrWarps, 0, st>>>(p);
+    switch (p.half) {
+    case 1: dbp_llr_kernel<UT, 1><<<p.W, kLlrThreads, 0, st>>>(p); break;
+    case 2: dbp_llr_kernel<UT, 2><<<p.W, kLlrThreads, 0, st>>>(p); break;
+    case 3: dbp_llr_kernel<UT, 3><<<p.W, kLlrThreads, 0, st>>>(p); break;
+    default: dbp_llr_kernel<UT, 4><<<p.W, kLlrThreads, 0, st>>>(p); break;
+    }
     return cudaGetLastError();
 }
 
 }  // namespace dbp
-
 extern "C" {
 
 dbp_status dbp_uplink_llr(dbp_handle_t h, const dbp_frame_desc *d, const void *H, const void *x_hat, float *llr,
@@ -181,15 +316,14 @@ dbp_status dbp_uplink_llr(dbp_handle_t h, const dbp_frame_desc *d, const void *H
     p.H = static_cast<const float2 *>(H);
     p.x = static_cast<const float2 *>(x_hat);
     p.llr = llr;
+    p.llr_align = 4;
+    while (p.llr_align < 16 && (reinterpret_cast<uintptr_t>(llr) % (2 * p.llr_align)) == 0) p.llr_align *= 2;
     p.W = d->W;
     p.N = d->N;
     p.B = d->B;
     p.U = d->U;
-    int L = 1;
-    while (L * L < d->qam_order) ++L;
     int m = 0;
     while ((1 << m) < d->qam_order) ++m;
-    p.L = L;
     p.m = m;
     p.half = m / 2;
     p.zf = (d->regularizer == DBP_REG_ZF);

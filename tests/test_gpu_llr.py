@@ -31,6 +31,10 @@ LLR_CASES = [
     (13, 5, 64, 4, 16, 64, 18.0, "mmse", "cg"),
     (9, 7, 80, 2, 5, 4, 4.0, "zf", "cg"),              # U=5 padded to 8, QPSK, ZF
     (6, 3, 256, 8, 32, 256, 25.0, "mmse", "admm"),     # U=32, 256-QAM
+    (11, 6, 36, 4, 3, 4, 6.0, "mmse", "cg"),           # U=3 padded to 4
+    (5, 6, 90, 3, 8, 64, 12.0, "mmse", "cg"),          # B=90: the last 4-row k-step reads zero rows
+    (7, 4, 300, 4, 8, 16, 10.0, "zf", "admm"),         # B=300: three staged chunks of H
+    (3, 14, 512, 8, 16, 4, 5.0, "mmse", "admm"),       # U=16 over several chunks, QPSK
 ]
 
 
@@ -74,3 +78,25 @@ def test_llr_rejects_unsupported_requests(dbp, handle):
         with pytest.raises(dbp.DbpError) as ei:
             dbp.dbp_uplink_llr(handle, dbp.frame_desc(**kw), buf, buf, out)
         assert ei.value.status == status
+
+
+@pytest.mark.parametrize("h_off,l_off", [(1, 0), (0, 1), (0, 2), (1, 3)])
+def test_llr_unaligned_buffers(dbp, handle, h_off, l_off):
+    """H starting 8 bytes past a 16-byte boundary (element-wise staging) and
+    LLR buffers 4 / 8 / 12 bytes past one (scalar and pair stores): the same
+    values as the aligned buffers."""
+    W, N, B, C, U, M = 9, 7, 128, 8, 8, 16
+    f = synth.uplink_frame(W, N, B, U, M, 9.0, seed=2700)
+    H32 = torch.from_numpy(f["H"].astype(np.complex64).reshape(-1))
+    x = torch.from_numpy((f["s"] * 0.9).astype(np.complex64)).cuda()
+    d = dbp.frame_desc(B, C, U, W, N, qam_order=M, T_max=3, N0=f["N0"], Es=1.0)
+    n = W * N * U * 4
+    ref = torch.zeros(n, dtype=torch.float32, device="cuda")
+    dbp.dbp_uplink_llr(handle, d, H32.cuda(), x, ref)
+    hb = torch.zeros(H32.numel() + 1, dtype=torch.complex64, device="cuda")
+    hb[h_off:h_off + H32.numel()] = H32.cuda()
+    lb = torch.full((n + 4,), float("nan"), dtype=torch.float32, device="cuda")
+    dbp.dbp_uplink_llr(handle, d, hb[h_off:], x, lb[l_off:l_off + n])
+    torch.cuda.synchronize()
+    assert torch.allclose(lb[l_off:l_off + n], ref, rtol=1e-5, atol=1e-5)
+    assert torch.isnan(lb[:l_off]).all() and torch.isnan(lb[l_off + n:]).all()
