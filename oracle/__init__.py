@@ -164,10 +164,21 @@ def _levels(M: int):
     return L, int(round(math.log2(M))) // 2
 
 
+def _axis(M: int):
+    """Per-axis PAM levels L, bits per axis and half-spacing a of the
+    unit-energy alphabet.  M = 2 is BPSK {-1, +1}: two levels on the real
+    axis only (no imaginary axis), a = 1."""
+    if M == 2:
+        return 2, 1, 1.0
+    L, half = _levels(M)
+    return L, half, math.sqrt(3.0 / (2.0 * (M - 1)))
+
+
 def box_radius(M: int) -> float:
-    """Radius r of the box covering the unit-energy square QAM alphabet."""
-    L, _ = _levels(M)
-    return (L - 1) * math.sqrt(3.0 / (2.0 * (M - 1)))
+    """Radius r of the box covering the unit-energy square QAM alphabet
+    (M = 2: the real segment [-1, 1] covering BPSK)."""
+    L, _, a = _axis(M)
+    return (L - 1) * a
 
 
 def slice_labels(x, M: int, dtype=np.float64) -> np.ndarray:
@@ -181,10 +192,10 @@ def slice_labels(x, M: int, dtype=np.float64) -> np.ndarray:
     which the decision is taken (float32 to mirror a float32 kernel: the
     products and sums are rounded to float32 one operation at a time).
     """
-    L, half = _levels(M)
+    L, half, a = _axis(M)
     x = np.asarray(x)
     ft = np.dtype(dtype).type
-    inv_a = ft(1.0 / math.sqrt(3.0 / (2.0 * (M - 1))))
+    inv_a = ft(1.0 / a)
     off = ft(L - 1)
 
     def axis(v):
@@ -195,15 +206,18 @@ def slice_labels(x, M: int, dtype=np.float64) -> np.ndarray:
         return k ^ (k >> 1)
 
     gi = axis(x.real)
+    if M == 2:   # BPSK: the real axis is the whole label
+        return gi.astype(np.uint8)
     gq = axis(x.imag)
     return ((gi << half) | gq).astype(np.uint8)
 
 
 def label_points(labels, M: int) -> np.ndarray:
     """Alphabet point of each Gray label (the slicer's own decoding)."""
-    L, half = _levels(M)
-    a = math.sqrt(3.0 / (2.0 * (M - 1)))
+    L, half, a = _axis(M)
     lab = np.asarray(labels, dtype=np.int64)
+    if M == 2:   # BPSK: label k is the real point 2k - 1
+        return (2.0 * lab - 1.0) + 0j
 
     def ungray(g):
         k = g.copy()

@@ -43,10 +43,13 @@ def _gray(k: int) -> int:
 
 
 def qam_alphabet(M: int) -> np.ndarray:
-    """Transmit alphabet: point of each label 0..M-1 (complex128, E_s = 1)."""
+    """Transmit alphabet: point of each label 0..M-1 (complex128, E_s = 1).
+    M = 2 is BPSK: label k is the real point 2k - 1."""
+    if M == 2:
+        return np.array([-1.0 + 0j, 1.0 + 0j])
     L = int(round(math.sqrt(M)))
     if L * L != M or M < 4 or (M & (M - 1)) != 0:
-        raise ValueError(f"square QAM order must be 4, 16, 64, 256: got {M}")
+        raise ValueError(f"alphabet order must be 2 (BPSK) or a square QAM order 4, 16, 64, 256: got {M}")
     half = int(round(math.log2(M))) // 2
     a = math.sqrt(3.0 / (2.0 * (M - 1)))
     pts = np.zeros(M, dtype=np.complex128)

@@ -57,6 +57,26 @@ def test_slicer_is_nearest_point(M):
     assert np.array_equal(lab[clear], best[clear].astype(np.uint8))
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_bpsk_alphabet_and_slicer(dtype):
+    """M = 2 (BPSK, the alphabet of the real-segment prox): the points are
+    -1 and +1, the slicer inverts them, picks the nearer point for any
+    complex input (the imaginary part plays no role) and sends 0 to the
+    lower level."""
+    pts = synth.qam_alphabet(2)
+    assert np.array_equal(pts, np.array([-1.0 + 0j, 1.0 + 0j]))
+    assert abs(np.mean(np.abs(pts) ** 2) - 1.0) < 1e-15
+    assert np.array_equal(oracle.slice_labels(pts, 2, dtype=dtype), np.array([0, 1], dtype=np.uint8))
+    assert np.array_equal(oracle.label_points(np.array([0, 1]), 2), pts)
+    rng = np.random.default_rng(17)
+    x = (rng.normal(size=3000) + 1j * rng.normal(size=3000)) * 1.5
+    dist = np.abs(x[:, None] - pts[None, :])
+    clear = np.abs(dist[:, 0] - dist[:, 1]) > 1e-9
+    assert np.array_equal(oracle.slice_labels(x, 2, dtype=dtype)[clear], np.argmin(dist, axis=1)[clear])
+    assert oracle.slice_labels(np.array([0.0 + 5j]), 2, dtype=dtype)[0] == 0
+    assert oracle.box_radius(2) == 1.0
+
+
 def test_slicer_ties_go_to_lower_level_and_clamp():
     M = 16
     a = math.sqrt(3.0 / (2.0 * (M - 1)))
@@ -196,18 +216,31 @@ def _prox_box(rho, r):
     return prox
 
 
-@pytest.mark.parametrize("reg", ["mmse", "zf", "box"])
+def _prox_bpsk(rho, r):
+    """argmin over real s with |s| <= r of sum_c rho/2 ||s - w_c||^2 by bounded
+    lstsq (the imaginary parts of w_c only add a constant)."""
+    def prox(ws):
+        U = ws[0].size
+        A = np.vstack([math.sqrt(rho) * np.eye(U) for _ in ws])
+        b = np.concatenate([math.sqrt(rho) * wc.real for wc in ws])
+        return optimize.lsq_linear(A, b, bounds=(-r, r), method="bvls", tol=1e-14).x + 0j
+    return prox
+
+
+@pytest.mark.parametrize("reg", ["mmse", "zf", "box", "bpsk"])
 @pytest.mark.parametrize("T", [1, 2, 3, 5])
 def test_admm_matches_generic_steps(reg, T):
     """Alg. 1 (steps reordered E3, E1, E2; T_max counts E1/E2 passes) equals
     Sec. III-B's ADMM solved step by step with generic solvers."""
-    f = _ul(W=2, N=2, B=24, U=4, M=16, snr=6.0, seed=11)
+    f = _ul(W=2, N=2, B=24, U=4, M=2 if reg == "bpsk" else 16, snr=6.0, seed=11)
     C, rho, gamma = 3, 0.9, 1.0
-    r = oracle.box_radius(16)
+    r = oracle.box_radius(2 if reg == "bpsk" else 16)
     if reg == "mmse":
         prox, code = _prox_quadratic(rho, f["N0"] / f["Es"]), oracle.REG_MMSE
     elif reg == "zf":
         prox, code = _prox_quadratic(rho, 0.0), oracle.REG_ZF
+    elif reg == "bpsk":
+        prox, code = _prox_bpsk(rho, r), oracle.REG_BPSK
     else:
         prox, code = _prox_box(rho, r), oracle.REG_BOX
     s = oracle.admm_ul(f["H"], f["y"], C=C, rho=rho, N0=f["N0"], T_max=T, gamma=gamma,
@@ -216,6 +249,37 @@ def test_admm_matches_generic_steps(reg, T):
         for n in range(2):
             ref = _admm_generic(f["H"][w], f["y"][w, n], C, rho, gamma, T, prox)
             assert np.abs(s[w, n] - ref).max() < 1e-10
+
+
+@pytest.mark.parametrize("reg", ["box", "bpsk"])
+@pytest.mark.parametrize("C", [1, 4])
+def test_admm_constrained_converges_to_bounded_least_squares(reg, C):
+    """With g the indicator of the box (E2-BOX) or of the real segment (BPSK),
+    (E0) is least squares under bounds: converged ADMM equals scipy's
+    bounded-variable least squares on the real form of y = H s, and some
+    bounds are active (the constraint does work at this SNR)."""
+    M = 2 if reg == "bpsk" else 4
+    f = _ul(W=2, N=3, B=16, U=4, M=M, snr=3.0, seed=23 + C)
+    r = oracle.box_radius(M)
+    s = oracle.admm_ul(f["H"], f["y"], C=C, rho=1.0, N0=f["N0"], T_max=4000,
+                       reg=oracle.REG_BPSK if reg == "bpsk" else oracle.REG_BOX, box_r=r)
+    active = 0
+    for w in range(2):
+        H = f["H"][w]
+        if reg == "bpsk":   # s real: [Re H; Im H] s = [Re y; Im y]
+            A = np.vstack([H.real, H.imag])
+        else:               # s = a + ib: [[Re H, -Im H], [Im H, Re H]] (a, b)
+            A = np.block([[H.real, -H.imag], [H.imag, H.real]])
+        for n in range(3):
+            y = f["y"][w, n]
+            sol = optimize.lsq_linear(A, np.concatenate([y.real, y.imag]), bounds=(-r, r),
+                                      method="bvls", tol=1e-14).x
+            ref = sol + 0j if reg == "bpsk" else sol[:4] + 1j * sol[4:]
+            assert np.abs(s[w, n] - ref).max() < 1e-8
+            active += int(np.sum(np.abs(sol) > r - 1e-12))
+    assert active > 0
+    if reg == "bpsk":
+        assert np.all(s.imag == 0.0)
 
 
 @pytest.mark.parametrize("algo", ["admm_mmse", "admm_zf", "dl"])
