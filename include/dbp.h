@@ -79,7 +79,11 @@ typedef enum dbp_precision {
 typedef enum dbp_regularizer {
     DBP_REG_ZF = 0,            /* g = 0                 : s = v              */
     DBP_REG_MMSE = 1,          /* g = N0/(2Es)||s||^2   : (E2-MMSE)          */
-    DBP_REG_BOX = 2            /* g = box indicator     : (E2-BOX), radius r */
+    DBP_REG_BOX = 2,           /* g = box indicator     : (E2-BOX), radius r */
+    DBP_REG_BPSK = 3           /* g = indicator of the real segment [-r, r]:
+                                * s_u = sign(Re v_u) min(|Re v_u|, r), Im s_u = 0
+                                * (the BPSK prox of Sec. III-B); qam_order 2
+                                * or 0 */
 } dbp_regularizer;
 
 /* Descriptor flags. */
@@ -95,7 +99,9 @@ typedef struct dbp_config {
 typedef struct dbp_frame_desc {
     int32_t B, C, U;           /* antennas, clusters (B % C == 0), users     */
     int32_t W, N;              /* subcarriers, OFDM symbols per subcarrier   */
-    int32_t qam_order;         /* 4, 16, 64 or 256: slicer alphabet; 0 = no
+    int32_t qam_order;         /* 4, 16, 64 or 256: slicer alphabet (unit-
+                                  energy Gray QAM); 2: BPSK {-1, +1}, label k
+                                  for 2k - 1, only with DBP_REG_BPSK; 0 = no
                                   labels                                     */
     int32_t T_max;             /* iterations: ADMM counts the init as the
                                   first (T_max >= 1); CG counts loop trips
@@ -108,7 +114,7 @@ typedef struct dbp_frame_desc {
     double gamma;              /* dual step gamma (the paper uses 1)         */
     double N0;                 /* noise variance per complex entry           */
     double Es;                 /* symbol energy E[|s_u|^2] > 0               */
-    double box_r;              /* box radius r for DBP_REG_BOX               */
+    double box_r;              /* radius r for DBP_REG_BOX and DBP_REG_BPSK  */
     double eps;                /* downlink: residual-interference bound
                                   epsilon >= 0 of (P0); the consensus step
                                   scales (s - w)/C by max{0, 1 - eps /

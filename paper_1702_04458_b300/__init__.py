@@ -38,7 +38,7 @@ DBP_ERR_UNIMPLEMENTED = 6
 DBP_PENDING = 7
 
 DBP_FP32, DBP_FP64, DBP_FP16, DBP_BF16 = 0, 1, 2, 3
-DBP_REG_ZF, DBP_REG_MMSE, DBP_REG_BOX = 0, 1, 2
+DBP_REG_ZF, DBP_REG_MMSE, DBP_REG_BOX, DBP_REG_BPSK = 0, 1, 2, 3
 DBP_FLAG_NORMALIZE = 1
 DBP_MAP_AUTO, DBP_MAP_CTA, DBP_MAP_CLUSTER = 0, 1, 2
 DBP_PATH_AUTO, DBP_PATH_GENERIC, DBP_PATH_TMA, DBP_PATH_MMA, DBP_PATH_BCAST = 0, 1, 2, 3, 4

@@ -276,10 +276,10 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_admm_kernel(const 
                     const int e = base + lane;
                     if (e < nvu) {
                         C2 a = consensus_sum<E>(grp, e, C);
-                        if (p.reg == 2) {
+                        if (p.reg >= 2) {   // (E2-BOX); BPSK: the real segment [-r, r]
                             const float r = p.f_box_r, ic = p.f_invC;
                             a.x = clip_r(a.x * ic, r);
-                            a.y = clip_r(a.y * ic, r);
+                            a.y = (p.reg == 2) ? clip_r(a.y * ic, r) : 0.f;
                         } else {
                             a = cscale(a, p.f_e2_scale);
                         }

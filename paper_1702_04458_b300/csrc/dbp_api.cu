@@ -88,8 +88,14 @@ dbp_status validate(dbp_context *h, const dbp_frame_desc *d, Kind kind) {
     const int umax = (d->precision == DBP_FP64) ? 16 : 32;
     if (d->U > umax)
         return fail(h, DBP_ERR_UNSUPPORTED, "U=%d exceeds %d users for this precision", d->U, umax);
-    if (d->qam_order != 0 && d->qam_order != 4 && d->qam_order != 16 && d->qam_order != 64 && d->qam_order != 256)
-        return fail(h, DBP_ERR_INVALID_ARG, "qam_order %d is not 0, 4, 16, 64 or 256", d->qam_order);
+    if (d->qam_order != 0 && d->qam_order != 2 && d->qam_order != 4 && d->qam_order != 16 && d->qam_order != 64 &&
+        d->qam_order != 256)
+        return fail(h, DBP_ERR_INVALID_ARG, "qam_order %d is not 0, 2, 4, 16, 64 or 256", d->qam_order);
+    const bool bpsk = (kind == K_ADMM_UL && d->regularizer == DBP_REG_BPSK);
+    if (d->qam_order == 2 && !bpsk)
+        return fail(h, DBP_ERR_INVALID_ARG, "qam_order 2 (BPSK) goes with the uplink ADMM BPSK regulariser");
+    if (bpsk && d->qam_order != 0 && d->qam_order != 2)
+        return fail(h, DBP_ERR_INVALID_ARG, "the BPSK regulariser slices BPSK: qam_order 2, or 0 for no labels");
     if (kind == K_CG_UL) {
         if (d->T_max < 0) return fail(h, DBP_ERR_INVALID_ARG, "CG needs T_max >= 0");
         if (d->regularizer != DBP_REG_ZF && d->regularizer != DBP_REG_MMSE)
@@ -105,10 +111,11 @@ dbp_status validate(dbp_context *h, const dbp_frame_desc *d, Kind kind) {
     if (kind != K_ADMM_DL && d->eps != 0.0)
         return fail(h, DBP_ERR_INVALID_ARG, "eps (the downlink residual bound of Lemma 2) must be 0 for the uplink");
     if (kind == K_ADMM_UL) {
-        if (d->regularizer < DBP_REG_ZF || d->regularizer > DBP_REG_BOX)
+        if (d->regularizer < DBP_REG_ZF || d->regularizer > DBP_REG_BPSK)
             return fail(h, DBP_ERR_INVALID_ARG, "unknown regulariser %d", d->regularizer);
-        if (d->regularizer == DBP_REG_BOX && !(d->box_r > 0.0))
-            return fail(h, DBP_ERR_INVALID_ARG, "BOX regulariser needs box_r > 0");
+        if ((d->regularizer == DBP_REG_BOX || d->regularizer == DBP_REG_BPSK) &&
+            !(d->box_r > 0.0 && std::isfinite(d->box_r)))
+            return fail(h, DBP_ERR_INVALID_ARG, "the BOX and BPSK regularisers need a finite box_r > 0");
     }
     if (kind != K_ADMM_DL && d->regularizer == DBP_REG_MMSE) {
         if (!(d->Es > 0.0) || !(d->N0 >= 0.0) || !std::isfinite(d->N0))
@@ -511,6 +518,11 @@ void fill_params(FusedParams &p, const dbp_frame_desc *d, const Shape &s) {
         p.qam_L = L;
         p.qam_half = m / 2;
         p.qam_inv_a = 1.0 / std::sqrt(3.0 / (2.0 * (M - 1)));
+        if (M == 2) {   // BPSK {-1, +1}: two levels on the real axis, label k for 2k - 1
+            p.qam_L = 2;
+            p.qam_half = 0;
+            p.qam_inv_a = 1.0;
+        }
     }
 }
 

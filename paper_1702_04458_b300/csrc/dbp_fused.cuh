@@ -474,10 +474,10 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
             auto prox = [&](C2 (&sum)[K::NN]) {
 #pragma unroll
                 for (int j = 0; j < K::NN; ++j) {
-                    if (p.reg == 2) {
+                    if (p.reg >= 2) {   // (E2-BOX); BPSK: the real segment [-r, r]
                         const T r = ParamSel<T>::get(p.box_r, p.f_box_r), ic = ParamSel<T>::get(p.invC, p.f_invC);
                         s_[j].x = clip_r(sum[j].x * ic, r);
-                        s_[j].y = clip_r(sum[j].y * ic, r);
+                        s_[j].y = (p.reg == 2) ? clip_r(sum[j].y * ic, r) : (T)0;
                     } else {
                         s_[j] = cscale(sum[j], ParamSel<T>::get(p.e2_scale, p.f_e2_scale));
                     }

@@ -326,10 +326,10 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
                     for (int base = c * 32; base < nvu; base += C * 32) {
                         const int e = base + lane;            // < E: in the buffers
                         C2 a = tc8_sum<CE>(grp, tc8_idx<PITCH>(e), C);
-                        if (p.reg == 2) {
+                        if (p.reg >= 2) {   // (E2-BOX); BPSK: the real segment [-r, r]
                             const float r = p.f_box_r, ic = p.f_invC;
                             a.x = clip_r(a.x * ic, r);
-                            a.y = clip_r(a.y * ic, r);
+                            a.y = (p.reg == 2) ? clip_r(a.y * ic, r) : 0.f;
                         } else {
                             a = cscale(a, p.f_e2_scale);
                         }

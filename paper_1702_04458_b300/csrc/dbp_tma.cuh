@@ -784,10 +784,10 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
                 auto prox = [&](C2 (&sum)[K::NN]) {
 #pragma unroll
                     for (int j = 0; j < K::NN; ++j) {
-                        if (p.reg == 2) {
+                        if (p.reg >= 2) {   // (E2-BOX); BPSK: the real segment [-r, r]
                             const float r = p.f_box_r, ic = p.f_invC;
                             s_[j].x = clip_r(sum[j].x * ic, r);
-                            s_[j].y = clip_r(sum[j].y * ic, r);
+                            s_[j].y = (p.reg == 2) ? clip_r(sum[j].y * ic, r) : 0.f;
                         } else {
                             s_[j] = cscale(sum[j], p.f_e2_scale);
                         }
