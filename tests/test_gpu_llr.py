@@ -100,3 +100,26 @@ def test_llr_unaligned_buffers(dbp, handle, h_off, l_off):
     torch.cuda.synchronize()
     assert torch.allclose(lb[l_off:l_off + n], ref, rtol=1e-5, atol=1e-5)
     assert torch.isnan(lb[:l_off]).all() and torch.isnan(lb[l_off + n:]).all()
+
+
+def test_llr_full_size_sampled(dbp, handle):
+    """B=128, C=8, U=8, 16-QAM, 1200 x 14 at 8 dB (the bench's soft_outputs
+    line): LLRs of the whole frame's ADMM estimate; the oracle recomputes the
+    statistics and LLRs of 48 sampled subcarriers from the same estimate."""
+    W, N, B, C, U, M = 1200, 14, 128, 8, 8, 16
+    f = synth.uplink_frame(W, N, B, U, M, 8.0, seed=synth.frame_seed(2, 4))
+    H32 = f["H"].astype(np.complex64)
+    Hd = torch.from_numpy(H32).cuda()
+    yd = torch.from_numpy(f["y"].astype(np.complex64)).cuda()
+    d = dbp.frame_desc(B, C, U, W, N, qam_order=M, T_max=3, N0=f["N0"], Es=1.0)
+    x = torch.zeros((W, N, U), dtype=torch.complex64, device="cuda")
+    dbp.dbp_uplink_admm(handle, d, Hd, yd, x, None)
+    llr = torch.zeros((W, N, U, 4), dtype=torch.float32, device="cuda")
+    dbp.dbp_uplink_llr(handle, d, Hd, x, llr)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(8).choice(W, size=48, replace=False))
+    mu, nu2 = oracle.llr_stats(H32[idx].astype(np.complex128), f["N0"], 1.0, oracle.REG_MMSE)
+    ref = oracle.llr_maxlog(x.cpu().numpy()[idx].astype(np.complex128), mu, nu2, M)
+    got = llr.cpu().numpy()[idx].astype(np.float64)
+    assert (np.abs(got - ref) / (1.0 + np.abs(ref))).max() <= 1e-3
+    assert np.isfinite(llr.cpu().numpy()).all()

@@ -770,3 +770,30 @@ def test_full_size_u32_sampled(dbp, handle):
     x, lab = run_ul(dbp, handle, f, 8, 3, "admm")
     ref = oracle_ul(sub, 8, 3, "admm", "fp32")
     assert _rel_per_vector(x[idx], ref).max() <= FP32_TOL
+
+
+def test_full_size_box_prox_sampled(dbp, handle):
+    """B=128, C=8, U=8, 16-QAM, 1200 x 14 at 4 dB, ADMM T=3 with the BOX prox
+    (the bench's box_prox line): sampled parity, box bound active."""
+    f = synth.uplink_frame(1200, 14, 128, 8, 16, 4.0, seed=synth.frame_seed(2, 2))
+    r = oracle.box_radius(16)
+    idx = _sample(1200, 48, 5)
+    sub = dict(f, H=f["H"][idx], y=f["y"][idx], W=len(idx))
+    x, lab = run_ul(dbp, handle, f, 8, 3, "admm", reg=dbp.DBP_REG_BOX, box_r=r)
+    ref = oracle_ul(sub, 8, 3, "admm", "fp32", reg=oracle.REG_BOX, box_r=r)
+    assert _rel_per_vector(x[idx], ref).max() <= FP32_TOL
+    assert_labels(x[idx], lab[idx], ref, 16, np.float32)
+    assert np.abs(x.real).max() <= np.float32(r) and np.any(np.abs(x.real) == np.float32(r))
+
+
+def test_full_size_downlink_eps_sampled(dbp, handle):
+    """B=256, C=16, U=16, 64-QAM, 1200 x 14, 5 iterations with eps = 0.05 (the
+    bench's downlink_eps line): sampled parity against the oracle's Lemma 2."""
+    f = synth.downlink_frame(1200, 14, 256, 16, 64, seed=synth.frame_seed(3, 1))
+    idx = _sample(1200, 24, 6)
+    x, _ = run_dl(dbp, handle, f, 16, 5, eps=0.05)
+    ref = oracle.admm_dl(_round(f["H"][idx], "fp32"), _round(f["s"][idx], "fp32"), C=16, rho=1.0, T_max=5,
+                         eps=0.05)
+    assert _rel_per_vector(x[idx], ref).max() <= FP32_TOL
+    ref0 = oracle.admm_dl(_round(f["H"][idx], "fp32"), _round(f["s"][idx], "fp32"), C=16, rho=1.0, T_max=5)
+    assert _rel_per_vector(ref, ref0).max() > 1e-3   # eps does change the result at this size
