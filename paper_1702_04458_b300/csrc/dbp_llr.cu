@@ -104,11 +104,25 @@ __global__ void __launch_bounds__(kLlrThreads) dbp_llr_kernel(const LlrParams p)
 
     // G = H^H H.  UT = 8: 3xTF32 m16n8k8 products (FP32 accuracy) over
     // k-steps of 4 rows, lane (gq, t) of each warp accumulating entries
-    // (gq, 2t), (gq, 2t + 1) of its k-steps.  Otherwise thread (u, g) sums
-    // row u over its rows on the CUDA cores.  Padded users give zero rows.
+    // (gq, 2t), (gq, 2t + 1) of its k-steps.  UT = 32: the same products for
+    // the blocks on and above the diagonal, each warp summing a quarter of
+    // every staged chunk (gram_mma3_acc), then row u per lane.  Otherwise
+    // thread (u, g) sums row u over its rows on the CUDA cores.  Padded users
+    // give zero rows.
     constexpr bool kTc = (UT == 8);
+    constexpr bool kTc32 = (UT == 32);
+    constexpr int kGbuf = kTc32 ? NW * 16 * (UT + 2) : 2;   // gram_mma3_rows' row buffers
+    __shared__ __align__(16) float2 gbuf[kGbuf];
     const int gq = lane >> 2, t = lane & 3;
     float gacc[4] = {0.f, 0.f, 0.f, 0.f};
+    constexpr int kMT = kTc32 ? UT / 8 : 1;
+    float acc32[kMT][kMT][4];
+#pragma unroll
+    for (int i = 0; i < kMT; ++i)
+#pragma unroll
+        for (int j = 0; j < kMT; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc32[i][j][e] = 0.f;
     float2 R[UT];
 #pragma unroll
     for (int v = 0; v < UT; ++v) R[v] = make_float2(0.f, 0.f);
@@ -127,12 +141,16 @@ __global__ void __launch_bounds__(kLlrThreads) dbp_llr_kernel(const LlrParams p)
             }
         }
         const int rows4 = (rows + 3) & ~3;
-        if (kTc) {   // a k-step reads four rows: the ones past B are zero
+        if (kTc || kTc32) {   // a k-step reads four rows: the ones past B are zero
             for (int i = rows * UT + tid; i < rows4 * UT; i += kLlrThreads) Hs[i] = make_float2(0.f, 0.f);
         }
         llr_cp_wait();
         __syncthreads();
-        if constexpr (kTc) {
+        if constexpr (kTc32) {
+            constexpr int kWarpRows = Cfg::kRows / NW;   // a multiple of 4
+            const int r0 = warp * kWarpRows, r1 = min(r0 + kWarpRows, rows4);
+            if (r1 > r0) gram_mma3_acc<UT>(Hs + r0 * UT, UT, r1 - r0, lane, acc32);
+        } else if constexpr (kTc) {
             for (int ks = warp; 4 * ks < rows4; ks += NW) {
                 float a[4];
                 hh_frag(Hs, 4 * ks, gq, t, a);
@@ -153,6 +171,7 @@ __global__ void __launch_bounds__(kLlrThreads) dbp_llr_kernel(const LlrParams p)
             }
         }
     }
+    if constexpr (kTc32) gram_mma3_rows<UT>(acc32, &gbuf[warp * 16 * (UT + 2)], lane, u, R);
     if constexpr (!kTc) {
 #pragma unroll
         for (int msk = UT; msk < 32; msk <<= 1) {   // the warp's row groups
@@ -204,7 +223,11 @@ __global__ void __launch_bounds__(kLlrThreads) dbp_llr_kernel(const LlrParams p)
 #pragma unroll
             for (int v = 0; v < UT; ++v)
                 if (v == u) R[v].x += (u < U) ? p.delta : 1.f;   // padded users: identity rows
-            gj_invert<UT>(R, scratch, u, lane);
+            if constexpr (kTc32) {
+                gj_invert_f<UT>(R, scratch, u, lane);   // the step loop stays rolled at 32 users
+            } else {
+                gj_invert<UT>(R, scratch, u, lane);
+            }
             float Auu = 0.f;
 #pragma unroll
             for (int v = 0; v < UT; ++v)

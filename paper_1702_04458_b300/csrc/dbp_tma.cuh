@@ -315,21 +315,15 @@ template <int UT, typename TIn> struct FP32Mma {
 // H[s][u] as stored, A_im = (-Im, Re) of it, B'[2s:2s+2][n] = B[s][n] as
 // stored; m16n8k8, four complex rows per k-step).  Output paths as gram_mma
 // and mf_mma.
+// Accumulates the Gram's blocks on and above the diagonal (the Gram is
+// Hermitian) over rows 0 .. h_rows - 1 of Hs (pitch hp; h_rows a multiple
+// of 4) into acc, which the caller zeroes; calls may continue one sum over
+// several row blocks.
 template <int UT>
-__device__ __forceinline__ void gram_mma3(const float2 *Hs, int hp, int h_rows, float2 *G, int lane, int u,
-                                          float2 (&R)[UT]) {
+__device__ __forceinline__ void gram_mma3_acc(const float2 *Hs, int hp, int h_rows, int lane,
+                                              float (&acc)[UT / 8][UT / 8][4]) {
     constexpr int MT = UT / 8;
-    constexpr int LD = UT + 2;
-    constexpr int PASSES = (UT > 16) ? UT / 16 : 1;
-    constexpr int MPP = MT / PASSES;
     const int g = lane >> 2, t = lane & 3;
-    float acc[MT][MT][4];
-#pragma unroll
-    for (int i = 0; i < MT; ++i)
-#pragma unroll
-        for (int j = 0; j < MT; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
     for (int s0 = 0; s0 < h_rows; s0 += 4) {
         uint32_t ah[MT][4], al[MT][4];
 #pragma unroll
@@ -340,14 +334,26 @@ __device__ __forceinline__ void gram_mma3(const float2 *Hs, int hp, int h_rows, 
             for (int i = 0; i < 4; ++i) split3(a[i], ah[mt][i], al[mt][i]);
         }
         // the B fragment of H_c for n-tile nt holds the values a[0], a[2] of
-        // m-tile nt; only the blocks on and above the diagonal (the Gram is
-        // Hermitian)
+        // m-tile nt
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
             for (int nt = mt; nt < MT; ++nt)
                 mma3(acc[mt][nt], ah[mt], al[mt], ah[nt][0], ah[nt][2], al[nt][0], al[nt][2]);
     }
+}
+
+// Writes the Gram accumulated by gram_mma3_acc through the row buffer G
+// (16 rows of pitch UT + 2) and returns row u in R (lane u); the blocks
+// below the diagonal are the conjugate transposes of those above it.
+template <int UT>
+__device__ __forceinline__ void gram_mma3_rows(const float (&acc)[UT / 8][UT / 8][4], float2 *G, int lane, int u,
+                                               float2 (&R)[UT]) {
+    constexpr int MT = UT / 8;
+    constexpr int LD = UT + 2;
+    constexpr int PASSES = (UT > 16) ? UT / 16 : 1;
+    constexpr int MPP = MT / PASSES;
+    const int g = lane >> 2, t = lane & 3;
 #pragma unroll
     for (int pass = 0; pass < PASSES; ++pass) {
 #pragma unroll
@@ -375,6 +381,21 @@ __device__ __forceinline__ void gram_mma3(const float2 *Hs, int hp, int h_rows, 
         }
         __syncwarp();
     }
+}
+
+template <int UT>
+__device__ __forceinline__ void gram_mma3(const float2 *Hs, int hp, int h_rows, float2 *G, int lane, int u,
+                                          float2 (&R)[UT]) {
+    constexpr int MT = UT / 8;
+    float acc[MT][MT][4];
+#pragma unroll
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < MT; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+    gram_mma3_acc<UT>(Hs, hp, h_rows, lane, acc);
+    gram_mma3_rows<UT>(acc, G, lane, u, R);
 }
 
 template <int UT>

@@ -35,6 +35,9 @@ LLR_CASES = [
     (5, 6, 90, 3, 8, 64, 12.0, "mmse", "cg"),          # B=90: the last 4-row k-step reads zero rows
     (7, 4, 300, 4, 8, 16, 10.0, "zf", "admm"),         # B=300: three staged chunks of H
     (3, 14, 512, 8, 16, 4, 5.0, "mmse", "admm"),       # U=16 over several chunks, QPSK
+    (4, 5, 150, 3, 32, 16, 15.0, "mmse", "cg"),        # U=32, B=150: a 54-row last chunk, zero rows to 56
+    (3, 4, 64, 4, 20, 64, 20.0, "mmse", "admm"),       # U=20 padded to 32 (element-wise staging)
+    (5, 6, 96, 4, 32, 4, 6.0, "zf", "admm"),           # U=32, ZF, B exactly one chunk
 ]
 
 
@@ -118,6 +121,29 @@ def test_llr_full_size_sampled(dbp, handle):
     dbp.dbp_uplink_llr(handle, d, Hd, x, llr)
     torch.cuda.synchronize()
     idx = np.sort(np.random.default_rng(8).choice(W, size=48, replace=False))
+    mu, nu2 = oracle.llr_stats(H32[idx].astype(np.complex128), f["N0"], 1.0, oracle.REG_MMSE)
+    ref = oracle.llr_maxlog(x.cpu().numpy()[idx].astype(np.complex128), mu, nu2, M)
+    got = llr.cpu().numpy()[idx].astype(np.float64)
+    assert (np.abs(got - ref) / (1.0 + np.abs(ref))).max() <= 1e-3
+    assert np.isfinite(llr.cpu().numpy()).all()
+
+
+def test_llr_full_size_u32_sampled(dbp, handle):
+    """B=256, C=8, U=32, 64-QAM, 3300 x 14 at 20 dB (the bench's
+    mixed_vs_fp32.soft_outputs line): LLRs of the whole frame's FP32 ADMM
+    estimate; the oracle recomputes 16 sampled subcarriers."""
+    W, N, B, C, U, M = 3300, 14, 256, 8, 32, 64
+    f = synth.uplink_frame(W, N, B, U, M, 20.0, seed=synth.frame_seed(4, 5))
+    H32 = f["H"].astype(np.complex64)
+    Hd = torch.from_numpy(H32).cuda()
+    yd = torch.from_numpy(f["y"].astype(np.complex64)).cuda()
+    d = dbp.frame_desc(B, C, U, W, N, qam_order=M, T_max=3, N0=f["N0"], Es=1.0)
+    x = torch.zeros((W, N, U), dtype=torch.complex64, device="cuda")
+    dbp.dbp_uplink_admm(handle, d, Hd, yd, x, None)
+    llr = torch.zeros((W, N, U, 6), dtype=torch.float32, device="cuda")
+    dbp.dbp_uplink_llr(handle, d, Hd, x, llr)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(9).choice(W, size=16, replace=False))
     mu, nu2 = oracle.llr_stats(H32[idx].astype(np.complex128), f["N0"], 1.0, oracle.REG_MMSE)
     ref = oracle.llr_maxlog(x.cpu().numpy()[idx].astype(np.complex128), mu, nu2, M)
     got = llr.cpu().numpy()[idx].astype(np.float64)
