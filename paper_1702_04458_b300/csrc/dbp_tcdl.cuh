@@ -90,6 +90,49 @@ __device__ __forceinline__ void tcdl_apply(const uint32_t (&qh)[2][4][4], const 
         }
 }
 
+// Column-split Gauss-Jordan inversion of the 16 x 16 HPD matrix held as in
+// gj_split<16> (lane (u, g) holds row u, columns 8 g .. 8 g + 7), with the
+// pivot row and the pivot column published through shared memory instead of
+// 20 shuffles per step: the two lanes of row k store its 16 entries, the
+// lanes of column k's group store that column, and every lane reads back
+// the row (four 16-byte broadcast loads), its multiplier and the pivot.  The
+// values and the arithmetic are those of gj_split<16>, so the results are
+// bit-identical.  sc: 64 complex, 16-byte aligned, two buffers used in
+// turn, so one __syncwarp per step suffices.
+__device__ __forceinline__ float gj_split16_s(float2 (&A)[8], int u, int g, float2 *sc) {
+    float min_piv = 3.4e38f;
+    __syncwarp();   // every lane has loaded its row before the buffers are written
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const int gk = k >> 3, ik = k & 7;
+        float2 *buf = sc + (k & 1) * 32;   // [0, 16): row k; [16, 32): column k
+        if (u == k) {
+#pragma unroll
+            for (int i = 0; i < 8; i += 2)
+                *reinterpret_cast<float4 *>(&buf[8 * g + i]) = make_float4(A[i].x, A[i].y, A[i + 1].x, A[i + 1].y);
+        }
+        if (g == gk) buf[16 + u] = A[ik];
+        __syncwarp();
+        const float2 piv = buf[16 + k];
+        const float2 f = buf[16 + u];
+        float2 rk[8];
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) ld2(&buf[8 * g + i], rk[i], rk[i + 1]);
+        min_piv = fminf(min_piv, piv.x);
+        const float dd = __frcp_rn(fmaf(piv.x, piv.x, piv.y * piv.y));
+        const float2 inv = make_float2(piv.x * dd, -piv.y * dd);
+        const bool me = (u == k);
+        const float2 fi = cmul(f, inv);                  // f_u / p
+        const float2 m = me ? make_float2(1.f - inv.x, -inv.y) : fi;
+        const float2 nm = make_float2(-m.x, -m.y);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) cmac(A[i], nm, rk[i]);
+        if (g == gk) A[ik] = me ? inv : make_float2(-fi.x, -fi.y);
+    }
+    return min_piv;
+}
+
+
 // B_c^{-1} of Alg. 3 for one cluster from the staged H_c (S x 16, row pitch
 // 16): the Gram conj(H_c^H H_c) on the tensor cores (3 x TF32), plus delta on
 // the diagonal, row-major into Qs (pitch QP), then the column-split
@@ -153,7 +196,7 @@ __device__ __forceinline__ void tcdl_operator(const float2 *Hs, int S, float2 *Q
         if (8 * gc + i == ur) dmax = A[i].x;
 #pragma unroll
     for (int m2 = 16; m2 > 0; m2 >>= 1) dmax = fmaxf(dmax, shfl_x(dmax, m2));
-    const float min_piv = gj_split<16>(A, ur, gc);
+    const float min_piv = gj_split16_s(A, ur, gc, Qs);   // B_c in Qs is no longer read
     __syncwarp();
     if (!(min_piv >= 0x1p-12f * dmax) && valid) {
         // FP64 retry: B_c and its inverse again in FP64 (row ur per lane)
