@@ -51,6 +51,7 @@ MIX = Workload(B=256, C=8, U=32, W=3300, N=14, M=64, T=3)
 MIX_SNR_DB = 20.0
 DL_EPS = 0.05                  # Lemma 2 relaxation of the downlink extension line
 MIX_SWEEP_DB = (10.0, 14.0, 18.0, 22.0, 26.0, 30.0)
+BPSK_SNR_DB = -6.0              # BPSK prox line: errors countable in one frame
 MIX_SWEEP_MAX_FRAMES = 12      # 12 x 8.87 Mbit = 1.06e8 bits
 SNRS_DB = [float(2 * i) for i in range(11)]
 ROTATE = 8
@@ -1122,6 +1123,29 @@ def main(argv=None) -> int:
                            rho=1.0, N0=d["N0"], Es=1.0, box_r=box_r) for d in dev]
     box_ms = back_to_back(lambda k: dbp.dbp_uplink_admm(h, dbox[k % ROTATE], dev[k % ROTATE]["H"],
                                                         dev[k % ROTATE]["y"], xa, la, sp), KX)
+    # the BPSK prox on a BPSK frame of the same shape: 8 rotating device copies
+    # (216 MB, larger than L2); the BER of the BPSK prox and of ZF (decision:
+    # the sign of the real part) on the frame
+    BP = Workload(B=UL.B, C=UL.C, U=UL.U, W=UL.W, N=UL.N, M=2, T=UL.T)
+    fb = synth.uplink_frame(UL.W, UL.N, UL.B, UL.U, 2, BPSK_SNR_DB, seed=synth.frame_seed(2, 90) + 100000 * rank)
+    Hb = torch.from_numpy(fb["H"].astype(np.complex64)).to(device)
+    yb = torch.from_numpy(fb["y"].astype(np.complex64)).to(device)
+    bpsk_in = [(Hb, yb)] + [(Hb.clone(), yb.clone()) for _ in range(ROTATE - 1)]
+    dbpsk = dbp.frame_desc(UL.B, UL.C, UL.U, UL.W, UL.N, qam_order=2, T_max=UL.T, regularizer=dbp.DBP_REG_BPSK,
+                           rho=1.0, N0=fb["N0"], Es=1.0, box_r=1.0)
+    lb = torch.empty((UL.W, UL.N, UL.U), dtype=torch.uint8, device=device)
+    bpsk_ms = back_to_back(lambda k: dbp.dbp_uplink_admm(h, dbpsk, bpsk_in[k % ROTATE][0], bpsk_in[k % ROTATE][1],
+                                                          xa, lb, sp), KX)
+    dbp.dbp_uplink_admm(h, dbpsk, Hb, yb, xa, lb, sp)
+    torch.cuda.synchronize(device)
+    nb = UL.W * UL.N * UL.U
+    bpsk_err = int((lb.cpu().numpy() != fb["labels"]).sum())
+    dzf = dbp.frame_desc(UL.B, UL.C, UL.U, UL.W, UL.N, qam_order=0, T_max=UL.T, regularizer=dbp.DBP_REG_ZF,
+                         rho=1.0, N0=fb["N0"], Es=1.0)
+    dbp.dbp_uplink_admm(h, dzf, Hb, yb, xa, None, sp)
+    torch.cuda.synchronize(device)
+    zf_err = int(((xa.real.cpu().numpy() > 0).astype(np.uint8) != fb["labels"]).sum())
+    del bpsk_in, Hb, yb, lb
     llr = torch.empty((UL.W, UL.N, UL.U, UL.M.bit_length() - 1), dtype=torch.float32, device=device)
     # the kernel reads H and x only (10.9 MB per frame): 24 rotating copies
     # (261 MB) keep its inputs out of L2 between launches
@@ -1137,6 +1161,11 @@ def main(argv=None) -> int:
                      "ms_per_frame": box_ms, "gbit_s": detected_bits(UL) / (box_ms / 1e3) / 1e9,
                      "launches": KX,
                      "roofline": roofline("admm_ul_box", "admm_ul", UL, box_ms, hbm_peak, hbm_src, alu_peak)},
+        "bpsk_prox": {"workload": (f"uplink ADMM T={UL.T}, BPSK prox r=1 at {BPSK_SNR_DB:g} dB: B={UL.B} C={UL.C} "
+                                   f"S={UL.S} U={UL.U} BPSK W={UL.W} N={UL.N} i.i.d. Rayleigh, fp32 complex"),
+                      "ms_per_frame": bpsk_ms, "gbit_s": detected_bits(BP) / (bpsk_ms / 1e3) / 1e9,
+                      "launches": KX, "ber": bpsk_err / nb, "ber_zf": zf_err / nb, "bits": nb,
+                      "roofline": roofline("admm_ul_bpsk", "admm_ul", BP, bpsk_ms, hbm_peak, hbm_src, alu_peak)},
         "soft_outputs": {"workload": workload_name(UL, "max-log LLRs of the ADMM estimate (MMSE statistics)"),
                          "ms_per_frame": llr_ms, "llr_gbit_s": detected_bits(UL) / (llr_ms / 1e3) / 1e9,
                          "launches": KX, "timing": "launches captured into one CUDA graph, one replay between "

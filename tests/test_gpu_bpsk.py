@@ -127,3 +127,28 @@ def test_bpsk_descriptor_checks(dbp, handle, kind, bad):
     with pytest.raises(dbp.DbpError) as ei:
         fn(handle, d, buf, buf, buf, None)
     assert ei.value.status == dbp.DBP_ERR_INVALID_ARG
+
+
+def test_bpsk_full_size_sampled(dbp, handle):
+    """B=128, C=8, U=8, BPSK, 1200 x 14 at -6 dB, ADMM T=3 with the BPSK prox
+    (the bench's bpsk_prox line): the whole frame on the GPU, the oracle on
+    48 sampled subcarriers; labels from the kernel's estimate."""
+    W, N, B, C, U, T = 1200, 14, 128, 8, 8, 3
+    f = synth.uplink_frame(W, N, B, U, 2, -6.0, seed=synth.frame_seed(2, 90))
+    Hd = torch.from_numpy(f["H"].astype(np.complex64)).cuda()
+    yd = torch.from_numpy(f["y"].astype(np.complex64)).cuda()
+    d = dbp.frame_desc(B, C, U, W, N, qam_order=2, T_max=T, regularizer=dbp.DBP_REG_BPSK, rho=1.0, N0=f["N0"],
+                       Es=1.0, box_r=1.0)
+    xd = torch.zeros((W, N, U), dtype=torch.complex64, device="cuda")
+    ld = torch.zeros((W, N, U), dtype=torch.uint8, device="cuda")
+    dbp.dbp_uplink_admm(handle, d, Hd, yd, xd, ld)
+    torch.cuda.synchronize()
+    x, lab = xd.cpu().numpy().astype(np.complex128), ld.cpu().numpy()
+    idx = np.sort(np.random.default_rng(10).choice(W, size=48, replace=False))
+    H = f["H"][idx].astype(np.complex64).astype(np.complex128)
+    y = f["y"][idx].astype(np.complex64).astype(np.complex128)
+    ref = oracle.admm_ul(H, y, C=C, rho=1.0, N0=f["N0"], Es=1.0, T_max=T, reg=oracle.REG_BPSK, box_r=1.0)
+    rel = np.linalg.norm(x[idx] - ref, axis=-1) / np.linalg.norm(ref, axis=-1)
+    assert rel.max() <= FP32_TOL
+    assert np.array_equal(lab, oracle.slice_labels(x, 2, dtype=np.float32))
+    assert np.all(x.imag == 0.0)
