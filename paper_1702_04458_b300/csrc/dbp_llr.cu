@@ -16,11 +16,11 @@
 // One CTA of four warps per subcarrier.  The CTA stages the B rows of H_w
 // into shared memory with asynchronous copies (every load of a chunk issued
 // before the first wait, so a subcarrier costs one memory round trip per
-// chunk, not one per row), thread (u, g) accumulates row u of G over the
-// rows g, g + G, ... of the chunk, the row groups are summed by shuffles
-// within a warp and through shared memory across warps, one warp inverts
-// the Gram in registers (Gauss-Jordan, HPD, no pivoting) for A_uu, and the
-// CTA's threads then run over the (symbol, user) entries of the subcarrier.
+// chunk, not one per row) and splits the Gram's rows over its warps (on the
+// tensor cores at 8 and 32 users, on the CUDA cores otherwise); the warps'
+// partial Grams are summed through shared memory, one warp inverts the Gram
+// in registers (Gauss-Jordan, HPD, no pivoting) for A_uu, and the CTA's
+// threads then run over the (symbol, user) entries of the subcarrier.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -39,7 +39,7 @@ struct LlrParams {
     const float2 *x;     // [W][N][U]
     float *llr;          // [W][N][U][m]
     int W, N, B, U;
-    int m, half;         // bits per symbol, bits per axis (the kernel's template argument)
+    int half;            // bits per axis (selects the kernel's template argument)
     int llr_align;       // largest power of two (up to 16) dividing the llr address
     int zf;              // 1: ZF statistics, 0: MMSE
     float delta, N0, Es;
@@ -347,7 +347,6 @@ dbp_status dbp_uplink_llr(dbp_handle_t h, const dbp_frame_desc *d, const void *H
     p.U = d->U;
     int m = 0;
     while ((1 << m) < d->qam_order) ++m;
-    p.m = m;
     p.half = m / 2;
     p.zf = (d->regularizer == DBP_REG_ZF);
     p.delta = p.zf ? 0.f : (float)(d->N0 / d->Es);
