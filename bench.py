@@ -360,6 +360,56 @@ def cpu_baseline(frames, seconds: float):
             "sample": f"{reps} full frames (1200 x 14, ADMM T=3 + CG T=8), {el:.1f} s, FP64 OpenMP over subcarriers"}
 
 
+def cpu_rows(seconds_per_row: float = 1.5):
+    """The oracle on the other measured rows, each on a small synthetic
+    sample of that row's shapes, repeated for about seconds_per_row and
+    scaled to one full frame (the oracle's time grows with the subcarriers)."""
+    import oracle
+    rows = {}
+
+    def timed(fn, sample_w, wl, what):
+        fn()
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            fn()
+            reps += 1
+            el = time.perf_counter() - t0
+            if el >= seconds_per_row:
+                break
+        frame_s = el / reps * wl.W / sample_w
+        return {"ms_per_frame": frame_s * 1e3, "gbit_s": detected_bits(wl) / frame_s / 1e9,
+                "sample": f"{what}: {sample_w} of {wl.W} subcarriers x {wl.N} symbols, {reps} repeats, {el:.1f} s"}
+
+    fd = synth.downlink_frame(16, DL.N, DL.B, DL.U, DL.M, seed=7001)
+    rows["downlink"] = timed(lambda: oracle.admm_dl(fd["H"], fd["s"], C=DL.C, rho=1.0, T_max=DL.T), 16, DL,
+                             f"Alg. 3, T={DL.T}")
+    fu = synth.uplink_frame(64, UL.N, UL.B, UL.U, UL.M, 4.0, seed=7002)
+    r16 = oracle.box_radius(UL.M)
+    rows["box_prox"] = timed(lambda: oracle.admm_ul(fu["H"], fu["y"], C=UL.C, rho=1.0, N0=fu["N0"], T_max=UL.T,
+                                                    reg=oracle.REG_BOX, box_r=r16), 64, UL, f"Alg. 1 BOX, T={UL.T}")
+    fb = synth.uplink_frame(64, UL.N, UL.B, UL.U, 2, BPSK_SNR_DB, seed=7003)
+    BP = Workload(B=UL.B, C=UL.C, U=UL.U, W=UL.W, N=UL.N, M=2, T=UL.T)
+    rows["bpsk_prox"] = timed(lambda: oracle.admm_ul(fb["H"], fb["y"], C=UL.C, rho=1.0, N0=fb["N0"], T_max=UL.T,
+                                                     reg=oracle.REG_BPSK, box_r=1.0), 64, BP, f"Alg. 1 BPSK, T={UL.T}")
+    x8 = oracle.admm_ul(fu["H"], fu["y"], C=UL.C, rho=1.0, N0=fu["N0"], T_max=UL.T)
+
+    def llr8():
+        mu, nu2 = oracle.llr_stats(fu["H"], fu["N0"], 1.0, oracle.REG_MMSE)
+        oracle.llr_maxlog(x8, mu, nu2, UL.M)
+    rows["soft_outputs"] = timed(llr8, 64, UL, "LLR statistics and max-log LLRs")
+    fm = synth.uplink_frame(8, MIX.N, MIX.B, MIX.U, MIX.M, MIX_SNR_DB, seed=7004)
+    rows["mixed_u32"] = timed(lambda: oracle.admm_ul(fm["H"], fm["y"], C=MIX.C, rho=1.0, N0=fm["N0"], T_max=MIX.T),
+                              8, MIX, f"Alg. 1 at U={MIX.U}, T={MIX.T}")
+    x32 = oracle.admm_ul(fm["H"], fm["y"], C=MIX.C, rho=1.0, N0=fm["N0"], T_max=MIX.T)
+
+    def llr32():
+        mu, nu2 = oracle.llr_stats(fm["H"], fm["N0"], 1.0, oracle.REG_MMSE)
+        oracle.llr_maxlog(x32, mu, nu2, MIX.M)
+    rows["soft_outputs_u32"] = timed(llr32, 8, MIX, "LLR statistics and max-log LLRs at U=32")
+    return rows
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -1334,6 +1384,7 @@ def main(argv=None) -> int:
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(frames, args.cpu_seconds)
+        cpu["rows"] = cpu_rows()
 
     dbp.dbp_destroy(h)
     if rank == 0:

@@ -74,3 +74,13 @@ def test_reference_arm_json_line(capsys, monkeypatch):
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_oracle_rows_beside_the_gpu_rows():
+    """cpu_baseline.rows: the oracle timed on a sample of every other measured
+    row (downlink, BOX / BPSK prox, U = 32, soft outputs), scaled to a frame."""
+    import bench
+    rows = bench.cpu_rows(0.05)
+    assert set(rows) == {"downlink", "box_prox", "bpsk_prox", "soft_outputs", "mixed_u32", "soft_outputs_u32"}
+    for name, r in rows.items():
+        assert r["ms_per_frame"] > 0 and r["gbit_s"] > 0 and " of " in r["sample"], name
