@@ -80,6 +80,44 @@ __device__ __forceinline__ void llr_stats_store(const LlrParams &p, float Auu, i
     inv_nus[u] = 1.f / nu2;
 }
 
+// Gauss-Jordan inversion of a 32 x 32 HPD matrix shared by the CTA's four
+// warps by columns: warp w, lane u holds entries (u, 8 w .. 8 w + 7) in A.
+// Step k publishes row k (lane k of every warp, its 8 entries) and column k
+// (warp k / 8) in one of two buffers of buf (2 x 64 complex, 16-byte
+// aligned) and every thread updates its 8 entries; one CTA barrier per step.
+// No pivoting (every pivot is a Schur complement of an HPD matrix).
+__device__ __forceinline__ void gj_cols32(float2 (&A)[8], int u, int w, float2 *buf) {
+#pragma unroll 1
+    for (int wk = 0; wk < 4; ++wk) {
+#pragma unroll
+        for (int ik = 0; ik < 8; ++ik) {
+            const int k = 8 * wk + ik;
+            float2 *b = buf + (ik & 1) * 64;   // [0, 32): row k; [32, 64): column k
+            if (u == k) {
+#pragma unroll
+                for (int i = 0; i < 8; i += 2)
+                    *reinterpret_cast<float4 *>(&b[8 * w + i]) = make_float4(A[i].x, A[i].y, A[i + 1].x, A[i + 1].y);
+            }
+            if (w == wk) b[32 + u] = A[ik];
+            __syncthreads();
+            const float2 piv = b[32 + k];
+            const float2 f = b[32 + u];
+            float2 rk[8];
+#pragma unroll
+            for (int i = 0; i < 8; i += 2) ld2(&b[8 * w + i], rk[i], rk[i + 1]);
+            const float dd = __frcp_rn(fmaf(piv.x, piv.x, piv.y * piv.y));
+            const float2 inv = make_float2(piv.x * dd, -piv.y * dd);
+            const bool me = (u == k);
+            const float2 fi = cmul(f, inv);                  // f_u / p
+            const float2 m = me ? make_float2(1.f - inv.x, -inv.y) : fi;
+            const float2 nm = make_float2(-m.x, -m.y);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) cmac(A[i], nm, rk[i]);
+            if (w == wk) A[ik] = me ? inv : make_float2(-fi.x, -fi.y);
+        }
+    }
+}
+
 template <int UT, int HALF>
 __global__ void __launch_bounds__(kLlrThreads) dbp_llr_kernel(const LlrParams p) {
     using Cfg = LlrCfg<UT>;
@@ -113,6 +151,7 @@ __global__ void __launch_bounds__(kLlrThreads) dbp_llr_kernel(const LlrParams p)
     constexpr bool kTc32 = (UT == 32);
     constexpr int kGbuf = kTc32 ? NW * 16 * (UT + 2) : 2;   // gram_mma3_rows' row buffers
     __shared__ __align__(16) float2 gbuf[kGbuf];
+    __shared__ __align__(16) float2 gjbuf[kTc32 ? 128 : 2];   // gj_cols32's two buffers
     const int gq = lane >> 2, t = lane & 3;
     float gacc[4] = {0.f, 0.f, 0.f, 0.f};
     constexpr int kMT = kTc32 ? UT / 8 : 1;
@@ -203,6 +242,37 @@ __global__ void __launch_bounds__(kLlrThreads) dbp_llr_kernel(const LlrParams p)
             gj8<float2, float>(e0, e1, gq, t);
             if (gq < U && (gq >> 1) == t) llr_stats_store(p, (gq & 1) ? e1.x : e0.x, gq, mus, inv_nus);
         }
+    } else if constexpr (kTc32) {
+        // part[(k UT + v) UT + u]: warp k + 1's entry (u, v) in the staging
+        // buffer; warp 0's in the Gram row buffers, free after the epilogue
+        float2 *part = Hs;
+        if (warp > 0) {
+#pragma unroll
+            for (int v = 0; v < UT; ++v) part[((warp - 1) * UT + v) * UT + u] = R[v];
+        } else {
+#pragma unroll
+            for (int v = 0; v < UT; ++v) gbuf[v * UT + u] = R[v];
+        }
+        __syncthreads();
+        float2 A[8];   // entries (u, 8 warp + i) of G + delta I
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int v = 8 * warp + i;
+            float2 a = gbuf[v * UT + u];
+#pragma unroll
+            for (int k = 0; k < NW - 1; ++k) {
+                const float2 q = part[(k * UT + v) * UT + u];
+                a.x += q.x;
+                a.y += q.y;
+            }
+            if (v == u) a.x += (u < U) ? p.delta : 1.f;   // padded users: identity rows
+            A[i] = a;
+        }
+        gj_cols32(A, u, warp, gjbuf);
+        // A_uu sits in warp u / 8 at index u % 8 (fixed register indices)
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (8 * warp + i == u && u < U) llr_stats_store(p, A[i].x, u, mus, inv_nus);
     } else {
         float2 *part = Hs;  // part[(k UT + v) UT + u]: warp k + 1's entry (u, v)
         if (warp > 0 && lane < UT) {
@@ -223,11 +293,7 @@ __global__ void __launch_bounds__(kLlrThreads) dbp_llr_kernel(const LlrParams p)
 #pragma unroll
             for (int v = 0; v < UT; ++v)
                 if (v == u) R[v].x += (u < U) ? p.delta : 1.f;   // padded users: identity rows
-            if constexpr (kTc32) {
-                gj_invert_f<UT>(R, scratch, u, lane);   // the step loop stays rolled at 32 users
-            } else {
-                gj_invert<UT>(R, scratch, u, lane);
-            }
+            gj_invert<UT>(R, scratch, u, lane);
             float Auu = 0.f;
 #pragma unroll
             for (int v = 0; v < UT; ++v)
