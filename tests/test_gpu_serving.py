@@ -187,3 +187,29 @@ def test_submission_errors_and_waits(dbp):
         dbp.dbp_server_stop(h)
     finally:
         dbp.dbp_destroy(h)
+
+
+def test_box_and_bpsk_frames_through_the_request_loop(dbp):
+    """Frames with the BOX and BPSK proxes (BPSK labels, qam_order 2) in a mix
+    with an MMSE frame: each result is bit-identical to the same frame alone."""
+    K = dbp
+    bpsk = Frame(dbp, K.DBP_KIND_UPLINK_ADMM, 128, 8, 8, 300, 14, 2, 3, seed=950)
+    bpsk.desc.regularizer, bpsk.desc.box_r = K.DBP_REG_BPSK, 1.0
+    box = Frame(dbp, K.DBP_KIND_UPLINK_ADMM, 128, 8, 8, 600, 14, 16, 3, seed=951)
+    box.desc.regularizer, box.desc.box_r = K.DBP_REG_BOX, float(3 * np.sqrt(3.0 / 30.0))
+    mmse = Frame(dbp, K.DBP_KIND_UPLINK_ADMM, 256, 8, 32, 300, 14, 64, 3, seed=952)
+    frames = [bpsk, box, mmse]
+    h = dbp.dbp_create(0)
+    try:
+        alone = [f.run_alone(dbp, h) for f in frames]
+        dbp.dbp_server_start(h, streams=3)
+        tickets = [dbp.dbp_submit(h, f.request(dbp, i)) for i, f in enumerate(frames)]
+        results = [dbp.dbp_wait(h, t, 120.0) for t in tickets]
+        dbp.dbp_server_stop(h)
+        for i, (f, r) in enumerate(zip(frames, results)):
+            assert r is not None and r.status == dbp.DBP_OK and r.user_tag == i
+            assert np.array_equal(f.out, alone[i][0]), i
+            assert np.array_equal(f.lab, alone[i][1]), i
+        assert np.all(bpsk.out.imag == 0.0) and set(np.unique(bpsk.lab)) <= {0, 1}
+    finally:
+        dbp.dbp_destroy(h)
