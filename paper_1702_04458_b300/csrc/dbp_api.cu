@@ -55,13 +55,13 @@ int max_warps_for(int prec, int UT) {
     return (UT <= 4) ? 16 : 8;
 }
 
-size_t smem_bytes_for(int prec, int UT, int nwarps) {
+size_t smem_bytes_for(int prec, int UT, int nwarps, bool clu = false) {
     size_t elems = 0;
     switch (UT) {
-    case 4: elems = dbp::fused_smem_elems<4>(nwarps); break;
-    case 8: elems = dbp::fused_smem_elems<8>(nwarps); break;
-    case 16: elems = dbp::fused_smem_elems<16>(nwarps); break;
-    default: elems = dbp::fused_smem_elems<32>(nwarps); break;
+    case 4: elems = dbp::fused_smem_elems<4>(nwarps, clu); break;
+    case 8: elems = dbp::fused_smem_elems<8>(nwarps, clu); break;
+    case 16: elems = dbp::fused_smem_elems<16>(nwarps, clu); break;
+    default: elems = dbp::fused_smem_elems<32>(nwarps, clu); break;
     }
     return elems * (prec == DBP_FP32 ? sizeof(float2) : sizeof(double2));
 }
@@ -484,7 +484,7 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
         s.nwarps = s.CPB;
         s.grid = (long long)d->W * CL;
     }
-    s.smem = smem_bytes_for(d->precision, UT, s.nwarps);
+    s.smem = smem_bytes_for(d->precision, UT, s.nwarps, s.clu);
     if (s.smem > h->smem_optin)
         return fail(h, DBP_ERR_UNSUPPORTED, "needs %zu B shared memory per CTA, device allows %zu", s.smem, h->smem_optin);
     if (s.grid > 0x7fffffffLL) return fail(h, DBP_ERR_UNSUPPORTED, "grid too large");

@@ -202,8 +202,10 @@ template <int UT> struct Tile {
     static constexpr int CONS_ELEMS = NCH * UT;             // per warp, per buffer
 };
 
-template <int UT> __host__ __device__ constexpr int fused_smem_elems(int nwarps) {
-    return nwarps * (Tile<UT>::WARP_ELEMS + 2 * Tile<UT>::CONS_ELEMS);
+template <int UT> __host__ __device__ constexpr int fused_smem_elems(int nwarps, bool clu = false) {
+    // clu: the thread-block-cluster mapping also keeps the reduced consensus
+    // slices, two buffers of CONS_ELEMS
+    return nwarps * (Tile<UT>::WARP_ELEMS + 2 * Tile<UT>::CONS_ELEMS) + (clu ? 2 * Tile<UT>::CONS_ELEMS : 0);
 }
 
 // Stage rows s0 .. s0+rows-1 of the cluster block H_c into Hs[SCH][HS_LD],
@@ -338,6 +340,7 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
     C2 *Vb = Ys + K::NCH * K::YS_LD;
     C2 *cons = smem + nwarps * K::WARP_ELEMS;          // [2][nwarps][NCH][UT]
     C2 *cons_grp = cons + (size_t)(pl * p.C) * K::CONS_ELEMS;
+    C2 *wsum = cons + (size_t)2 * nwarps * K::CONS_ELEMS;   // CLU: [2][NCH][UT] reduced slices
 
     const int S = p.S, U = p.U, N = p.N, B = p.B;
     const C2 *Hc = reinterpret_cast<const C2 *>(p.H) + ((size_t)(valid ? w : 0) * B + (size_t)c * S) * U;
@@ -398,26 +401,39 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
         C2 acc[K::NN];
 
         // Consensus over the C clusters of this subcarrier: every warp
-        // publishes its U-vector, all warps read all C of them and form the
-        // sum in cluster order.
+        // publishes its U-vector and every entry is summed in cluster order.
+        // In one CTA every warp reads all C contributions of its entries.
+        // Across the CTAs of a thread-block cluster the sum takes two
+        // phases, so that each contribution crosses to another CTA once:
+        // warp c sums its slice of the entries over the C contributions
+        // (reading the other CTAs' shared memory), then every warp reads its
+        // entries' sums from the CTA that owns them.
         auto consensus = [&](const C2 (&val)[K::NN], C2 (&sum)[K::NN]) {
             C2 *mine = cons + ((size_t)buf * nwarps + warp) * K::CONS_ELEMS;
 #pragma unroll
             for (int j = 0; j < K::NN; ++j) mine[(g + K::G * j) * UT + u] = val[j];
             if (CLU) {
-                cooperative_groups::this_cluster().sync();
+                cooperative_groups::cluster_group cg_cl = cooperative_groups::this_cluster();
+                constexpr int E = K::CONS_ELEMS;
+                const int per = (E + p.C - 1) / p.C;
+                cg_cl.sync();
+                for (int e = c * per + lane; e < min(E, (c + 1) * per); e += 32) {
+                    C2 a = cz(C2());
+                    for (int rk = 0; rk < p.CL; ++rk) {
+                        const C2 *rb = cg_cl.map_shared_rank(cons + (size_t)buf * nwarps * E, rk);
+                        for (int lw = 0; lw < p.CPB; ++lw) {
+                            const C2 t = rb[(size_t)lw * E + e];
+                            a.x += t.x;
+                            a.y += t.y;
+                        }
+                    }
+                    wsum[buf * E + e] = a;
+                }
+                cg_cl.sync();
 #pragma unroll
                 for (int j = 0; j < K::NN; ++j) {
-                    C2 a = cz(C2());
                     const int idx = (g + K::G * j) * UT + u;
-                    for (int cc = 0; cc < p.C; ++cc) {
-                        const int rk = cc / p.CPB, lw = cc - rk * p.CPB;
-                        C2 *loc = cons + ((size_t)buf * nwarps + lw) * K::CONS_ELEMS + idx;
-                        const C2 t = *cooperative_groups::this_cluster().map_shared_rank(loc, rk);
-                        a.x += t.x;
-                        a.y += t.y;
-                    }
-                    sum[j] = a;
+                    sum[j] = *cg_cl.map_shared_rank(wsum + buf * E + idx, (idx / per) / p.CPB);
                 }
             } else {
                 __syncthreads();
