@@ -55,13 +55,13 @@ int max_warps_for(int prec, int UT) {
     return (UT <= 4) ? 16 : 8;
 }
 
-size_t smem_bytes_for(int prec, int UT, int nwarps, bool clu = false) {
+size_t smem_bytes_for(int prec, int UT, int nwarps, int subcarriers) {
     size_t elems = 0;
     switch (UT) {
-    case 4: elems = dbp::fused_smem_elems<4>(nwarps, clu); break;
-    case 8: elems = dbp::fused_smem_elems<8>(nwarps, clu); break;
-    case 16: elems = dbp::fused_smem_elems<16>(nwarps, clu); break;
-    default: elems = dbp::fused_smem_elems<32>(nwarps, clu); break;
+    case 4: elems = dbp::fused_smem_elems<4>(nwarps, subcarriers); break;
+    case 8: elems = dbp::fused_smem_elems<8>(nwarps, subcarriers); break;
+    case 16: elems = dbp::fused_smem_elems<16>(nwarps, subcarriers); break;
+    default: elems = dbp::fused_smem_elems<32>(nwarps, subcarriers); break;
     }
     return elems * (prec == DBP_FP32 ? sizeof(float2) : sizeof(double2));
 }
@@ -457,7 +457,7 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
         const int target = t.warps_per_cta > 0 ? t.warps_per_cta : 8;
         int P = target / C;
         if (P < 1) P = 1;
-        while (P > 1 && (P * C > maxw || smem_bytes_for(d->precision, UT, P * C) > h->smem_optin)) --P;
+        while (P > 1 && (P * C > maxw || smem_bytes_for(d->precision, UT, P * C, P) > h->smem_optin)) --P;
         s.clu = false;
         s.P = P;
         s.CPB = C;
@@ -484,7 +484,7 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
         s.nwarps = s.CPB;
         s.grid = (long long)d->W * CL;
     }
-    s.smem = smem_bytes_for(d->precision, UT, s.nwarps, s.clu);
+    s.smem = smem_bytes_for(d->precision, UT, s.nwarps, s.clu ? 1 : s.P);
     if (s.smem > h->smem_optin)
         return fail(h, DBP_ERR_UNSUPPORTED, "needs %zu B shared memory per CTA, device allows %zu", s.smem, h->smem_optin);
     if (s.grid > 0x7fffffffLL) return fail(h, DBP_ERR_UNSUPPORTED, "grid too large");

@@ -202,10 +202,10 @@ template <int UT> struct Tile {
     static constexpr int CONS_ELEMS = NCH * UT;             // per warp, per buffer
 };
 
-template <int UT> __host__ __device__ constexpr int fused_smem_elems(int nwarps, bool clu = false) {
-    // clu: the thread-block-cluster mapping also keeps the reduced consensus
-    // slices, two buffers of CONS_ELEMS
-    return nwarps * (Tile<UT>::WARP_ELEMS + 2 * Tile<UT>::CONS_ELEMS) + (clu ? 2 * Tile<UT>::CONS_ELEMS : 0);
+template <int UT> __host__ __device__ constexpr int fused_smem_elems(int nwarps, int subcarriers) {
+    // per warp: staging and contribution buffers; per subcarrier of the CTA:
+    // the reduced consensus sums, two buffers of CONS_ELEMS
+    return nwarps * (Tile<UT>::WARP_ELEMS + 2 * Tile<UT>::CONS_ELEMS) + subcarriers * 2 * Tile<UT>::CONS_ELEMS;
 }
 
 // Stage rows s0 .. s0+rows-1 of the cluster block H_c into Hs[SCH][HS_LD],
@@ -340,7 +340,9 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
     C2 *Vb = Ys + K::NCH * K::YS_LD;
     C2 *cons = smem + nwarps * K::WARP_ELEMS;          // [2][nwarps][NCH][UT]
     C2 *cons_grp = cons + (size_t)(pl * p.C) * K::CONS_ELEMS;
-    C2 *wsum = cons + (size_t)2 * nwarps * K::CONS_ELEMS;   // CLU: [2][NCH][UT] reduced slices
+    // reduced consensus sums [2][subcarriers of the CTA][NCH][UT]
+    C2 *wsum = cons + (size_t)2 * nwarps * K::CONS_ELEMS;
+    const int nsub = CLU ? 1 : p.P;
 
     const int S = p.S, U = p.U, N = p.N, B = p.B;
     const C2 *Hc = reinterpret_cast<const C2 *>(p.H) + ((size_t)(valid ? w : 0) * B + (size_t)c * S) * U;
@@ -401,13 +403,11 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
         C2 acc[K::NN];
 
         // Consensus over the C clusters of this subcarrier: every warp
-        // publishes its U-vector and every entry is summed in cluster order.
-        // In one CTA every warp reads all C contributions of its entries.
-        // Across the CTAs of a thread-block cluster the sum takes two
-        // phases, so that each contribution crosses to another CTA once:
-        // warp c sums its slice of the entries over the C contributions
-        // (reading the other CTAs' shared memory), then every warp reads its
-        // entries' sums from the CTA that owns them.
+        // publishes its U-vector and every entry is summed in cluster order,
+        // in two phases: warp c sums its slice of the entries over the C
+        // contributions, then every warp reads its entries' sums.  Across the
+        // CTAs of a thread-block cluster the contributions and the sums are
+        // read through DSMEM, each contribution crossing CTAs once.
         auto consensus = [&](const C2 (&val)[K::NN], C2 (&sum)[K::NN]) {
             C2 *mine = cons + ((size_t)buf * nwarps + warp) * K::CONS_ELEMS;
 #pragma unroll
@@ -436,19 +436,23 @@ __global__ void __launch_bounds__(Bounds<T, UT>::threads) dbp_fused_kernel(const
                     sum[j] = *cg_cl.map_shared_rank(wsum + buf * E + idx, (idx / per) / p.CPB);
                 }
             } else {
+                constexpr int E = K::CONS_ELEMS;
+                const int per = (E + p.C - 1) / p.C;
+                C2 *ws = wsum + ((size_t)buf * nsub + pl) * E;
                 __syncthreads();
-                const C2 *grp = cons_grp + (size_t)buf * nwarps * K::CONS_ELEMS;
-#pragma unroll
-                for (int j = 0; j < K::NN; ++j) {
+                const C2 *grp = cons_grp + (size_t)buf * nwarps * E;
+                for (int e = c * per + lane; e < min(E, (c + 1) * per); e += 32) {
                     C2 a = cz(C2());
-                    const int idx = (g + K::G * j) * UT + u;
                     for (int cc = 0; cc < p.C; ++cc) {
-                        const C2 t = grp[(size_t)cc * K::CONS_ELEMS + idx];
+                        const C2 t = grp[(size_t)cc * E + e];
                         a.x += t.x;
                         a.y += t.y;
                     }
-                    sum[j] = a;
+                    ws[e] = a;
                 }
+                __syncthreads();
+#pragma unroll
+                for (int j = 0; j < K::NN; ++j) sum[j] = ws[(g + K::G * j) * UT + u];
             }
             buf ^= 1;
         };
