@@ -688,8 +688,21 @@ __global__ void dbp_scale_kernel(typename C2Of<T>::type *x, size_t n, const doub
     const double e = *energy;
     const double beta = (e > 0.0) ? sqrt(count / e) : 0.0;
     const T b = (T)beta;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
+    // four independent loads in flight per thread before the stores
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        auto a0 = x[i], a1 = x[i + stride], a2 = x[i + 2 * stride], a3 = x[i + 3 * stride];
+        a0.x *= b; a0.y *= b;
+        a1.x *= b; a1.y *= b;
+        a2.x *= b; a2.y *= b;
+        a3.x *= b; a3.y *= b;
+        x[i] = a0;
+        x[i + stride] = a1;
+        x[i + 2 * stride] = a2;
+        x[i + 3 * stride] = a3;
+    }
+    for (; i < n; i += stride) {
         x[i].x *= b;
         x[i].y *= b;
     }
