@@ -119,7 +119,7 @@ __device__ __forceinline__ void gj_cols32(float2 (&A)[8], int u, int w, float2 *
 }
 
 template <int UT, int HALF>
-__global__ void __launch_bounds__(kLlrThreads) dbp_llr_kernel(const LlrParams p) {
+__global__ void __launch_bounds__(kLlrThreads, UT == 32 ? 5 : 1) dbp_llr_kernel(const LlrParams p) {
     using Cfg = LlrCfg<UT>;
     constexpr int NW = kLlrThreads / 32;   // warps per CTA
     constexpr int G = kLlrThreads / UT;    // row groups per CTA
