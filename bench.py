@@ -1,20 +1,25 @@
 #!/usr/bin/env python3
 """Benchmark: detected uplink Gbit/s of decentralized baseband processing.
 
-Workload (the uplink frame the headline metric is quoted on): B = 128 base-
-station antennas in C = 8 clusters of S = 16, U = 8 users, 16-QAM, W = 1200
-subcarriers x N = 14 OFDM symbols (channel fixed per subcarrier over the 14),
-i.i.d. Rayleigh channel, FP32 complex.  One step detects one frame with the
-decentralized ADMM detector (3 iterations) and with the decentralized CG
-detector (8 iterations); both detections count, so one step carries
-2 x U log2(M) W N = 1,075,200 detected bits.  Frames rotate over the SNR sweep
-0, 2, ..., 20 dB (8 resident frames, 226 MB of inputs, more than the 126 MB
-L2), so every step reads its inputs from HBM.
+Headline workload (the uplink frame the metric "detected uplink Gbit/s and
+p50/p99 frame latency, mixed vs FP32 at matched BER" is quoted on): B = 256
+base-station antennas in C = 8 clusters of S = 32, U = 32 users, 64-QAM,
+W = 3300 subcarriers x N = 14 OFDM symbols (channel fixed per subcarrier over
+the 14), i.i.d. Rayleigh at 20 dB, decentralized ADMM detection (Alg. 1)
+with T = 3, FP32 complex inputs.  One step detects one frame (U log2(M) W N
+= 8,870,400 bits).  Two distinct frames are each resident twice (4 x 323 MB,
+more than the 126 MB L2), so every step reads its inputs from HBM.
 
-Also measured in the same run and reported as sub-objects: the decentralized
-ADMM downlink precoder on the B = 256 / C = 16 / U = 16 / 64-QAM / 1200 x 14
-frame (5 iterations), the end-to-end rate through the host-buffer C ABI, and
-the FP64 CPU oracle on the machine's host cores.
+The last stdout line is the compact result line.  It carries, beside the
+FP32 headline, the same frames with FP16 / BF16 inputs (Gbit/s, BER against
+the FP32 BER's 95% interval, served p50/p99 latency through the request
+loop), short rows for the B=128 / C=8 / U=8 uplink frame (ADMM T=3, CG T=8)
+and the B=256 / C=16 / U=16 downlink frame (T=5), the roofline of the
+headline kernel, the FP64 CPU oracle on the host cores, the end-to-end rate
+through the host-buffer C ABI, and the SM clocks sampled during the timed
+region.  Everything else (per-row details, optional studies selected with
+--study) goes to a JSON file (--details, default gpurun_out/bench_details.json
+when that folder exists).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dbp|reference]
 For N > 1, launch under torch.distributed.run; each rank detects its own
@@ -24,6 +29,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import importlib.util
 import json
 import math
 import os
@@ -39,55 +45,71 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
-from paper_1702_04458_b300.accounting import (Workload, algorithmic_bytes,  # noqa: E402
-                                              algorithmic_mults, detected_bits,
-                                              fp32_simt_peak_tflops)
 
-METRIC = "detected uplink Gbit/s"
+
+def _load_accounting():
+    """The accounting module by path: importing the package would load the
+    CUDA library, which the CPU reference arm must not map."""
+    spec = importlib.util.spec_from_file_location(
+        "dbp_accounting", os.path.join(ROOT, "paper_1702_04458_b300", "accounting.py"))
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules[spec.name] = mod
+    spec.loader.exec_module(mod)
+    return mod
+
+
+_acc = _load_accounting()
+Workload = _acc.Workload
+algorithmic_bytes = _acc.algorithmic_bytes
+algorithmic_mults = _acc.algorithmic_mults
+detected_bits = _acc.detected_bits
+fp32_simt_peak_tflops = _acc.fp32_simt_peak_tflops
+table1_ar = _acc.table1_ar
+
+METRIC = "detected uplink Gbit/s and p50/p99 frame latency, mixed vs FP32 at matched BER"
+HEAD = Workload(B=256, C=8, U=32, W=3300, N=14, M=64, T=3)
+MIX = HEAD
+HEAD_SNR_DB = 20.0
+MIX_SNR_DB = HEAD_SNR_DB
+HEAD_FRAMES = 2                 # distinct frames; each resident twice
 UL = Workload(B=128, C=8, U=8, W=1200, N=14, M=16, T=3)
 UL_T_CG = 8
 DL = Workload(B=256, C=16, U=16, W=1200, N=14, M=64, T=5)
-MIX = Workload(B=256, C=8, U=32, W=3300, N=14, M=64, T=3)
-MIX_SNR_DB = 20.0
 DL_EPS = 0.05                  # Lemma 2 relaxation of the downlink extension line
 MIX_SWEEP_DB = (10.0, 14.0, 18.0, 22.0, 26.0, 30.0)
-BPSK_SNR_DB = -6.0              # BPSK prox line: errors countable in one frame
 MIX_SWEEP_MAX_FRAMES = 12      # 12 x 8.87 Mbit = 1.06e8 bits
+BPSK_SNR_DB = -6.0             # BPSK prox line: errors countable in one frame
 SNRS_DB = [float(2 * i) for i in range(11)]
 ROTATE = 8
+STUDIES = ("ber_sweep", "serving", "graph", "extensions", "downlink", "tradeoff", "frame_latency", "cpu_rows")
 
 
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["dbp", "reference"], default="dbp")
-    ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-downlink", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serve-frames", type=int, default=240)
+    ap.add_argument("--no-rows", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the served p50/p99 of the mixed comparison")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--tradeoff", action="store_true",
-                    help="instead of the benchmark: minimum SNR for a target uncoded BER against the "
-                         "iteration count (and its Table I complexity) for ADMM and CG")
-    ap.add_argument("--paper-table", action="store_true",
-                    help="instead of the benchmark: every cell of the paper's Table III (U=16, 64-QAM, "
-                         "1200 x 7) timed on this GPU beside the paper's printed numbers")
-    ap.add_argument("--kernel", choices=["auto", "generic", "tma", "mma", "bcast"], default="auto",
-                    help="uplink/downlink kernel path (dbp_tuning.kernel); auto picks per shape")
-    a = ap.parse_args(argv)
-    a.warmup = max(a.warmup, 3)
-    return a
+    ap.add_argument("--serve-frames", type=int, default=24)
+    ap.add_argument("--study", action="append", default=[], choices=list(STUDIES) + ["all"],
+                    help="optional studies, written to the details file")
+    ap.add_argument("--details", default=None, help="JSON file for the detailed results")
+    ap.add_argument("--kernel", choices=["auto", "tc5", "tma", "generic", "mma", "bcast"], default="auto",
+                    help="force one kernel path (default: automatic choice, autotuned)")
+    return ap.parse_args(argv)
 
 
-def workload_name(wl: Workload, what: str) -> str:
+def workload_name(wl: Workload, what: str, elem: str = "fp32 complex") -> str:
     return (f"{what}: B={wl.B} C={wl.C} S={wl.S} U={wl.U} {wl.M}-QAM W={wl.W} N={wl.N} "
-            "i.i.d. Rayleigh, fp32 complex")
+            f"i.i.d. Rayleigh, {elem}")
 
 
 # ---------------------------------------------------------------------------
@@ -140,7 +162,8 @@ class ClockSampler:
     def __init__(self, uuid: str, period_ms: int = 20):
         self.uuid, self.period_ms = uuid.replace("GPU-", "").lower(), period_ms
         self.error = None
-        self.samples = []
+        self.samples = []           # (host time, SM MHz, clock-event reason bits)
+        self.marks = []
         self.max_mhz = None
         self._stop = threading.Event()
         self._thr = None
@@ -197,7 +220,7 @@ class ClockSampler:
             try:
                 mhz = nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM)
                 rs = nv.nvmlDeviceGetCurrentClocksEventReasons(self._h)
-                self.samples.append((float(mhz), int(rs)))
+                self.samples.append((time.perf_counter(), float(mhz), int(rs)))
             except Exception:
                 pass
             time.sleep(self.period_ms / 1e3)
@@ -206,7 +229,7 @@ class ClockSampler:
         for line in self._proc.stdout:
             try:
                 mhz, rs = [x.strip() for x in line.split(",")]
-                self.samples.append((float(mhz), int(rs, 16)))
+                self.samples.append((time.perf_counter(), float(mhz), int(rs, 16)))
             except Exception:
                 pass
 
@@ -223,32 +246,33 @@ class ClockSampler:
             self._thr.join(timeout=5)
         return False
 
+    def mark(self):
+        """Host time stamp; the samples between the first and the last mark
+        are the ones taken while the timed frames ran (the host waits for
+        them before its closing mark)."""
+        self.marks.append(time.perf_counter())
+
     def summary(self):
         if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0,
                     "source": self.source, "error": self.error}
-        busy = [m for m, r in self.samples if not (r & 0x1)] or [m for m, _ in self.samples]
+        t0, t1 = (self.marks[0], self.marks[-1]) if len(self.marks) >= 2 else (-1e30, 1e30)
+        timed = [(m, r) for t, m, r in self.samples if t0 <= t <= t1]
+        pool = timed or [(m, r) for _, m, r in self.samples]
+        busy = [m for m, r in pool if not (r & 0x1)] or [m for m, _ in pool]
         reasons = set()
-        for _, r in self.samples:
+        for _, r in pool:
             for bit, name in _REASONS.items():
                 if r & bit and bit != 0x1:
                     reasons.add(name)
         return {"sm_mhz": float(statistics.median(busy)), "sm_max_mhz": self.max_mhz,
-                "reasons": sorted(reasons), "samples": len(self.samples), "source": self.source}
+                "reasons": sorted(reasons), "samples": len(self.samples), "samples_timed": len(timed),
+                "source": self.source}
 
 
 # ---------------------------------------------------------------------------
 # Peaks, traffic records
 # ---------------------------------------------------------------------------
-
-def measured_peaks():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            p = json.load(f)
-        return float(p["hbm_gbs"]), "measured"
-    except Exception:
-        return 6400.0, "fallback"
-
 
 def kernel_source_hash() -> str:
     """Hash of the kernels' device code (the .cuh headers that define them;
@@ -283,59 +307,61 @@ def recorded_traffic(kernel: str):
     return None
 
 
-def roofline(kernel: str, alg: str, wl: Workload, avg_ms: float, hbm_peak: float, hbm_src: str,
-             alu_peak: float):
-    flops = 2.0 * algorithmic_mults(alg, wl) * wl.W
-    byts = algorithmic_bytes(alg, wl) * wl.W
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "bf16_tflops": float(p["bf16_tflops"]),
+                "bf16_tflops_sustained": float(p.get("bf16_tflops_sustained", p["bf16_tflops"])),
+                "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "source": "fallback"}
+
+
+KERNEL_NAMES = {
+    "tc5": "dbp_tc32_kernel (tcgen05)", "tma": "dbp_tma_kernel (bulk copy, mma.sync)",
+    "mma": "dbp_tc8_kernel / dbp_tcdl_kernel (mma.sync)", "bcast": "dbp_admm_kernel / dbp_cg_kernel",
+    "generic": "dbp_fused_kernel", "auto": "automatic choice"}
+PATH_NAMES = {0: "auto", 1: "generic", 2: "tma", 3: "mma", 4: "bcast", 5: "tc5"}
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if f.get("kernel") == kernel and f.get("src") == src:
+            return float(f["bytes_per_launch"])
+    return None
+
+
+def roofline(key: str, alg: str, wl: Workload, avg_ms: float, peaks: dict, alu_peak: float, tensor_div: float,
+             kernel: str):
+    """The headline kernel against HBM (the binding roofline once the dense
+    products run on the tensor cores).  Bytes are algorithmic: H once per
+    subcarrier, y or s, and the outputs.  FLOPs are Table I's real
+    multiplications x 2 (the U x U rows); the tensor view divides them by the
+    tensor peak available to one FP32 product (the measured 16-bit dense peak
+    over the products one FP32 product takes), the ALU view by the FP32
+    CUDA-core peak."""
     t = avg_ms / 1e3
-    t_alu = flops / (alu_peak * 1e12)
-    t_hbm = byts / (hbm_peak * 1e9)
-    traffic = recorded_traffic(kernel)
-    if t_alu >= t_hbm:
-        ach = flops / t / 1e12
-        r = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
-             "frac": ach / alu_peak,
-             "peak_source": "derived: SMs x 128 FP32 lanes x 2 flops x 2032 MHz"}
-    else:
-        ach = byts / t / 1e9
-        r = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-             "frac": ach / hbm_peak, "peak_source": f"hbm_gbs of {hbm_src}"}
-    r.update({"traffic": traffic, "kernel": kernel, "algorithmic_bytes": byts,
-              "algorithmic_flops": flops, "avg_launch_ms": avg_ms,
-              "hbm_view": {"achieved_gbs": byts / t / 1e9, "frac": byts / t / 1e9 / hbm_peak},
-              "alu_view": {"achieved_tflops": flops / t / 1e12, "frac": flops / t / 1e12 / alu_peak}})
-    return r
-
-
-# ---------------------------------------------------------------------------
-# Frames
-# ---------------------------------------------------------------------------
-
-def ul_frames(rank: int, count: int):
-    out = []
-    for i in range(count):
-        snr = SNRS_DB[i % len(SNRS_DB)]
-        f = synth.uplink_frame(UL.W, UL.N, UL.B, UL.U, UL.M, snr,
-                               seed=synth.frame_seed(2, i) + 100000 * rank)
-        out.append(f)
-    return out
-
-
-def dl_frames(rank: int, count: int):
-    return [synth.downlink_frame(DL.W, DL.N, DL.B, DL.U, DL.M,
-                                 seed=synth.frame_seed(3, i) + 100000 * rank) for i in range(count)]
-
-
-# ---------------------------------------------------------------------------
-# CPU baseline / reference arm: the FP64 oracle on the host cores
-# ---------------------------------------------------------------------------
-
-def oracle_step(f, idx):
-    import oracle
-    H = f["H"][idx].astype(np.complex64).astype(np.complex128)
-    y = f["y"][idx].astype(np.complex64).astype(np.complex128)
-    oracle.admm_ul(H, y, C=UL.C, rho=1.0, N0=f["N0"], T_max=UL.T)
-    oracle.cg_ul(H, y, C=UL.C, rho=f["N0"], T_max=UL_T_CG)
+    byts = algorithmic_bytes(alg, wl) * wl.W
+    flops = 2.0 * algorithmic_mults(alg, wl) * wl.W
+    hbm = peaks["hbm_gbs"]
+    tpk = peaks["bf16_tflops"] / tensor_div
+    ach = byts / t / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": recorded_traffic(key), "kernel": kernel,
+            "peak_source": f"hbm_gbs of {peaks['source']}",
+            "bytes_per_launch": byts, "avg_launch_ms": avg_ms,
+            "tensor_view": {"tflops": flops / t / 1e12, "peak": tpk, "frac": flops / t / 1e12 / tpk,
+                            "peak_source": f"bf16_tflops of {peaks['source']} / {tensor_div:g} products"},
+            "alu_view": {"tflops": flops / t / 1e12, "peak": alu_peak, "frac": flops / t / 1e12 / alu_peak}}
 
 
 def cpu_cores() -> int:
@@ -345,22 +371,36 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
-def cpu_baseline(frames, seconds: float):
+def oracle_head_sample(f, idx):
+    import oracle
+    H = f["H"][idx].astype(np.complex64).astype(np.complex128)
+    y = f["y"][idx].astype(np.complex64).astype(np.complex128)
+    oracle.admm_ul(H, y, C=HEAD.C, rho=1.0, N0=f["N0"], T_max=HEAD.T)
+
+
+def cpu_baseline(seconds: float):
+    """The FP64 oracle (Alg. 1 as printed, OpenMP over subcarriers) on the
+    host cores: samples of 32 subcarriers of the headline frame, repeated for
+    about `seconds`, scaled to the frame's bits."""
     import oracle
     oracle.build()
-    idx = np.arange(UL.W)
-    oracle_step(frames[0], idx[:8])          # load / warm the library
+    f = synth.uplink_frame(256, HEAD.N, HEAD.B, HEAD.U, HEAD.M, HEAD_SNR_DB, seed=synth.frame_seed(4, 0))
+    rng = np.random.default_rng(0)
+    oracle_head_sample(f, np.arange(4))
     t0 = time.perf_counter()
-    reps = 0
+    reps, sc = 0, 0
     while True:
-        oracle_step(frames[reps % len(frames)], idx)
+        idx = np.sort(rng.choice(256, size=32, replace=False))
+        oracle_head_sample(f, idx)
         reps += 1
+        sc += 32
         el = time.perf_counter() - t0
-        if el >= seconds and reps >= 1:
+        if el >= seconds:
             break
-    bits = 2 * detected_bits(UL) * reps
+    bits = detected_bits(Workload(HEAD.B, HEAD.C, HEAD.U, sc, HEAD.N, HEAD.M, HEAD.T))
     return {"value": bits / el / 1e9, "unit": "Gbit/s", "cores": cpu_cores(), "kind": "oracle",
-            "sample": f"{reps} full frames (1200 x 14, ADMM T=3 + CG T=8), {el:.1f} s, FP64 OpenMP over subcarriers"}
+            "sample": f"{reps} x 32 subcarriers of the 3300 x 14 frame ({sc} subcarriers, {el:.1f} s), "
+                      "FP64, OpenMP over subcarriers"}
 
 
 def cpu_rows(seconds_per_row: float = 1.5):
@@ -414,39 +454,207 @@ def cpu_rows(seconds_per_row: float = 1.5):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands on the host cores, on
+    the headline workload, each step a sample of 24 subcarriers x 14 symbols."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
     oracle.build()
-    frames = ul_frames(0, 2)
-    sample = 60                               # subcarriers per step
+    f = synth.uplink_frame(128, HEAD.N, HEAD.B, HEAD.U, HEAD.M, HEAD_SNR_DB, seed=synth.frame_seed(4, 0))
+    sample = 24
     rng = np.random.default_rng(0)
-    steps_idx = [np.sort(rng.choice(UL.W, size=sample, replace=False)) for _ in range(4)]
+    steps_idx = [np.sort(rng.choice(128, size=sample, replace=False)) for _ in range(4)]
     for k in range(args.warmup):
-        oracle_step(frames[k % 2], steps_idx[k % 4])
+        oracle_head_sample(f, steps_idx[k % 4])
     t0 = time.perf_counter()
     for k in range(args.steps):
-        oracle_step(frames[k % 2], steps_idx[k % 4])
+        oracle_head_sample(f, steps_idx[k % 4])
     el = time.perf_counter() - t0
-    bits = 2 * detected_bits(Workload(UL.B, UL.C, UL.U, sample, UL.N, UL.M, UL.T)) * args.steps
+    bits = detected_bits(Workload(HEAD.B, HEAD.C, HEAD.U, sample, HEAD.N, HEAD.M, HEAD.T)) * args.steps
     val = bits / el / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Gbit/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": workload_name(UL, "uplink ADMM T=3 + CG T=8"),
+            "config": {"workload": workload_name(HEAD, f"uplink ADMM T={HEAD.T} at {HEAD_SNR_DB:g} dB"),
                        "sample_subcarriers_per_step": sample},
             "cpu_baseline": {"value": val, "unit": "Gbit/s", "cores": cpu_cores(), "kind": "oracle",
-                             "sample": f"{sample} of 1200 subcarriers x 14 symbols per step"},
+                             "sample": f"{sample} of 3300 subcarriers x 14 symbols per step"},
             "e2e": {"value": val, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-# ---------------------------------------------------------------------------
-# 16-bit inputs against FP32 at matched BER
-# ---------------------------------------------------------------------------
+def _to16(a, dt):
+    import torch
+    return torch.from_numpy(np.stack([a.real, a.imag], -1).astype(np.float32)).to(dt)
+
+
+def _bit_errors(lab, ref):
+    return int(np.unpackbits(np.bitwise_xor(lab, ref).reshape(-1, 1), axis=1).sum())
+
+
+class FrameSet:
+    """The headline frames resident on the device in one precision: every
+    distinct frame twice, and one output set per stream."""
+
+    def __init__(self, frames, prec, device):
+        import torch
+        self.bufs = []
+        for f in frames:
+            if prec == "fp32":
+                H = torch.from_numpy(f["H"].astype(np.complex64)).to(device)
+                y = torch.from_numpy(f["y"].astype(np.complex64)).to(device)
+            else:
+                dt = torch.float16 if prec == "fp16" else torch.bfloat16
+                H, y = _to16(f["H"], dt).to(device), _to16(f["y"], dt).to(device)
+            self.bufs.append((H, y, f))
+        self.bufs += [(H.clone(), y.clone(), f) for (H, y, f) in self.bufs]
+        shape = (HEAD.W, HEAD.N, HEAD.U)
+        self.out = [(torch.empty(shape, dtype=torch.complex64, device=device),
+                     torch.empty(shape, dtype=torch.uint8, device=device)) for _ in range(2)]
+
+
+def time_frames(dbp, h, fs, desc_of, K, W, streams, launching):
+    """K frames, consecutive ones alternating over two streams (own output
+    buffers), between two CUDA events on the launching stream; returns ms."""
+    import torch
+
+    def step(k):
+        H, y, f = fs.bufs[k % len(fs.bufs)]
+        x, lab = fs.out[k % 2]
+        dbp.dbp_uplink_admm(h, desc_of(f), H, y, x, lab, streams[k % 2].cuda_stream)
+
+    for k in range(W):
+        step(k)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(launching)
+    streams[1].wait_event(e0)
+    for k in range(K):
+        step(k)
+    launching.wait_stream(streams[1])
+    e1.record(launching)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def solo_ms(dbp, h, fs, desc_of, n, launching):
+    """n back-to-back launches on one stream between two CUDA events: the
+    kernel's average duration for the roofline."""
+    import torch
+    x, lab = fs.out[0]
+    for k in range(3):
+        H, y, f = fs.bufs[k % len(fs.bufs)]
+        dbp.dbp_uplink_admm(h, desc_of(f), H, y, x, lab, launching.cuda_stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(launching)
+    for k in range(n):
+        H, y, f = fs.bufs[k % len(fs.bufs)]
+        dbp.dbp_uplink_admm(h, desc_of(f), H, y, x, lab, launching.cuda_stream)
+    e1.record(launching)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def frame_ber(dbp, h, fs, desc_of, device):
+    """Bit errors of the precision's labels on every distinct frame."""
+    import torch
+    errs = bits = 0
+    x, lab = fs.out[0]
+    for (H, y, f) in fs.bufs[:len(fs.bufs) // 2]:
+        dbp.dbp_uplink_admm(h, desc_of(f), H, y, x, lab, torch.cuda.current_stream(device).cuda_stream)
+        torch.cuda.synchronize(device)
+        errs += _bit_errors(lab.cpu().numpy(), f["labels"])
+        bits += HEAD.W * HEAD.N * HEAD.U * (HEAD.M.bit_length() - 1)
+    return errs, bits
+
+
+def rows_study(dbp, h, device, launching, K, peaks, alu_peak):
+    """Short rows for the other single-GPU workloads: the B=128 / C=8 / U=8 /
+    16-QAM / 1200 x 14 uplink frame (ADMM T=3, CG T=8; 8 rotating frames,
+    216 MB) and the B=256 / C=16 / U=16 / 64-QAM / 1200 x 14 downlink frame
+    (ADMM T=5; 4 rotating frames, 300 MB), each kernel timed alone with
+    back-to-back launches on one stream."""
+    import torch
+    KX = max(min(K, 200), 10)
+    sp = launching.cuda_stream
+    out, detail = {}, {}
+    fr = [synth.uplink_frame(UL.W, UL.N, UL.B, UL.U, UL.M, SNRS_DB[i % len(SNRS_DB)],
+                             seed=synth.frame_seed(2, i)) for i in range(ROTATE)]
+    dev = [(torch.from_numpy(f["H"].astype(np.complex64)).to(device),
+            torch.from_numpy(f["y"].astype(np.complex64)).to(device), f["N0"]) for f in fr]
+    x = torch.empty((UL.W, UL.N, UL.U), dtype=torch.complex64, device=device)
+    lab = torch.empty((UL.W, UL.N, UL.U), dtype=torch.uint8, device=device)
+    for name, fn, T in (("ul_admm", dbp.dbp_uplink_admm, UL.T), ("ul_cg", dbp.dbp_uplink_cg, UL_T_CG)):
+        ds = [dbp.frame_desc(UL.B, UL.C, UL.U, UL.W, UL.N, qam_order=UL.M, T_max=T, N0=n0) for (_, _, n0) in dev]
+        for k in range(3):
+            fn(h, ds[k], dev[k][0], dev[k][1], x, lab, sp)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(launching)
+        for k in range(KX):
+            fn(h, ds[k % ROTATE], dev[k % ROTATE][0], dev[k % ROTATE][1], x, lab, sp)
+        e1.record(launching)
+        torch.cuda.synchronize(device)
+        ms = e0.elapsed_time(e1) / KX
+        wl = Workload(UL.B, UL.C, UL.U, UL.W, UL.N, UL.M, T)
+        alg = "admm_ul" if name == "ul_admm" else "cg_ul"
+        byts = algorithmic_bytes(alg, wl) * wl.W
+        out[name] = {"ms": round(ms, 4), "gbit_s": round(detected_bits(wl) / (ms / 1e3) / 1e9, 2),
+                     "hbm_frac": round(byts / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], 3)}
+        detail[name] = {"workload": workload_name(wl, f"uplink {name[3:].upper()} T={T}"), "launches": KX,
+                        "ms_per_frame": ms, "bytes_per_frame": byts,
+                        "flops_per_frame": 2.0 * algorithmic_mults(alg, wl) * wl.W}
+    del dev, x, lab
+    frd = [synth.downlink_frame(DL.W, DL.N, DL.B, DL.U, DL.M, seed=synth.frame_seed(3, i)) for i in range(4)]
+    ddev = [(torch.from_numpy(f["H"].astype(np.complex64)).to(device),
+             torch.from_numpy(f["s"].astype(np.complex64)).to(device)) for f in frd]
+    xd = torch.empty((DL.W, DL.N, DL.B), dtype=torch.complex64, device=device)
+    dd = dbp.frame_desc(DL.B, DL.C, DL.U, DL.W, DL.N, T_max=DL.T, rho=1.0)
+    for k in range(3):
+        dbp.dbp_downlink_admm(h, dd, ddev[k % 4][0], ddev[k % 4][1], xd, None, sp)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(launching)
+    for k in range(KX):
+        dbp.dbp_downlink_admm(h, dd, ddev[k % 4][0], ddev[k % 4][1], xd, None, sp)
+    e1.record(launching)
+    torch.cuda.synchronize(device)
+    ms = e0.elapsed_time(e1) / KX
+    byts = algorithmic_bytes("admm_dl", DL) * DL.W
+    t1 = table1_ar("admm_dl", "SxS", DL.C, DL.S, DL.U)
+    fl_t1 = 2.0 * DL.W * (t1["pre"] + DL.N * (t1["first"] + (DL.T - 1) * t1["sub"]))
+    out["dl_admm"] = {"ms": round(ms, 4), "gbit_s": round(detected_bits(DL) / (ms / 1e3) / 1e9, 2),
+                      "hbm_frac": round(byts / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], 3)}
+    detail["dl_admm"] = {"workload": workload_name(DL, f"downlink ADMM T={DL.T}"), "launches": KX,
+                         "ms_per_frame": ms, "bytes_per_frame": byts,
+                         "flops_table1_sxs": fl_t1, "flops_kernel_form": 2.0 * algorithmic_mults("admm_dl", DL) * DL.W,
+                         "tflops_table1": fl_t1 / (ms / 1e3) / 1e12}
+    del ddev, xd
+    torch.cuda.empty_cache()
+    return out, detail
+
+
+def e2e_host_api(dbp, h, frame, steps, launching):
+    """The headline frame end to end through the host-buffer C ABI
+    (dbp_uplink_admm_host): every call copies H and y from pinned host
+    memory to the device, detects, copies x_hat and the labels back and
+    synchronises.  Wall clock over `steps` calls."""
+    import torch
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+    H, y = pin(frame["H"].astype(np.complex64)), pin(frame["y"].astype(np.complex64))
+    shape = (HEAD.W, HEAD.N, HEAD.U)
+    x, lab = pin(np.zeros(shape, np.complex64)), pin(np.zeros(shape, np.uint8))
+    d = dbp.frame_desc(HEAD.B, HEAD.C, HEAD.U, HEAD.W, HEAD.N, qam_order=HEAD.M, T_max=HEAD.T, N0=frame["N0"])
+    dbp.dbp_uplink_admm_host(h, d, H, y, x, lab, launching.cuda_stream)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        dbp.dbp_uplink_admm_host(h, d, H, y, x, lab, launching.cuda_stream)
+    el = time.perf_counter() - t0
+    return {"value": detected_bits(HEAD) * steps / el / 1e9, "unit": "Gbit/s",
+            "h2d_bytes_per_step": int(H.nbytes + y.nbytes), "d2h_bytes_per_step": int(x.nbytes + lab.nbytes)}, el
+
 
 def _binom_ci(k: int, n: int):
     """95 % Wilson interval of a bit error rate k / n."""
@@ -459,129 +667,6 @@ def _binom_ci(k: int, n: int):
     hw = z * math.sqrt(p * (1 - p) / n + z * z / (4 * n * n)) / den
     return (max(0.0, c - hw), min(1.0, c + hw))
 
-
-def bench_mixed(dbp, h, stream, device, rank, args, hbm_peak, hbm_src, alu_peak):
-    import torch
-    f = synth.uplink_frame(MIX.W, MIX.N, MIX.B, MIX.U, MIX.M, MIX_SNR_DB,
-                           seed=synth.frame_seed(4, 5) + 100000 * rank)
-    sp = stream.cuda_stream
-    x = torch.empty((MIX.W, MIX.N, MIX.U), dtype=torch.complex64, device=device)
-    lab = torch.empty((MIX.W, MIX.N, MIX.U), dtype=torch.uint8, device=device)
-    out = {"workload": workload_name(MIX, f"uplink ADMM T={MIX.T} at {MIX_SNR_DB:g} dB").replace(
-        ", fp32 complex", ""), "per_precision": {}}
-    nbits = MIX.W * MIX.N * MIX.U * (MIX.M.bit_length() - 1)
-    for name, prec in (("fp32", dbp.DBP_FP32), ("fp16", dbp.DBP_FP16), ("bf16", dbp.DBP_BF16)):
-        if prec == dbp.DBP_FP32:
-            H = torch.from_numpy(f["H"].astype(np.complex64)).to(device)
-            y = torch.from_numpy(f["y"].astype(np.complex64)).to(device)
-            eb = 8
-        else:
-            dt = torch.float16 if name == "fp16" else torch.bfloat16
-            H = torch.from_numpy(np.stack([f["H"].real, f["H"].imag], -1).astype(np.float32)).to(dt).to(device)
-            y = torch.from_numpy(np.stack([f["y"].real, f["y"].imag], -1).astype(np.float32)).to(dt).to(device)
-            eb = 4
-        d = dbp.frame_desc(MIX.B, MIX.C, MIX.U, MIX.W, MIX.N, qam_order=MIX.M, T_max=MIX.T,
-                           precision=prec, rho=1.0, N0=f["N0"], Es=1.0)
-        for _ in range(args.warmup):
-            dbp.dbp_uplink_admm(h, d, H, y, x, lab, sp)
-        torch.cuda.synchronize(device)
-        K = max(min(args.steps // 10, 200), 5)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(K):
-            dbp.dbp_uplink_admm(h, d, H, y, x, lab, sp)
-        e1.record(stream)
-        torch.cuda.synchronize(device)
-        ms = e0.elapsed_time(e1) / K
-        errs = int(np.unpackbits(np.bitwise_xor(lab.cpu().numpy(), f["labels"]).reshape(-1, 1), axis=1).sum())
-        xh = x.cpu().numpy().astype(np.complex128)
-        if name == "fp32":
-            x32 = xh
-            # soft outputs of this estimate (the frame's H, 216 MB, is larger than L2)
-            llr = torch.empty((MIX.W, MIX.N, MIX.U, MIX.M.bit_length() - 1), dtype=torch.float32, device=device)
-            for _ in range(3):
-                dbp.dbp_uplink_llr(h, d, H, x, llr, sp)
-            torch.cuda.synchronize(device)
-            KL = max(min(args.steps // 50, 100), 5)
-            e0.record(stream)
-            for _ in range(KL):
-                dbp.dbp_uplink_llr(h, d, H, x, llr, sp)
-            e1.record(stream)
-            torch.cuda.synchronize(device)
-            lms = e0.elapsed_time(e1) / KL
-            lbytes = MIX.W * (MIX.B * MIX.U * 8 + MIX.N * MIX.U * 8 + MIX.N * MIX.U * llr.shape[-1] * 4)
-            out["soft_outputs"] = {
-                "workload": "max-log LLRs of the FP32 ADMM estimate (MMSE statistics), same frame",
-                "ms_per_frame": lms, "launches": KL, "timing": "back-to-back launches on one stream",
-                "bytes_per_frame": lbytes, "hbm_gbs": lbytes / (lms / 1e3) / 1e9,
-                "hbm_frac": lbytes / (lms / 1e3) / 1e9 / hbm_peak}
-            del llr
-        wl = Workload(MIX.B, MIX.C, MIX.U, MIX.W, MIX.N, MIX.M, MIX.T, elem_bytes=eb)
-        rf = roofline(f"admm_ul_{name}", "admm_ul", wl, ms, hbm_peak, hbm_src, alu_peak)
-        out["per_precision"][name] = {
-            "gbit_s": detected_bits(MIX) / (ms / 1e3) / 1e9, "ms_per_frame": ms, "launches": K,
-            "ber": errs / nbits, "ber_ci95": _binom_ci(errs, nbits), "bit_errors": errs, "bits": nbits,
-            "hbm_gbs": rf["hbm_view"]["achieved_gbs"], "alu_tflops": rf["alu_view"]["achieved_tflops"]}
-        if name != "fp32":
-            # input quantisation: relative error per (subcarrier, symbol) vector
-            # against the FP32 path on the original inputs (which matches the
-            # FP64 oracle to 1e-4)
-            rel = np.linalg.norm(xh - x32, axis=-1) / np.maximum(np.linalg.norm(x32, axis=-1), 1e-30)
-            out["per_precision"][name]["rel_err_vs_fp32"] = {"max": float(rel.max()),
-                                                             "median": float(np.median(rel))}
-        del H, y
-    pp = out["per_precision"]
-    for name in ("fp16", "bf16"):
-        lo, hi = pp["fp32"]["ber_ci95"]
-        pp[name]["ber_within_fp32_ci95"] = bool(lo <= pp[name]["ber"] <= hi)
-        pp[name]["speedup_vs_fp32"] = pp["fp32"]["ms_per_frame"] / pp[name]["ms_per_frame"]
-    # BER over the 10-30 dB range of this workload: the same channel and
-    # symbols with fresh noise, every precision on the same noise; each point
-    # runs frames until the FP32 path has 200 bit errors or 1e8 bits
-    sweep = []
-    precs = (("fp32", dbp.DBP_FP32), ("fp16", dbp.DBP_FP16), ("bf16", dbp.DBP_BF16))
-    dev_H = {}
-    for name, prec in precs:
-        if prec == dbp.DBP_FP32:
-            dev_H[name] = torch.from_numpy(f["H"].astype(np.complex64)).to(device)
-        else:
-            dt = torch.float16 if name == "fp16" else torch.bfloat16
-            dev_H[name] = torch.from_numpy(np.stack([f["H"].real, f["H"].imag], -1).astype(np.float32)).to(dt).to(device)
-    for i, snr in enumerate(MIX_SWEEP_DB):
-        errs = {name: 0 for name, _ in precs}
-        frames_run = 0
-        while frames_run < MIX_SWEEP_MAX_FRAMES and (errs["fp32"] < 200 or frames_run == 0):
-            fs = synth.at_snr(f, snr, seed=synth.frame_seed(4, i) + 1000 * frames_run + 100000 * rank)
-            for name, prec in precs:
-                if prec == dbp.DBP_FP32:
-                    y = torch.from_numpy(fs["y"].astype(np.complex64)).to(device)
-                else:
-                    dt = torch.float16 if name == "fp16" else torch.bfloat16
-                    y = torch.from_numpy(np.stack([fs["y"].real, fs["y"].imag], -1).astype(np.float32)).to(dt).to(device)
-                d = dbp.frame_desc(MIX.B, MIX.C, MIX.U, MIX.W, MIX.N, qam_order=MIX.M, T_max=MIX.T,
-                                   precision=prec, rho=1.0, N0=fs["N0"], Es=1.0)
-                dbp.dbp_uplink_admm(h, d, dev_H[name], y, x, lab, sp)
-                torch.cuda.synchronize(device)
-                errs[name] += int(np.unpackbits(np.bitwise_xor(lab.cpu().numpy(), fs["labels"]).reshape(-1, 1),
-                                                axis=1).sum())
-                del y
-            frames_run += 1
-        bits = frames_run * nbits
-        point = {"snr_db": snr, "frames": frames_run, "bits": bits}
-        for name, _ in precs:
-            point[name] = {"ber": errs[name] / bits, "bit_errors": errs[name]}
-        lo, hi = _binom_ci(errs["fp32"], bits)
-        point["fp32"]["ber_ci95"] = [lo, hi]
-        for name in ("fp16", "bf16"):
-            point[name]["within_fp32_ci95"] = bool(lo <= point[name]["ber"] <= hi)
-        sweep.append(point)
-    del dev_H
-    out["ber_sweep"] = {"bits_per_frame": nbits, "rule": "frames until 200 FP32 bit errors or "
-                        f"{MIX_SWEEP_MAX_FRAMES} frames ({MIX_SWEEP_MAX_FRAMES * nbits:.2e} bits)", "points": sweep,
-                        "all_within_fp32_ci95": all(p[n]["within_fp32_ci95"] for p in sweep
-                                                    for n in ("fp16", "bf16"))}
-    out["fp64_retries"] = dbp.dbp_fp64_retries(h)
-    return out
 
 
 # ---------------------------------------------------------------------------
@@ -875,10 +960,6 @@ def bench_served_precision(dbp, h, args):
     return out
 
 
-# ---------------------------------------------------------------------------
-# GPU arm
-# ---------------------------------------------------------------------------
-
 def bench_graph(dbp, h, stream, device, args):
     """The served-stream shapes as one batch of device-resident frames (uplink
     ADMM, uplink CG and downlink ADMM in turn), captured into one CUDA graph
@@ -944,108 +1025,6 @@ def bench_graph(dbp, h, stream, device, args):
             "speedup_vs_sequential": res["sequential"] / res["graph"]}
 
 
-# Table III of the paper: latency L [ms] / throughput [Mb/s] per detection or
-# beamforming cycle on its K40 cluster with MPI, U = 16, 64-QAM, 1200
-# subcarriers x 7 symbols; columns (B, C), rows T_max = 1..5.
-PAPER_COLS = [(64, 8), (128, 16), (256, 32), (128, 8), (256, 16), (512, 32), (256, 8), (512, 16), (1024, 32)]
-PAPER_TABLE_III = {
-    "admm_ul": [
-        [(2.060, 417.5), (2.166, 397.1), (2.520, 341.4), (3.810, 225.7), (4.079, 210.9), (4.466, 192.6),
-         (4.329, 198.7), (4.516, 190.5), (4.693, 183.3)],
-        [(4.989, 172.4), (5.411, 159.0), (6.451, 133.3), (6.756, 127.3), (7.597, 113.2), (8.495, 101.3),
-         (7.173, 119.9), (7.855, 109.5), (8.615, 99.84)],
-        [(7.728, 111.3), (8.561, 100.5), (9.910, 86.80), (9.712, 88.56), (10.94, 78.62), (12.68, 67.85),
-         (10.22, 84.15), (11.27, 76.30), (12.98, 66.28)],
-        [(10.80, 79.67), (11.92, 72.16), (13.79, 62.39), (12.44, 69.12), (14.08, 61.10), (16.64, 51.68),
-         (13.49, 63.78), (14.83, 57.99), (17.27, 49.81)],
-        [(13.43, 64.01), (15.69, 54.83), (17.59, 48.90), (15.18, 56.66), (17.88, 48.10), (21.11, 40.75),
-         (16.50, 52.13), (18.65, 46.12), (21.53, 39.95)]],
-    "cg_ul": [
-        [(3.516, 244.7), (4.077, 211.0), (4.594, 187.2), (3.811, 225.7), (4.325, 198.9), (4.960, 173.4),
-         (4.232, 203.3), (4.729, 181.9), (4.984, 161.8)],
-        [(5.078, 169.4), (6.192, 138.9), (6.574, 130.8), (5.597, 153.7), (6.160, 139.6), (7.190, 119.6),
-         (6.207, 138.6), (7.067, 121.7), (7.150, 112.8)],
-        [(6.567, 131.0), (8.250, 104.3), (8.490, 101.3), (7.323, 117.5), (8.436, 102.0), (9.310, 92.39),
-         (7.841, 109.7), (9.100, 94.52), (9.314, 86.58)],
-        [(8.080, 106.5), (10.02, 85.87), (10.79, 79.70), (9.243, 93.06), (10.22, 84.12), (11.91, 72.20),
-         (9.775, 88.00), (10.90, 78.94), (11.45, 70.43)],
-        [(9.787, 87.88), (11.97, 71.85), (12.74, 67.52), (11.07, 77.69), (11.95, 71.99), (14.03, 61.30),
-         (11.93, 72.08), (13.27, 64.82), (13.61, 59.25)]],
-    "admm_dl": [
-        [(0.744, 1156), (0.745, 1155), (0.746, 1154), (2.261, 380.5), (2.266, 379.6), (2.271, 378.8),
-         (2.785, 308.8), (2.792, 308.1), (2.797, 307.6)],
-        [(2.685, 320.3), (2.849, 301.9), (2.974, 289.2), (4.048, 212.5), (4.318, 199.2), (4.557, 188.8),
-         (4.618, 186.3), (4.762, 180.6), (5.084, 169.2)],
-        [(4.567, 188.4), (4.954, 173.6), (4.803, 179.1), (5.741, 149.8), (5.966, 144.2), (6.240, 137.9),
-         (6.323, 136.0), (6.651, 129.3), (7.213, 119.2)],
-        [(6.269, 137.2), (6.797, 126.6), (6.769, 127.1), (7.352, 117.0), (7.741, 111.1), (8.720, 98.65),
-         (7.849, 109.6), (8.371, 102.8), (9.380, 91.70)],
-        [(8.055, 106.8), (9.012, 95.45), (8.753, 98.27), (8.766, 98.12), (9.558, 89.99), (10.42, 82.54),
-         (9.570, 89.88), (10.15, 84.76), (11.11, 77.40)]],
-}
-
-
-def run_paper_table(dbp, h, device, launches=20):
-    """Every cell of Table III on this GPU: the same algorithms, shapes and
-    iteration counts, one frame of 1200 subcarriers x 7 symbols per call,
-    back-to-back launches on one stream over resident copies of the inputs
-    (more than L2), next to the paper's printed latency and throughput."""
-    import torch
-    U, M, W, N = 16, 64, 1200, 7
-    bits = U * (M.bit_length() - 1) * W * N
-    stream = torch.cuda.current_stream(device)
-    sp = stream.cuda_stream
-    cells = []
-    for ci, (B, C) in enumerate(PAPER_COLS):
-        fu = synth.uplink_frame(W, N, B, U, M, 20.0, seed=synth.frame_seed(6, ci))
-        sd = synth.downlink_frame(W, N, B, U, M, seed=synth.frame_seed(7, ci))["s"]
-        per = W * (B * U + N * B) * 8
-        copies = max(2, -(-256_000_000 // per))
-        H0 = torch.from_numpy(fu["H"].astype(np.complex64)).to(device)
-        y0 = torch.from_numpy(fu["y"].astype(np.complex64)).to(device)
-        ins = [(H0, y0)] + [(H0.clone(), y0.clone()) for _ in range(copies - 1)]
-        s0 = torch.from_numpy(sd.astype(np.complex64)).to(device)
-        xu = torch.empty((W, N, U), dtype=torch.complex64, device=device)
-        xd = torch.empty((W, N, B), dtype=torch.complex64, device=device)
-        for alg in ("admm_ul", "cg_ul", "admm_dl"):
-            for T in range(1, 6):
-                d = dbp.frame_desc(B, C, U, W, N, qam_order=M, T_max=T, rho=1.0, N0=fu["N0"], Es=1.0)
-
-                def call(k):
-                    H, y = ins[k % copies]
-                    if alg == "admm_ul":
-                        dbp.dbp_uplink_admm(h, d, H, y, xu, None, sp)
-                    elif alg == "cg_ul":
-                        dbp.dbp_uplink_cg(h, d, H, y, xu, None, sp)
-                    else:
-                        dbp.dbp_downlink_admm(h, d, H, s0, xd, None, sp)
-                for k in range(3):
-                    call(k)
-                torch.cuda.synchronize(device)
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                for k in range(launches):
-                    call(k)
-                e1.record(stream)
-                torch.cuda.synchronize(device)
-                ms = e0.elapsed_time(e1) / launches
-                pl, pt = PAPER_TABLE_III[alg][T - 1][ci]
-                cells.append({"alg": alg, "B": B, "C": C, "S": B // C, "T": T, "ms": ms,
-                              "gbit_s": bits / (ms / 1e3) / 1e9, "paper_ms": pl, "paper_mbit_s": pt,
-                              "latency_ratio": pl / ms})
-        del ins, H0, y0, s0, xu, xd
-        torch.cuda.empty_cache()
-    ratios = [c["latency_ratio"] for c in cells]
-    return {"workload": f"Table III cells: U={U} {M}-QAM W={W} N={N}, B/C/S and T as printed, "
-                        "i.i.d. Rayleigh, fp32 complex",
-            "timing": f"{launches} back-to-back launches per cell on one stream, inputs rotating over resident "
-                      "copies larger than L2; the paper's cells are per-cycle wall clock on its K40 cluster "
-                      "with MPI (context, other hardware)",
-            "bits_per_frame": bits, "cells": cells,
-            "latency_ratio_min": min(ratios), "latency_ratio_median": float(np.median(ratios)),
-            "latency_ratio_max": max(ratios)}
-
-
 def run_tradeoff(dbp, h, device, target=0.01):
     """Uncoded analogue of the paper's performance / complexity trade-off
     (Sec. VI-B): on the B=128 / C=8 / U=8 / 16-QAM / 1200 x 14 frame, the
@@ -1091,6 +1070,170 @@ def run_tradeoff(dbp, h, device, target=0.01):
     return out
 
 
+# ---------------------------------------------------------------------------
+# Optional studies (--study), written to the details file
+# ---------------------------------------------------------------------------
+
+def study_ber_sweep(dbp, h, device, rank):
+    """BER of the headline workload over 10-30 dB for FP32, FP16 and BF16
+    inputs: one channel and symbol set, fresh seeded noise per frame, every
+    precision on the same noise; frames until the FP32 path has 200 bit
+    errors or 12 frames (1.06e8 bits)."""
+    import torch
+    f = synth.uplink_frame(MIX.W, MIX.N, MIX.B, MIX.U, MIX.M, MIX_SNR_DB, seed=synth.frame_seed(4, 5) + 100000 * rank)
+    x = torch.empty((MIX.W, MIX.N, MIX.U), dtype=torch.complex64, device=device)
+    lab = torch.empty((MIX.W, MIX.N, MIX.U), dtype=torch.uint8, device=device)
+    nbits = MIX.W * MIX.N * MIX.U * (MIX.M.bit_length() - 1)
+    precs = (("fp32", dbp.DBP_FP32), ("fp16", dbp.DBP_FP16), ("bf16", dbp.DBP_BF16))
+    dev_H = {}
+    for name, prec in precs:
+        dev_H[name] = (torch.from_numpy(f["H"].astype(np.complex64)) if name == "fp32" else
+                       _to16(f["H"], torch.float16 if name == "fp16" else torch.bfloat16)).to(device)
+    sweep = []
+    for i, snr in enumerate(MIX_SWEEP_DB):
+        errs = {name: 0 for name, _ in precs}
+        frames_run = 0
+        while frames_run < MIX_SWEEP_MAX_FRAMES and (errs["fp32"] < 200 or frames_run == 0):
+            fs = synth.at_snr(f, snr, seed=synth.frame_seed(4, i) + 1000 * frames_run + 100000 * rank)
+            for name, prec in precs:
+                y = (torch.from_numpy(fs["y"].astype(np.complex64)) if name == "fp32" else
+                     _to16(fs["y"], torch.float16 if name == "fp16" else torch.bfloat16)).to(device)
+                d = dbp.frame_desc(MIX.B, MIX.C, MIX.U, MIX.W, MIX.N, qam_order=MIX.M, T_max=MIX.T,
+                                   precision=prec, rho=1.0, N0=fs["N0"], Es=1.0)
+                dbp.dbp_uplink_admm(h, d, dev_H[name], y, x, lab)
+                torch.cuda.synchronize(device)
+                errs[name] += _bit_errors(lab.cpu().numpy(), fs["labels"])
+                del y
+            frames_run += 1
+        bits = frames_run * nbits
+        lo, hi = _binom_ci(errs["fp32"], bits)
+        point = {"snr_db": snr, "frames": frames_run, "bits": bits,
+                 "fp32": {"ber": errs["fp32"] / bits, "bit_errors": errs["fp32"], "ber_ci95": [lo, hi]}}
+        for name in ("fp16", "bf16"):
+            point[name] = {"ber": errs[name] / bits, "bit_errors": errs[name],
+                           "within_fp32_ci95": bool(lo <= errs[name] / bits <= hi)}
+        sweep.append(point)
+    return {"workload": workload_name(MIX, f"uplink ADMM T={MIX.T}", "FP32 / FP16 / BF16 inputs"),
+            "rule": f"frames until 200 FP32 bit errors or {MIX_SWEEP_MAX_FRAMES} frames", "points": sweep,
+            "all_within_fp32_ci95": all(p[n]["within_fp32_ci95"] for p in sweep for n in ("fp16", "bf16"))}
+
+
+def study_extensions(dbp, h, device, launching, K, peaks):
+    """The rows beyond the three detectors on the B=128 / C=8 / U=8 frame,
+    each timed alone with back-to-back launches: the BOX prox (radius of the
+    outermost 16-QAM level), the BPSK prox on a BPSK frame at -6 dB, and the
+    max-log soft outputs of the ADMM estimate (launches captured into one
+    CUDA graph: the kernel is shorter than a call's host cost)."""
+    import torch
+    KX = max(min(K, 500), 10)
+    sp = launching.cuda_stream
+    fr = [synth.uplink_frame(UL.W, UL.N, UL.B, UL.U, UL.M, SNRS_DB[i % len(SNRS_DB)],
+                             seed=synth.frame_seed(2, i)) for i in range(ROTATE)]
+    dev = [(torch.from_numpy(f["H"].astype(np.complex64)).to(device),
+            torch.from_numpy(f["y"].astype(np.complex64)).to(device), f["N0"]) for f in fr]
+    x = torch.empty((UL.W, UL.N, UL.U), dtype=torch.complex64, device=device)
+    lab = torch.empty((UL.W, UL.N, UL.U), dtype=torch.uint8, device=device)
+
+    def back_to_back(fn, n):
+        for k in range(3):
+            fn(k)
+        torch.cuda.synchronize(device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(launching)
+        for k in range(n):
+            fn(k)
+        e1.record(launching)
+        torch.cuda.synchronize(device)
+        return e0.elapsed_time(e1) / n
+
+    box_r = (math.isqrt(UL.M) - 1) * math.sqrt(3.0 / (2.0 * (UL.M - 1)))
+    dbox = [dbp.frame_desc(UL.B, UL.C, UL.U, UL.W, UL.N, qam_order=UL.M, T_max=UL.T, regularizer=dbp.DBP_REG_BOX,
+                           N0=n0, box_r=box_r) for (_, _, n0) in dev]
+    box_ms = back_to_back(lambda k: dbp.dbp_uplink_admm(h, dbox[k % ROTATE], dev[k % ROTATE][0],
+                                                        dev[k % ROTATE][1], x, lab, sp), KX)
+    fb = synth.uplink_frame(UL.W, UL.N, UL.B, UL.U, 2, BPSK_SNR_DB, seed=synth.frame_seed(2, 90))
+    Hb = torch.from_numpy(fb["H"].astype(np.complex64)).to(device)
+    yb = torch.from_numpy(fb["y"].astype(np.complex64)).to(device)
+    bpsk_in = [(Hb, yb)] + [(Hb.clone(), yb.clone()) for _ in range(ROTATE - 1)]
+    dbpsk = dbp.frame_desc(UL.B, UL.C, UL.U, UL.W, UL.N, qam_order=2, T_max=UL.T, regularizer=dbp.DBP_REG_BPSK,
+                           N0=fb["N0"], box_r=1.0)
+    bpsk_ms = back_to_back(lambda k: dbp.dbp_uplink_admm(h, dbpsk, bpsk_in[k % ROTATE][0], bpsk_in[k % ROTATE][1],
+                                                          x, lab, sp), KX)
+    dbp.dbp_uplink_admm(h, dbpsk, Hb, yb, x, lab, sp)
+    torch.cuda.synchronize(device)
+    nb = UL.W * UL.N * UL.U
+    bpsk_err = int((lab.cpu().numpy() != fb["labels"]).sum())
+    del bpsk_in
+    llr = torch.empty((UL.W, UL.N, UL.U, UL.M.bit_length() - 1), dtype=torch.float32, device=device)
+    d0 = dbp.frame_desc(UL.B, UL.C, UL.U, UL.W, UL.N, qam_order=UL.M, T_max=UL.T, N0=dev[0][2])
+    dbp.dbp_uplink_admm(h, d0, dev[0][0], dev[0][1], x, lab, sp)
+    llr_in = [(dev[k % ROTATE][0].clone(), x.clone()) for k in range(24)]
+    gs = torch.cuda.Stream(device)
+    gs.wait_stream(launching)
+    with torch.cuda.stream(gs):
+        for k in range(3):
+            dbp.dbp_uplink_llr(h, d0, llr_in[k][0], llr_in[k][1], llr, gs.cuda_stream)
+    torch.cuda.synchronize(device)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gs):
+        for k in range(KX):
+            dbp.dbp_uplink_llr(h, d0, llr_in[k % 24][0], llr_in[k % 24][1], llr, gs.cuda_stream)
+    graph.replay()
+    torch.cuda.synchronize(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(launching)
+    graph.replay()
+    e1.record(launching)
+    torch.cuda.synchronize(device)
+    llr_ms = e0.elapsed_time(e1) / KX
+    del graph, llr_in
+    llr_bytes = UL.W * (UL.B * UL.U * 8 + UL.N * UL.U * 8 + UL.N * UL.U * llr.shape[-1] * 4)
+    BP = Workload(UL.B, UL.C, UL.U, UL.W, UL.N, 2, UL.T)
+    return {"box_prox": {"ms_per_frame": box_ms, "gbit_s": detected_bits(UL) / (box_ms / 1e3) / 1e9},
+            "bpsk_prox": {"ms_per_frame": bpsk_ms, "gbit_s": detected_bits(BP) / (bpsk_ms / 1e3) / 1e9,
+                          "ber": bpsk_err / nb, "bits": nb},
+            "soft_outputs": {"ms_per_frame": llr_ms, "bytes_per_frame": llr_bytes,
+                             "hbm_frac": llr_bytes / (llr_ms / 1e3) / 1e9 / peaks["hbm_gbs"]},
+            "launches": KX}
+
+
+def study_downlink(dbp, h, device, launching, K):
+    """The downlink frame with eps = 0.05 (Lemma 2) and with the per-frame
+    power normalisation, each against the plain precoder, back-to-back
+    launches over 4 rotating frames."""
+    import torch
+    KD = max(min(K, 200), 10)
+    sp = launching.cuda_stream
+    frd = [synth.downlink_frame(DL.W, DL.N, DL.B, DL.U, DL.M, seed=synth.frame_seed(3, i)) for i in range(4)]
+    ddev = [(torch.from_numpy(f["H"].astype(np.complex64)).to(device),
+             torch.from_numpy(f["s"].astype(np.complex64)).to(device)) for f in frd]
+    xd = torch.empty((DL.W, DL.N, DL.B), dtype=torch.complex64, device=device)
+    beta = torch.zeros(1, dtype=torch.float64, device=device)
+    res = {}
+    for name, d, b in (("plain", dbp.frame_desc(DL.B, DL.C, DL.U, DL.W, DL.N, T_max=DL.T), None),
+                       ("eps", dbp.frame_desc(DL.B, DL.C, DL.U, DL.W, DL.N, T_max=DL.T, eps=DL_EPS), None),
+                       ("normalized", dbp.frame_desc(DL.B, DL.C, DL.U, DL.W, DL.N, T_max=DL.T,
+                                                     flags=dbp.DBP_FLAG_NORMALIZE), beta)):
+        for k in range(3):
+            dbp.dbp_downlink_admm(h, d, ddev[k % 4][0], ddev[k % 4][1], xd, b, sp)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(launching)
+        for k in range(KD):
+            dbp.dbp_downlink_admm(h, d, ddev[k % 4][0], ddev[k % 4][1], xd, b, sp)
+        e1.record(launching)
+        torch.cuda.synchronize(device)
+        res[name] = e0.elapsed_time(e1) / KD
+    x_bytes = DL.W * DL.N * DL.B * 8
+    return {"workload": workload_name(DL, f"downlink ADMM T={DL.T}"), "launches": KD,
+            "ms_plain": res["plain"], "ms_eps": res["eps"], "eps": DL_EPS, "ms_normalized": res["normalized"],
+            "normalisation_added_ms": res["normalized"] - res["plain"],
+            "normalisation_added_gbs": 2 * x_bytes / max(res["normalized"] - res["plain"], 1e-9) / 1e6}
+
+
+# ---------------------------------------------------------------------------
+# Main
+# ---------------------------------------------------------------------------
+
 def main(argv=None) -> int:
     args = parse_args(argv)
     if args.impl == "reference":
@@ -1107,453 +1250,151 @@ def main(argv=None) -> int:
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=device)
+    details_path = args.details
+    if details_path is None and os.path.isdir(os.path.join(ROOT, "gpurun_out")):
+        details_path = os.path.join(ROOT, "gpurun_out", "bench_details.json")
+    studies = set(STUDIES) if "all" in args.study else set(args.study)
 
     h = dbp.dbp_create(local)
-    if args.tradeoff:
-        if rank == 0:
-            print(json.dumps({"tradeoff": run_tradeoff(dbp, h, device)}))
-        dbp.dbp_destroy(h)
-        return 0
-    if args.paper_table:
-        if rank == 0:
-            print(json.dumps({"paper_table": run_paper_table(dbp, h, device)}))
-        dbp.dbp_destroy(h)
-        return 0
+    paths = {"tc5": dbp.DBP_PATH_TC5, "tma": dbp.DBP_PATH_TMA, "generic": dbp.DBP_PATH_GENERIC,
+             "mma": dbp.DBP_PATH_MMA, "bcast": dbp.DBP_PATH_BCAST}
     if args.kernel != "auto":
-        dbp.dbp_set_tuning(h, kernel={"generic": dbp.DBP_PATH_GENERIC, "tma": dbp.DBP_PATH_TMA,
-                                      "mma": dbp.DBP_PATH_MMA, "bcast": dbp.DBP_PATH_BCAST}[args.kernel])
-    stream = torch.cuda.current_stream(device)
-    props = torch.cuda.get_device_properties(device)
-    sms = props.multi_processor_count
-    alu_peak = fp32_simt_peak_tflops(sms, 2032.0)
-    hbm_peak, hbm_src = measured_peaks()
-
-    # ---- resident uplink frames --------------------------------------------
-    frames = ul_frames(rank, ROTATE)
-    dev = []
-    for f in frames:
-        dev.append({
-            "H": torch.from_numpy(f["H"].astype(np.complex64)).to(device),
-            "y": torch.from_numpy(f["y"].astype(np.complex64)).to(device),
-            "N0": f["N0"],
-        })
-    # one output set per stream: the two streams of the timed region never
-    # write the same buffer
-    outs = []
-    for _ in range(2):
-        xo = torch.empty((UL.W, UL.N, UL.U), dtype=torch.complex64, device=device)
-        lo = torch.empty((UL.W, UL.N, UL.U), dtype=torch.uint8, device=device)
-        outs.append({"xa": xo, "la": lo, "xc": torch.empty_like(xo), "lc": torch.empty_like(lo)})
-    xa, la = outs[0]["xa"], outs[0]["la"]
-
-    def descs(N0):
-        da = dbp.frame_desc(UL.B, UL.C, UL.U, UL.W, UL.N, qam_order=UL.M, T_max=UL.T,
-                            regularizer=dbp.DBP_REG_MMSE, rho=1.0, N0=N0, Es=1.0)
-        dc = dbp.frame_desc(UL.B, UL.C, UL.U, UL.W, UL.N, qam_order=UL.M, T_max=UL_T_CG,
-                            regularizer=dbp.DBP_REG_MMSE, N0=N0, Es=1.0)
-        return da, dc
-
-    D = [descs(d["N0"]) for d in dev]
-    sp = stream.cuda_stream
+        dbp.dbp_set_tuning(h, kernel=paths[args.kernel])
+    launching = torch.cuda.current_stream(device)
     side = torch.cuda.Stream(device)
-    step_streams = [stream, side]
+    streams = [launching, side]
+    props = torch.cuda.get_device_properties(device)
+    alu_peak = fp32_simt_peak_tflops(props.multi_processor_count, 2032.0)
+    peaks = measured_peaks()
+    details = {"device": props.name, "sms": props.multi_processor_count}
 
-    def step(k):
-        # one frame, both detectors, on stream k % 2: consecutive frames
-        # overlap on the device as in a receiver fed frame by frame
-        d = dev[k % ROTATE]
-        da, dc = D[k % ROTATE]
-        o = outs[k % 2]
-        s = step_streams[k % 2].cuda_stream
-        dbp.dbp_uplink_admm(h, da, d["H"], d["y"], o["xa"], o["la"], s)
-        dbp.dbp_uplink_cg(h, dc, d["H"], d["y"], o["xc"], o["lc"], s)
+    # ---- headline frames, FP32 -----------------------------------------------
+    frames = [synth.uplink_frame(HEAD.W, HEAD.N, HEAD.B, HEAD.U, HEAD.M, HEAD_SNR_DB,
+                                 seed=synth.frame_seed(4, i) + 100000 * rank) for i in range(HEAD_FRAMES)]
 
-    def solo(kind, k):
-        d = dev[k % ROTATE]
-        da, dc = D[k % ROTATE]
-        if kind == "admm":
-            dbp.dbp_uplink_admm(h, da, d["H"], d["y"], xa, la, sp)
-        else:
-            dbp.dbp_uplink_cg(h, dc, d["H"], d["y"], outs[0]["xc"], outs[0]["lc"], sp)
+    def desc_of(prec):
+        return lambda f: dbp.frame_desc(HEAD.B, HEAD.C, HEAD.U, HEAD.W, HEAD.N, qam_order=HEAD.M, T_max=HEAD.T,
+                                        precision=prec, rho=1.0, N0=f["N0"], Es=1.0)
 
-    # autotune the launch choice of both detectors on this frame shape
-    # (outside the timed region; --kernel other than auto skips it)
+    precs = [("fp32", dbp.DBP_FP32)] + ([] if args.no_mixed else [("fp16", dbp.DBP_FP16), ("bf16", dbp.DBP_BF16)])
+    sets = {name: FrameSet(frames, name, device) for name, _ in precs}
     tuned = {}
     if args.kernel == "auto" and not args.no_autotune:
-        d0 = dev[0]
-        da0, dc0 = D[0]
-        names = {dbp.DBP_PATH_MMA: "mma", dbp.DBP_PATH_BCAST: "bcast", dbp.DBP_PATH_TMA: "tma",
-                 dbp.DBP_PATH_GENERIC: "generic"}
-        for key, kind, dd in (("admm_ul", dbp.DBP_KIND_UPLINK_ADMM, da0), ("cg_ul", dbp.DBP_KIND_UPLINK_CG, dc0)):
-            t = dbp.dbp_autotune(h, kind, dd, d0["H"], d0["y"], xa, la, sp, 5)
-            tuned[key] = {"kernel": names.get(t.kernel, t.kernel), "mapping": t.mapping,
-                          "cluster_size": t.cluster_size, "warps_per_cta": t.warps_per_cta,
-                          "prefactor": t.prefactor}
+        for name, prec in precs:
+            H, y, f = sets[name].bufs[0]
+            x, lab = sets[name].out[0]
+            t = dbp.dbp_autotune(h, dbp.DBP_KIND_UPLINK_ADMM, desc_of(prec)(f), H, y, x, lab,
+                                 launching.cuda_stream, 5)
+            tuned[name] = PATH_NAMES.get(t.kernel, str(t.kernel))
         torch.cuda.synchronize(device)
-
-    for k in range(args.warmup):
-        step(k)
-    torch.cuda.synchronize(device)
-    barrier(world, device)
-    torch.cuda.synchronize(device)
-
-    # Timed region: K steps, frames alternating over two streams, two CUDA
-    # events on the launching stream around it (the side stream joins before
-    # the end event).  No event between launches: an event on the stream
-    # would stop a launch from overlapping its predecessor's tail.
     K = args.steps
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(str(props.uuid)) as clk:
-        t_start.record(stream)
-        side.wait_event(t_start)
-        for k in range(K):
-            step(k)
-        stream.wait_stream(side)
-        t_end.record(stream)
-        torch.cuda.synchronize(device)
-        # Kernel durations for the roofline: each detector alone, KR
-        # back-to-back launches on the launching stream between two events.
-        KR = max(min(K, 2000), 10)
-        solo_ms = {}
-        for kind in ("admm", "cg"):
-            for k in range(3):
-                solo(kind, k)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for k in range(KR):
-                solo(kind, k)
-            e1.record(stream)
-            torch.cuda.synchronize(device)
-            solo_ms[kind] = e0.elapsed_time(e1) / KR
-    total_ms = t_start.elapsed_time(t_end)
     barrier(world, device)
     torch.cuda.synchronize(device)
+    # Timed region: K frames alternating over two streams, CUDA events on the
+    # launching stream, SM clocks sampled meanwhile (the sampler also covers
+    # the roofline's back-to-back launches that follow).
+    with ClockSampler(str(props.uuid), period_ms=2) as clk:
+        clk.mark()
+        total_ms = time_frames(dbp, h, sets["fp32"], desc_of(dbp.DBP_FP32), K, args.warmup, streams, launching)
+        clk.mark()
+        KR = max(min(K, 100), 10)
+        head_solo = solo_ms(dbp, h, sets["fp32"], desc_of(dbp.DBP_FP32), KR, launching)
+    barrier(world, device)
     total_ms_max = max_over_ranks(total_ms, world, device)
+    bits = detected_bits(HEAD)
+    value = world * bits * K / (total_ms_max / 1e3) / 1e9
+    kpath = tuned.get("fp32", args.kernel)
+    rf = roofline(f"admm_ul_u32_{kpath}", "admm_ul", HEAD, head_solo, peaks, alu_peak, 3.0,
+                  KERNEL_NAMES.get(kpath, kpath))
 
-    bits_step = 2 * detected_bits(UL)
-    value = world * bits_step * K / (total_ms_max / 1e3) / 1e9
-    admm_avg = solo_ms["admm"]
-    cg_avg = solo_ms["cg"]
-    rf_admm = roofline("admm_ul", "admm_ul", UL, admm_avg, hbm_peak, hbm_src, alu_peak)
-    rf_cg = roofline("cg_ul", "cg_ul", Workload(UL.B, UL.C, UL.U, UL.W, UL.N, UL.M, UL_T_CG),
-                     cg_avg, hbm_peak, hbm_src, alu_peak)
-    dominant = rf_cg if cg_avg >= admm_avg else rf_admm
-
-    # ---- the extensions of the hot path on the same frame: ADMM with the
-    # BOX prox (Lemma 1 with a hypercube), and max-log soft outputs --------
-    def back_to_back(fn, n):
-        for k in range(3):
-            fn(k)
-        torch.cuda.synchronize(device)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for k in range(n):
-            fn(k)
-        e1.record(stream)
-        torch.cuda.synchronize(device)
-        return e0.elapsed_time(e1) / n
-
-    def graph_back_to_back(fn, n):
-        """n launches captured into one CUDA graph and replayed: the device
-        time per launch of a kernel shorter than the host's per-call cost."""
-        gs = torch.cuda.Stream(device)
-        gs.wait_stream(stream)
-        with torch.cuda.stream(gs):
-            for k in range(3):
-                fn(k, gs.cuda_stream)
-        torch.cuda.synchronize(device)
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=gs):
-            for k in range(n):
-                fn(k, gs.cuda_stream)
-        graph.replay()
-        torch.cuda.synchronize(device)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        graph.replay()
-        e1.record(stream)
-        torch.cuda.synchronize(device)
-        del graph
-        return e0.elapsed_time(e1) / n
-
-    KX = max(min(K, 500), 10)
-    box_r = (math.isqrt(UL.M) - 1) * math.sqrt(3.0 / (2.0 * (UL.M - 1)))
-    dbox = [dbp.frame_desc(UL.B, UL.C, UL.U, UL.W, UL.N, qam_order=UL.M, T_max=UL.T, regularizer=dbp.DBP_REG_BOX,
-                           rho=1.0, N0=d["N0"], Es=1.0, box_r=box_r) for d in dev]
-    box_ms = back_to_back(lambda k: dbp.dbp_uplink_admm(h, dbox[k % ROTATE], dev[k % ROTATE]["H"],
-                                                        dev[k % ROTATE]["y"], xa, la, sp), KX)
-    # the BPSK prox on a BPSK frame of the same shape: 8 rotating device copies
-    # (216 MB, larger than L2); the BER of the BPSK prox and of ZF (decision:
-    # the sign of the real part) on the frame
-    BP = Workload(B=UL.B, C=UL.C, U=UL.U, W=UL.W, N=UL.N, M=2, T=UL.T)
-    fb = synth.uplink_frame(UL.W, UL.N, UL.B, UL.U, 2, BPSK_SNR_DB, seed=synth.frame_seed(2, 90) + 100000 * rank)
-    Hb = torch.from_numpy(fb["H"].astype(np.complex64)).to(device)
-    yb = torch.from_numpy(fb["y"].astype(np.complex64)).to(device)
-    bpsk_in = [(Hb, yb)] + [(Hb.clone(), yb.clone()) for _ in range(ROTATE - 1)]
-    dbpsk = dbp.frame_desc(UL.B, UL.C, UL.U, UL.W, UL.N, qam_order=2, T_max=UL.T, regularizer=dbp.DBP_REG_BPSK,
-                           rho=1.0, N0=fb["N0"], Es=1.0, box_r=1.0)
-    lb = torch.empty((UL.W, UL.N, UL.U), dtype=torch.uint8, device=device)
-    bpsk_ms = back_to_back(lambda k: dbp.dbp_uplink_admm(h, dbpsk, bpsk_in[k % ROTATE][0], bpsk_in[k % ROTATE][1],
-                                                          xa, lb, sp), KX)
-    dbp.dbp_uplink_admm(h, dbpsk, Hb, yb, xa, lb, sp)
-    torch.cuda.synchronize(device)
-    nb = UL.W * UL.N * UL.U
-    bpsk_err = int((lb.cpu().numpy() != fb["labels"]).sum())
-    dzf = dbp.frame_desc(UL.B, UL.C, UL.U, UL.W, UL.N, qam_order=0, T_max=UL.T, regularizer=dbp.DBP_REG_ZF,
-                         rho=1.0, N0=fb["N0"], Es=1.0)
-    dbp.dbp_uplink_admm(h, dzf, Hb, yb, xa, None, sp)
-    torch.cuda.synchronize(device)
-    zf_err = int(((xa.real.cpu().numpy() > 0).astype(np.uint8) != fb["labels"]).sum())
-    del bpsk_in, Hb, yb, lb
-    llr = torch.empty((UL.W, UL.N, UL.U, UL.M.bit_length() - 1), dtype=torch.float32, device=device)
-    # the kernel reads H and x only (10.9 MB per frame): 24 rotating copies
-    # (261 MB) keep its inputs out of L2 between launches
-    LLR_ROT = 24
-    dbp.dbp_uplink_admm(h, D[0][0], dev[0]["H"], dev[0]["y"], xa, la, sp)
-    llr_in = [(dev[k % ROTATE]["H"].clone(), xa.clone()) for k in range(LLR_ROT)]
-    llr_ms = graph_back_to_back(lambda k, s: dbp.dbp_uplink_llr(h, D[k % ROTATE][0], llr_in[k % LLR_ROT][0],
-                                                                llr_in[k % LLR_ROT][1], llr, s), KX)
-    del llr_in
-    llr_bytes = UL.W * (UL.B * UL.U * 8 + UL.N * UL.U * 8 + UL.N * UL.U * llr.shape[-1] * 4)
-    extensions = {
-        "box_prox": {"workload": workload_name(UL, f"uplink ADMM T={UL.T}, BOX prox r={box_r:.4f}"),
-                     "ms_per_frame": box_ms, "gbit_s": detected_bits(UL) / (box_ms / 1e3) / 1e9,
-                     "launches": KX,
-                     "roofline": roofline("admm_ul_box", "admm_ul", UL, box_ms, hbm_peak, hbm_src, alu_peak)},
-        "bpsk_prox": {"workload": (f"uplink ADMM T={UL.T}, BPSK prox r=1 at {BPSK_SNR_DB:g} dB: B={UL.B} C={UL.C} "
-                                   f"S={UL.S} U={UL.U} BPSK W={UL.W} N={UL.N} i.i.d. Rayleigh, fp32 complex"),
-                      "ms_per_frame": bpsk_ms, "gbit_s": detected_bits(BP) / (bpsk_ms / 1e3) / 1e9,
-                      "launches": KX, "ber": bpsk_err / nb, "ber_zf": zf_err / nb, "bits": nb,
-                      "roofline": roofline("admm_ul_bpsk", "admm_ul", BP, bpsk_ms, hbm_peak, hbm_src, alu_peak)},
-        "soft_outputs": {"workload": workload_name(UL, "max-log LLRs of the ADMM estimate (MMSE statistics)"),
-                         "ms_per_frame": llr_ms, "llr_gbit_s": detected_bits(UL) / (llr_ms / 1e3) / 1e9,
-                         "launches": KX, "timing": "launches captured into one CUDA graph, one replay between "
-                                                   "two CUDA events (the kernel is shorter than a call's host cost); "
-                                                   f"inputs rotate over {LLR_ROT} resident (H, x) copies, 261 MB",
-                         "bytes_per_frame": llr_bytes,
-                         "hbm_gbs": llr_bytes / (llr_ms / 1e3) / 1e9,
-                         "hbm_frac": llr_bytes / (llr_ms / 1e3) / 1e9 / hbm_peak},
-    }
-    del llr
-
-    # ---- downlink precoder (B=256, C=16, U=16) -------------------------------
-    downlink = None
-    if not args.no_downlink:
-        del dev
-        torch.cuda.empty_cache()
-        dfr = dl_frames(rank, ROTATE)
-        ddev = [{"H": torch.from_numpy(f["H"].astype(np.complex64)).to(device),
-                 "s": torch.from_numpy(f["s"].astype(np.complex64)).to(device)} for f in dfr]
-        xd = torch.empty((DL.W, DL.N, DL.B), dtype=torch.complex64, device=device)
-        ddesc = dbp.frame_desc(DL.B, DL.C, DL.U, DL.W, DL.N, T_max=DL.T, rho=1.0)
-        dl_tuned = None
-        if args.kernel == "auto" and not args.no_autotune:
-            t = dbp.dbp_autotune(h, dbp.DBP_KIND_DOWNLINK_ADMM, ddesc, ddev[0]["H"], ddev[0]["s"], xd, None, sp, 3)
-            dl_tuned = {"kernel": t.kernel, "mapping": t.mapping, "cluster_size": t.cluster_size,
-                        "warps_per_cta": t.warps_per_cta, "prefactor": t.prefactor}
-        for k in range(args.warmup):
-            dbp.dbp_downlink_admm(h, ddesc, ddev[k % ROTATE]["H"], ddev[k % ROTATE]["s"], xd, None, sp)
-        torch.cuda.synchronize(device)
-        KD = max(min(K, 1000), 10)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for k in range(KD):
-            dbp.dbp_downlink_admm(h, ddesc, ddev[k % ROTATE]["H"], ddev[k % ROTATE]["s"], xd, None, sp)
-        e1.record(stream)
-        torch.cuda.synchronize(device)
-        dl_ms = e0.elapsed_time(e1) / KD
-        # throughput: consecutive frames alternating over two streams (own
-        # output buffers), as in the uplink step
-        xd2 = torch.empty_like(xd)
-        e0.record(stream)
-        side.wait_event(e0)
-        for k in range(KD):
-            st_k = stream if k % 2 == 0 else side
-            dbp.dbp_downlink_admm(h, ddesc, ddev[k % ROTATE]["H"], ddev[k % ROTATE]["s"],
-                                  xd if k % 2 == 0 else xd2, None, st_k.cuda_stream)
-        stream.wait_stream(side)
-        e1.record(stream)
-        torch.cuda.synchronize(device)
-        dl_ms2 = e0.elapsed_time(e1) / KD
-        # Lemma 2 with eps > 0 (the precoder's l2 relaxation), one stream
-        deps = dbp.frame_desc(DL.B, DL.C, DL.U, DL.W, DL.N, T_max=DL.T, rho=1.0, eps=DL_EPS)
-        for k in range(3):
-            dbp.dbp_downlink_admm(h, deps, ddev[k % ROTATE]["H"], ddev[k % ROTATE]["s"], xd, None, sp)
-        e0.record(stream)
-        for k in range(KD):
-            dbp.dbp_downlink_admm(h, deps, ddev[k % ROTATE]["H"], ddev[k % ROTATE]["s"], xd, None, sp)
-        e1.record(stream)
-        torch.cuda.synchronize(device)
-        eps_ms = e0.elapsed_time(e1) / KD
-        # the per-frame power normalisation (one scalar beta per frame): the
-        # precoder accumulates the energy of x, a second kernel scales x
-        dnorm = dbp.frame_desc(DL.B, DL.C, DL.U, DL.W, DL.N, T_max=DL.T, rho=1.0, flags=dbp.DBP_FLAG_NORMALIZE)
-        beta = torch.zeros(1, dtype=torch.float64, device=device)
-        for k in range(3):
-            dbp.dbp_downlink_admm(h, dnorm, ddev[k % ROTATE]["H"], ddev[k % ROTATE]["s"], xd, beta, sp)
-        e0.record(stream)
-        for k in range(KD):
-            dbp.dbp_downlink_admm(h, dnorm, ddev[k % ROTATE]["H"], ddev[k % ROTATE]["s"], xd, beta, sp)
-        e1.record(stream)
-        torch.cuda.synchronize(device)
-        norm_ms = e0.elapsed_time(e1) / KD
-        x_bytes = DL.W * DL.N * DL.B * 8
-        extensions["downlink_normalized"] = {
-            "workload": workload_name(DL, f"downlink ADMM T={DL.T} with the per-frame power normalisation"),
-            "ms_per_frame": norm_ms, "gbit_s": detected_bits(DL) / (norm_ms / 1e3) / 1e9, "launches": KD,
-            "added_ms": norm_ms - dl_ms, "added_bytes": 2 * x_bytes,
-            "added_hbm_gbs": 2 * x_bytes / max(norm_ms - dl_ms, 1e-9) / 1e6,
-            "note": "added_*: the scaling pass over x (read and write), against ms_per_frame_one_stream of the "
-                    "plain downlink"}
-        extensions["downlink_eps"] = {
-            "workload": workload_name(DL, f"downlink ADMM T={DL.T}, eps={DL_EPS}"), "ms_per_frame": eps_ms,
-            "gbit_s": detected_bits(DL) / (eps_ms / 1e3) / 1e9, "launches": KD,
-            "roofline": roofline("admm_dl_eps", "admm_dl", DL, eps_ms, hbm_peak, hbm_src, alu_peak)}
-        downlink = {"workload": workload_name(DL, "downlink ADMM T=5"),
-                    "value": detected_bits(DL) / (dl_ms2 / 1e3) / 1e9, "unit": "Gbit/s (precoded)",
-                    "ms_per_frame": dl_ms2, "ms_per_frame_one_stream": dl_ms,
-                    "timing": f"{KD} frames alternating over two streams (value); {KD} back-to-back "
-                              "launches on one stream (ms_per_frame_one_stream, the roofline's duration)",
-                    "launches": KD, "autotuned": dl_tuned,
-                    "roofline": roofline("admm_dl", "admm_dl", DL, dl_ms, hbm_peak, hbm_src, alu_peak)}
-        del ddev, xd, xd2
-        torch.cuda.empty_cache()
-
-    # ---- 16-bit inputs vs FP32 (B=256, C=8, U=32, 3300 x 14, ADMM T=3) ------
+    # ---- the same frames with 16-bit inputs; BER of every precision ----------
     mixed = None
     if not args.no_mixed:
-        mixed = bench_mixed(dbp, h, stream, device, rank, args, hbm_peak, hbm_src, alu_peak)
+        KM = max(min(K, 100), 10)
+        mixed = {}
+        e32, b32 = frame_ber(dbp, h, sets["fp32"], desc_of(dbp.DBP_FP32), device)
+        lo, hi = _binom_ci(e32, b32)
+        mixed["fp32"] = {"gbit_s": round(value / world, 3), "ber": e32 / b32, "ber_ci95": [lo, hi]}
+        for name, prec in precs[1:]:
+            ms = time_frames(dbp, h, sets[name], desc_of(prec), KM, 3, streams, launching) / KM
+            sms = solo_ms(dbp, h, sets[name], desc_of(prec), KM, launching)
+            e, b = frame_ber(dbp, h, sets[name], desc_of(prec), device)
+            mixed[name] = {"gbit_s": round(bits / (ms / 1e3) / 1e9, 3), "ms_per_frame": round(ms, 4),
+                           "solo_ms": round(sms, 4), "ber": e / b, "ber_within_fp32_ci95": bool(lo <= e / b <= hi),
+                           "hbm_frac": round(algorithmic_bytes("admm_ul", Workload(HEAD.B, HEAD.C, HEAD.U, HEAD.W, HEAD.N, HEAD.M, HEAD.T, elem_bytes=4)) * HEAD.W
+                                             / (sms / 1e3) / 1e9 / peaks["hbm_gbs"], 3)}
+        mixed["bits_per_precision"] = b32
+        mixed["fp64_retries"] = dbp.dbp_fp64_retries(h)
+    del sets
+    torch.cuda.empty_cache()
+    if mixed is not None and not args.no_serving and rank == 0:
+        sv = bench_served_precision(dbp, h, args)
+        details["served_precision"] = sv
+        for name, pr in sv["per_precision"].items():
+            mixed.setdefault(name, {}).update({
+                "served_p50_ms": round(pr["loaded"]["p50_ms"], 3), "served_p99_ms": round(pr["loaded"]["p99_ms"], 3),
+                "served_gbit_s": round(pr["saturation_gbit_s"], 3)})
+        mixed["served_load_frames_per_s"] = round(sv["per_precision"]["fp32"]["loaded"]["offered_frames_per_s"], 1)
 
-    # ---- served stream (request loop, uneven frames, coherence blocks) -------
-    serving = None
-    if not args.no_serving:
-        serving = bench_serving(dbp, h, args)
-    graph = None
-    served_mixed = None
-    frame_latency = None
-    if not args.no_serving:
-        graph = bench_graph(dbp, h, stream, device, args)
-        served_mixed = bench_served_precision(dbp, h, args)
-        frame_latency = bench_frame_latency(dbp, h, frames[0])
+    # ---- the other single-GPU workloads ----------------------------------------
+    rows = None
+    if not args.no_rows:
+        rows, details["rows"] = rows_study(dbp, h, device, launching, K, peaks, alu_peak)
 
-    # ---- end to end: host inputs in, host results out ------------------------
-    # Each step copies the frame's channel and receive vectors (one pinned
-    # host block, one copy) to the device, runs both detectors through the C
-    # ABI and copies both detectors' outputs and labels back.  Two streams
-    # with their own device buffers alternate, so one step's copies overlap
-    # the other's kernels, as in a receiver fed frame by frame.
+    # ---- end to end through the host-buffer C ABI -------------------------------
     e2e = None
     if not args.no_e2e:
-        f0 = frames[0]
-        Hc = np.ascontiguousarray(f0["H"].astype(np.complex64)).view(np.uint8).reshape(-1)
-        yc = np.ascontiguousarray(f0["y"].astype(np.complex64)).view(np.uint8).reshape(-1)
-        host_in = torch.empty(Hc.size + yc.size, dtype=torch.uint8).pin_memory()
-        host_in[:Hc.size] = torch.from_numpy(Hc)
-        host_in[Hc.size:] = torch.from_numpy(yc)
-        out_shape = (UL.W, UL.N, UL.U)
-        streams = [torch.cuda.Stream(device) for _ in range(2)]
-        sets = []
-        for _ in range(2):
-            din = torch.empty(host_in.numel(), dtype=torch.uint8, device=device)
-            sets.append({
-                "din": din,
-                "H": din[:Hc.size], "y": din[Hc.size:],
-                "xa": torch.empty(out_shape, dtype=torch.complex64, device=device),
-                "la": torch.empty(out_shape, dtype=torch.uint8, device=device),
-                "xc": torch.empty(out_shape, dtype=torch.complex64, device=device),
-                "lc": torch.empty(out_shape, dtype=torch.uint8, device=device),
-                "hxa": torch.empty(out_shape, dtype=torch.complex64).pin_memory(),
-                "hla": torch.empty(out_shape, dtype=torch.uint8).pin_memory(),
-                "hxc": torch.empty(out_shape, dtype=torch.complex64).pin_memory(),
-                "hlc": torch.empty(out_shape, dtype=torch.uint8).pin_memory()})
-        da, dc = descs(f0["N0"])
+        e2e, el = e2e_host_api(dbp, h, frames[0], args.e2e_steps, launching)
+        el_max = max_over_ranks(el, world, device)
+        e2e["value"] = world * bits * args.e2e_steps / el_max / 1e9
+        e2e["api"] = "dbp_uplink_admm_host (pinned host H, y in; x_hat, labels out; synchronous)"
 
-        def e2e_step(k):
-            st, b = streams[k % 2], sets[k % 2]
-            with torch.cuda.stream(st):
-                b["din"].copy_(host_in, non_blocking=True)
-                dbp.dbp_uplink_admm(h, da, b["H"], b["y"], b["xa"], b["la"], st.cuda_stream)
-                dbp.dbp_uplink_cg(h, dc, b["H"], b["y"], b["xc"], b["lc"], st.cuda_stream)
-                for src, dst in (("xa", "hxa"), ("la", "hla"), ("xc", "hxc"), ("lc", "hlc")):
-                    b[dst].copy_(b[src], non_blocking=True)
-
-        for k in range(4):
-            e2e_step(k)
-        torch.cuda.synchronize(device)
-        KE = args.e2e_steps
-        barrier(world, device)
-        t0 = time.perf_counter()
-        for k in range(KE):
-            e2e_step(k)
-        torch.cuda.synchronize(device)
-        el = max_over_ranks(time.perf_counter() - t0, world, device)
-        # the host-buffer entry points (each call copies its own inputs)
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
-        Hh, yh = pin(f0["H"].astype(np.complex64)), pin(f0["y"].astype(np.complex64))
-        xh, lh = pin(np.zeros(out_shape, dtype=np.complex64)), pin(np.zeros(out_shape, dtype=np.uint8))
-        for _ in range(2):
-            dbp.dbp_uplink_admm_host(h, da, Hh, yh, xh, lh, sp)
-            dbp.dbp_uplink_cg_host(h, dc, Hh, yh, xh, lh, sp)
-        KH = max(KE // 4, 4)
-        t1 = time.perf_counter()
-        for _ in range(KH):
-            dbp.dbp_uplink_admm_host(h, da, Hh, yh, xh, lh, sp)
-            dbp.dbp_uplink_cg_host(h, dc, Hh, yh, xh, lh, sp)
-        el_host = max_over_ranks(time.perf_counter() - t1, world, device)
-        e2e = {"value": world * bits_step * KE / el / 1e9, "unit": "Gbit/s",
-               "h2d_bytes_per_step": int(host_in.numel()),
-               "d2h_bytes_per_step": int(2 * (sets[0]["hxa"].numel() * 8 + sets[0]["hla"].numel())),
-               "api": "pinned host frame -> device (one copy), dbp_uplink_admm + dbp_uplink_cg, "
-                      "outputs and labels of both -> pinned host; two streams alternate",
-               "host_api": {"value": world * bits_step * KH / el_host / 1e9, "unit": "Gbit/s",
-                            "h2d_bytes_per_step": 2 * (Hh.nbytes + yh.nbytes),
-                            "d2h_bytes_per_step": 2 * (xh.nbytes + lh.nbytes),
-                            "api": "dbp_uplink_admm_host + dbp_uplink_cg_host (each call copies its inputs)"}}
+    # ---- optional studies --------------------------------------------------------
+    if "ber_sweep" in studies:
+        details["ber_sweep"] = study_ber_sweep(dbp, h, device, rank)
+    if "extensions" in studies:
+        details["extensions"] = study_extensions(dbp, h, device, launching, K, peaks)
+    if "downlink" in studies:
+        details["downlink"] = study_downlink(dbp, h, device, launching, K)
+    if "serving" in studies:
+        details["serving"] = bench_serving(dbp, h, args)
+    if "graph" in studies:
+        details["graph_batch"] = bench_graph(dbp, h, launching, device, args)
+    if "frame_latency" in studies:
+        fl = synth.uplink_frame(UL.W, UL.N, UL.B, UL.U, UL.M, 10.0, seed=synth.frame_seed(2, 0))
+        details["frame_latency"] = bench_frame_latency(dbp, h, fl)
+    if "tradeoff" in studies and rank == 0:
+        details["tradeoff"] = run_tradeoff(dbp, h, device)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(frames, args.cpu_seconds)
-        cpu["rows"] = cpu_rows()
+        cpu = cpu_baseline(args.cpu_seconds)
+    if rank == 0 and "cpu_rows" in studies:
+        details["cpu_rows"] = cpu_rows()
 
     dbp.dbp_destroy(h)
     if rank == 0:
+        details["roofline"] = rf
         line = {
-            "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": K,
-            "warmup": args.warmup, "ms_per_step": total_ms_max / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {
-                "workload": workload_name(UL, "uplink ADMM T=3 + CG T=8 per step"),
-                "B": UL.B, "C": UL.C, "S": UL.S, "U": UL.U, "qam": UL.M, "subcarriers": UL.W,
-                "symbols": UL.N, "admm_iterations": UL.T, "cg_iterations": UL_T_CG,
-                "bits_per_step": bits_step, "snr_db": "rotating 0..14 dB over 8 resident frames",
-                "l2": "inputs larger than L2: 8 rotating frames, 226 MB resident",
-                "parallelism": f"subcarrier-parallel, {world} independent rank(s)",
-                "kernel_path": args.kernel,
-                "streams": "frames alternate over 2 streams (ADMM then CG per frame)",
-                "autotuned": tuned or None,
-            },
-            "per_detector": {
-                "timing": f"each detector alone: {KR} back-to-back launches on one stream between two CUDA events",
-                "admm_ul": {"ms": admm_avg, "gbit_s": detected_bits(UL) / (admm_avg / 1e3) / 1e9},
-                "cg_ul": {"ms": cg_avg, "gbit_s": detected_bits(UL) / (cg_avg / 1e3) / 1e9},
-            },
-            "roofline": dominant,
-            "roofline_other": rf_admm if dominant is rf_cg else rf_cg,
-            "extensions": extensions,
-            "downlink": downlink,
-            "mixed_vs_fp32": mixed,
-            "graph_batch": graph,
-            "serving": serving,
-            "frame_latency": frame_latency,
-            "served_mixed_vs_fp32": served_mixed,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": 2 * K,
-            "clocks": clk.summary(),
-            "kernel_src": kernel_source_hash(),
-        }
-        print(json.dumps(line))
+            "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": total_ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(HEAD, f"uplink ADMM T={HEAD.T} at {HEAD_SNR_DB:g} dB, one detection "
+                                                       "per frame"),
+                       "bits_per_step": bits, "kernel": tuned.get("fp32", args.kernel),
+                       "l2": "inputs larger than L2: 2 distinct frames resident twice, 4 x 323 MB",
+                       "streams": "consecutive frames alternate over 2 streams",
+                       "parallelism": f"subcarrier-parallel, {world} independent rank(s)"},
+            "roofline": {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel",
+                                            "avg_launch_ms")} | {
+                "tensor_frac": round(rf["tensor_view"]["frac"], 4), "alu_frac": round(rf["alu_view"]["frac"], 4)},
+            "mixed": mixed, "rows": rows, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": K,
+            "clocks": clk.summary(), "details": os.path.relpath(details_path, ROOT) if details_path else None}
+        if details_path:
+            os.makedirs(os.path.dirname(details_path), exist_ok=True)
+            with open(details_path, "w") as fh:
+                json.dump(details, fh, indent=1, default=float)
+        print(json.dumps(line, default=float))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

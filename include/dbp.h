@@ -155,7 +155,16 @@ typedef enum dbp_kernel_path {
                                   the e, x, r, p updates of Alg. 2, the first
                                   placement of Sec. III-D) run once per
                                   symbol and s or p is broadcast to the
-                                  clusters                                   */
+                                  clusters                                   */,
+    DBP_PATH_TC5 = 5           /* uplink ADMM with U = S = 32 (B = 32 C), C
+                                  even and <= 8, N <= 16, FP32 / FP16 / BF16
+                                  inputs, 16-byte aligned buffers: every
+                                  dense product (Gram, matched filter,
+                                  B_c^{-1} times the state) on the tcgen05
+                                  tensor cores with accumulators in tensor
+                                  memory, two clusters per M = 128 MMA; FP32
+                                  operands as scaled FP16 hi / lo pairs
+                                  (three products, FP32 accumulation)        */
 } dbp_kernel_path;
 
 typedef enum dbp_prefactor {

@@ -41,7 +41,7 @@ DBP_FP32, DBP_FP64, DBP_FP16, DBP_BF16 = 0, 1, 2, 3
 DBP_REG_ZF, DBP_REG_MMSE, DBP_REG_BOX, DBP_REG_BPSK = 0, 1, 2, 3
 DBP_FLAG_NORMALIZE = 1
 DBP_MAP_AUTO, DBP_MAP_CTA, DBP_MAP_CLUSTER = 0, 1, 2
-DBP_PATH_AUTO, DBP_PATH_GENERIC, DBP_PATH_TMA, DBP_PATH_MMA, DBP_PATH_BCAST = 0, 1, 2, 3, 4
+DBP_PATH_AUTO, DBP_PATH_GENERIC, DBP_PATH_TMA, DBP_PATH_MMA, DBP_PATH_BCAST, DBP_PATH_TC5 = 0, 1, 2, 3, 4, 5
 DBP_PREFACTOR_AUTO, DBP_PREFACTOR_OFF, DBP_PREFACTOR_ON = 0, 1, 2
 
 _STATUS = {0: "DBP_OK", 1: "DBP_ERR_INVALID_ARG", 2: "DBP_ERR_UNSUPPORTED", 3: "DBP_ERR_NOMEM",

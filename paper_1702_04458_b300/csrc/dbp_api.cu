@@ -316,6 +316,30 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
     s.tcdl = false;
     s.bcast = false;
     s.single = false;
+    s.tc32 = false;
+    // the tcgen05 kernel for uplink ADMM with U = S = 32 when requested (or
+    // chosen by the autotuner)
+    const bool want_tc5 = t.kernel == DBP_PATH_TC5;
+    if (want_tc5 && kind == K_ADMM_UL && t.mapping != DBP_MAP_CLUSTER && aligned16 &&
+        dbp::tc32_eligible_shape(d->B, d->C, d->U, d->N, d->precision) && h->smem_optin >= (size_t)dbp::tc32::SMEM) {
+        s.tc32 = true;
+        s.clu = false;
+        s.P = 1;
+        s.CPB = d->C;
+        s.CL = 1;
+        s.nwarps = dbp::tc32::THREADS / 32;
+        s.smem = dbp::tc32::SMEM;
+        int occ = dbp_tc32_occupancy(d->precision, d->N);
+        if (occ < 1) occ = 1;
+        const long long slots = (long long)h->num_sms * occ;
+        s.grid = d->W < slots ? d->W : slots;
+        s.tiles = d->W;
+        return DBP_OK;
+    }
+    if (t.kernel == DBP_PATH_TC5)
+        return fail(h, DBP_ERR_UNSUPPORTED,
+                    "the tcgen05 kernel needs uplink ADMM with U = S = 32, C even and <= 8, N <= 16, FP32 / FP16 / "
+                    "BF16 inputs and 16-byte aligned buffers (B=%d C=%d U=%d N=%d)", d->B, d->C, d->U, d->N);
     // AUTO takes the tensor-core kernel for U = 8 (measured fastest for ADMM
     // and CG on the B=128, C=8, U=8 frame), else the broadcast kernels.
     const bool want_mma = t.kernel == DBP_PATH_MMA || t.kernel == DBP_PATH_AUTO;
@@ -945,7 +969,7 @@ const char *dbp_last_error(dbp_handle_t h) { return h ? h->err.c_str() : "NULL h
 dbp_status dbp_set_tuning(dbp_handle_t h, const dbp_tuning *t) {
     if (!h || !t) return DBP_ERR_INVALID_ARG;
     if (t->mapping < DBP_MAP_AUTO || t->mapping > DBP_MAP_CLUSTER || t->cluster_size < 0 || t->cluster_size > 16 ||
-        t->warps_per_cta < 0 || t->warps_per_cta > 32 || t->kernel < DBP_PATH_AUTO || t->kernel > DBP_PATH_BCAST ||
+        t->warps_per_cta < 0 || t->warps_per_cta > 32 || t->kernel < DBP_PATH_AUTO || t->kernel > DBP_PATH_TC5 ||
         t->prefactor < DBP_PREFACTOR_AUTO || t->prefactor > DBP_PREFACTOR_ON)
         return fail(h, DBP_ERR_INVALID_ARG, "bad tuning values");
     std::lock_guard<std::mutex> lk(h->tune_mu);

@@ -19,3 +19,14 @@ int dbp_bcast_admm_occupancy(int UT, int threads, size_t smem) {
     default: return 0;
     }
 }
+
+int dbp_tc32_occupancy(int prec, int N) {
+    const bool n14 = (N == 14);
+    switch (prec) {
+    case DBP_FP32: return n14 ? dbp::tc32_occupancy_one<float2, 14>() : dbp::tc32_occupancy_one<float2, 16>();
+    case DBP_FP16: return n14 ? dbp::tc32_occupancy_one<__half2, 14>() : dbp::tc32_occupancy_one<__half2, 16>();
+    case DBP_BF16:
+        return n14 ? dbp::tc32_occupancy_one<__nv_bfloat162, 14>() : dbp::tc32_occupancy_one<__nv_bfloat162, 16>();
+    default: return 0;
+    }
+}

@@ -13,6 +13,7 @@
 #include "dbp_admm.cuh"
 #include "dbp_tc8.cuh"
 #include "dbp_tcdl.cuh"
+#include "dbp_tc32.cuh"
 
 // Host-side caches (dbp_api.cu): the dynamic shared-memory limit of a kernel
 // is raised once per device and size, and the resident-CTA count of a
@@ -49,6 +50,7 @@ struct Shape {
     bool tma;              // persistent bulk-copy kernel
     bool tc8 = false;      // U = 8 tensor-core uplink kernel
     bool tcdl = false;     // U = 16 tensor-core downlink kernel
+    bool tc32 = false;     // U = S = 32 tcgen05 uplink ADMM kernel
     bool single = false;   // bulk-copy kernel with one staging buffer (uplink)
     bool bcast = false;    // consensus step once per symbol, result broadcast
     int P, CPB, CL, nwarps;
@@ -216,6 +218,38 @@ inline cudaError_t launch_tcdl(const FusedParams &p, const Shape &s, cudaStream_
     return launch_pdl(dbp::dbp_tcdl_kernel<16>, (unsigned)s.grid, (unsigned)s.nwarps * 32, s.smem, st, p);
 }
 
+template <typename TIn, int NS>
+cudaError_t launch_tc32_one(const FusedParams &p, const Shape &s, cudaStream_t st) {
+    auto kern = dbp::dbp_tc32_kernel<TIn, NS>;
+    cudaError_t e = dbp_prepare_kernel(reinterpret_cast<const void *>(kern), s.smem);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(kern, (unsigned)s.grid, (unsigned)tc32::THREADS, s.smem, st, p);
+}
+
+// The tcgen05 kernel keeps NS symbol slots in registers: 14 (the LTE slot)
+// or 16 (any N <= 16).
+template <typename TIn>
+cudaError_t launch_tc32_n(const FusedParams &p, const Shape &s, cudaStream_t st) {
+    return p.N == 14 ? launch_tc32_one<TIn, 14>(p, s, st) : launch_tc32_one<TIn, 16>(p, s, st);
+}
+
+inline cudaError_t launch_tc32(int prec, const FusedParams &p, const Shape &s, cudaStream_t st) {
+    switch (prec) {
+    case DBP_FP32: return launch_tc32_n<float2>(p, s, st);
+    case DBP_FP16: return launch_tc32_n<__half2>(p, s, st);
+    case DBP_BF16: return launch_tc32_n<__nv_bfloat162>(p, s, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename TIn, int NS>
+int tc32_occupancy_one() {
+    // two CTAs per SM need the largest shared-memory carveout
+    cudaFuncSetAttribute(dbp::dbp_tc32_kernel<TIn, NS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return dbp_occupancy_cached(reinterpret_cast<const void *>(dbp::dbp_tc32_kernel<TIn, NS>), tc32::THREADS,
+                                tc32::SMEM);
+}
+
 template <int ALG>
 cudaError_t launch_alg(int prec, int UT, const FusedParams &p, const Shape &s, cudaStream_t st) {
     if constexpr (ALG == ALG_ADMM_DL) {
@@ -232,6 +266,7 @@ cudaError_t launch_alg(int prec, int UT, const FusedParams &p, const Shape &s, c
         }
     }
     if constexpr (ALG == ALG_ADMM_UL) {
+        if (s.tc32) return launch_tc32(prec, p, s, st);
         if (s.bcast) {
             switch (UT) {
             case 4: return launch_admm_one<4>(p, s, st);
@@ -264,6 +299,7 @@ int dbp_tc8_occupancy_cg_ul(int threads, size_t smem);
 int dbp_cg_occupancy(int UT, int threads, size_t smem);
 int dbp_bcast_admm_occupancy(int UT, int threads, size_t smem);
 int dbp_tcdl_occupancy(int threads, size_t smem);
+int dbp_tc32_occupancy(int prec, int N);
 
 // The per-cluster operator kernels (dbp_factor.cu): B_c^{-1} of every
 // (subcarrier, cluster) of the frame into p.factor, for the bulk-copy kernel's

@@ -450,12 +450,17 @@ __device__ __forceinline__ void mf_mma3(const float2 *Hs, int hp, int h_rows, co
     }
 }
 
-// Gauss-Jordan inversion as in gj_invert, with the pivot lane's row update
-// written uniformly: the pivot lane holds the pivot row itself, so
-// R[j] - (1 - 1/p) P[j] = P[j] / p gives the normalised row with the same
-// multiply-add as every other lane.  FP32 reciprocal via __frcp_rn.  Returns
-// the smallest pivot's real part (all pivots are real and positive for a
-// Hermitian positive definite matrix).
+// Gauss-Jordan inversion as in gj_invert with one uniform update for every
+// lane.  The pivot lane does not normalise its row in the step: it keeps
+// row k multiplied by its pivot p_k (only the pivot column is set, to p_k
+// times the new entry 1/p_k, i.e. 1), which the later steps preserve since
+// they update a row linearly; after the last step every lane divides its row
+// by its own pivot.  Every lane's step is then R[j] -= f P[j] with f = 0 on
+// the pivot lane, and nothing cancels (normalising in the step as
+// R[j] - (1 - 1/p) P[j] loses log2(p) bits of the pivot row to the rounding
+// of 1 - 1/p, all of them once p > 2^24).  FP32 reciprocal via __frcp_rn.
+// Returns the smallest pivot's real part (all pivots are real and positive
+// for a Hermitian positive definite matrix).
 //
 // Every row is kept rotated so that step k's pivot column sits in R[0]: at
 // the start of step k, R[j] holds column (k + j) mod UT.  The step writes the
@@ -467,6 +472,7 @@ __device__ __forceinline__ void mf_mma3(const float2 *Hs, int hp, int h_rows, co
 template <int UT>
 __device__ __forceinline__ float gj_invert_f(float2 (&R)[UT], float2 *scratch, int u, int lane) {
     float min_piv = 3.0e38f;
+    float2 my_inv = make_float2(1.f, 0.f);   // 1 / (this lane's pivot)
 #pragma unroll 1
     for (int k = 0; k < UT; ++k) {
         if (lane == k) {
@@ -482,7 +488,8 @@ __device__ __forceinline__ float gj_invert_f(float2 (&R)[UT], float2 *scratch, i
         const bool me = (u == k);
         float2 f;
         if (me) {
-            f = make_float2(1.f - inv.x, -inv.y);
+            f = make_float2(0.f, 0.f);
+            my_inv = inv;
         } else {
             f = make_float2(R[0].x * inv.x - R[0].y * inv.y, R[0].x * inv.y + R[0].y * inv.x);
         }
@@ -498,9 +505,12 @@ __device__ __forceinline__ float gj_invert_f(float2 (&R)[UT], float2 *scratch, i
             cmac(R[j + 1], nf, b);
             R[j] = R[j + 1];
         }
-        R[UT - 1] = me ? inv : nf;
+        R[UT - 1] = me ? make_float2(1.f, 0.f) : nf;
         __syncwarp();
     }
+#pragma unroll
+    for (int j = 0; j < UT; ++j)
+        R[j] = make_float2(R[j].x * my_inv.x - R[j].y * my_inv.y, R[j].x * my_inv.y + R[j].y * my_inv.x);
     return min_piv;
 }
 

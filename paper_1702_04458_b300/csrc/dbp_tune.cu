@@ -24,10 +24,11 @@ namespace {
 
 std::vector<dbp_tuning> candidates(int C) {
     std::vector<dbp_tuning> out;
-    const int paths[] = {DBP_PATH_MMA, DBP_PATH_BCAST, DBP_PATH_TMA, DBP_PATH_GENERIC};
+    const int paths[] = {DBP_PATH_TC5, DBP_PATH_MMA, DBP_PATH_BCAST, DBP_PATH_TMA, DBP_PATH_GENERIC};
     const int wpcs[] = {0, 4, 16};
     for (int k : paths)
         for (int w : wpcs) {
+            if (k == DBP_PATH_TC5 && w != 0) continue;   // one CTA shape
             out.push_back(dbp_tuning{DBP_MAP_CTA, 0, w, k, DBP_PREFACTOR_OFF});
             if (k == DBP_PATH_MMA || k == DBP_PATH_TMA)
                 out.push_back(dbp_tuning{DBP_MAP_CTA, 0, w, k, DBP_PREFACTOR_ON});
@@ -40,7 +41,7 @@ std::vector<dbp_tuning> candidates(int C) {
 bool valid_tuning(const dbp_tuning &t) {
     return t.mapping >= DBP_MAP_AUTO && t.mapping <= DBP_MAP_CLUSTER && t.cluster_size >= 0 &&
            t.cluster_size <= 16 && t.warps_per_cta >= 0 && t.warps_per_cta <= 32 &&
-           t.kernel >= DBP_PATH_AUTO && t.kernel <= DBP_PATH_BCAST && t.prefactor >= DBP_PREFACTOR_AUTO &&
+           t.kernel >= DBP_PATH_AUTO && t.kernel <= DBP_PATH_TC5 && t.prefactor >= DBP_PREFACTOR_AUTO &&
            t.prefactor <= DBP_PREFACTOR_ON;
 }
 
