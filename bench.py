@@ -246,6 +246,21 @@ class ClockSampler:
             self._thr.join(timeout=5)
         return False
 
+    def sample_now(self):
+        """One NVML sample from the calling thread (no-op for nvidia-smi)."""
+        if self.source == "nvml":
+            try:
+                nv = self._nv
+                self.samples.append((time.perf_counter(), float(nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM)),
+                                     int(nv.nvmlDeviceGetCurrentClocksEventReasons(self._h))))
+            except Exception:
+                pass
+
+    def wait_first(self, timeout_s: float = 5.0):
+        t0 = time.perf_counter()
+        while not self.samples and time.perf_counter() - t0 < timeout_s:
+            time.sleep(0.005)
+
     def mark(self):
         """Host time stamp; the samples between the first and the last mark
         are the ones taken while the timed frames ran (the host waits for
@@ -265,9 +280,12 @@ class ClockSampler:
             for bit, name in _REASONS.items():
                 if r & bit and bit != 0x1:
                     reasons.add(name)
-        return {"sm_mhz": float(statistics.median(busy)), "sm_max_mhz": self.max_mhz,
-                "reasons": sorted(reasons), "samples": len(self.samples), "samples_timed": len(timed),
-                "source": self.source}
+        out = {"sm_mhz": float(statistics.median(busy)), "sm_max_mhz": self.max_mhz,
+               "reasons": sorted(reasons), "samples": len(self.samples), "samples_timed": len(timed),
+               "source": self.source}
+        if self.error:
+            out["error"] = self.error[:120]
+        return out
 
 
 # ---------------------------------------------------------------------------
@@ -516,9 +534,11 @@ class FrameSet:
                      torch.empty(shape, dtype=torch.uint8, device=device)) for _ in range(2)]
 
 
-def time_frames(dbp, h, fs, desc_of, K, W, streams, launching):
+def time_frames(dbp, h, fs, desc_of, K, W, streams, launching, clk=None):
     """K frames, consecutive ones alternating over two streams (own output
-    buffers), between two CUDA events on the launching stream; returns ms."""
+    buffers), between two CUDA events on the launching stream; returns ms.
+    With a clock sampler, the host samples the SM clock until the end event
+    has completed."""
     import torch
 
     def step(k):
@@ -532,10 +552,17 @@ def time_frames(dbp, h, fs, desc_of, K, W, streams, launching):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(launching)
     streams[1].wait_event(e0)
+    if clk is not None:
+        clk.mark()
     for k in range(K):
         step(k)
     launching.wait_stream(streams[1])
     e1.record(launching)
+    if clk is not None:
+        while not e1.query():
+            clk.sample_now()
+            time.sleep(0.0005)
+        clk.mark()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1)
 
@@ -1268,6 +1295,7 @@ def main(argv=None) -> int:
     peaks = measured_peaks()
     details = {"device": props.name, "sms": props.multi_processor_count}
 
+    clk = ClockSampler(str(props.uuid), period_ms=5).__enter__()
     # ---- headline frames, FP32 -----------------------------------------------
     frames = [synth.uplink_frame(HEAD.W, HEAD.N, HEAD.B, HEAD.U, HEAD.M, HEAD_SNR_DB,
                                  seed=synth.frame_seed(4, i) + 100000 * rank) for i in range(HEAD_FRAMES)]
@@ -1291,14 +1319,13 @@ def main(argv=None) -> int:
     barrier(world, device)
     torch.cuda.synchronize(device)
     # Timed region: K frames alternating over two streams, CUDA events on the
-    # launching stream, SM clocks sampled meanwhile (the sampler also covers
-    # the roofline's back-to-back launches that follow).
-    with ClockSampler(str(props.uuid), period_ms=2) as clk:
-        clk.mark()
-        total_ms = time_frames(dbp, h, sets["fp32"], desc_of(dbp.DBP_FP32), K, args.warmup, streams, launching)
-        clk.mark()
-        KR = max(min(K, 100), 10)
-        head_solo = solo_ms(dbp, h, sets["fp32"], desc_of(dbp.DBP_FP32), KR, launching)
+    # launching stream, SM clocks sampled meanwhile (a sampler thread, and the
+    # host itself until the end event has completed).
+    clk.wait_first()
+    total_ms = time_frames(dbp, h, sets["fp32"], desc_of(dbp.DBP_FP32), K, args.warmup, streams, launching, clk)
+    KR = max(min(K, 100), 10)
+    head_solo = solo_ms(dbp, h, sets["fp32"], desc_of(dbp.DBP_FP32), KR, launching)
+    clk.__exit__(None, None, None)
     barrier(world, device)
     total_ms_max = max_over_ranks(total_ms, world, device)
     bits = detected_bits(HEAD)

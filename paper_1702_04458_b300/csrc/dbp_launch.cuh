@@ -242,12 +242,26 @@ inline cudaError_t launch_tc32(int prec, const FusedParams &p, const Shape &s, c
     }
 }
 
+// Resident CTAs per SM of the tcgen05 kernel: from the device's shared
+// memory and register file directly (the kernel is built for two: 128
+// registers per thread, 104 KB of shared memory, 256 tensor-memory columns).
 template <typename TIn, int NS>
 int tc32_occupancy_one() {
-    // two CTAs per SM need the largest shared-memory carveout
     cudaFuncSetAttribute(dbp::dbp_tc32_kernel<TIn, NS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    return dbp_occupancy_cached(reinterpret_cast<const void *>(dbp::dbp_tc32_kernel<TIn, NS>), tc32::THREADS,
-                                tc32::SMEM);
+    if (dbp_prepare_kernel(reinterpret_cast<const void *>(dbp::dbp_tc32_kernel<TIn, NS>), tc32::SMEM) != cudaSuccess)
+        return 1;
+    int dev = 0, smem_sm = 0, smem_block_reserved = 0, regs_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_block_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, dbp::dbp_tc32_kernel<TIn, NS>) != cudaSuccess) return 1;
+    const int by_smem = smem_sm / (tc32::SMEM + smem_block_reserved);
+    const int by_regs = regs_sm / (fa.numRegs * tc32::THREADS);
+    int occ = by_smem < by_regs ? by_smem : by_regs;
+    if (occ > 2) occ = 2;        // 2 x 256 tensor-memory columns
+    return occ < 1 ? 1 : occ;
 }
 
 template <int ALG>

@@ -62,9 +62,10 @@ constexpr int HT_LO = 8192;
 constexpr int VT = 65536;          // 4 pairs x 8 KB: raw y[w] | y / state tiles (hi, lo) | consensus partials
 constexpr int VT_PAIR = 8192;
 constexpr int VT_LO = 4096;
-constexpr int SCR = 98304;         // per-warp Gauss-Jordan pivot row (FP64 on retry)
-constexpr int SCR_WARP = 512;
+constexpr int SCR = 98304;         // per-warp Gauss-Jordan pivot buffers (FP64 rows on retry)
+constexpr int SCR_WARP = 1024;
 constexpr int SLOTS = SCR + 8 * SCR_WARP;   // scale exponents and warp maxima
+constexpr int PARAMS = SLOTS + 160;        // OpParams of the operator phase (64 B)
 constexpr int BARS = SLOTS + 256;
 constexpr int SMEM = BARS + 64;
 constexpr int TMEM_COLS = 256;
@@ -143,6 +144,90 @@ __device__ __forceinline__ void ld32(uint32_t taddr, float (&a)[32]) {
 
 }  // namespace tc32
 
+// In-register Gauss-Jordan inversion of a 32 x 32 Hermitian positive
+// definite matrix held by one warp as 4 x 8 blocks: lane l = 4 rg + cg owns
+// rows 4 rg .. 4 rg + 3 and columns 8 cg .. 8 cg + 7 (A[r][c]).
+// Step k: the lanes holding column k publish it (colbuf), the lanes holding
+// row k publish it (rowbuf), every lane updates its block with the rank-1
+// term f_i a_kj, f_i = a_ik / a_kk, and the owners of column k write the new
+// column (-f_i; 1 on the pivot row, whose row stays multiplied by its pivot
+// until the final scaling).  Buffers alternate between steps, so one warp
+// barrier per step orders writes and reads.  The step loop is unrolled by 8
+// so every register index is static.  Returns the smallest pivot (real part).
+__device__ __forceinline__ float gj2d_invert(float2 (&A)[4][8], float2 *buf, int lane) {
+    const int rg = lane >> 2, cg = lane & 3;
+    float min_piv = 3.0e38f;
+    float2 myinv[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) myinv[r] = make_float2(1.f, 0.f);
+#pragma unroll 1
+    for (int k0 = 0; k0 < 32; k0 += 8) {
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const int k = k0 + kk;
+            float2 *colbuf = buf + (kk & 1) * 64, *rowbuf = colbuf + 32;
+            const bool ownc = (cg == (k >> 3)), ownr = (rg == (k >> 2));
+            if (ownc) {
+                *reinterpret_cast<float4 *>(&colbuf[4 * rg]) = make_float4(A[0][kk].x, A[0][kk].y, A[1][kk].x, A[1][kk].y);
+                *reinterpret_cast<float4 *>(&colbuf[4 * rg + 2]) = make_float4(A[2][kk].x, A[2][kk].y, A[3][kk].x, A[3][kk].y);
+            }
+            if (ownr) {
+#pragma unroll
+                for (int c = 0; c < 8; c += 2)
+                    *reinterpret_cast<float4 *>(&rowbuf[8 * cg + c]) =
+                        make_float4(A[kk & 3][c].x, A[kk & 3][c].y, A[kk & 3][c + 1].x, A[kk & 3][c + 1].y);
+            }
+            __syncwarp();
+            const float2 pk = colbuf[k];
+            min_piv = fminf(min_piv, pk.x);
+            const float d = __frcp_rn(fmaf(pk.x, pk.x, pk.y * pk.y));
+            const float2 inv = make_float2(pk.x * d, -pk.y * d);
+            float2 f[4], p[8];
+            {
+                float2 a, b;
+                ld2(&colbuf[4 * rg], a, b);
+                f[0] = a; f[1] = b;
+                ld2(&colbuf[4 * rg + 2], a, b);
+                f[2] = a; f[3] = b;
+#pragma unroll
+                for (int c = 0; c < 8; c += 2) {
+                    ld2(&rowbuf[8 * cg + c], a, b);
+                    p[c] = a; p[c + 1] = b;
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const bool piv = ownr && (r == (kk & 3));
+                const float2 a = f[r];
+                f[r] = piv ? make_float2(0.f, 0.f) : make_float2(a.x * inv.x - a.y * inv.y, a.x * inv.y + a.y * inv.x);
+                if (piv) myinv[r] = inv;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float2 nf = make_float2(-f[r].x, -f[r].y);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) cmac(A[r][c], nf, p[c]);
+            }
+            if (ownc) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const bool piv = ownr && (r == (kk & 3));
+                    A[r][kk] = piv ? make_float2(1.f, 0.f) : make_float2(-f[r].x, -f[r].y);
+                }
+            }
+            __syncwarp();
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float2 a = A[r][c];
+            A[r][c] = make_float2(a.x * myinv[r].x - a.y * myinv[r].y, a.x * myinv[r].y + a.y * myinv[r].x);
+        }
+    return min_piv;
+}
+
 // Write B_c^{-1} (row `lane` in R) as the cluster's operator tile (hi / lo,
 // scaled by 2^e with e from the warp's largest magnitude, stored at *eslot).
 __device__ __forceinline__ void tc32_put_operator(const float2 (&R)[32], unsigned char *th, int clw, int *eslot,
@@ -176,6 +261,42 @@ __device__ __forceinline__ void tc32_put_operator(const float2 (&R)[32], unsigne
     }
 }
 
+// Write B_c^{-1} held as 4 x 8 blocks (lane 4 rg + cg: rows 4 rg .. + 3,
+// columns 8 cg .. + 7) as the cluster's operator tile (hi / lo, scaled by
+// 2^e with e from the warp's largest magnitude, stored at *eslot): the
+// lane's 8 columns are one 16-byte K chunk of each of its tile rows.
+__device__ __forceinline__ void tc32_put_operator_2d(const float2 (&A)[4][8], unsigned char *th, int clw, int *eslot,
+                                                     int lane) {
+    using namespace tc32;
+    const int rg = lane >> 2, cg = lane & 3;
+    float mb = 0.f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) mb = fmaxf(mb, fmaxf(fabsf(A[r][c].x), fabsf(A[r][c].y)));
+    const int eb = scale_exp(warp_max(mb));
+    if (lane == 0) *eslot = eb;
+    const float sb = exp2i(eb);
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int pc = 0; pc < 2; ++pc) {
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const float2 a = A[r][2 * t], b = A[r][2 * t + 1];
+                uint32_t ha, la, hb, lb;
+                split16((pc ? a.y : a.x) * sb, ha, la);
+                split16((pc ? b.y : b.x) * sb, hb, lb);
+                hw[t] = pack2(ha, hb);
+                lw[t] = pack2(la, lb);
+            }
+            const int o = off16(64 * clw + arow(pc, 4 * rg + r), 8 * cg);
+            *reinterpret_cast<uint4 *>(th + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4 *>(th + HT_LO + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+}
+
 // FP64 recomputation of one cluster's operator (whole warp): the Gram
 // H_c^H H_c + delta I from the cluster block in global memory (row u per
 // lane), its Gauss-Jordan inverse in FP64, rounded to FP32 and written as
@@ -207,6 +328,69 @@ __device__ __noinline__ void tc32_fp64_operator(const TIn *Hg, double delta, dou
     tc32_put_operator(R, th, clw, eslot, lane);
 }
 
+// What the operator phase needs besides shared memory, kept in shared
+// memory by the kernel so that the phase is called without arguments.
+struct OpParams {
+    const void *H;              // inputs in global memory (FP64 retry)
+    unsigned int *retries;      // FP64 retry counter
+    double delta;               // diagonal loading rho
+    long long row0;             // first H row of the subcarrier (w B)
+    int C;
+};
+
+// The operator phase of one subcarrier (whole CTA): warp c < C loads its
+// cluster's Gram as 4 x 8 blocks (from the XOR-swizzled planes Gr, Gi of the
+// Gram readout), waits until every warp has, inverts it by Gauss-Jordan
+// elimination with the pivot check, recomputes it in FP64 if a pivot was too
+// small, and writes B_c^{-1} as the cluster's operator tile.
+template <typename TIn>
+__device__ __forceinline__ void tc32_operator_phase() {
+    using namespace tc32;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rg = lane >> 2, cg = lane & 3;
+    const OpParams &op = *reinterpret_cast<const OpParams *>(sm + PARAMS);
+    int *eslot = reinterpret_cast<int *>(sm + SLOTS);
+    const int C = op.C;
+    float2 A[4][8];
+    if (warp < C) {
+        const float *gr = reinterpret_cast<const float *>(sm + HT + (warp >> 1) * HT_PAIR + (warp & 1) * 8192);
+        const float *gi = gr + 1024;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = 4 * rg + r;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int ch = 2 * cg + h;
+                const float4 a = *reinterpret_cast<const float4 *>(gr + i * 32 + 4 * (ch ^ (i & 7)));
+                const float4 b = *reinterpret_cast<const float4 *>(gi + i * 32 + 4 * (ch ^ (i & 7)));
+                A[r][4 * h + 0] = make_float2(a.x, b.x);
+                A[r][4 * h + 1] = make_float2(a.y, b.y);
+                A[r][4 * h + 2] = make_float2(a.z, b.z);
+                A[r][4 * h + 3] = make_float2(a.w, b.w);
+            }
+        }
+    }
+    __syncthreads();        // every Gram block is in registers
+    if (warp < C) {
+        float dmax = 0.f;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (4 * rg + r == 8 * cg + c) dmax = fmaxf(dmax, A[r][c].x);
+        dmax = warp_max(dmax);
+        float2 *scr = reinterpret_cast<float2 *>(sm + SCR + warp * SCR_WARP);
+        const float min_piv = gj2d_invert(A, scr, lane);
+        unsigned char *th = sm + HT + (warp >> 1) * HT_PAIR;
+        if (!(min_piv >= 0x1p-12f * dmax)) {
+            if (lane == 0) eslot[24 + warp] = 1;    // FP64 retry after the phase
+        } else {
+            tc32_put_operator_2d(A, th, warp & 1, eslot + 16 + warp, lane);
+        }
+    }
+}
+
 template <typename TIn, int NS>
 __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedParams p) {
     using namespace tc32;
@@ -229,13 +413,19 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
     uint64_t *bar_mma = bar_ld + 1;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_ld + 2);
     int *abort_flag = reinterpret_cast<int *>(tslot + 1);
-    int *eslot = reinterpret_cast<int *>(sm + SLOTS);           // eH[8] | eY[8] | eB[8]
-    float *mslot = reinterpret_cast<float *>(sm + SLOTS + 96);  // per-warp maxima
+    int *eslot = reinterpret_cast<int *>(sm + SLOTS);           // eH[8] | eY[8] | eB[8] | retry flags[8]
+    float *mslot = reinterpret_cast<float *>(sm + SLOTS + 128); // per-warp maxima
 
     if (tid == 0) {
         mbar_init(bar_ld, 1);
         mbar_init(bar_mma, 1);
         *abort_flag = 0;
+        for (int k = 0; k < 8; ++k) eslot[24 + k] = 0;
+        OpParams *op = reinterpret_cast<OpParams *>(sm + PARAMS);
+        op->H = p.H;
+        op->retries = p.retries;
+        op->delta = p.delta;
+        op->C = p.C;
         fence_mbar_init();
     }
     if (warp == 0) {
@@ -570,39 +760,19 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
         if (*abort_flag) break;
 
         // ---- B_c^{-1}: Gauss-Jordan per warp, pivot check, FP64 retry --------
-        float2 R[32];
-        if (warp < C) {
-            const float *gr = reinterpret_cast<const float *>(sm + HT + (warp >> 1) * HT_PAIR + (warp & 1) * 8192);
-            const float *gi = gr + 1024;
-#pragma unroll
-            for (int ch = 0; ch < 8; ++ch) {
-                const float4 a = *reinterpret_cast<const float4 *>(gr + lane * 32 + 4 * (ch ^ (lane & 7)));
-                const float4 b = *reinterpret_cast<const float4 *>(gi + lane * 32 + 4 * (ch ^ (lane & 7)));
-                R[4 * ch + 0] = make_float2(a.x, b.x);
-                R[4 * ch + 1] = make_float2(a.y, b.y);
-                R[4 * ch + 2] = make_float2(a.z, b.z);
-                R[4 * ch + 3] = make_float2(a.w, b.w);
-            }
-        }
-        __syncthreads();        // every Gram row is in registers
-        if (warp < C) {
-            float dmax = 0.f;
-#pragma unroll
-            for (int v = 0; v < 32; ++v)
-                if (v == lane) dmax = R[v].x;
-            dmax = warp_max(dmax);
-            float2 *scr = reinterpret_cast<float2 *>(sm + SCR + warp * SCR_WARP);
-            const float min_piv = gj_invert_f<32>(R, scr, lane, lane);
-            unsigned char *th = sm + HT + (warp >> 1) * HT_PAIR;
-            if (!(min_piv >= 0x1p-12f * dmax)) {
-                // FP64 retry: this cluster's Gram from the inputs in global
-                // memory and its inverse, in FP64, written as the operator
-                const TIn *Hg = static_cast<const TIn *>(p.H) + ((size_t)w * B + (size_t)warp * 32) * 32;
-                tc32_fp64_operator<TIn>(Hg, p.delta, reinterpret_cast<double2 *>(scr), th, warp & 1, eslot + 16 + warp,
-                                        lane);
-                if (lane == 0 && p.retries) atomicAdd(p.retries, 1u);
-            } else {
-                tc32_put_operator(R, th, warp & 1, eslot + 16 + warp, lane);
+        if (tid == 0) reinterpret_cast<OpParams *>(sm + PARAMS)->row0 = (long long)w * B;
+        __syncthreads();
+        tc32_operator_phase<TIn>();
+        if (warp < C && eslot[24 + warp]) {
+            // FP64 retry: this cluster's Gram from the inputs in global
+            // memory and its inverse, in FP64, written as the operator
+            const TIn *Hg = static_cast<const TIn *>(p.H) + ((size_t)w * B + (size_t)warp * 32) * 32;
+            __syncwarp();
+            tc32_fp64_operator<TIn>(Hg, p.delta, reinterpret_cast<double2 *>(sm + SCR + warp * SCR_WARP),
+                                    sm + HT + (warp >> 1) * HT_PAIR, warp & 1, eslot + 16 + warp, lane);
+            if (lane == 0) {
+                eslot[24 + warp] = 0;
+                if (p.retries) atomicAdd(p.retries, 1u);
             }
         }
         tc5::fence_smem_to_async();

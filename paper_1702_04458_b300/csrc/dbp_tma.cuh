@@ -469,6 +469,18 @@ __device__ __forceinline__ void mf_mma3(const float2 *Hs, int hp, int h_rows, co
 // in order.  Every step is then the same code with fixed register indices,
 // so the step loop stays rolled (a fully unrolled UT = 32 elimination is
 // several thousand instructions and thrashes the instruction cache).
+// Pivot-row load for the elimination: an ordered shared-memory load, so that
+// the compiler does not hoist the whole row ahead of the multiply-adds (which
+// would keep a second row in registers).
+__device__ __forceinline__ void ld2_ordered(const float2 *p, float2 &a, float2 &b) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"((unsigned)__cvta_generic_to_shared(p)));
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+}
+
 template <int UT>
 __device__ __forceinline__ float gj_invert_f(float2 (&R)[UT], float2 *scratch, int u, int lane) {
     float min_piv = 3.0e38f;
