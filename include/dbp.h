@@ -60,7 +60,8 @@ typedef enum dbp_status {
     DBP_ERR_CUDA = 4,          /* a CUDA runtime call or launch failed       */
     DBP_ERR_TIMEOUT = 5,       /* a bounded wait ran out                     */
     DBP_ERR_UNIMPLEMENTED = 6, /* entry point not provided by this library   */
-    DBP_PENDING = 7            /* submitted work has not completed yet       */
+    DBP_PENDING = 7,           /* submitted work has not completed yet       */
+    DBP_ERR_CANCELLED = 8      /* a queued request was cancelled (dbp_cancel)*/
 } dbp_status;
 
 typedef enum dbp_precision {
@@ -93,7 +94,14 @@ typedef enum dbp_regularizer {
 typedef struct dbp_config {
     int32_t device;            /* CUDA device ordinal                        */
     int32_t reserved;
-    uint64_t hbm_budget_bytes; /* workspace budget; 0 = no limit             */
+    uint64_t hbm_budget_bytes; /* cap on the device memory the library itself
+                                  allocates for this handle (host-variant
+                                  staging buffers, the request loop's pool,
+                                  the separate operator kernel's buffers, the
+                                  normalisation accumulator); an allocation
+                                  past it fails with DBP_ERR_NOMEM.  0 = no
+                                  limit.  The caller's own buffers do not
+                                  count                                      */
 } dbp_config;
 
 typedef struct dbp_frame_desc {
@@ -318,11 +326,20 @@ typedef struct dbp_server_config {
                                   channels; 0 = 2 GiB                        */
 } dbp_server_config;
 
+/* dbp_request.flags */
+#define DBP_REQ_DEVICE_BUFFERS 1u  /* H, in, out, labels and beta_out are
+                                      device pointers (caller-owned, alive
+                                      until the ticket finishes): the frame
+                                      runs on them in place, with no host
+                                      copies; only the resident per-cluster
+                                      operator of a coherence block comes
+                                      from the pool                          */
+
 typedef struct dbp_request {
     int32_t kind;              /* dbp_kind                                   */
-    int32_t reserved;
+    uint32_t flags;            /* DBP_REQ_*; 0 = host buffers               */
     dbp_frame_desc desc;
-    const void *H;             /* host [W][B][U]                             */
+    const void *H;             /* host [W][B][U] (device with the flag)      */
     const void *in;            /* host y [W][N][B] (uplink), s [W][N][U]     */
     void *out;                 /* host x_hat [W][N][U] or x [W][N][B]        */
     uint8_t *labels;           /* host [W][N][U] or NULL (uplink)            */
@@ -351,10 +368,18 @@ dbp_status dbp_server_start(dbp_handle_t h, const dbp_server_config *cfg);
  * frames still queued with DBP_ERR_TIMEOUT and release the pool. */
 dbp_status dbp_server_stop(dbp_handle_t h);
 
-/* Queue one frame.  The descriptor and pointers are copied; the host
- * buffers must stay valid until dbp_poll / dbp_wait reports the ticket
- * finished.  DBP_ERR_INVALID_ARG for a bad descriptor (checked here). */
+/* Queue one frame.  The descriptor and pointers are copied; the buffers
+ * must stay valid until dbp_poll / dbp_wait reports the ticket finished.
+ * DBP_ERR_INVALID_ARG for a bad descriptor or unknown flags (checked here);
+ * DBP_ERR_NOMEM if the frame's staged inputs and outputs alone are larger
+ * than the pool (it could never be admitted). */
 dbp_status dbp_submit(dbp_handle_t h, const dbp_request *req, uint64_t *ticket);
+
+/* Cancel a frame that is still queued: DBP_OK (the ticket then finishes
+ * with status DBP_ERR_CANCELLED and nothing ran), DBP_PENDING if it has
+ * already been admitted (it runs to completion and keeps its ticket),
+ * DBP_ERR_INVALID_ARG for an unknown or already finished ticket. */
+dbp_status dbp_cancel(dbp_handle_t h, uint64_t ticket);
 
 /* DBP_PENDING while the frame is queued or running; otherwise fills *res,
  * releases the ticket and returns DBP_OK (res->status holds the frame's own
@@ -431,33 +456,51 @@ dbp_status dbp_graph_launch(dbp_graph_t g, void *stream);
 /* Release the graph (waits for its launches to finish). */
 dbp_status dbp_graph_destroy(dbp_graph_t g);
 
+/* ------------------------------------------------------------------------
+ * Test hook of the bounded device waits (the paper has no counterpart).
+ * Every wait of a kernel on its input copies is bounded: it gives up after a
+ * limit, raises a device status bit and the kernel returns normally, and the
+ * host reports DBP_ERR_TIMEOUT (dbp_device_status, the host-buffer variants).
+ * With DBP_TEST_STARVE_COPY set, later calls on the handle arm every input
+ * copy's mbarrier with 16 bytes more than the copy delivers, so the barrier
+ * never completes, and use a wait limit of about 1 ms: the waits run out
+ * without any fault, the kernels return and their outputs are unspecified.
+ * dbp_set_test_faults(h, 0) restores normal operation.
+ * ------------------------------------------------------------------------ */
+#define DBP_TEST_STARVE_COPY 1u
+dbp_status dbp_set_test_faults(dbp_handle_t h, uint32_t flags);
+
 /* Largest subcarrier count W accepted by dbp_downlink_admm_static. */
 #define DBP_STATIC_MAX_SUBCARRIERS 16384
 
 /* Downlink beamforming with power normalisation that allocates no device
  * memory.  The paper has no counterpart: this entry point exists for
- * callers that cannot call cudaMalloc -- code running while a stream is
- * captured into a CUDA graph (allocation cannot be captured), processes
- * whose device memory is entirely reserved by another allocator, and
- * real-time front ends that must not allocate after start-up.
- * dbp_downlink_admm with DBP_FLAG_NORMALIZE allocates a small accumulator
- * on its first use; this call instead keeps its scratch (one partial energy
- * per subcarrier, plus the frame total and beta) in a fixed library-owned
- * device array of DBP_STATIC_MAX_SUBCARRIERS + 2 doubles that every GPU
- * which loads the library holds until the process exits.
+ * callers that cannot call cudaMalloc -- processes whose device memory is
+ * entirely reserved by another allocator, and real-time front ends that
+ * must not allocate once they are running.  dbp_downlink_admm with
+ * DBP_FLAG_NORMALIZE allocates a small accumulator on its first use; this
+ * call instead keeps its scratch (one partial energy per subcarrier, plus
+ * the frame total and beta) in a fixed library-owned device array of
+ * DBP_STATIC_MAX_SUBCARRIERS + 2 doubles that every GPU which loads the
+ * library holds until the process exits.  It never runs the separate
+ * operator kernel (whose buffer comes from a pool).
  * Same arguments and results as dbp_downlink_admm: x is scaled in place by
  * beta = sqrt(B*W*N / sum|x|^2) when DBP_FLAG_NORMALIZE is set (the sum is
  * taken per subcarrier and then over subcarriers in a fixed order, so beta
  * does not depend on scheduling), and beta is stored at beta_out (device)
  * if non-NULL.  The caller still passes every input and output buffer.
  * Errors: DBP_ERR_UNSUPPORTED when W > DBP_STATIC_MAX_SUBCARRIERS (no work
- * is enqueued), otherwise as dbp_downlink_admm.
+ * is enqueued); DBP_ERR_CUDA, without enqueueing anything, when a CUDA error
+ * from earlier work is still pending; otherwise as dbp_downlink_admm.  Every
+ * error leaves its text in dbp_last_error.
  * Set-up: the first call on each device (with that device current) looks
- * up the array's device address; make that first call before any stream
- * capture.  Every call reuses the same array: two calls whose work overlaps
- * on the GPU (different streams, or different host threads) race on it and
- * must be serialised by the caller.  Each call overwrites every scratch
- * entry it reads, so nothing has to be cleared between calls. */
+ * up the array's device address and keeps it for the life of the process;
+ * make that first call before any stream capture, and do not use the entry
+ * point after cudaDeviceReset.  Every call reuses the same array: two calls
+ * whose work overlaps on the GPU (different streams, or different host
+ * threads) race on it and must be serialised by the caller.  Each call
+ * overwrites every scratch entry it reads, so nothing has to be cleared
+ * between calls. */
 dbp_status dbp_downlink_admm_static(dbp_handle_t h, const dbp_frame_desc *d,
                                     const void *H, const void *s, void *x,
                                     double *beta_out, void *stream);

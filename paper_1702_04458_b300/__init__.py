@@ -36,6 +36,7 @@ DBP_ERR_CUDA = 4
 DBP_ERR_TIMEOUT = 5
 DBP_ERR_UNIMPLEMENTED = 6
 DBP_PENDING = 7
+DBP_ERR_CANCELLED = 8
 
 DBP_FP32, DBP_FP64, DBP_FP16, DBP_BF16 = 0, 1, 2, 3
 DBP_REG_ZF, DBP_REG_MMSE, DBP_REG_BOX, DBP_REG_BPSK = 0, 1, 2, 3
@@ -45,7 +46,8 @@ DBP_PATH_AUTO, DBP_PATH_GENERIC, DBP_PATH_TMA, DBP_PATH_MMA, DBP_PATH_BCAST, DBP
 DBP_PREFACTOR_AUTO, DBP_PREFACTOR_OFF, DBP_PREFACTOR_ON = 0, 1, 2
 
 _STATUS = {0: "DBP_OK", 1: "DBP_ERR_INVALID_ARG", 2: "DBP_ERR_UNSUPPORTED", 3: "DBP_ERR_NOMEM",
-           4: "DBP_ERR_CUDA", 5: "DBP_ERR_TIMEOUT", 6: "DBP_ERR_UNIMPLEMENTED", 7: "DBP_PENDING"}
+           4: "DBP_ERR_CUDA", 5: "DBP_ERR_TIMEOUT", 6: "DBP_ERR_UNIMPLEMENTED", 7: "DBP_PENDING",
+           8: "DBP_ERR_CANCELLED"}
 
 
 class dbp_config(ctypes.Structure):
@@ -224,11 +226,8 @@ _lib.dbp_downlink_admm_static.argtypes = [_H, ctypes.POINTER(dbp_frame_desc), _P
 
 
 def dbp_downlink_admm_static(h, d, H, s, x, beta_out=None, stream=None) -> None:
-    st = _lib.dbp_downlink_admm_static(h, ctypes.byref(d), _ptr(H), _ptr(s), _ptr(x),
-                                       _ptr(beta_out), _stream(stream))
-    if st == DBP_ERR_UNSUPPORTED and d.W > DBP_STATIC_MAX_SUBCARRIERS:
-        raise DbpError(st, f"W={d.W} exceeds DBP_STATIC_MAX_SUBCARRIERS={DBP_STATIC_MAX_SUBCARRIERS}")
-    _check(h, st)
+    _check(h, _lib.dbp_downlink_admm_static(h, ctypes.byref(d), _ptr(H), _ptr(s), _ptr(x),
+                                            _ptr(beta_out), _stream(stream)))
 
 
 # ---------------------------------------------------------------------------
@@ -242,7 +241,7 @@ class dbp_server_config(ctypes.Structure):
 
 
 class dbp_request(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("desc", dbp_frame_desc),
+    _fields_ = [("kind", ctypes.c_int32), ("flags", ctypes.c_uint32), ("desc", dbp_frame_desc),
                 ("H", ctypes.c_void_p), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
                 ("labels", ctypes.c_void_p), ("beta_out", ctypes.c_void_p),
                 ("channel_key", ctypes.c_uint64), ("coherence_epoch", ctypes.c_uint64),
@@ -275,9 +274,14 @@ def dbp_server_stop(h) -> None:
     _check(h, _lib.dbp_server_stop(h))
 
 
+DBP_REQ_DEVICE_BUFFERS = 1
+
+
 def request(kind, desc, H, inp, out, labels=None, beta_out=None, channel_key=0, coherence_epoch=0,
-            user_tag=0) -> dbp_request:
-    return dbp_request(kind, 0, desc, _ptr(H), _ptr(inp), _ptr(out), _ptr(labels), _ptr(beta_out),
+            user_tag=0, flags=0) -> dbp_request:
+    """flags=DBP_REQ_DEVICE_BUFFERS: H, inp, out, labels, beta_out are device
+    buffers (e.g. CUDA tensors) used in place; otherwise host buffers."""
+    return dbp_request(kind, flags, desc, _ptr(H), _ptr(inp), _ptr(out), _ptr(labels), _ptr(beta_out),
                        channel_key, coherence_epoch, user_tag)
 
 
@@ -285,6 +289,29 @@ def dbp_submit(h, req: dbp_request) -> int:
     t = ctypes.c_uint64(0)
     _check(h, _lib.dbp_submit(h, ctypes.byref(req), ctypes.byref(t)))
     return int(t.value)
+
+
+DBP_TEST_STARVE_COPY = 1
+_lib.dbp_set_test_faults.restype = _S
+_lib.dbp_set_test_faults.argtypes = [_H, ctypes.c_uint32]
+
+
+def dbp_set_test_faults(h, flags: int) -> None:
+    _check(h, _lib.dbp_set_test_faults(h, flags))
+
+
+_lib.dbp_cancel.restype = _S
+_lib.dbp_cancel.argtypes = [_H, ctypes.c_uint64]
+
+
+def dbp_cancel(h, ticket: int) -> bool:
+    """True if the queued frame was cancelled (its ticket then finishes with
+    DBP_ERR_CANCELLED), False if it was already admitted and runs."""
+    st = _lib.dbp_cancel(h, ticket)
+    if st == DBP_PENDING:
+        return False
+    _check(h, st)
+    return True
 
 
 def dbp_poll(h, ticket: int):

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_admm_kernel(const 
         const uint32_t hbytes = (uint32_t)(S * UT * 8);
         const uint32_t ybytes = (uint32_t)(S * 8);
         fence_proxy_async();
-        if (lane == 0) mbar_arrive_expect_tx(bar, hbytes + (uint32_t)N * ybytes);
+        if (lane == 0) mbar_arrive_expect_tx(bar, hbytes + (uint32_t)N * ybytes + p.starve_bytes);
         __syncwarp();
         if (lane == 0) bulk_g2s(wb, Hg + ((size_t)w * B + (size_t)c * S) * UT, hbytes, bar);
         for (int n = lane; n < N; n += 32)
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_admm_kernel(const 
         const int nw = (tile + (int)gridDim.x) * P + pl;
         const bool prefetch = (tile + (int)gridDim.x < p.tiles) && nw < W;
         if (valid) {
-            mbar_wait_bounded(bar, phase, p.status);
+            mbar_wait_bounded(bar, phase, p.status, p.wait_iters);
             phase ^= 1u;
         }
 

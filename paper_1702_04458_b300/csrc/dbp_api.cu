@@ -689,6 +689,10 @@ bool stream_capturing(cudaStream_t st) {
     return cs != cudaStreamCaptureStatusNone;
 }
 
+// Whether `bytes` more of library-owned device memory fit the handle's
+// budget (dbp_config.hbm_budget_bytes; 0 = no limit).
+bool budget_allows(const dbp_context *h, size_t bytes) { return h->budget == 0 || h->used + bytes <= h->budget; }
+
 dbp_status run_ex(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void *H, const void *vin,
                   void *out, uint8_t *labels, double *beta_out, cudaStream_t st, const DbpExec *ex,
                   bool *factor_used) {
@@ -736,6 +740,10 @@ dbp_status run_ex(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void
     p.off_g = s.off_g;
     p.off_v = s.off_v;
     p.warp_bytes = s.warp_bytes;
+    if (h->test_faults & DBP_TEST_STARVE_COPY) {
+        p.starve_bytes = 16;         // the input copies' barriers never complete
+        p.wait_iters = 1 << 14;      // and give up after ~1 ms
+    }
     p.H = H;
     p.vin = vin;
     p.out = out;
@@ -745,9 +753,12 @@ dbp_status run_ex(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void
     if (norm) {
         if (!energy) {
             if (!h->energy) {
+                if (!budget_allows(h, sizeof(double)))
+                    return fail(h, DBP_ERR_NOMEM, "the normalisation accumulator exceeds the handle's HBM budget");
                 e = cudaMalloc(&h->energy, sizeof(double));
                 if (e != cudaSuccess)
                     return fail(h, DBP_ERR_NOMEM, "cudaMalloc(energy): %s", cudaGetErrorString(e));
+                h->used += sizeof(double);
             }
             energy = h->energy;
         }
@@ -769,12 +780,17 @@ dbp_status run_ex(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void
     // fused kernel then loads it (factor_mode 2) from a stream-ordered buffer
     // that is returned to the pool after it.
     void *ws = nullptr;
-    const bool pre_wanted = tune.prefactor == DBP_PREFACTOR_ON && !ex && prefactor_available(d, kind, s, UT);
+    // not for callers that allocate nothing (ex->no_workspace), nor inside
+    // the request loop (which brings its own resident operators)
+    const bool pre_wanted = tune.prefactor == DBP_PREFACTOR_ON && !(ex && ex->no_workspace) && !ex &&
+                            prefactor_available(d, kind, s, UT);
     if (pre_wanted && !stream_capturing(st)) {
         cudaMemPool_t pool = nullptr;
         v = factor_pool(h, &pool);
         if (v != DBP_OK) return v;
         const size_t bytes = (size_t)d->W * d->C * UT * UT * sizeof(float2);
+        if (!budget_allows(h, bytes))
+            return fail(h, DBP_ERR_NOMEM, "operator buffer of %zu bytes exceeds the handle's HBM budget", bytes);
         e = cudaMallocFromPoolAsync(&ws, bytes, pool, st);
         if (e != cudaSuccess) return fail(h, DBP_ERR_NOMEM, "operator buffer (%zu bytes): %s", bytes, cudaGetErrorString(e));
         dbp::FactorParams fp{};
@@ -827,12 +843,17 @@ dbp_status run(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void *H
 dbp_status ensure_dev(dbp_context *h, int slot, size_t bytes) {
     if (h->dev_cap[slot] >= bytes) return DBP_OK;
     if (h->dev[slot]) cudaFree(h->dev[slot]);
+    h->used -= h->dev_cap[slot];
     h->dev[slot] = nullptr;
     h->dev_cap[slot] = 0;
     if (bytes == 0) return DBP_OK;
+    if (!budget_allows(h, bytes))
+        return fail(h, DBP_ERR_NOMEM, "staging buffer of %zu bytes exceeds the handle's HBM budget (%llu of %llu used)",
+                    bytes, (unsigned long long)h->used, (unsigned long long)h->budget);
     cudaError_t e = cudaMalloc(&h->dev[slot], bytes);
     if (e != cudaSuccess) return fail(h, DBP_ERR_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
     h->dev_cap[slot] = bytes;
+    h->used += bytes;
     return DBP_OK;
 }
 
@@ -916,7 +937,13 @@ int dbp_padded_users(int U) { return next_pow2_ut(U); }
 
 extern "C" {
 
-const char *dbp_version(void) { return "dbp-b300 0.1 (sm_103a)"; }
+const char *dbp_version(void) { return "dbp-b300 0.2 (sm_103a)"; }
+
+dbp_status dbp_set_test_faults(dbp_handle_t h, uint32_t flags) {
+    if (!h || (flags & ~DBP_TEST_STARVE_COPY)) return DBP_ERR_INVALID_ARG;
+    h->test_faults = flags;
+    return DBP_OK;
+}
 
 dbp_status dbp_create(dbp_handle_t *out, const dbp_config *cfg) {
     if (!out) return DBP_ERR_INVALID_ARG;

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_cg_kernel(const Fu
         const uint32_t hbytes = (uint32_t)(S * UT * 8);
         const uint32_t ybytes = (uint32_t)(S * 8);
         fence_proxy_async();
-        if (lane == 0) mbar_arrive_expect_tx(bar, hbytes + (uint32_t)N * ybytes);
+        if (lane == 0) mbar_arrive_expect_tx(bar, hbytes + (uint32_t)N * ybytes + p.starve_bytes);
         __syncwarp();
         if (lane == 0) bulk_g2s(wb, Hg + ((size_t)w * B + (size_t)c * S) * UT, hbytes, bar);
         for (int n = lane; n < N; n += 32)
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_cg_kernel(const Fu
         const int nw = (tile + (int)gridDim.x) * P + pl;
         const bool prefetch = (tile + (int)gridDim.x < p.tiles) && nw < W;
         if (valid) {
-            mbar_wait_bounded(bar, phase, p.status);
+            mbar_wait_bounded(bar, phase, p.status, p.wait_iters);
             phase ^= 1u;
         }
 
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_cg_kernel(const Fu
                     ev.y = fmaf(rcg, pv.y, ws.y);
                     const float pe = group_sum<UT>(pv.x * ev.x + pv.y * ev.y);
                     const bool go = !(rr < 0.f) && rr != 0.f && pe != 0.f;
-                    const float alpha = go ? __fdividef(rr, pe) : 0.f;
+                    const float alpha = go ? __fdiv_rn(rr, pe) : 0.f;
                     if (go) {
                         xv.x = fmaf(alpha, pv.x, xv.x);
                         xv.y = fmaf(alpha, pv.y, xv.y);
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_cg_kernel(const Fu
                     const float rn = group_sum<UT>(rv.x * rv.x + rv.y * rv.y);
                     if (ok) {
                         if (go) {
-                            const float beta = __fdividef(rn, rr);
+                            const float beta = __fdiv_rn(rn, rr);
                             pv.x = fmaf(beta, pv.x, rv.x);
                             pv.y = fmaf(beta, pv.y, rv.y);
                             pb[e] = pv;

@@ -88,6 +88,11 @@ struct FusedParams {
     // G_c (CG).
     float2 *factor;
     int factor_mode;
+    // Test hook of the bounded waits (0 = off): bytes added to every input
+    // copy's expected transaction count (so that its barrier never
+    // completes) and the wait limit in polling iterations.
+    int starve_bytes;
+    int wait_iters;
 };
 
 // ---------------------------------------------------------------------------

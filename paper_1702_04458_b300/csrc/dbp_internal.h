@@ -15,11 +15,13 @@ struct dbp_server;
 
 struct dbp_context {
     int device = 0;
-    uint64_t budget = 0;
+    uint64_t budget = 0;                 // cap on library-owned device memory (0: none)
+    uint64_t used = 0;                   // library-owned device memory in use
     int num_sms = 0;
     size_t smem_optin = 0;
     std::string err;
     dbp_tuning tuning{};
+    uint32_t test_faults = 0;            // dbp_set_test_faults
     double *energy = nullptr;            // downlink power accumulator
     int *status = nullptr;               // device status word of the kernels
     void *dev[4] = {nullptr, nullptr, nullptr, nullptr};   // host-variant buffers

@@ -77,6 +77,7 @@ class Arena {
         }
     }
     char *at(size_t off) const { return base_ + off; }
+    size_t size() const { return size_; }
 
   private:
     char *base_ = nullptr;
@@ -145,6 +146,7 @@ struct dbp_server {
         return std::chrono::duration<double, std::micro>(Clock::now() - origin).count();
     }
 
+    static bool on_device(const Job &j) { return (j.req.flags & DBP_REQ_DEVICE_BUFFERS) != 0; }
     size_t in_bytes(const Job &j) const {
         const dbp_frame_desc &d = j.req.desc;
         const size_t e = dbp_in_elem_bytes(d.precision);
@@ -180,7 +182,7 @@ struct dbp_server {
         }
     }
     void drop_resident(Resident *r) {
-        arena.release(r->h_off, r->h_bytes);
+        if (r->h_bytes) arena.release(r->h_off, r->h_bytes);
         for (Factor &f : r->factors)
             if (f.bytes) arena.release(f.off, f.bytes);
         if (r->uploaded) cudaEventDestroy(r->uploaded);
@@ -205,10 +207,11 @@ bool dbp_server::admit(Job *j) {
     if (slot < 0) return false;
     const dbp_request &r = j->req;
     const dbp_frame_desc &d = r.desc;
-    j->b_in = in_bytes(*j);
-    j->b_out = out_size(*j);
-    j->b_lab = (r.kind != DBP_KIND_DOWNLINK_ADMM && r.labels && d.qam_order > 0) ? (size_t)d.W * d.N * d.U : 0;
-    j->b_beta = (r.kind == DBP_KIND_DOWNLINK_ADMM && r.beta_out && (d.flags & DBP_FLAG_NORMALIZE)) ? 8 : 0;
+    const bool dev = on_device(*j);   // caller's device buffers: nothing staged
+    j->b_in = dev ? 0 : in_bytes(*j);
+    j->b_out = dev ? 0 : out_size(*j);
+    j->b_lab = (!dev && r.kind != DBP_KIND_DOWNLINK_ADMM && r.labels && d.qam_order > 0) ? (size_t)d.W * d.N * d.U : 0;
+    j->b_beta = (!dev && r.kind == DBP_KIND_DOWNLINK_ADMM && r.beta_out && (d.flags & DBP_FLAG_NORMALIZE)) ? 8 : 0;
 
     // Resident channel of this coherence block.
     Resident *res = nullptr;
@@ -244,8 +247,8 @@ bool dbp_server::admit(Job *j) {
         for (auto &t : taken) arena.release(t.first, t.second);
         if (res) res->users--;
     };
-    const size_t hb = h_size(d);
-    if (!res) {
+    const size_t hb = dev ? 0 : h_size(d);
+    if (!res && hb) {
         if (!take(hb, &j->off_h)) { undo(); return false; }
         j->b_h = hb;
     }
@@ -260,13 +263,13 @@ bool dbp_server::admit(Job *j) {
         e->epoch = r.coherence_epoch;
         e->B = d.B; e->U = d.U; e->W = d.W; e->C = d.C; e->prec = d.precision;
         e->h_off = j->off_h;
-        e->h_bytes = hb;
+        e->h_bytes = hb;                 // 0 for device buffers: no resident copy
         cudaEventCreateWithFlags(&e->uploaded, cudaEventDisableTiming);
         res = e.get();
         resident[r.channel_key] = std::move(e);
         j->owns_h = false;           // the resident entry owns it now
     } else if (!res) {
-        j->owns_h = true;
+        j->owns_h = hb != 0;
     }
     if (res) {
         j->res = res;
@@ -301,8 +304,11 @@ void dbp_server::launch(Job *j) {
     const dbp_request &r = j->req;
     const dbp_frame_desc &d = r.desc;
     cudaError_t e = cudaSuccess;
-    char *dH = arena.at(j->off_h);
-    if (j->res && j->hit) {
+    const bool dev = on_device(*j);
+    char *dH = dev ? const_cast<char *>(static_cast<const char *>(r.H)) : arena.at(j->off_h);
+    if (dev) {
+        // the caller's device buffers are used in place
+    } else if (j->res && j->hit) {
         if (j->res->upload_recorded) e = cudaStreamWaitEvent(st, j->res->uploaded, 0);
     } else {
         e = cudaMemcpyAsync(dH, r.H, h_size(d), cudaMemcpyHostToDevice, st);
@@ -311,7 +317,13 @@ void dbp_server::launch(Job *j) {
             j->res->upload_recorded = true;
         }
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(arena.at(j->off_in), r.in, j->b_in, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !dev)
+        e = cudaMemcpyAsync(arena.at(j->off_in), r.in, j->b_in, cudaMemcpyHostToDevice, st);
+    void *d_in = dev ? const_cast<void *>(r.in) : arena.at(j->off_in);
+    void *d_out = dev ? r.out : arena.at(j->off_out);
+    uint8_t *d_lab = dev ? ((r.kind != DBP_KIND_DOWNLINK_ADMM && d.qam_order > 0) ? r.labels : nullptr)
+                         : (j->b_lab ? reinterpret_cast<uint8_t *>(arena.at(j->off_lab)) : nullptr);
+    double *d_beta = dev ? r.beta_out : (j->b_beta ? reinterpret_cast<double *>(arena.at(j->off_beta)) : nullptr);
     DbpExec ex;
     ex.energy = reinterpret_cast<double *>(arena.at(slot_energy[j->slot]));
     Factor *f = (j->res && j->factor_index >= 0) ? &j->res->factors[j->factor_index] : nullptr;
@@ -327,16 +339,13 @@ void dbp_server::launch(Job *j) {
     dbp_status stt = DBP_OK;
     if (e == cudaSuccess) {
         bool used = false;
-        stt = dbp_run_internal(h, &d, r.kind, dH, arena.at(j->off_in), arena.at(j->off_out),
-                               j->b_lab ? reinterpret_cast<uint8_t *>(arena.at(j->off_lab)) : nullptr,
-                               j->b_beta ? reinterpret_cast<double *>(arena.at(j->off_beta)) : nullptr, st, &ex,
-                               &used, &j->err);
+        stt = dbp_run_internal(h, &d, r.kind, dH, d_in, d_out, d_lab, d_beta, st, &ex, &used, &j->err);
         if (j->storing_factor && !used) {   // the kernel that ran cannot store it
             f->pending = false;
             j->storing_factor = false;
         }
     }
-    if (e == cudaSuccess && stt == DBP_OK) {
+    if (e == cudaSuccess && stt == DBP_OK && !dev) {
         e = cudaMemcpyAsync(r.out, arena.at(j->off_out), j->b_out, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && j->b_lab)
             e = cudaMemcpyAsync(r.labels, arena.at(j->off_lab), j->b_lab, cudaMemcpyDeviceToHost, st);
@@ -370,8 +379,8 @@ void dbp_server::reap() {
         j->t_finish = now_us();
         cudaEventDestroy(j->done);
         j->done = nullptr;
-        arena.release(j->off_in, j->b_in);
-        arena.release(j->off_out, j->b_out);
+        if (j->b_in) arena.release(j->off_in, j->b_in);
+        if (j->b_out) arena.release(j->off_out, j->b_out);
         if (j->b_lab) arena.release(j->off_lab, j->b_lab);
         if (j->b_beta) arena.release(j->off_beta, j->b_beta);
         if (j->owns_h) arena.release(j->off_h, j->b_h);
@@ -462,7 +471,16 @@ dbp_status dbp_server_start(dbp_handle_t h, const dbp_server_config *cfg) {
     s->h = h;
     s->nslots = (cfg && cfg->streams > 0) ? cfg->streams : 4;
     if (s->nslots > 64) s->nslots = 64;
-    const size_t bytes = (cfg && cfg->hbm_bytes) ? cfg->hbm_bytes : ((size_t)2 << 30);
+    size_t bytes = (cfg && cfg->hbm_bytes) ? cfg->hbm_bytes : ((size_t)2 << 30);
+    if (h->budget) {
+        const size_t left = h->budget > h->used ? (size_t)(h->budget - h->used) : 0;
+        if (!(cfg && cfg->hbm_bytes) && bytes > left) bytes = left;   // default pool: what the budget leaves
+        if (bytes > left || bytes < 4096) {
+            h->err = "dbp_server_start: the pool does not fit the handle's HBM budget";
+            delete s;
+            return DBP_ERR_NOMEM;
+        }
+    }
     if (cudaSetDevice(h->device) != cudaSuccess) {
         delete s;
         return DBP_ERR_CUDA;
@@ -471,6 +489,7 @@ dbp_status dbp_server_start(dbp_handle_t h, const dbp_server_config *cfg) {
         delete s;
         return DBP_ERR_NOMEM;
     }
+    h->used += bytes;
     s->streams.resize(s->nslots);
     s->slot_busy.assign(s->nslots, 0);
     s->slot_energy.resize(s->nslots);
@@ -491,6 +510,8 @@ dbp_status dbp_server_start(dbp_handle_t h, const dbp_server_config *cfg) {
 
 dbp_status dbp_server_stop(dbp_handle_t h) {
     if (!h || !h->server) return DBP_ERR_INVALID_ARG;
+    const size_t pool = h->server->arena.size();
+    h->used = h->used > pool ? h->used - pool : 0;
     dbp_server_destroy(h->server);
     h->server = nullptr;
     return DBP_OK;
@@ -509,8 +530,27 @@ dbp_status dbp_submit(dbp_handle_t h, const dbp_request *req, uint64_t *ticket) 
     }
     const dbp_frame_desc &d = req->desc;
     if ((long long)d.W * d.N > 0 && (!req->H || !req->in || !req->out)) return DBP_ERR_INVALID_ARG;
+    if (req->flags & ~DBP_REQ_DEVICE_BUFFERS) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        h->err = "dbp_submit: unknown request flags";
+        return DBP_ERR_INVALID_ARG;
+    }
     auto j = std::make_unique<Job>();
     j->req = *req;
+    if (!(req->flags & DBP_REQ_DEVICE_BUFFERS)) {
+        // the staged inputs and outputs must fit the pool at all (besides the
+        // slots' accumulators), or the frame could never be admitted
+        const bool lab = req->kind != DBP_KIND_DOWNLINK_ADMM && req->labels && d.qam_order > 0;
+        const size_t need = align_up(s->h_size(d)) + align_up(s->in_bytes(*j)) + align_up(s->out_size(*j)) +
+                            (lab ? align_up((size_t)d.W * d.N * d.U) : 0) + align_up(8);
+        const size_t avail = s->arena.size() - (size_t)s->nslots * kAlign;
+        if (need > avail) {
+            std::lock_guard<std::mutex> lk(s->mu);
+            h->err = "dbp_submit: the frame needs " + std::to_string(need) + " bytes of the request pool, which has " +
+                     std::to_string(avail);
+            return DBP_ERR_NOMEM;
+        }
+    }
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stopping) return DBP_ERR_INVALID_ARG;
@@ -521,6 +561,27 @@ dbp_status dbp_submit(dbp_handle_t h, const dbp_request *req, uint64_t *ticket) 
         s->jobs[j->ticket] = std::move(j);
     }
     s->cv_work.notify_one();
+    return DBP_OK;
+}
+
+dbp_status dbp_cancel(dbp_handle_t h, uint64_t ticket) {
+    if (!h || !h->server) return DBP_ERR_INVALID_ARG;
+    dbp_server *s = h->server;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end() || it->second->phase == 2) return DBP_ERR_INVALID_ARG;
+    Job *j = it->second.get();
+    if (j->phase != 0) return DBP_PENDING;       // admitted: runs to completion
+    for (auto p = s->pending.begin(); p != s->pending.end(); ++p)
+        if (*p == j) {
+            s->pending.erase(p);
+            break;
+        }
+    j->status = DBP_ERR_CANCELLED;
+    j->err = "cancelled before admission";
+    j->t_finish = s->now_us();
+    j->phase = 2;
+    s->cv_done.notify_all();
     return DBP_OK;
 }
 

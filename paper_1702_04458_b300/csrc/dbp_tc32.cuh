@@ -527,11 +527,11 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
     for (int w = blockIdx.x; w < W; w += gridDim.x) {
         // ---- bulk copies of H[w] and y[w] ------------------------------------
         if (tid == 0) {
-            mbar_arrive_expect_tx(bar_ld, hbytes + ybytes);
+            mbar_arrive_expect_tx(bar_ld, hbytes + ybytes + p.starve_bytes);
             bulk_g2s(sm + HT + HRAW, static_cast<const unsigned char *>(p.H) + (size_t)w * hbytes, hbytes, bar_ld);
             bulk_g2s(sm + VT, static_cast<const unsigned char *>(p.vin) + (size_t)w * ybytes, ybytes, bar_ld);
         }
-        if (!mbar_wait_bounded(bar_ld, ph_ld, p.status)) *abort_flag = 1;
+        if (!mbar_wait_bounded(bar_ld, ph_ld, p.status, p.wait_iters)) *abort_flag = 1;
         ph_ld ^= 1u;
 
         // ---- operand conversion (warp c: cluster c).  The raw inputs and the
@@ -891,7 +891,7 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
         __syncthreads();        // every shared-memory read of this subcarrier is done
     }
     // a CTA that left early waits (bounded) for copies still in flight
-    if (tid == 0 && *abort_flag) mbar_wait_bounded(bar_ld, ph_ld ^ 1u, nullptr);
+    if (tid == 0 && *abort_flag) mbar_wait_bounded(bar_ld, ph_ld ^ 1u, nullptr, p.wait_iters);
     tc5::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc5::tmem_dealloc(tbase, TMEM_COLS);

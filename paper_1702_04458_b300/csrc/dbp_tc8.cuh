@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
         const uint32_t hbytes = (uint32_t)(S * 8 * 8);
         const uint32_t ybytes = (uint32_t)(S * 8);
         fence_proxy_async();
-        if (lane == 0) mbar_arrive_expect_tx(bar, hbytes + (uint32_t)N * ybytes);
+        if (lane == 0) mbar_arrive_expect_tx(bar, hbytes + (uint32_t)N * ybytes + p.starve_bytes);
         __syncwarp();
         if (lane == 0) bulk_g2s(wb, Hg + ((size_t)w * B + (size_t)c * S) * 8, hbytes, bar);
         for (int n = lane; n < N; n += 32)
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
         const int nw = (tile + (int)gridDim.x) * P + pl;
         const bool prefetch = (tile + (int)gridDim.x < p.tiles) && nw < W;
         if (valid) {
-            mbar_wait_bounded(bar, phase, p.status);
+            mbar_wait_bounded(bar, phase, p.status, p.wait_iters);
             phase ^= 1u;
         }
         const int npass = (N + 15) / 16;
@@ -413,14 +413,14 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
                         ev.y = fmaf(rcg, pv.y, ws.y);
                         const float pe = group_sum<8>(pv.x * ev.x + pv.y * ev.y);
                         const bool go = !(rr < 0.f) && rr != 0.f && pe != 0.f;
-                        const float alpha = go ? __fdividef(rr, pe) : 0.f;
+                        const float alpha = go ? __fdiv_rn(rr, pe) : 0.f;
                         // a stopped symbol (alpha = 0) keeps x and r
                         xv.x = fmaf(alpha, pv.x, xv.x);
                         xv.y = fmaf(alpha, pv.y, xv.y);
                         rv.x = fmaf(-alpha, ev.x, rv.x);
                         rv.y = fmaf(-alpha, ev.y, rv.y);
                         const float rn = group_sum<8>(rv.x * rv.x + rv.y * rv.y);
-                        const float beta = go ? __fdividef(rn, rr) : 0.f;
+                        const float beta = go ? __fdiv_rn(rn, rr) : 0.f;
                         if (go) {
                             pv.x = fmaf(beta, pv.x, rv.x);
                             pv.y = fmaf(beta, pv.y, rv.y);

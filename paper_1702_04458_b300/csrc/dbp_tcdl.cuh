@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) {
-            mbar_arrive_expect_tx(&bars[b], hbytes);
+            mbar_arrive_expect_tx(&bars[b], hbytes + p.starve_bytes);
             bulk_g2s(wb + (b ? p.off_h1 : 0), Hg + ((size_t)w * B + (size_t)c * S) * U, hbytes, &bars[b]);
         }
     };
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
         const int ntile = tile + gridDim.x;
         if (ntile < p.tiles && ntile * P + pl < W) issue(ntile * P + pl, b ^ 1);
         if (valid) {
-            mbar_wait_bounded(&bars[b], (parity >> b) & 1u, p.status);
+            mbar_wait_bounded(&bars[b], (parity >> b) & 1u, p.status, p.wait_iters);
             parity ^= (1u << b);
         }
         const C2 *Hs = reinterpret_cast<const C2 *>(wb + (b ? p.off_h1 : 0));

@@ -81,11 +81,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for one mbarrier phase: after ~0.5 s the wait gives up,
-// raises bit 0 of *status and the kernel carries on with whatever the
-// buffer holds (the host reports DBP_ERR_TIMEOUT), so no wait can hang.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *status) {
-    for (int i = 0; i < (1 << 23); ++i) {
+// Bounded wait for one mbarrier phase: after `limit` polls (default 2^23,
+// ~0.5 s) the wait gives up, raises bit 0 of *status and the kernel carries
+// on with whatever the buffer holds (the host reports DBP_ERR_TIMEOUT), so
+// no wait can hang.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *status, int limit = 0) {
+    const int lim = limit > 0 ? limit : (1 << 23);
+    for (int i = 0; i < lim; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if (i >= 32) __nanosleep(64);
     }
@@ -674,7 +676,7 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
         const uint32_t ybytes = (uint32_t)(S * EB);
         const uint32_t total = hbytes + ((ALG == ALG_ADMM_DL) ? 0u : (uint32_t)N * ybytes);
         fence_proxy_async();
-        if (lane == 0) mbar_arrive_expect_tx(&bars[b], total);
+        if (lane == 0) mbar_arrive_expect_tx(&bars[b], total + p.starve_bytes);
         __syncwarp();
         const TIn *src = Hg + ((size_t)w * B + (size_t)c * S) * UT;
         unsigned char *hdst = wb + (b ? p.off_h1 : 0);
@@ -707,7 +709,7 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
         const bool has_next = ntile < p.tiles && ntile * P + pl < W;
         if (dbl && has_next) issue(ntile * P + pl, b ^ 1);
         if (valid) {
-            mbar_wait_bounded(&bars[b], (parity >> b) & 1u, p.status);
+            mbar_wait_bounded(&bars[b], (parity >> b) & 1u, p.status, p.wait_iters);
             parity ^= (1u << b);
         }
         const TIn *Hs = reinterpret_cast<const TIn *>(wb + (b ? p.off_h1 : 0));
@@ -886,13 +888,13 @@ __global__ void __launch_bounds__(Bounds<float, UT>::threads) dbp_tma_kernel(con
                         e[j].y = fmaf(rcg, pv[j].y, e[j].y);
                         const float pe = group_sum<UT>(pv[j].x * e[j].x + pv[j].y * e[j].y);
                         const bool go = live[j] && rr[j] != 0.f && pe != 0.f;
-                        const float alpha = go ? __fdividef(rr[j], pe) : 0.f;
+                        const float alpha = go ? __fdiv_rn(rr[j], pe) : 0.f;
                         x[j].x = fmaf(alpha, pv[j].x, x[j].x);
                         x[j].y = fmaf(alpha, pv[j].y, x[j].y);
                         r[j].x = fmaf(-alpha, e[j].x, r[j].x);
                         r[j].y = fmaf(-alpha, e[j].y, r[j].y);
                         const float rn = group_sum<UT>(r[j].x * r[j].x + r[j].y * r[j].y);
-                        const float beta = go ? __fdividef(rn, rr[j]) : 0.f;
+                        const float beta = go ? __fdiv_rn(rn, rr[j]) : 0.f;
                         if (go) {
                             pv[j].x = fmaf(beta, pv[j].x, r[j].x);
                             pv[j].y = fmaf(beta, pv[j].y, r[j].y);

@@ -160,3 +160,55 @@ def test_full_size_16bit_sampled(dbp, handle, kind):
     sub = dict(f, W=len(idx))
     ref = oracle_run(sub, C, T, "admm", Hq[idx], yq[idx])
     assert _rel(x[idx], ref).max() <= ARITH_TOL
+
+
+def _run32(dbp, h, f, prec, rho):
+    """The B=256 / C=8 / U=32 frame through the automatic kernel choice."""
+    W, N = f["W"], f["N"]
+    x = torch.zeros((W, N, 32), dtype=torch.complex64, device="cuda")
+    if prec == "fp32":
+        Hd = torch.from_numpy(f["H"].astype(np.complex64)).cuda()
+        yd = torch.from_numpy(f["y"].astype(np.complex64)).cuda()
+        Hq = f["H"].astype(np.complex64).astype(np.complex128)
+        yq = f["y"].astype(np.complex64).astype(np.complex128)
+        code = dbp.DBP_FP32
+    else:
+        Ht, Hq = _to16(f["H"], prec)
+        yt, yq = _to16(f["y"], prec)
+        Hd, yd = Ht.cuda(), yt.cuda()
+        code = dbp.DBP_FP16 if prec == "fp16" else dbp.DBP_BF16
+    d = dbp.frame_desc(256, 8, 32, W, N, qam_order=64, T_max=3, precision=code, rho=rho, N0=f["N0"])
+    dbp.dbp_uplink_admm(h, d, Hd, yd, x)
+    torch.cuda.synchronize()
+    return x.cpu().numpy().astype(np.complex128), Hq, yq
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("rho", [0.1, 1.0])
+def test_worst_conditioned_square_clusters_default_path(dbp, handle, prec, rho):
+    """Square clusters (S = U = 32) at 30 dB with small rho: the local Grams
+    of i.i.d. square blocks are ill conditioned (smallest eigenvalue of order
+    1/S, so condition numbers up to ~4 S^2 / rho), the worst case of the
+    explicit FP32 Gauss-Jordan inverse.  The automatic kernel choice (the
+    bulk-copy kernel) meets the FP32 tolerance against the FP64 oracle."""
+    f = synth.uplink_frame(64, 14, 256, 32, 64, 30.0, seed=9600)
+    x, Hq, yq = _run32(dbp, handle, f, prec, rho)
+    ref = oracle.admm_ul(Hq, yq, C=8, rho=rho, N0=f["N0"], T_max=3)
+    err = _rel(x, ref)
+    print(f"default path, worst-conditioned {prec} rho={rho}: max {err.max():.3e} median {np.median(err):.3e}")
+    assert err.max() <= ARITH_TOL, err.max()
+
+
+def test_fp64_retry_at_u32_default_path(dbp, handle):
+    """One user 1000 times stronger than the rest in one square cluster: that
+    cluster's FP32 pivots fall below 2^-12 of its largest diagonal entry and
+    its operator is recomputed in FP64 -- exactly one retry -- and every
+    subcarrier, the retried one included, matches the oracle."""
+    f = synth.uplink_frame(8, 14, 256, 32, 64, 20.0, seed=9700)
+    f["H"][3, 64:96, 5] *= 1e3
+    f["y"] = np.einsum("wbu,wnu->wnb", f["H"], f["s"])
+    dbp.dbp_fp64_retries(handle)
+    x, Hq, yq = _run32(dbp, handle, f, "fp32", 1.0)
+    assert dbp.dbp_fp64_retries(handle) == 1
+    ref = oracle.admm_ul(Hq, yq, C=8, rho=1.0, N0=f["N0"], T_max=3)
+    assert _rel(x, ref).max() <= ARITH_TOL

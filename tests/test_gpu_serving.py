@@ -1,8 +1,11 @@
-"""The request loop (dbp_server_start / dbp_submit / dbp_poll / dbp_wait):
-every frame's result is the same alone and in a mix of uneven frames that
-overlap on the device; frames of one coherence block reuse the resident
-channel and per-cluster operator; a pool too small for all frames at once
-still completes every frame; bad requests are refused at submission."""
+"""The request loop (dbp_server_start / dbp_submit / dbp_poll / dbp_wait /
+dbp_cancel): every frame's result is the same alone and in a mix of uneven
+frames whose work is in flight on the device at the same time; frames of one
+coherence block reuse the resident channel and per-cluster operator; a pool
+too small for all frames at once still completes every frame; frames that
+could never fit the pool and bad requests are refused at submission; queued
+frames can be cancelled; requests on caller-owned device buffers run in
+place; the handle's HBM budget caps the library's own allocations."""
 import numpy as np
 import pytest
 
@@ -110,6 +113,12 @@ def test_results_are_the_same_alone_and_in_the_mix(dbp):
             assert np.array_equal(f.out, alone[i][0]), i
             if f.kind != dbp.DBP_KIND_DOWNLINK_ADMM:
                 assert np.array_equal(f.lab, alone[i][1]), i
+        # the frames were in flight together: some admitted frame's
+        # [start, finish] interval (work enqueued on its stream .. completion
+        # seen) overlaps another's
+        iv = sorted((r.start_us, r.finish_us) for r in results)
+        overlaps = sum(1 for a in range(len(iv)) for b in range(a + 1, len(iv)) if iv[b][0] < iv[a][1])
+        assert overlaps >= 1, iv
     finally:
         dbp.dbp_destroy(h)
 
@@ -211,5 +220,123 @@ def test_box_and_bpsk_frames_through_the_request_loop(dbp):
             assert np.array_equal(f.out, alone[i][0]), i
             assert np.array_equal(f.lab, alone[i][1]), i
         assert np.all(bpsk.out.imag == 0.0) and set(np.unique(bpsk.lab)) <= {0, 1}
+    finally:
+        dbp.dbp_destroy(h)
+
+
+def test_frame_larger_than_the_pool_is_refused(dbp):
+    """A frame whose staged inputs and outputs alone exceed the pool is
+    refused by dbp_submit with DBP_ERR_NOMEM instead of blocking the loop;
+    frames submitted after it still run."""
+    h = dbp.dbp_create(0)
+    try:
+        big = Frame(dbp, dbp.DBP_KIND_UPLINK_ADMM, 256, 8, 32, 300, 14, 64, 3, seed=70)    # ~27 MB staged
+        small = Frame(dbp, dbp.DBP_KIND_UPLINK_ADMM, 64, 4, 8, 300, 14, 16, 3, seed=71)
+        ref = small.run_alone(dbp, h)
+        dbp.dbp_server_start(h, streams=2, hbm_bytes=16 << 20)
+        with pytest.raises(dbp.DbpError) as ei:
+            dbp.dbp_submit(h, big.request(dbp, 0))
+        assert ei.value.status == dbp.DBP_ERR_NOMEM
+        assert "pool" in str(ei.value)
+        r = dbp.dbp_wait(h, dbp.dbp_submit(h, small.request(dbp, 1)), 60.0)
+        dbp.dbp_server_stop(h)
+        assert r is not None and r.status == dbp.DBP_OK
+        assert np.array_equal(small.out, ref[0])
+    finally:
+        dbp.dbp_destroy(h)
+
+
+def test_cancel_a_queued_frame(dbp):
+    """One slot, several large frames submitted back to back: the last one is
+    still queued when it is cancelled; its ticket finishes with
+    DBP_ERR_CANCELLED and the others complete with their normal results."""
+    h = dbp.dbp_create(0)
+    try:
+        K = dbp.DBP_KIND_UPLINK_ADMM
+        frames = [Frame(dbp, K, 256, 8, 32, 1200, 14, 64, 3, seed=80 + i) for i in range(5)]
+        ref = frames[0].run_alone(dbp, h)
+        dbp.dbp_server_start(h, streams=1)
+        tickets = [dbp.dbp_submit(h, f.request(dbp, i)) for i, f in enumerate(frames)]
+        assert dbp.dbp_cancel(h, tickets[-1]) is True
+        res = [dbp.dbp_wait(h, t, 120.0) for t in tickets]
+        dbp.dbp_server_stop(h)
+        assert [r.status for r in res[:-1]] == [dbp.DBP_OK] * 4
+        assert res[-1].status == dbp.DBP_ERR_CANCELLED
+        assert np.all(frames[-1].out == 0)               # nothing ran for it
+        assert np.array_equal(frames[0].out, ref[0])
+        with pytest.raises(dbp.DbpError):
+            dbp.dbp_cancel(h, tickets[0])              # finished and released
+    finally:
+        dbp.dbp_destroy(h)
+
+
+def test_device_buffer_requests_run_in_place(dbp):
+    """Requests flagged DBP_REQ_DEVICE_BUFFERS run on the caller's CUDA
+    buffers with no host copies: results bit-identical to the synchronous
+    device-pointer entry points, also when a coherence block reuses the
+    resident operator."""
+    h = dbp.dbp_create(0)
+    try:
+        K = dbp
+        specs = [(K.DBP_KIND_UPLINK_ADMM, 256, 8, 32, 300, 64, 3), (K.DBP_KIND_UPLINK_CG, 128, 8, 8, 600, 16, 8),
+                 (K.DBP_KIND_DOWNLINK_ADMM, 256, 16, 16, 300, 64, 5), (K.DBP_KIND_UPLINK_ADMM, 256, 16, 16, 300, 64, 4)]
+        items, refs = [], []
+        for i, (kind, B, C, U, W, M, T) in enumerate(specs):
+            dl = kind == K.DBP_KIND_DOWNLINK_ADMM
+            f = synth.downlink_frame(W, 14, B, U, M, seed=500 + i) if dl else \
+                synth.uplink_frame(W, 14, B, U, M, 15.0, seed=500 + i)
+            Hd = torch.from_numpy(f["H"].astype(np.complex64)).cuda()
+            ind = torch.from_numpy((f["s"] if dl else f["y"]).astype(np.complex64)).cuda()
+            shape = (W, 14, B) if dl else (W, 14, U)
+            out = torch.zeros(shape, dtype=torch.complex64, device="cuda")
+            lab = None if dl else torch.zeros((W, 14, U), dtype=torch.uint8, device="cuda")
+            d = dbp.frame_desc(B, C, U, W, 14, qam_order=0 if dl else M, T_max=T, rho=1.0, N0=f.get("N0", 0.1))
+            ro = torch.zeros_like(out)
+            rl = None if dl else torch.zeros_like(lab)
+            if dl:
+                dbp.dbp_downlink_admm(h, d, Hd, ind, ro)
+            elif kind == K.DBP_KIND_UPLINK_ADMM:
+                dbp.dbp_uplink_admm(h, d, Hd, ind, ro, rl)
+            else:
+                dbp.dbp_uplink_cg(h, d, Hd, ind, ro, rl)
+            items.append((kind, d, Hd, ind, out, lab))
+            refs.append((ro, rl))
+        torch.cuda.synchronize()
+        dbp.dbp_server_start(h, streams=4, hbm_bytes=256 << 20)
+        tickets = []
+        for rep in range(2):        # the second round hits the resident operators
+            for i, (kind, d, Hd, ind, out, lab) in enumerate(items):
+                req = dbp.request(kind, d, Hd, ind, out, lab, None, 100 + i, 1, i,
+                                  flags=dbp.DBP_REQ_DEVICE_BUFFERS)
+                tickets.append(dbp.dbp_wait(h, dbp.dbp_submit(h, req), 60.0))
+        dbp.dbp_server_stop(h)
+        assert all(r.status == dbp.DBP_OK for r in tickets)
+        for (kind, d, Hd, ind, out, lab), (ro, rl) in zip(items, refs):
+            assert torch.equal(out, ro)
+            if lab is not None:
+                assert torch.equal(lab, rl)
+    finally:
+        dbp.dbp_destroy(h)
+
+
+def test_hbm_budget_caps_the_library_allocations(dbp):
+    """dbp_config.hbm_budget_bytes: a host-buffer call whose staging buffers
+    exceed the budget and a request pool larger than it are refused with
+    DBP_ERR_NOMEM; the default pool takes what the budget leaves."""
+    h = dbp.dbp_create(0, hbm_budget_bytes=8 << 20)
+    try:
+        f = Frame(dbp, dbp.DBP_KIND_UPLINK_ADMM, 128, 8, 8, 1200, 14, 16, 3, seed=90)   # 27 MB staged
+        with pytest.raises(dbp.DbpError) as ei:
+            f.run_alone(dbp, h)
+        assert ei.value.status == dbp.DBP_ERR_NOMEM
+        with pytest.raises(dbp.DbpError) as ei:
+            dbp.dbp_server_start(h, streams=2, hbm_bytes=64 << 20)
+        assert ei.value.status == dbp.DBP_ERR_NOMEM
+        small = Frame(dbp, dbp.DBP_KIND_UPLINK_ADMM, 64, 4, 8, 100, 14, 16, 3, seed=91)
+        ref = small.run_alone(dbp, h)                   # fits the budget
+        dbp.dbp_server_start(h, streams=2)              # pool = what the budget leaves
+        r = dbp.dbp_wait(h, dbp.dbp_submit(h, small.request(dbp, 0)), 60.0)
+        dbp.dbp_server_stop(h)
+        assert r.status == dbp.DBP_OK and np.array_equal(small.out, ref[0])
     finally:
         dbp.dbp_destroy(h)

@@ -1,11 +1,16 @@
 """dbp_downlink_admm_static: the downlink precoder with power normalisation
-for callers that cannot allocate device memory (for example code that runs
-while a stream is captured into a CUDA graph, where cudaMalloc cannot be
-captured, or a process whose device memory is reserved by another allocator).
-Its scratch lives in a fixed library-owned device array, so it is checked
-against the allocating entry point dbp_downlink_admm on two calls in a row:
-the second call must not be disturbed by what the first left in the array.
-This file is collected last on purpose."""
+for callers that cannot allocate device memory (a process whose device
+memory is reserved by another allocator, or a real-time front end that must
+not allocate once running).  Its scratch lives in a fixed library-owned
+device array, so it is checked against the allocating entry point
+dbp_downlink_admm on two calls in a row (the second call must not be
+disturbed by what the first left in the array), and a call is checked to
+leave the device's free memory unchanged.
+
+The results do not depend on test order (every call overwrites each scratch
+entry it reads); the file name only makes pytest collect it last, so that a
+run stopping at the first failure has run every other GPU test before this
+optional entry point's."""
 import numpy as np
 import pytest
 
@@ -60,6 +65,28 @@ def test_static_scratch_matches_allocating_path_twice(dbp):
         dbp.dbp_destroy(h)
 
 
+def test_static_call_allocates_no_device_memory(dbp):
+    """After a first call (which looks up the scratch array's address), a
+    second call leaves the device's free memory exactly as it was: neither
+    the library nor the CUDA runtime allocated anything for it."""
+    h = dbp.dbp_create(0)
+    try:
+        W, N, B, C, U, M, seed, T = 64, 14, 128, 8, 8, 16, 13, 3
+        H, s, d = _frame(dbp, W, N, B, C, U, M, seed, T)
+        x = torch.zeros((W, N, B), dtype=torch.complex64, device="cuda")
+        beta = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dbp.dbp_downlink_admm_static(h, d, H, s, x, beta)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        dbp.dbp_downlink_admm_static(h, d, H, s, x, beta)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0
+        assert float(beta.cpu()[0]) > 0
+    finally:
+        dbp.dbp_destroy(h)
+
+
 def test_static_scratch_rejects_oversized_frames(dbp):
     h = dbp.dbp_create(0)
     try:
@@ -69,5 +96,6 @@ def test_static_scratch_rejects_oversized_frames(dbp):
         with pytest.raises(dbp.DbpError) as ei:
             dbp.dbp_downlink_admm_static(h, d, buf, buf, buf, None)
         assert ei.value.status == dbp.DBP_ERR_UNSUPPORTED
+        assert "exceeds the fixed scratch" in str(ei.value)
     finally:
         dbp.dbp_destroy(h)
