@@ -28,6 +28,7 @@ frames (subcarrier-parallel weak scaling, no data-path collective).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import importlib.util
 import json
@@ -104,6 +105,9 @@ def parse_args(argv=None):
     ap.add_argument("--details", default=None, help="JSON file for the detailed results")
     ap.add_argument("--kernel", choices=["auto", "tc5", "tma", "generic", "mma", "bcast"], default="auto",
                     help="force one kernel path (default: automatic choice, autotuned)")
+    ap.add_argument("--head-subcarriers", type=int, default=None,
+                    help="subcarriers of the headline frame (default 3300); smaller frames keep ncu captures short, "
+                         "and a line measured on one names its size in config.workload")
     return ap.parse_args(argv)
 
 
@@ -342,20 +346,6 @@ KERNEL_NAMES = {
     "mma": "dbp_tc8_kernel / dbp_tcdl_kernel (mma.sync)", "bcast": "dbp_admm_kernel / dbp_cg_kernel",
     "generic": "dbp_fused_kernel", "auto": "automatic choice"}
 PATH_NAMES = {0: "auto", 1: "generic", 2: "tma", 3: "mma", 4: "bcast", 5: "tc5"}
-
-
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-    if not os.path.exists(path):
-        return None
-    src = kernel_source_hash()
-    for line in open(path):
-        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
-        if f.get("kernel") == kernel and f.get("src") == src:
-            return float(f["bytes_per_launch"])
-    return None
 
 
 def roofline(key: str, alg: str, wl: Workload, avg_ms: float, peaks: dict, alu_peak: float, tensor_div: float,
@@ -1262,7 +1252,11 @@ def study_downlink(dbp, h, device, launching, K):
 # ---------------------------------------------------------------------------
 
 def main(argv=None) -> int:
+    global HEAD, MIX
     args = parse_args(argv)
+    if args.head_subcarriers:
+        HEAD = dataclasses.replace(HEAD, W=args.head_subcarriers)
+        MIX = HEAD
     if args.impl == "reference":
         return run_reference(args)
 
@@ -1409,7 +1403,8 @@ def main(argv=None) -> int:
             "config": {"workload": workload_name(HEAD, f"uplink ADMM T={HEAD.T} at {HEAD_SNR_DB:g} dB, one detection "
                                                        "per frame"),
                        "bits_per_step": bits, "kernel": tuned.get("fp32", args.kernel),
-                       "l2": "inputs larger than L2: 2 distinct frames resident twice, 4 x 323 MB",
+                       "l2": "inputs larger than L2: 2 distinct frames resident twice, "
+                              f"4 x {algorithmic_bytes('admm_ul', HEAD) * HEAD.W / 1e6:.0f} MB",
                        "streams": "consecutive frames alternate over 2 streams",
                        "parallelism": f"subcarrier-parallel, {world} independent rank(s)"},
             "roofline": {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel",
