@@ -208,11 +208,15 @@ cudaError_t launch_admm_one(const FusedParams &p, const Shape &s, cudaStream_t s
     return launch_pdl(kern, (unsigned)s.grid, (unsigned)s.nwarps * 32, s.smem, st, p);
 }
 
-inline int tcdl_occupancy(int threads, size_t smem) {
+// (a template so that only the unit that calls it compiles the kernel)
+template <int = 0>
+int tcdl_occupancy(int threads, size_t smem) {
     return dbp_occupancy_cached(reinterpret_cast<const void *>(dbp::dbp_tcdl_kernel<16>), threads, smem);
 }
 
-inline cudaError_t launch_tcdl(const FusedParams &p, const Shape &s, cudaStream_t st) {
+// (a template so that only the unit that calls it compiles the kernel)
+template <int = 0>
+cudaError_t launch_tcdl(const FusedParams &p, const Shape &s, cudaStream_t st) {
     cudaError_t e = dbp_prepare_kernel(reinterpret_cast<const void *>(dbp::dbp_tcdl_kernel<16>), s.smem);
     if (e != cudaSuccess) return e;
     return launch_pdl(dbp::dbp_tcdl_kernel<16>, (unsigned)s.grid, (unsigned)s.nwarps * 32, s.smem, st, p);
@@ -233,7 +237,9 @@ cudaError_t launch_tc32_n(const FusedParams &p, const Shape &s, cudaStream_t st)
     return p.N == 14 ? launch_tc32_one<TIn, 14>(p, s, st) : launch_tc32_one<TIn, 16>(p, s, st);
 }
 
-inline cudaError_t launch_tc32(int prec, const FusedParams &p, const Shape &s, cudaStream_t st) {
+// (a template so that only the unit that calls it compiles the kernel)
+template <int = 0>
+cudaError_t launch_tc32(int prec, const FusedParams &p, const Shape &s, cudaStream_t st) {
     switch (prec) {
     case DBP_FP32: return launch_tc32_n<float2>(p, s, st);
     case DBP_FP16: return launch_tc32_n<__half2>(p, s, st);

@@ -64,10 +64,11 @@ constexpr int VT_PAIR = 8192;
 constexpr int VT_LO = 4096;
 constexpr int SCR = 98304;         // per-warp Gauss-Jordan pivot buffers (FP64 rows on retry)
 constexpr int SCR_WARP = 1024;
-constexpr int SLOTS = SCR + 8 * SCR_WARP;   // scale exponents and warp maxima
-constexpr int PARAMS = SLOTS + 160;        // OpParams of the operator phase (64 B)
-constexpr int BARS = SLOTS + 256;
-constexpr int SMEM = BARS + 64;
+constexpr int SLOTS = SCR + 8 * SCR_WARP;   // scale exponents (40 ints) and warp maxima (8 floats)
+constexpr int MSLOT = SLOTS + 160;
+constexpr int BARS = SLOTS + 256;          // copy and CTA-MMA mbarriers, TMEM slot, abort flag; per-warp mbarriers
+constexpr int BAR_OP = BARS + 64;
+constexpr int SMEM = BARS + 128;
 constexpr int TMEM_COLS = 256;
 constexpr int PART_LD = 20;        // floats per consensus partial row (16 used, padded against bank conflicts)
 
@@ -115,19 +116,26 @@ __device__ __forceinline__ uint32_t pack2(uint32_t a, uint32_t b) { return a | (
 
 // D (+)= A B^T over K = 32 (two K steps of 16): A tile of 128 rows at a_hi /
 // a_lo, B tile at b_hi / b_lo (shared-memory byte addresses); three products
-// with the split, one (hi only) without.
+// with the split, one (hi only) without.  The small terms (lo hi, hi lo) are
+// accumulated first and hi hi last: the tensor core's FP32 accumulation
+// loses bits of terms added to a larger running sum (measured on sm_103a:
+// up to 5.8 units of 2^-24 sum|ab| with hi hi first, 1.8 with it last; an
+// FP32 FMA chain over the same 16 terms: 2.9).
 __device__ __forceinline__ void mma_k32(uint32_t d, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo,
                                         uint32_t id, bool split) {
+    if (split) {
 #pragma unroll
-    for (int ks = 0; ks < 2; ++ks) {
-        const uint32_t o = ks * 256;
-        const uint64_t ah = tc5::sdesc(a_hi + o, 128, 512), bh = tc5::sdesc(b_hi + o, 128, 512);
-        tc5::mma_f16(d, ah, bh, id, ks > 0 ? 1u : 0u);
-        if (split) {
-            tc5::mma_f16(d, ah, tc5::sdesc(b_lo + o, 128, 512), id, 1u);
-            tc5::mma_f16(d, tc5::sdesc(a_lo + o, 128, 512), bh, id, 1u);
-        }
+        for (int ks = 0; ks < 2; ++ks)
+            tc5::mma_f16(d, tc5::sdesc(a_lo + ks * 256, 128, 512), tc5::sdesc(b_hi + ks * 256, 128, 512), id,
+                         ks > 0 ? 1u : 0u);
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks)
+            tc5::mma_f16(d, tc5::sdesc(a_hi + ks * 256, 128, 512), tc5::sdesc(b_lo + ks * 256, 128, 512), id, 1u);
     }
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks)
+        tc5::mma_f16(d, tc5::sdesc(a_hi + ks * 256, 128, 512), tc5::sdesc(b_hi + ks * 256, 128, 512), id,
+                     (split || ks > 0) ? 1u : 0u);
 }
 
 __device__ __forceinline__ float warp_max(float v) {
@@ -144,74 +152,85 @@ __device__ __forceinline__ void ld32(uint32_t taddr, float (&a)[32]) {
 
 }  // namespace tc32
 
-// In-register Gauss-Jordan inversion of a 32 x 32 Hermitian positive
-// definite matrix held by one warp as 4 x 8 blocks: lane l = 4 rg + cg owns
-// rows 4 rg .. 4 rg + 3 and columns 8 cg .. 8 cg + 7 (A[r][c]).
-// Step k: the lanes holding column k publish it (colbuf), the lanes holding
+// In-register Gauss-Jordan elimination of an NR x NC matrix [A | R], NR =
+// 8 RB, NC = 4 CB, with A (the first NR columns) Hermitian positive
+// definite, held by one warp as RB x CB blocks: lane l = 4 rg + cg owns rows
+// RB rg .. RB rg + RB - 1 and columns CB cg .. CB cg + CB - 1 (M[r][c]).  It
+// leaves [A^{-1} | A^{-1} R] in place (just A^{-1} when NC = NR).  Step k
+// (k < NR): the lanes holding column k publish it (colbuf), the lanes holding
 // row k publish it (rowbuf), every lane updates its block with the rank-1
-// term f_i a_kj, f_i = a_ik / a_kk, and the owners of column k write the new
+// term f_i m_kj, f_i = m_ik / m_kk, and the owners of column k write the new
 // column (-f_i; 1 on the pivot row, whose row stays multiplied by its pivot
-// until the final scaling).  Buffers alternate between steps, so one warp
-// barrier per step orders writes and reads.  The step loop is unrolled by 8
-// so every register index is static.  Returns the smallest pivot (real part).
-__device__ __forceinline__ float gj2d_invert(float2 (&A)[4][8], float2 *buf, int lane) {
+// until the final scaling).  Buffers alternate between steps (2 (NR + NC)
+// float2), so one warp barrier per step orders writes and reads.  The step
+// loop is unrolled by CB so every register index is static.  Returns the
+// smallest pivot (real part).
+template <int RB, int CB>
+__device__ __forceinline__ float gj_blk_invert(float2 (&A)[RB][CB], float2 *buf, int lane) {
+    constexpr int NN = 8 * RB, NC = 4 * CB;
+    static_assert(NC >= NN && NN % CB == 0 && CB % RB == 0 && RB % 2 == 0, "8 x 4 lane grid of RB x CB blocks");
     const int rg = lane >> 2, cg = lane & 3;
     float min_piv = 3.0e38f;
-    float2 myinv[4];
+    float2 myinv[RB];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) myinv[r] = make_float2(1.f, 0.f);
+    for (int r = 0; r < RB; ++r) myinv[r] = make_float2(1.f, 0.f);
 #pragma unroll 1
-    for (int k0 = 0; k0 < 32; k0 += 8) {
+    for (int k0 = 0; k0 < NN; k0 += CB) {
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
+        for (int kk = 0; kk < CB; ++kk) {
             const int k = k0 + kk;
-            float2 *colbuf = buf + (kk & 1) * 64, *rowbuf = colbuf + 32;
-            const bool ownc = (cg == (k >> 3)), ownr = (rg == (k >> 2));
+            const int rr = kk % RB;                 // pivot row inside its block
+            float2 *colbuf = buf + (kk & 1) * (NN + NC), *rowbuf = colbuf + NN;
+            const bool ownc = (cg == k0 / CB), ownr = (rg == k / RB);
             if (ownc) {
-                *reinterpret_cast<float4 *>(&colbuf[4 * rg]) = make_float4(A[0][kk].x, A[0][kk].y, A[1][kk].x, A[1][kk].y);
-                *reinterpret_cast<float4 *>(&colbuf[4 * rg + 2]) = make_float4(A[2][kk].x, A[2][kk].y, A[3][kk].x, A[3][kk].y);
+#pragma unroll
+                for (int r = 0; r < RB; r += 2)
+                    *reinterpret_cast<float4 *>(&colbuf[RB * rg + r]) =
+                        make_float4(A[r][kk].x, A[r][kk].y, A[r + 1][kk].x, A[r + 1][kk].y);
             }
             if (ownr) {
 #pragma unroll
-                for (int c = 0; c < 8; c += 2)
-                    *reinterpret_cast<float4 *>(&rowbuf[8 * cg + c]) =
-                        make_float4(A[kk & 3][c].x, A[kk & 3][c].y, A[kk & 3][c + 1].x, A[kk & 3][c + 1].y);
+                for (int c = 0; c < CB; c += 2)
+                    *reinterpret_cast<float4 *>(&rowbuf[CB * cg + c]) =
+                        make_float4(A[rr][c].x, A[rr][c].y, A[rr][c + 1].x, A[rr][c + 1].y);
             }
             __syncwarp();
             const float2 pk = colbuf[k];
             min_piv = fminf(min_piv, pk.x);
             const float d = __frcp_rn(fmaf(pk.x, pk.x, pk.y * pk.y));
             const float2 inv = make_float2(pk.x * d, -pk.y * d);
-            float2 f[4], p[8];
-            {
-                float2 a, b;
-                ld2(&colbuf[4 * rg], a, b);
-                f[0] = a; f[1] = b;
-                ld2(&colbuf[4 * rg + 2], a, b);
-                f[2] = a; f[3] = b;
+            float2 f[RB], pr[CB];
 #pragma unroll
-                for (int c = 0; c < 8; c += 2) {
-                    ld2(&rowbuf[8 * cg + c], a, b);
-                    p[c] = a; p[c + 1] = b;
-                }
+            for (int r = 0; r < RB; r += 2) {
+                float2 a, b;
+                ld2(&colbuf[RB * rg + r], a, b);
+                f[r] = a;
+                f[r + 1] = b;
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const bool piv = ownr && (r == (kk & 3));
+            for (int c = 0; c < CB; c += 2) {
+                float2 a, b;
+                ld2(&rowbuf[CB * cg + c], a, b);
+                pr[c] = a;
+                pr[c + 1] = b;
+            }
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const bool piv = ownr && (r == rr);
                 const float2 a = f[r];
                 f[r] = piv ? make_float2(0.f, 0.f) : make_float2(a.x * inv.x - a.y * inv.y, a.x * inv.y + a.y * inv.x);
                 if (piv) myinv[r] = inv;
             }
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
+            for (int r = 0; r < RB; ++r) {
                 const float2 nf = make_float2(-f[r].x, -f[r].y);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) cmac(A[r][c], nf, p[c]);
+                for (int c = 0; c < CB; ++c) cmac(A[r][c], nf, pr[c]);
             }
             if (ownc) {
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const bool piv = ownr && (r == (kk & 3));
+                for (int r = 0; r < RB; ++r) {
+                    const bool piv = ownr && (r == rr);
                     A[r][kk] = piv ? make_float2(1.f, 0.f) : make_float2(-f[r].x, -f[r].y);
                 }
             }
@@ -219,9 +238,9 @@ __device__ __forceinline__ float gj2d_invert(float2 (&A)[4][8], float2 *buf, int
         }
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < RB; ++r)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < CB; ++c) {
             const float2 a = A[r][c];
             A[r][c] = make_float2(a.x * myinv[r].x - a.y * myinv[r].y, a.x * myinv[r].y + a.y * myinv[r].x);
         }
@@ -261,42 +280,6 @@ __device__ __forceinline__ void tc32_put_operator(const float2 (&R)[32], unsigne
     }
 }
 
-// Write B_c^{-1} held as 4 x 8 blocks (lane 4 rg + cg: rows 4 rg .. + 3,
-// columns 8 cg .. + 7) as the cluster's operator tile (hi / lo, scaled by
-// 2^e with e from the warp's largest magnitude, stored at *eslot): the
-// lane's 8 columns are one 16-byte K chunk of each of its tile rows.
-__device__ __forceinline__ void tc32_put_operator_2d(const float2 (&A)[4][8], unsigned char *th, int clw, int *eslot,
-                                                     int lane) {
-    using namespace tc32;
-    const int rg = lane >> 2, cg = lane & 3;
-    float mb = 0.f;
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) mb = fmaxf(mb, fmaxf(fabsf(A[r][c].x), fabsf(A[r][c].y)));
-    const int eb = scale_exp(warp_max(mb));
-    if (lane == 0) *eslot = eb;
-    const float sb = exp2i(eb);
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int pc = 0; pc < 2; ++pc) {
-            uint32_t hw[4], lw[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const float2 a = A[r][2 * t], b = A[r][2 * t + 1];
-                uint32_t ha, la, hb, lb;
-                split16((pc ? a.y : a.x) * sb, ha, la);
-                split16((pc ? b.y : b.x) * sb, hb, lb);
-                hw[t] = pack2(ha, hb);
-                lw[t] = pack2(la, lb);
-            }
-            const int o = off16(64 * clw + arow(pc, 4 * rg + r), 8 * cg);
-            *reinterpret_cast<uint4 *>(th + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            *reinterpret_cast<uint4 *>(th + HT_LO + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-        }
-}
-
 // FP64 recomputation of one cluster's operator (whole warp): the Gram
 // H_c^H H_c + delta I from the cluster block in global memory (row u per
 // lane), its Gauss-Jordan inverse in FP64, rounded to FP32 and written as
@@ -328,67 +311,378 @@ __device__ __noinline__ void tc32_fp64_operator(const TIn *Hg, double delta, dou
     tc32_put_operator(R, th, clw, eslot, lane);
 }
 
-// What the operator phase needs besides shared memory, kept in shared
-// memory by the kernel so that the phase is called without arguments.
-struct OpParams {
-    const void *H;              // inputs in global memory (FP64 retry)
-    unsigned int *retries;      // FP64 retry counter
-    double delta;               // diagonal loading rho
-    long long row0;             // first H row of the subcarrier (w B)
-    int C;
-};
+namespace tc32 {
 
-// The operator phase of one subcarrier (whole CTA): warp c < C loads its
-// cluster's Gram as 4 x 8 blocks (from the XOR-swizzled planes Gr, Gi of the
-// Gram readout), waits until every warp has, inverts it by Gauss-Jordan
-// elimination with the pivot check, recomputes it in FP64 if a pivot was too
-// small, and writes B_c^{-1} as the cluster's operator tile.
-template <typename TIn>
-__device__ __forceinline__ void tc32_operator_phase() {
+// ---- blocked inverse (operator phase) ------------------------------------
+// Cluster c's own 8 KB while its inverse is formed: chunk 0 and chunk 1 are
+// the hi and lo halves of its final operator tile (rows 64 (c & 1) .. + 63 of
+// pair c / 2), so no other warp touches them.  The Gram readout leaves
+// there the FP32 planes of A11, A12 and A22 and the A12 column tile; the
+// operator phase reuses the A11 and A12 planes for K = 16 operand tiles and
+// the planes of P = A11^{-1}.
+__device__ __forceinline__ int chunk0(int c) { return HT + (c >> 1) * HT_PAIR + (c & 1) * 4096; }
+__device__ __forceinline__ int chunk1(int c) { return chunk0(c) + HT_LO; }
+constexpr int SLOT0 = 0, SLOT1 = 2048, SLOT_LO = 1024;     // chunk 0: A11 planes, then a tile | A12 column tile
+constexpr int PL_A11 = 0;                                   // chunk 0
+constexpr int PL_A22 = 0, PL_A12 = 2048, PL_IM = 1024;      // chunk 1: A22 (then S) | A12 (then P)
+
+// Element (i, j) of a 16 x 16 FP32 plane (floats): 16-byte chunks XOR-
+// swizzled by row, so a lane per row (4 x 16 B) and a 2 x 4 block per lane
+// both read without bank conflicts beyond the minimum.
+__device__ __forceinline__ int pl16(int i, int j) { return i * 16 + 4 * ((j >> 2) ^ (i & 3)) + (j & 3); }
+
+// Byte offset of 16-bit element (row, k) of a K = 16 operand tile: 32-byte
+// rows as two 16-byte core matrices 128 B apart (LBO), 8-row groups 256 B
+// apart (SBO).  A 32-row tile is 1 KB.
+__device__ __forceinline__ int offk16(int row, int k) {
+    return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+// Complex product from a real one: D[(p, i), (p', j)] = sum_k comp_p(A'_ik)
+// comp_p'(B'_jk) in lane 16 p + i, column 16 p' + j.  Lane (p, i) returns
+// component p of row i of A B (PLAIN: Re = D00 - D11, Im = D01 + D10),
+// of A^H B with A' = A^T (CONJ_A: Re = D00 + D11, Im = D01 - D10) or of
+// A B^H with B' = B (CONJ_B: Re = D00 + D11, Im = D10 - D01), scaled by us.
+enum { PLAIN = 0, CONJ_A = 1, CONJ_B = 2 };
+template <int MODE>
+__device__ __forceinline__ void cprod_read(uint32_t taddr, float us, int pp, float (&out)[16]) {
+    float a[32];
+    tc5::ld_x32(taddr, a);
+    tc5::ld_wait();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const float own = a[j], recv = __shfl_xor_sync(0xffffffffu, a[16 + j], 16);
+        float v;
+        if (MODE == PLAIN) v = pp ? own + recv : own - recv;
+        else if (MODE == CONJ_A) v = pp ? recv - own : own + recv;
+        else v = pp ? own - recv : own + recv;
+        out[j] = v * us;
+    }
+}
+
+// One warp's product D = A B^T over K = 16 from hi / lo tiles: three MMAs
+// (lo hi, hi lo, hi hi) into the warp's 32 tensor-memory columns, completion
+// on the warp's mbarrier.  `a_win` is the start of a 128-row window whose
+// rows 32 m .. 32 m + 31 are the warp's A tile (m = its lane quadrant); the
+// other rows are other clusters' bytes, and their products land in lanes no
+// other warp reads at these columns.
+__device__ __forceinline__ void issue_prod(uint32_t d, uint32_t a_win, uint32_t b_tile, uint64_t *bar) {
+    constexpr uint32_t id = tc5::idesc(tc5::FMT_F16, 128, 32);
+    tc5::fence_after_sync();
+    const uint64_t ah = tc5::sdesc(a_win, 128, 256), al = tc5::sdesc(a_win + SLOT_LO, 128, 256);
+    const uint64_t bh = tc5::sdesc(b_tile, 128, 256), bl = tc5::sdesc(b_tile + SLOT_LO, 128, 256);
+    tc5::mma_f16(d, al, bh, id, 0u);       // small terms first (see mma_k32)
+    tc5::mma_f16(d, ah, bl, id, 1u);
+    tc5::mma_f16(d, ah, bh, id, 1u);
+    tc5::commit(bar);
+}
+
+// hi / lo words of x (already scaled) as one 16-bit store each.
+__device__ __forceinline__ void st_split(unsigned char *hi_tile, int off, float x) {
+    uint32_t h, l;
+    split16(x, h, l);
+    *reinterpret_cast<uint16_t *>(hi_tile + off) = (uint16_t)h;
+    *reinterpret_cast<uint16_t *>(hi_tile + SLOT_LO + off) = (uint16_t)l;
+}
+// A tile row from 16 values (K = 0..15): two 16-byte chunks per half.
+__device__ __forceinline__ void st_row16(unsigned char *hi_tile, int row, const float (&v)[16], float sc) {
+#pragma unroll
+    for (int k8 = 0; k8 < 2; ++k8) {
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            uint32_t ha, la, hb, lb;
+            split16(v[8 * k8 + 2 * t] * sc, ha, la);
+            split16(v[8 * k8 + 2 * t + 1] * sc, hb, lb);
+            hw[t] = pack2(ha, hb);
+            lw[t] = pack2(la, lb);
+        }
+        const int o = offk16(row, 8 * k8);
+        *reinterpret_cast<uint4 *>(hi_tile + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(hi_tile + SLOT_LO + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+}
+__device__ __forceinline__ float absmax16(const float (&v)[16]) {
+    float m = 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) m = fmaxf(m, fabsf(v[j]));
+    return m;
+}
+__device__ __forceinline__ float absmax_blk8(const float2 (&M)[2][8]) {
+    float m = 0.f;
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) m = fmaxf(m, fmaxf(fabsf(M[r][c].x), fabsf(M[r][c].y)));
+    return m;
+}
+// Rows 2 rg, 2 rg + 1, columns j0 .. j0 + 7 of a 16 x 16 complex matrix from
+// its planes (re; im 256 floats further), as 2 x 8 block columns, and back.
+__device__ __forceinline__ void ld_blk8(const float *re, float2 (&M)[2][8], int rg, int j0) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int i = 2 * rg + r;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const float4 x = *reinterpret_cast<const float4 *>(re + pl16(i, j0 + 4 * t));
+            const float4 y = *reinterpret_cast<const float4 *>(re + 256 + pl16(i, j0 + 4 * t));
+            M[r][4 * t + 0] = make_float2(x.x, y.x);
+            M[r][4 * t + 1] = make_float2(x.y, y.y);
+            M[r][4 * t + 2] = make_float2(x.z, y.z);
+            M[r][4 * t + 3] = make_float2(x.w, y.w);
+        }
+    }
+}
+__device__ __forceinline__ void st_blk8(float *re, const float2 (&M)[2][8], int rg, int j0) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int i = 2 * rg + r;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            *reinterpret_cast<float4 *>(re + pl16(i, j0 + 4 * t)) =
+                make_float4(M[r][4 * t].x, M[r][4 * t + 1].x, M[r][4 * t + 2].x, M[r][4 * t + 3].x);
+            *reinterpret_cast<float4 *>(re + 256 + pl16(i, j0 + 4 * t)) =
+                make_float4(M[r][4 * t].y, M[r][4 * t + 1].y, M[r][4 * t + 2].y, M[r][4 * t + 3].y);
+        }
+    }
+}
+// Rows 2 rg, 2 rg + 1 of a 2 x 8 block as the hi / lo chunk (K = k0 .. k0 + 7)
+// of tile rows (p, row0 + 2 rg + r), scaled by sc.
+__device__ __forceinline__ void st_chunk8(unsigned char *hi_tile, const float2 (&M)[2][8], int rg, int row0, int k0,
+                                          float sc) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int pc = 0; pc < 2; ++pc) {
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                uint32_t ha, la, hb, lb;
+                split16((pc ? M[r][2 * t].y : M[r][2 * t].x) * sc, ha, la);
+                split16((pc ? M[r][2 * t + 1].y : M[r][2 * t + 1].x) * sc, hb, lb);
+                hw[t] = pack2(ha, hb);
+                lw[t] = pack2(la, lb);
+            }
+            const int o = offk16(16 * pc + row0 + 2 * rg + r, k0);
+            *reinterpret_cast<uint4 *>(hi_tile + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4 *>(hi_tile + SLOT_LO + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+}
+// Component p of row i of a 16 x 16 plane pair (16 floats).
+__device__ __forceinline__ void ld_row(const float *re, int pp, int i, float (&v)[16]) {
+    const float *pl = re + 256 * pp;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const float4 x = *reinterpret_cast<const float4 *>(pl + pl16(i, 4 * t));
+        v[4 * t] = x.x;
+        v[4 * t + 1] = x.y;
+        v[4 * t + 2] = x.z;
+        v[4 * t + 3] = x.w;
+    }
+}
+
+}  // namespace tc32
+
+// B_c^{-1} of one cluster (whole warp) by the 2 x 2 block inverse with 16 x 16
+// blocks of A = G_c + delta I (A21 = A12^H), as two eliminations and two
+// tensor-core products:
+//   [P | X]   = A11^{-1} [I | A12]      Gauss-Jordan on [A11 | A12]
+//   S         = A22 - A12^H X           tensor cores
+//   [Q | Y^H] = S^{-1} [I | X^H]        Gauss-Jordan on [S | X^H]
+//   Z         = Y X^H                   tensor cores
+//   A^{-1}    = [P + Z, -Y; -Y^H, Q].
+// X and Y come from eliminations, not from products with the explicit
+// inverses P and Q: a product with an explicit inverse of an ill-conditioned
+// block leaves a residual A^{-1} A - I that grows with that block's
+// condition number, while these eliminations keep it at the level of the
+// 32 x 32 one (the operator is applied to vectors close to G_c s, so the
+// residual is what reaches the estimate).  The pivots of the two
+// eliminations are those of the 32 x 32 one, so the same pivot check
+// applies.  The products run on the tensor cores, issued by the warp itself
+// (FP16 hi / lo operands scaled by powers of two, FP32 accumulators), so the
+// warp never waits for another.  Expects the Gram readout's planes and A12
+// column tile (scale exponent e12) in the cluster's chunks.  Writes the
+// operator tile (scale at *eslot_b) unless a pivot fails the check (returns
+// false, writes nothing) or a wait gives up (timed_out).
+__device__ __forceinline__ bool tc32_blocked_operator(int c, int e12, uint32_t sbase, uint32_t tbase,
+                                                      uint64_t *bar, uint32_t &ph, const FusedParams &p,
+                                                      int *eslot_b, bool &timed_out) {
     using namespace tc32;
     extern __shared__ __align__(1024) unsigned char sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rg = lane >> 2, cg = lane & 3;
-    const OpParams &op = *reinterpret_cast<const OpParams *>(sm + PARAMS);
-    int *eslot = reinterpret_cast<int *>(sm + SLOTS);
-    const int C = op.C;
-    float2 A[4][8];
-    if (warp < C) {
-        const float *gr = reinterpret_cast<const float *>(sm + HT + (warp >> 1) * HT_PAIR + (warp & 1) * 8192);
-        const float *gi = gr + 1024;
+    const int rg = lane >> 2, cg = lane & 3, pp = lane >> 4, ii = lane & 15;
+    const bool right = cg >= 2;                 // the lane holds columns 16.. of [A | R]
+    const int j8 = 8 * (cg & 1);                // ... starting at column j8 of its 16 x 16 block
+    const int m = warp & 3;
+    unsigned char *c0 = sm + chunk0(c), *c1 = sm + chunk1(c);
+    float *pA11 = reinterpret_cast<float *>(c0 + PL_A11), *pA22 = reinterpret_cast<float *>(c1 + PL_A22);
+    float *pA12 = reinterpret_cast<float *>(c1 + PL_A12);      // later the planes of P
+    float *pYH = reinterpret_cast<float *>(c0 + SLOT1);         // planes of Y^H (after the A12 tile)
+    unsigned char *slot0 = c0 + SLOT0, *slot1 = c0 + SLOT1;
+    const uint32_t s0 = sbase + (uint32_t)chunk0(c) + SLOT0, s1 = sbase + (uint32_t)chunk0(c) + SLOT1;
+    const uint32_t dcol = tbase + 32u * (uint32_t)warp;                      // the warp's columns
+    const uint32_t dread = dcol + ((uint32_t)(32 * m) << 16);                // ... in its lane quadrant
+    float2 *scr = reinterpret_cast<float2 *>(sm + SCR + warp * SCR_WARP);
+
+    // Issue the product (A window at a_tile - m KB) and wait for it.
+    auto run = [&](uint32_t a_tile, uint32_t b_tile) -> bool {
+        tc5::fence_smem_to_async();
+        tc5::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) issue_prod(dcol, a_tile - 1024u * (uint32_t)m, b_tile, bar);
+        __syncwarp();
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, ph, p.status));
+        ph ^= 1u;
+        tc5::fence_after_sync();
+        return ok;
+    };
+
+    // largest diagonal entry of A (both blocks)
+    const float dmax = warp_max((lane < 16 ? pA11 : pA22)[pl16(ii, ii)]);
+    float2 M[2][8];                                             // [A11 | A12], then [P | X]
+    ld_blk8(right ? pA12 : pA11, M, rg, j8);
+    __syncwarp();
+    const float mp1 = gj_blk_invert<2, 8>(M, scr, lane);
+
+    // P as FP32 planes (for B11); X as the B operand of A12^H X: rows (p', j)
+    // hold comp_p'(X_kj), K = k (a column of X per row: 2-byte stores)
+    const int eX = scale_exp(warp_max(right ? absmax_blk8(M) : 0.f));
+    const float sX = exp2i(eX);
+    if (!right) {
+        st_blk8(pA12, M, rg, j8);
+    } else {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int i = 4 * rg + r;
+        for (int r = 0; r < 2; ++r)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int ch = 2 * cg + h;
-                const float4 a = *reinterpret_cast<const float4 *>(gr + i * 32 + 4 * (ch ^ (i & 7)));
-                const float4 b = *reinterpret_cast<const float4 *>(gi + i * 32 + 4 * (ch ^ (i & 7)));
-                A[r][4 * h + 0] = make_float2(a.x, b.x);
-                A[r][4 * h + 1] = make_float2(a.y, b.y);
-                A[r][4 * h + 2] = make_float2(a.z, b.z);
-                A[r][4 * h + 3] = make_float2(a.w, b.w);
+            for (int cc = 0; cc < 8; ++cc) {
+                const int k = 2 * rg + r, j = j8 + cc;
+                st_split(slot0, offk16(j, k), M[r][cc].x * sX);
+                st_split(slot0, offk16(16 + j, k), M[r][cc].y * sX);
             }
+    }
+    // S = A22 - A12^H X
+    if (!run(s1, s0)) { timed_out = true; return false; }
+    {
+        float sv[16], a22[16];
+        cprod_read<CONJ_A>(dread, exp2i(-(e12 + eX)), pp, sv);
+        ld_row(pA22, pp, ii, a22);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            *reinterpret_cast<float4 *>(pA22 + 256 * pp + pl16(ii, 4 * t)) =
+                make_float4(a22[4 * t] - sv[4 * t], a22[4 * t + 1] - sv[4 * t + 1], a22[4 * t + 2] - sv[4 * t + 2],
+                            a22[4 * t + 3] - sv[4 * t + 3]);
+    }
+    __syncwarp();
+    // [S | X^H]: S from its planes; X^H_ki = conj(X_ik) from the X column tile
+    // (row k, K = i: the same rounded X the product above used)
+    float2 N2[2][8];
+    if (!right) {
+        ld_blk8(pA22, N2, rg, j8);
+    } else {
+        const float us = exp2i(-eX);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            float v[2][8];
+#pragma unroll
+            for (int pc = 0; pc < 2; ++pc) {
+                const int o = offk16(16 * pc + 2 * rg + r, j8);
+                const uint4 h = *reinterpret_cast<const uint4 *>(slot0 + o);
+                const uint4 l = *reinterpret_cast<const uint4 *>(slot0 + SLOT_LO + o);
+                const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[t]));
+                    const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[t]));
+                    v[pc][2 * t] = (hf.x + lf.x) * us;
+                    v[pc][2 * t + 1] = (hf.y + lf.y) * us;
+                }
+            }
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) N2[r][cc] = make_float2(v[0][cc], -v[1][cc]);
         }
     }
-    __syncthreads();        // every Gram block is in registers
-    if (warp < C) {
-        float dmax = 0.f;
+    __syncwarp();
+    // X as the A operand of nothing more and the B operand of Y X^H: rows
+    // (p, i) hold comp_p(X_ik), K = k
+    if (right) st_chunk8(slot0, M, rg, 0, j8, sX);
+    const float mp2 = gj_blk_invert<2, 8>(N2, scr, lane);      // N2 = [Q | Y^H]
+
+    // Y^H through FP32 planes, so that lane (p, i) holds row i of Y
+    if (right) st_blk8(pYH, N2, rg, j8);
+    __syncwarp();
+    float yv[16];
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+    for (int k = 0; k < 16; ++k) {
+        const float h = pYH[256 * pp + pl16(k, ii)];
+        yv[k] = pp ? -h : h;                                    // comp_p(Y_ik) = comp_p(conj(Y^H_ki))
+    }
+    __syncwarp();
+    const int eY = scale_exp(warp_max(absmax16(yv)));
+    st_row16(slot1, 16 * pp + ii, yv, exp2i(eY));
+    // Z = Y X^H;  B11 = P + Z
+    if (!run(s1, s0)) { timed_out = true; return false; }
+    float bv[16];
+    {
+        float pv[16];
+        cprod_read<CONJ_B>(dread, exp2i(-(eY + eX)), pp, bv);
+        ld_row(pA12, pp, ii, pv);
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                if (4 * rg + r == 8 * cg + c) dmax = fmaxf(dmax, A[r][c].x);
-        dmax = warp_max(dmax);
-        float2 *scr = reinterpret_cast<float2 *>(sm + SCR + warp * SCR_WARP);
-        const float min_piv = gj2d_invert(A, scr, lane);
-        unsigned char *th = sm + HT + (warp >> 1) * HT_PAIR;
-        if (!(min_piv >= 0x1p-12f * dmax)) {
-            if (lane == 0) eslot[24 + warp] = 1;    // FP64 retry after the phase
-        } else {
-            tc32_put_operator_2d(A, th, warp & 1, eslot + 16 + warp, lane);
+        for (int j = 0; j < 16; ++j) bv[j] += pv[j];
+    }
+    if (!(fminf(mp1, mp2) >= 0x1p-12f * dmax)) return false;   // FP64 retry
+
+    // The operator tile: rows 64 (c & 1) + arow(p, u), K = v (two 16-byte
+    // chunks per 8 columns), one scale for the whole inverse.
+    const int eB = scale_exp(warp_max(fmaxf(fmaxf(absmax16(bv), absmax16(yv)), absmax_blk8(N2))));
+    if (lane == 0) *eslot_b = eB;
+    const float sB = exp2i(eB);
+    __syncwarp();        // every lane has read the planes the tile overwrites
+    unsigned char *th = sm + HT + (c >> 1) * HT_PAIR;
+    const int rbase = 64 * (c & 1);
+    // rows u = i < 16: [B11 | -Y] (component pp)
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+#pragma unroll
+        for (int k8 = 0; k8 < 2; ++k8) {
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const float xa = half ? -yv[8 * k8 + 2 * t] : bv[8 * k8 + 2 * t];
+                const float xb = half ? -yv[8 * k8 + 2 * t + 1] : bv[8 * k8 + 2 * t + 1];
+                uint32_t ha, la, hb, lb;
+                split16(xa * sB, ha, la);
+                split16(xb * sB, hb, lb);
+                hw[t] = pack2(ha, hb);
+                lw[t] = pack2(la, lb);
+            }
+            const int o = off16(rbase + arow(pp, ii), 16 * half + 8 * k8);
+            *reinterpret_cast<uint4 *>(th + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4 *>(th + HT_LO + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
     }
+    // rows u = 16 + k: [-Y^H | Q] from the second elimination's blocks
+    {
+        const float sg = right ? -sB : sB;
+        const int k0 = right ? j8 : 16 + j8;
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int pc = 0; pc < 2; ++pc) {
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    uint32_t ha, la, hb, lb;
+                    split16((pc ? N2[r][2 * t].y : N2[r][2 * t].x) * sg, ha, la);
+                    split16((pc ? N2[r][2 * t + 1].y : N2[r][2 * t + 1].x) * sg, hb, lb);
+                    hw[t] = pack2(ha, hb);
+                    lw[t] = pack2(la, lb);
+                }
+                const int o = off16(rbase + arow(pc, 16 + 2 * rg + r), k0);
+                *reinterpret_cast<uint4 *>(th + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4 *>(th + HT_LO + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+    }
+    return true;
 }
 
 template <typename TIn, int NS>
@@ -413,19 +707,17 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
     uint64_t *bar_mma = bar_ld + 1;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar_ld + 2);
     int *abort_flag = reinterpret_cast<int *>(tslot + 1);
-    int *eslot = reinterpret_cast<int *>(sm + SLOTS);           // eH[8] | eY[8] | eB[8] | retry flags[8]
-    float *mslot = reinterpret_cast<float *>(sm + SLOTS + 128); // per-warp maxima
+    // eH[8] | eY[8] | eB[8] | retry flags[8] | e12[8]
+    int *eslot = reinterpret_cast<int *>(sm + SLOTS);
+    float *mslot = reinterpret_cast<float *>(sm + MSLOT);      // per-warp maxima
+    uint64_t *bar_op = reinterpret_cast<uint64_t *>(sm + BAR_OP) + warp;   // this warp's products
 
     if (tid == 0) {
         mbar_init(bar_ld, 1);
         mbar_init(bar_mma, 1);
+        for (int k = 0; k < 8; ++k) mbar_init(reinterpret_cast<uint64_t *>(sm + BAR_OP) + k, 1);
         *abort_flag = 0;
         for (int k = 0; k < 8; ++k) eslot[24 + k] = 0;
-        OpParams *op = reinterpret_cast<OpParams *>(sm + PARAMS);
-        op->H = p.H;
-        op->retries = p.retries;
-        op->delta = p.delta;
-        op->C = p.C;
         fence_mbar_init();
     }
     if (warp == 0) {
@@ -440,7 +732,7 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
     const uint32_t sbase = tc5::smem_addr(sm);
     grid_dependency_wait();
 
-    uint32_t ph_ld = 0, ph_mma = 0;
+    uint32_t ph_ld = 0, ph_mma = 0, ph_op = 0;
     const uint32_t hbytes = (uint32_t)B * 32u * EB;            // H[w]: B rows x U = 32
     const uint32_t ybytes = (uint32_t)N * (uint32_t)B * EB;    // y[w]: N rows x B
     const uint32_t id_in = tc5::idesc(Op16<GOp>::fmt, 128, 64);     // matched filter
@@ -738,31 +1030,61 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
                     for (int e = 0; e < 16; ++e) b0[16 + e] = x[e];
                 }
                 const float us = exp2i(-2 * eslot[c]);
-                float *plane = reinterpret_cast<float *>(sm + HT + j * HT_PAIR + cl * 8192 + pp * 4096);
+                float g[32];
 #pragma unroll
-                for (int ch = 0; ch < 8; ++ch) {
-                    float g[4];
+                for (int e = 0; e < 32; ++e) {
+                    const float recv = __shfl_xor_sync(0xffffffffu, b1[e], 16);
+                    // Re G = D00 + D11 (p = 0), Im G = D01 - D10 (p = 1)
+                    float v = (pp ? recv - b0[e] : b0[e] + recv) * us;
+                    if (pp == 0 && e == uu) v += p.f_delta;
+                    g[e] = v;
+                }
+                // The blocks of A = G_c + rho I the blocked inverse needs, in
+                // the cluster's own chunks: A11, A12 and A22 as FP32 planes,
+                // A12 also as the column tile (rows (p', j) hold
+                // comp_p'(A12_kj), K = k).
+                const int i16 = uu & 15;
+                float *plA = reinterpret_cast<float *>(uu < 16 ? sm + chunk0(c) + PL_A11 + pp * PL_IM
+                                                               : sm + chunk1(c) + PL_A22 + pp * PL_IM);
+                const int eA = uu < 16 ? 0 : 16;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    *reinterpret_cast<float4 *>(plA + pl16(i16, 4 * t)) =
+                        make_float4(g[eA + 4 * t], g[eA + 4 * t + 1], g[eA + 4 * t + 2], g[eA + 4 * t + 3]);
+                if (uu < 16) {      // warp-uniform: q even holds rows 0..15
+                    float *pl12 = reinterpret_cast<float *>(sm + chunk1(c) + PL_A12 + pp * PL_IM);
+                    float m12 = 0.f;
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        const int e = 4 * ch + t;
-                        const float recv = __shfl_xor_sync(0xffffffffu, b1[e], 16);
-                        // Re G = D00 + D11 (p = 0), Im G = D01 - D10 (p = 1)
-                        float v = (pp ? recv - b0[e] : b0[e] + recv) * us;
-                        if (pp == 0 && e == uu) v += p.f_delta;
-                        g[t] = v;
+                        *reinterpret_cast<float4 *>(pl12 + pl16(i16, 4 * t)) =
+                            make_float4(g[16 + 4 * t], g[17 + 4 * t], g[18 + 4 * t], g[19 + 4 * t]);
+                        m12 = fmaxf(m12, fmaxf(fmaxf(fabsf(g[16 + 4 * t]), fabsf(g[17 + 4 * t])),
+                                               fmaxf(fabsf(g[18 + 4 * t]), fabsf(g[19 + 4 * t]))));
                     }
-                    *reinterpret_cast<float4 *>(plane + uu * 32 + 4 * (ch ^ (uu & 7))) = make_float4(g[0], g[1], g[2], g[3]);
+                    const int e12 = scale_exp(warp_max(m12));
+                    if (lane == 0) eslot[32 + c] = e12;
+                    const float s12 = exp2i(e12);
+                    unsigned char *t12 = sm + chunk0(c) + SLOT1;
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) st_split(t12, offk16(16 * pp + jj, i16), g[16 + jj] * s12);
                 }
             }
+            tc5::fence_smem_to_async();
             tc5::fence_before_sync();
             __syncthreads();
         }
         if (*abort_flag) break;
 
-        // ---- B_c^{-1}: Gauss-Jordan per warp, pivot check, FP64 retry --------
-        if (tid == 0) reinterpret_cast<OpParams *>(sm + PARAMS)->row0 = (long long)w * B;
-        __syncthreads();
-        tc32_operator_phase<TIn>();
+        // ---- B_c^{-1}: blocked inverse per warp, pivot check, FP64 retry -----
+        if (warp < C) {
+            bool timed_out = false;
+            if (!tc32_blocked_operator(warp, eslot[32 + warp], sbase, tbase, bar_op, ph_op, p, eslot + 16 + warp,
+                                       timed_out)) {
+                if (timed_out) *abort_flag = 1;
+                else if (lane == 0) eslot[24 + warp] = 1;
+            }
+            __syncwarp();
+        }
         if (warp < C && eslot[24 + warp]) {
             // FP64 retry: this cluster's Gram from the inputs in global
             // memory and its inverse, in FP64, written as the operator
@@ -776,7 +1098,9 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
             }
         }
         tc5::fence_smem_to_async();
+        tc5::fence_before_sync();
         __syncthreads();
+        if (*abort_flag) break;
 
         // ---- operator products: y_reg, then one per iteration ----------------
         auto issue_op = [&]() {
