@@ -142,10 +142,13 @@ typedef enum dbp_mapping {
 } dbp_mapping;
 
 typedef enum dbp_kernel_path {
-    DBP_PATH_AUTO = 0,         /* uplink: DBP_PATH_MMA, else DBP_PATH_BCAST,
-                                  else DBP_PATH_TMA; downlink: DBP_PATH_MMA,
-                                  else DBP_PATH_TMA; each where eligible,
-                                  then DBP_PATH_GENERIC                      */
+    DBP_PATH_AUTO = 0,         /* uplink ADMM: DBP_PATH_TC5 (unless the
+                                  operator kernel or a resident operator is
+                                  asked for), then as uplink CG: DBP_PATH_MMA,
+                                  else DBP_PATH_BCAST, else DBP_PATH_TMA;
+                                  downlink: DBP_PATH_MMA, else DBP_PATH_TMA;
+                                  each where eligible, then
+                                  DBP_PATH_GENERIC                           */
     DBP_PATH_GENERIC = 1,      /* per-subcarrier kernel with staged loads:
                                   any shape, FP64, thread-block clusters     */
     DBP_PATH_TMA = 2,          /* persistent kernel fed by cp.async.bulk:
@@ -172,7 +175,10 @@ typedef enum dbp_kernel_path {
                                   tensor cores with accumulators in tensor
                                   memory, two clusters per M = 128 MMA; FP32
                                   operands as scaled FP16 hi / lo pairs
-                                  (three products, FP32 accumulation)        */
+                                  (three products, FP32 accumulation);
+                                  B_c^{-1} by the 2 x 2 block inverse (two
+                                  16-row eliminations, two tensor-core
+                                  products per cluster)                      */
 } dbp_kernel_path;
 
 typedef enum dbp_prefactor {

@@ -307,7 +307,7 @@ void bcast_layout(const dbp_frame_desc *d, Kind kind, int UT, Shape &s) {
 }
 
 dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool aligned16, Shape &s,
-                        const dbp_tuning &t) {
+                        const dbp_tuning &t, bool resident = false) {
     const int UT = next_pow2_ut(d->U);
     const int maxw = max_warps_for(d->precision, UT);
     const int C = d->C;
@@ -317,9 +317,13 @@ dbp_status choose_shape(dbp_context *h, const dbp_frame_desc *d, Kind kind, bool
     s.bcast = false;
     s.single = false;
     s.tc32 = false;
-    // the tcgen05 kernel for uplink ADMM with U = S = 32 when requested (or
-    // chosen by the autotuner)
-    const bool want_tc5 = t.kernel == DBP_PATH_TC5;
+    // the tcgen05 kernel for uplink ADMM with U = S = 32: when requested, and
+    // by default (measured faster and more accurate than the bulk-copy
+    // kernel on these shapes), except where the caller asks for what only
+    // the bulk-copy kernel does: the separate operator kernel
+    // (DBP_PREFACTOR_ON) or an operator kept resident across calls
+    const bool want_tc5 = t.kernel == DBP_PATH_TC5 ||
+                          (t.kernel == DBP_PATH_AUTO && t.prefactor != DBP_PREFACTOR_ON && !resident);
     if (want_tc5 && kind == K_ADMM_UL && t.mapping != DBP_MAP_CLUSTER && aligned16 &&
         dbp::tc32_eligible_shape(d->B, d->C, d->U, d->N, d->precision) && h->smem_optin >= (size_t)dbp::tc32::SMEM) {
         s.tc32 = true;
@@ -718,7 +722,7 @@ dbp_status run_ex(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void
             if (it != h->tuned.end()) tune = it->second;
         }
     }
-    v = choose_shape(h, d, kind, a16, s, tune);
+    v = choose_shape(h, d, kind, a16, s, tune, ex && ex->factor && ex->factor_mode != 0);
     if (v != DBP_OK) return v;
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");

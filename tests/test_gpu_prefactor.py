@@ -73,8 +73,13 @@ class Case:
 
 
 def _run_with(dbp, h, case, prefactor):
+    # The operator kernel serves the bulk-copy and downlink tensor-core
+    # kernels; uplink ADMM at U = S = 32 would otherwise run on the tcgen05
+    # kernel whenever the operator kernel is off, so its comparisons pin the
+    # bulk-copy path.
+    path = dbp.DBP_PATH_TMA if (case.kind == "admm" and case.shape[2] == 32) else dbp.DBP_PATH_AUTO
     try:
-        dbp.dbp_set_tuning(h, prefactor=prefactor)
+        dbp.dbp_set_tuning(h, kernel=path, prefactor=prefactor)
         out = case.run(dbp, h)
         torch.cuda.synchronize()
     finally:

@@ -273,8 +273,11 @@ def test_cancel_a_queued_frame(dbp):
 def test_device_buffer_requests_run_in_place(dbp):
     """Requests flagged DBP_REQ_DEVICE_BUFFERS run on the caller's CUDA
     buffers with no host copies: results bit-identical to the synchronous
-    device-pointer entry points, also when a coherence block reuses the
-    resident operator."""
+    device-pointer entry points on the same kernel path, also when a
+    coherence block reuses the resident operator.  (A resident operator
+    needs the bulk-copy kernel, so the loop runs uplink ADMM at U = S = 32
+    there, where a synchronous call defaults to the tcgen05 kernel; the
+    reference pins that path.)"""
     h = dbp.dbp_create(0)
     try:
         K = dbp
@@ -296,7 +299,10 @@ def test_device_buffer_requests_run_in_place(dbp):
             if dl:
                 dbp.dbp_downlink_admm(h, d, Hd, ind, ro)
             elif kind == K.DBP_KIND_UPLINK_ADMM:
+                if U == 32 and B == 32 * C:
+                    dbp.dbp_set_tuning(h, kernel=dbp.DBP_PATH_TMA)
                 dbp.dbp_uplink_admm(h, d, Hd, ind, ro, rl)
+                dbp.dbp_set_tuning(h)
             else:
                 dbp.dbp_uplink_cg(h, d, Hd, ind, ro, rl)
             items.append((kind, d, Hd, ind, out, lab))
