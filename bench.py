@@ -379,8 +379,11 @@ def cpu_cores() -> int:
         return os.cpu_count() or 1
 
 
-def oracle_head_sample(f, idx):
+def oracle_head_sample(f, idx, fp32: bool = False):
     import oracle
+    if fp32:        # the same source built in FP32: the plain CPU program
+        oracle.admm_ul_fp32(f["H"][idx], f["y"][idx], C=HEAD.C, rho=1.0, N0=f["N0"], T_max=HEAD.T)
+        return
     H = f["H"][idx].astype(np.complex64).astype(np.complex128)
     y = f["y"][idx].astype(np.complex64).astype(np.complex128)
     oracle.admm_ul(H, y, C=HEAD.C, rho=1.0, N0=f["N0"], T_max=HEAD.T)
@@ -389,26 +392,38 @@ def oracle_head_sample(f, idx):
 def cpu_baseline(seconds: float):
     """The FP64 oracle (Alg. 1 as printed, OpenMP over subcarriers) on the
     host cores: samples of 32 subcarriers of the headline frame, repeated for
-    about `seconds`, scaled to the frame's bits."""
+    about `seconds`, scaled to the frame's bits.  Beside it, `fp32`: the same
+    source built in FP32 (a plain CPU program, not a reference) on the same
+    samples for about half as long."""
     import oracle
     oracle.build()
     f = synth.uplink_frame(256, HEAD.N, HEAD.B, HEAD.U, HEAD.M, HEAD_SNR_DB, seed=synth.frame_seed(4, 0))
-    rng = np.random.default_rng(0)
-    oracle_head_sample(f, np.arange(4))
-    t0 = time.perf_counter()
-    reps, sc = 0, 0
-    while True:
-        idx = np.sort(rng.choice(256, size=32, replace=False))
-        oracle_head_sample(f, idx)
-        reps += 1
-        sc += 32
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
+    f["H"] = f["H"].astype(np.complex64)
+    f["y"] = f["y"].astype(np.complex64)
+
+    def timed(limit, fp32):
+        rng = np.random.default_rng(0)
+        oracle_head_sample(f, np.arange(4), fp32)
+        t0 = time.perf_counter()
+        reps, sc = 0, 0
+        while True:
+            idx = np.sort(rng.choice(256, size=32, replace=False))
+            oracle_head_sample(f, idx, fp32)
+            reps += 1
+            sc += 32
+            el = time.perf_counter() - t0
+            if el >= limit:
+                return reps, sc, el
+
+    reps, sc, el = timed(seconds, False)
     bits = detected_bits(Workload(HEAD.B, HEAD.C, HEAD.U, sc, HEAD.N, HEAD.M, HEAD.T))
+    r32, sc32, el32 = timed(seconds / 2, True)
+    bits32 = detected_bits(Workload(HEAD.B, HEAD.C, HEAD.U, sc32, HEAD.N, HEAD.M, HEAD.T))
     return {"value": bits / el / 1e9, "unit": "Gbit/s", "cores": cpu_cores(), "kind": "oracle",
             "sample": f"{reps} x 32 subcarriers of the 3300 x 14 frame ({sc} subcarriers, {el:.1f} s), "
-                      "FP64, OpenMP over subcarriers"}
+                      "FP64, OpenMP over subcarriers",
+            "fp32": {"value": bits32 / el32 / 1e9, "kind": "the oracle source built in FP32 (plain CPU)",
+                     "sample": f"{r32} x 32 subcarriers ({el32:.1f} s)"}}
 
 
 def cpu_rows(seconds_per_row: float = 1.5):

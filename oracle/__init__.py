@@ -30,6 +30,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB32 = os.path.join(_HERE, "liboracle32.so")
 
 REG_ZF, REG_MMSE, REG_BOX, REG_BPSK = 0, 1, 2, 3
 MODE_AUTO, MODE_UXU, MODE_SXS = 0, 1, 2
@@ -38,15 +39,32 @@ _ERRORS = {-1: "bad argument", -2: "singular matrix", -3: "out of memory"}
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so (gcc, OpenMP over subcarriers)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp",
-               "-o", _LIB, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+    """Compile oracle.c into liboracle.so (gcc, OpenMP over subcarriers), and
+    the same source with ORACLE_REAL=float into liboracle32.so (the plain
+    FP32 CPU program the benchmark times beside the oracle; never a
+    reference)."""
+    for lib, extra in ((_LIB, []), (_LIB32, ["-DORACLE_REAL=float"])):
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+            cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp"] + extra + ["-o", lib, _SRC, "-lm"]
+            subprocess.run(cmd, check=True)
     return _LIB
 
 
 _lib = None
+_lib32 = None
+
+
+def _load32():
+    """The FP32 build: only Alg. 1 is bound (the CPU baseline's detector)."""
+    global _lib32
+    if _lib32 is None:
+        build()
+        lib = ctypes.CDLL(_LIB32)
+        P, I, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+        lib.oracle_admm_ul.argtypes = [I, I, I, I, I, P, P, F, F, F, F, I, I, F, I, P]
+        lib.oracle_admm_ul.restype = I
+        _lib32 = lib
+    return _lib32
 
 
 def _load():
@@ -100,6 +118,23 @@ def admm_ul(H, y, C: int, rho: float, N0: float, Es: float = 1.0, T_max: int = 3
                                 rho, gamma, N0, Es, T_max, reg, box_r, mode,
                                 out.ctypes.data)
     _check(rc, "admm_ul")
+    return out
+
+
+def admm_ul_fp32(H, y, C: int, rho: float, N0: float, Es: float = 1.0, T_max: int = 3,
+                 gamma: float = 1.0, reg: int = REG_MMSE, box_r: float = 1.0,
+                 mode: int = MODE_AUTO) -> np.ndarray:
+    """Alg. 1 from the same source built in FP32 (complex64 in and out).  A
+    timed CPU program for the benchmark's plain-CPU line, not a reference:
+    parity is always checked against the FP64 build (admm_ul)."""
+    H = np.ascontiguousarray(np.asarray(H), dtype=np.complex64)
+    y = np.ascontiguousarray(np.asarray(y), dtype=np.complex64)
+    W, N, B, U = _shape_ul(H, y)
+    out = np.zeros((W, N, U), dtype=np.complex64)
+    rc = _load32().oracle_admm_ul(W, N, B, C, U, H.ctypes.data, y.ctypes.data,
+                                  rho, gamma, N0, Es, T_max, reg, box_r, mode,
+                                  out.ctypes.data)
+    _check(rc, "admm_ul (FP32 build)")
     return out
 
 

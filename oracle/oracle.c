@@ -32,12 +32,19 @@
  *
  * Return codes: 0 ok, -1 bad argument, -2 singular matrix, -3 out of memory.
  */
-#include <complex.h>
-#include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <tgmath.h>
 
-typedef double complex cplx;
+/* The oracle's arithmetic is double.  The CPU baseline also compiles this
+ * same source with ORACLE_REAL=float, as a plain FP32 program that is only
+ * timed (the survey's "plain CPU" line); the math functions are the
+ * type-generic ones of <tgmath.h>, so both builds run the same steps. */
+#ifndef ORACLE_REAL
+#define ORACLE_REAL double
+#endif
+typedef ORACLE_REAL real;
+typedef ORACLE_REAL complex cplx;
 
 enum { REG_ZF = 0, REG_MMSE = 1, REG_BOX = 2, REG_BPSK = 3 };
 enum { MODE_AUTO = 0, MODE_UXU = 1, MODE_SXS = 2 };
@@ -60,9 +67,9 @@ static int inv_gj(int n, const cplx *A, cplx *Ainv, cplx *work)
     }
     for (int k = 0; k < n; ++k) {
         int piv = k;
-        double best = cabs(work[k * m + k]);
+        real best = cabs(work[k * m + k]);
         for (int i = k + 1; i < n; ++i) {
-            double a = cabs(work[i * m + k]);
+            real a = cabs(work[i * m + k]);
             if (a > best) { best = a; piv = i; }
         }
         if (best == 0.0) return ERR_SINGULAR;
@@ -108,7 +115,7 @@ static void mvh(int rows, int cols, const cplx *A, const cplx *x, cplx *out)
 }
 
 /* G = A^H A + delta I (cols x cols), A is rows x cols. */
-static void gram_ha(int rows, int cols, const cplx *A, double delta, cplx *G)
+static void gram_ha(int rows, int cols, const cplx *A, real delta, cplx *G)
 {
     for (int i = 0; i < cols; ++i)
         for (int j = 0; j < cols; ++j) {
@@ -119,7 +126,7 @@ static void gram_ha(int rows, int cols, const cplx *A, double delta, cplx *G)
 }
 
 /* G = A A^H + delta I (rows x rows), A is rows x cols. */
-static void gram_ah(int rows, int cols, const cplx *A, double delta, cplx *G)
+static void gram_ah(int rows, int cols, const cplx *A, real delta, cplx *G)
 {
     for (int i = 0; i < rows; ++i)
         for (int j = 0; j < rows; ++j) {
@@ -149,23 +156,23 @@ static void *xmalloc(size_t n) { return malloc(n ? n : 1); }
 /* Step (E2) via Lemma 1: s = argmin_s g(s) + C rho/2 ||s - v||^2,      */
 /* v = w / C.  Closed forms (E2-ZF), (E2-MMSE), (E2-BOX) and BPSK.      */
 /* ------------------------------------------------------------------ */
-static double clip(double a, double r)
+static real clip(real a, real r)
 {
-    double m = fabs(a) < r ? fabs(a) : r;
+    real m = fabs(a) < r ? fabs(a) : r;
     return a < 0.0 ? -m : m;
 }
 
-static void prox_e2(int reg, int U, int C, double rho, double N0, double Es,
-                    double box_r, const cplx *w, cplx *s)
+static void prox_e2(int reg, int U, int C, real rho, real N0, real Es,
+                    real box_r, const cplx *w, cplx *s)
 {
     for (int u = 0; u < U; ++u) {
-        cplx v = w[u] / (double)C;
+        cplx v = w[u] / (real)C;
         switch (reg) {
         case REG_ZF:   /* (E2-ZF): s = v */
             s[u] = v;
             break;
         case REG_MMSE: /* Alg. 1 scaling (N0/(rho Es) + C)^{-1} w, i.e. (E2-MMSE) */
-            s[u] = w[u] / (N0 / (rho * Es) + (double)C);
+            s[u] = w[u] / (N0 / (rho * Es) + (real)C);
             break;
         case REG_BOX:  /* (E2-BOX): per-axis projection onto [-r, r] */
             s[u] = clip(creal(v), box_r) + I * clip(cimag(v), box_r);
@@ -185,8 +192,8 @@ static void prox_e2(int reg, int U, int C, double rho, double N0, double Es,
 /* ------------------------------------------------------------------ */
 int oracle_admm_ul(int W, int N, int B, int C, int U,
                    const cplx *H, const cplx *y,
-                   double rho, double gamma, double N0, double Es,
-                   int T_max, int reg, double box_r, int mode, cplx *s_out)
+                   real rho, real gamma, real N0, real Es,
+                   int T_max, int reg, real box_r, int mode, cplx *s_out)
 {
     if (check_shape(W, N, B, C, U) != OK || T_max < 1 || !(rho > 0.0)) return ERR_ARG;
     if (reg < REG_ZF || reg > REG_BPSK) return ERR_ARG;
@@ -297,7 +304,7 @@ int oracle_admm_ul(int W, int N, int B, int C, int U,
 /* rho is the CG regulariser: N0/Es for MMSE, 0 for ZF (Sec. III-D).   */
 /* ------------------------------------------------------------------ */
 int oracle_cg_ul(int W, int N, int B, int C, int U,
-                 const cplx *H, const cplx *y, double rho, int T_max,
+                 const cplx *H, const cplx *y, real rho, int T_max,
                  cplx *x_out)
 {
     if (check_shape(W, N, B, C, U) != OK || T_max < 0 || rho < 0.0) return ERR_ARG;
@@ -341,20 +348,20 @@ int oracle_cg_ul(int W, int N, int B, int C, int U,
                 }
                 /* e = rho p + w */
                 for (int u = 0; u < U; ++u) e[u] = rho * p[u] + wv[u];
-                double rr = 0.0, pe = 0.0;
+                real rr = 0.0, pe = 0.0;
                 for (int u = 0; u < U; ++u) {
                     rr += creal(r[u]) * creal(r[u]) + cimag(r[u]) * cimag(r[u]);
                     pe += creal(conj(p[u]) * e[u]);
                 }
                 if (rr == 0.0 || pe == 0.0) break;
-                double alpha = rr / pe;
+                real alpha = rr / pe;
                 for (int u = 0; u < U; ++u) x[u] += alpha * p[u];
-                double rr_new = 0.0;
+                real rr_new = 0.0;
                 for (int u = 0; u < U; ++u) {
                     r[u] -= alpha * e[u];
                     rr_new += creal(r[u]) * creal(r[u]) + cimag(r[u]) * cimag(r[u]);
                 }
-                double beta = rr_new / rr;
+                real beta = rr_new / rr;
                 for (int u = 0; u < U; ++u) p[u] = r[u] + beta * p[u];
             }
             cplx *xo = x_out + ((size_t)w * N + n) * U;
@@ -373,8 +380,8 @@ int oracle_cg_ul(int W, int N, int B, int C, int U,
 /*       2 = S x S.                                                     */
 /* ------------------------------------------------------------------ */
 int oracle_admm_dl(int W, int N, int B, int C, int U,
-                   const cplx *H, const cplx *s, double rho, double gamma,
-                   double eps, int T_max, int mode, cplx *x_out)
+                   const cplx *H, const cplx *s, real rho, real gamma,
+                   real eps, int T_max, int mode, cplx *x_out)
 {
     if (check_shape(W, N, B, C, U) != OK || T_max < 1 || !(rho > 0.0) || eps < 0.0)
         return ERR_ARG;
@@ -437,7 +444,7 @@ int oracle_admm_dl(int W, int N, int B, int C, int U,
             }                                                                   \
         } while (0)
 
-        const double init_scale = fmax((double)U / (double)B, 1.0 / (double)C);
+        const real init_scale = fmax((real)U / (real)B, 1.0 / (real)C);
         for (int n = 0; n < N && !bad; ++n) {
             const cplx *sw = s + ((size_t)w * N + n) * U;
             /* Init: z_c = max{U/B, 1/C} s, lambda_c = 0, x_c = P1(z_c). */
@@ -461,9 +468,9 @@ int oracle_admm_dl(int W, int N, int B, int C, int U,
                 }
                 /* (P2) via Lemma 2: z_c = w_c + k (s/C - w/C),
                  * k = max{0, 1 - eps/||s - w||} (k = 1 for eps = 0). */
-                double k = 1.0;
+                real k = 1.0;
                 if (eps > 0.0) {
-                    double nrm = 0.0;
+                    real nrm = 0.0;
                     for (int u = 0; u < U; ++u) {
                         cplx dlt = sw[u] - wv[u];
                         nrm += creal(dlt) * creal(dlt) + cimag(dlt) * cimag(dlt);
@@ -473,7 +480,7 @@ int oracle_admm_dl(int W, int N, int B, int C, int U,
                 }
                 for (int c = 0; c < C; ++c) {
                     for (int u = 0; u < U; ++u) {
-                        z[c * U + u] = wc[c * U + u] + k * (sw[u] - wv[u]) / (double)C;
+                        z[c * U + u] = wc[c * U + u] + k * (sw[u] - wv[u]) / (real)C;
                         /* (P3): lambda_c = lambda_c - gamma (m_c - z_c) */
                         lam[c * U + u] -= gamma * (m[c * U + u] - z[c * U + u]);
                         v[u] = z[c * U + u] + lam[c * U + u];
@@ -497,7 +504,7 @@ int oracle_admm_dl(int W, int N, int B, int C, int U,
 
 /* x = (H^H H + delta I)^{-1} H^H y; delta = N0/Es (MMSE) or 0 (ZF). */
 int oracle_lmmse_ul(int W, int N, int B, int U, const cplx *H, const cplx *y,
-                    double delta, cplx *x_out)
+                    real delta, cplx *x_out)
 {
     if (W < 0 || N < 0 || B <= 0 || U <= 0 || delta < 0.0) return ERR_ARG;
     int status = OK;
