@@ -500,9 +500,8 @@ dbp_status dbp_set_test_faults(dbp_handle_t h, uint32_t flags);
  * from earlier work is still pending; otherwise as dbp_downlink_admm.  Every
  * error leaves its text in dbp_last_error.
  * Set-up: the first call on each device (with that device current) looks
- * up the array's device address and keeps it for the life of the process;
- * make that first call before any stream capture, and do not use the entry
- * point after cudaDeviceReset.  Every call reuses the same array: two calls
+ * up the array's device address (a CUDA runtime query) and keeps it for the
+ * life of the process; do not use the entry point after cudaDeviceReset.  Every call reuses the same array: two calls
  * whose work overlaps on the GPU (different streams, or different host
  * threads) race on it and must be serialised by the caller.  Each call
  * overwrites every scratch entry it reads, so nothing has to be cleared
