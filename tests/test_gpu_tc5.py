@@ -81,6 +81,7 @@ CASES = [
     (9, 9, 2, 2, 4, 6.0),                # B=64, C=2 (one pair), ragged N
     (5, 1, 8, 1, 64, 25.0),              # N=1, T=1 (init and prox only)
     (4, 14, 8, 6, 256, 30.0),            # T=6, 256-QAM
+    (11, 14, 6, 3, 64, 18.0),            # C=6: three pairs, the second Gram round holds one
 ]
 
 
@@ -191,3 +192,23 @@ def test_tc5_rejects_other_shapes(dbp, handle):
         with pytest.raises(dbp.DbpError) as ei:
             dbp.dbp_uplink_admm(handle, d, buf, buf, buf)
         assert ei.value.status == dbp.DBP_ERR_UNSUPPORTED
+
+
+def test_tc5_is_the_default_for_eligible_shapes(dbp, handle):
+    """AUTO runs uplink ADMM at U = S = 32 on the tcgen05 kernel (bit-identical
+    to asking for it), and on the bulk-copy kernel when the separate operator
+    kernel is asked for (bit-identical to asking for that path)."""
+    W, N, C, T, M = 40, 14, 8, 3, 64
+    f = synth.uplink_frame(W, N, 32 * C, 32, M, 20.0, seed=9800)
+    outs = {}
+    for name, kw in (("auto", {}), ("tc5", {"kernel": dbp.DBP_PATH_TC5}),
+                     ("auto_pre", {"prefactor": dbp.DBP_PREFACTOR_ON}),
+                     ("tma_pre", {"kernel": dbp.DBP_PATH_TMA, "prefactor": dbp.DBP_PREFACTOR_ON})):
+        dbp.dbp_set_tuning(handle, **kw)
+        try:
+            outs[name] = run(dbp, handle, f["H"], f["y"], C, T, M, f["N0"])[:2]
+        finally:
+            dbp.dbp_set_tuning(handle, kernel=dbp.DBP_PATH_TC5)     # the module's setting
+    assert np.array_equal(outs["auto"][0], outs["tc5"][0]) and np.array_equal(outs["auto"][1], outs["tc5"][1])
+    assert np.array_equal(outs["auto_pre"][0], outs["tma_pre"][0])
+    assert not np.array_equal(outs["auto"][0], outs["auto_pre"][0])     # two different kernels
