@@ -18,8 +18,8 @@ and the B=256 / C=16 / U=16 downlink frame (T=5), the roofline of the
 headline kernel, the FP64 CPU oracle on the host cores, the end-to-end rate
 through the host-buffer C ABI, and the SM clocks sampled during the timed
 region.  Everything else (per-row details, optional studies selected with
---study) goes to a JSON file (--details, default gpurun_out/bench_details.json
-when that folder exists).
+--study) goes to a JSON file (--details, default bench_details.json beside
+this script).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dbp|reference]
 For N > 1, launch under torch.distributed.run; each rank detects its own
@@ -1286,9 +1286,7 @@ def main(argv=None) -> int:
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=device)
-    details_path = args.details
-    if details_path is None and os.path.isdir(os.path.join(ROOT, "gpurun_out")):
-        details_path = os.path.join(ROOT, "gpurun_out", "bench_details.json")
+    details_path = args.details if args.details else os.path.join(ROOT, "bench_details.json")
     studies = set(STUDIES) if "all" in args.study else set(args.study)
 
     h = dbp.dbp_create(local)
@@ -1428,7 +1426,8 @@ def main(argv=None) -> int:
             "mixed": mixed, "rows": rows, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": K,
             "clocks": clk.summary(), "details": os.path.relpath(details_path, ROOT) if details_path else None}
         if details_path:
-            os.makedirs(os.path.dirname(details_path), exist_ok=True)
+            if os.path.dirname(details_path):
+                os.makedirs(os.path.dirname(details_path), exist_ok=True)
             with open(details_path, "w") as fh:
                 json.dump(details, fh, indent=1, default=float)
         print(json.dumps(line, default=float))
