@@ -161,13 +161,20 @@ __device__ __forceinline__ void ld32(uint32_t taddr, float (&a)[32]) {
 // row k publish it (rowbuf), every lane updates its block with the rank-1
 // term f_i m_kj, f_i = m_ik / m_kk, and the owners of column k write the new
 // column (-f_i; 1 on the pivot row, whose row stays multiplied by its pivot
-// until the final scaling).  Buffers alternate between steps (2 (NR + NC)
-// float2), so one warp barrier per step orders writes and reads.  The step
+// until the final scaling).  Buffers alternate between steps (2 (NR + 4 CB
+// + 8) float2: 896 bytes for RB = 2, CB = 8), so one warp barrier per step
+// orders writes and reads.  The step
 // loop is unrolled by CB so every register index is static.  Returns the
 // smallest pivot (real part).
 template <int RB, int CB>
 __device__ __forceinline__ float gj_blk_invert(float2 (&A)[RB][CB], float2 *buf, int lane) {
     constexpr int NN = 8 * RB, NC = 4 * CB;
+    // The pivot row is published as four groups of CB entries, one per
+    // column group cg, CBP = CB + 2 entries apart: 16-byte aligned, and with
+    // 80-byte strides (CB = 8) the four groups sit in different banks, so the
+    // row's broadcast loads and stores are free of bank conflicts (with 64-
+    // byte strides groups 0 and 2, 1 and 3 collide).
+    constexpr int CBP = CB + 2;
     static_assert(NC >= NN && NN % CB == 0 && CB % RB == 0 && RB % 2 == 0, "8 x 4 lane grid of RB x CB blocks");
     const int rg = lane >> 2, cg = lane & 3;
     float min_piv = 3.0e38f;
@@ -180,7 +187,7 @@ __device__ __forceinline__ float gj_blk_invert(float2 (&A)[RB][CB], float2 *buf,
         for (int kk = 0; kk < CB; ++kk) {
             const int k = k0 + kk;
             const int rr = kk % RB;                 // pivot row inside its block
-            float2 *colbuf = buf + (kk & 1) * (NN + NC), *rowbuf = colbuf + NN;
+            float2 *colbuf = buf + (kk & 1) * (NN + 4 * CBP), *rowbuf = colbuf + NN;
             const bool ownc = (cg == k0 / CB), ownr = (rg == k / RB);
             if (ownc) {
 #pragma unroll
@@ -191,7 +198,7 @@ __device__ __forceinline__ float gj_blk_invert(float2 (&A)[RB][CB], float2 *buf,
             if (ownr) {
 #pragma unroll
                 for (int c = 0; c < CB; c += 2)
-                    *reinterpret_cast<float4 *>(&rowbuf[CB * cg + c]) =
+                    *reinterpret_cast<float4 *>(&rowbuf[CBP * cg + c]) =
                         make_float4(A[rr][c].x, A[rr][c].y, A[rr][c + 1].x, A[rr][c + 1].y);
             }
             __syncwarp();
@@ -210,7 +217,7 @@ __device__ __forceinline__ float gj_blk_invert(float2 (&A)[RB][CB], float2 *buf,
 #pragma unroll
             for (int c = 0; c < CB; c += 2) {
                 float2 a, b;
-                ld2(&rowbuf[CB * cg + c], a, b);
+                ld2(&rowbuf[CBP * cg + c], a, b);
                 pr[c] = a;
                 pr[c + 1] = b;
             }
