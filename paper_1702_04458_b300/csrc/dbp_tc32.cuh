@@ -289,29 +289,48 @@ __device__ __forceinline__ void tc32_put_operator(const float2 (&R)[32], unsigne
 
 // FP64 recomputation of one cluster's operator (whole warp): the Gram
 // H_c^H H_c + delta I from the cluster block in global memory (row u per
-// lane), its Gauss-Jordan inverse in FP64, rounded to FP32 and written as
-// the operator tile.  Out of line: it runs only when an FP32 pivot was too
-// small, and its FP64 rows must not weigh on the kernel's registers.
+// lane), its Gauss-Jordan inverse in FP64 (the steps of gj_invert, in the
+// same order), rounded to FP32 and written as the operator tile.  Out of
+// line and with rolled loops over a row kept in local memory: it runs only
+// when an FP32 pivot was too small, so its code stays a few KB instead of
+// the hundreds of KB an unrolled FP64 elimination takes, and its rows do
+// not weigh on the kernel's registers.
 template <typename TIn>
 __device__ __noinline__ void tc32_fp64_operator(const TIn *Hg, double delta, double2 *scr, unsigned char *th, int clw,
                                                 int *eslot, int lane) {
     double2 D[32];
-#pragma unroll
-    for (int v = 0; v < 32; ++v) D[v] = make_double2(0.0, 0.0);
-    for (int s = 0; s < 32; ++s) {
-        const float2 hu = to_f2(Hg[s * 32 + lane]);
-        const double2 hd = make_double2(hu.x, hu.y);
-#pragma unroll
-        for (int v = 0; v < 32; ++v) {
-            const float2 hv = to_f2(Hg[s * 32 + v]);
-            cmacc(D[v], hd, make_double2(hv.x, hv.y));
+#pragma unroll 1
+    for (int v = 0; v < 32; ++v) {
+        double2 acc = make_double2(0.0, 0.0);
+#pragma unroll 1
+        for (int s = 0; s < 32; ++s) {
+            const float2 hu = to_f2(Hg[s * 32 + lane]), hv = to_f2(Hg[s * 32 + v]);
+            cmacc(acc, make_double2(hu.x, hu.y), make_double2(hv.x, hv.y));
         }
+        if (v == lane) acc.x += delta;
+        D[v] = acc;
     }
-#pragma unroll
-    for (int v = 0; v < 32; ++v)
-        if (v == lane) D[v].x += delta;
     __syncwarp();
-    gj_invert<32>(D, scr, lane, lane);
+#pragma unroll 1
+    for (int k = 0; k < 32; ++k) {
+        if (lane == k) {
+#pragma unroll 1
+            for (int j = 0; j < 32; ++j) scr[j] = D[j];
+        }
+        __syncwarp();
+        const double2 inv = crcp(scr[k]);
+        const bool me = (lane == k);
+        const double2 f = me ? make_double2(-inv.x, -inv.y) : cmul(D[k], inv);
+#pragma unroll 1
+        for (int j = 0; j < 32; ++j) {
+            if (j == k) continue;
+            double2 base = me ? make_double2(0.0, 0.0) : D[j];
+            cmac(base, make_double2(-f.x, -f.y), scr[j]);
+            D[j] = base;
+        }
+        D[k] = me ? inv : make_double2(-f.x, -f.y);
+        __syncwarp();
+    }
     float2 R[32];
 #pragma unroll
     for (int v = 0; v < 32; ++v) R[v] = make_float2((float)D[v].x, (float)D[v].y);
