@@ -543,7 +543,7 @@ __device__ __forceinline__ bool tc32_blocked_operator(int c, int e12, uint32_t s
     unsigned char *c0 = sm + chunk0(c), *c1 = sm + chunk1(c);
     float *pA11 = reinterpret_cast<float *>(c0 + PL_A11), *pA22 = reinterpret_cast<float *>(c1 + PL_A22);
     float *pA12 = reinterpret_cast<float *>(c1 + PL_A12);      // later the planes of P
-    float *pYH = reinterpret_cast<float *>(c0 + SLOT1);         // planes of Y^H (after the A12 tile)
+    float *pYH = reinterpret_cast<float *>(c0 + SLOT0);         // planes of Y^H (after the X column tile)
     unsigned char *slot0 = c0 + SLOT0, *slot1 = c0 + SLOT1;
     const uint32_t s0 = sbase + (uint32_t)chunk0(c) + SLOT0, s1 = sbase + (uint32_t)chunk0(c) + SLOT1;
     const uint32_t dcol = tbase + 32u * (uint32_t)warp;                      // the warp's columns
@@ -565,73 +565,80 @@ __device__ __forceinline__ bool tc32_blocked_operator(int c, int e12, uint32_t s
 
     // largest diagonal entry of A (both blocks)
     const float dmax = warp_max((lane < 16 ? pA11 : pA22)[pl16(ii, ii)]);
-    float2 M[2][8];                                             // [A11 | A12], then [P | X]
+    // M = [A11 | A12] -> [P | X] (pass 0), then [S | X^H] -> [Q | Y^H]
+    // (pass 1): one copy of the elimination's code serves both (a smaller
+    // kernel for the instruction caches; measured faster in FP32 and FP16).
+    float2 M[2][8];
     ld_blk8(right ? pA12 : pA11, M, rg, j8);
-    __syncwarp();
-    const float mp1 = gj_blk_invert<2, 8>(M, scr, lane);
-
-    // P as FP32 planes (for B11); X as the B operand of A12^H X: rows (p', j)
-    // hold comp_p'(X_kj), K = k (a column of X per row: 2-byte stores)
-    const int eX = scale_exp(warp_max(right ? absmax_blk8(M) : 0.f));
-    const float sX = exp2i(eX);
-    if (!right) {
-        st_blk8(pA12, M, rg, j8);
-    } else {
+    float mp = 3.0e38f;
+    int eX = 0;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+        __syncwarp();
+        mp = fminf(mp, gj_blk_invert<2, 8>(M, scr, lane));
+        if (pass == 1) break;
+        // P as FP32 planes (for B11); X as the B operand of A12^H X: rows
+        // (p', j) hold comp_p'(X_kj), K = k (a column of X per row: 2-byte
+        // stores)
+        eX = scale_exp(warp_max(right ? absmax_blk8(M) : 0.f));
+        const float sX = exp2i(eX);
+        if (!right) {
+            st_blk8(pA12, M, rg, j8);
+        } else {
 #pragma unroll
-        for (int r = 0; r < 2; ++r)
+            for (int r = 0; r < 2; ++r)
 #pragma unroll
-            for (int cc = 0; cc < 8; ++cc) {
-                const int k = 2 * rg + r, j = j8 + cc;
-                st_split(slot0, offk16(j, k), M[r][cc].x * sX);
-                st_split(slot0, offk16(16 + j, k), M[r][cc].y * sX);
-            }
-    }
-    // S = A22 - A12^H X
-    if (!run(s1, s0)) { timed_out = true; return false; }
-    {
-        float sv[16], a22[16];
-        cprod_read<CONJ_A>(dread, exp2i(-(e12 + eX)), pp, sv);
-        ld_row(pA22, pp, ii, a22);
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-            *reinterpret_cast<float4 *>(pA22 + 256 * pp + pl16(ii, 4 * t)) =
-                make_float4(a22[4 * t] - sv[4 * t], a22[4 * t + 1] - sv[4 * t + 1], a22[4 * t + 2] - sv[4 * t + 2],
-                            a22[4 * t + 3] - sv[4 * t + 3]);
-    }
-    __syncwarp();
-    // [S | X^H]: S from its planes; X^H_ki = conj(X_ik) from the X column tile
-    // (row k, K = i: the same rounded X the product above used)
-    float2 N2[2][8];
-    if (!right) {
-        ld_blk8(pA22, N2, rg, j8);
-    } else {
-        const float us = exp2i(-eX);
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            float v[2][8];
-#pragma unroll
-            for (int pc = 0; pc < 2; ++pc) {
-                const int o = offk16(16 * pc + 2 * rg + r, j8);
-                const uint4 h = *reinterpret_cast<const uint4 *>(slot0 + o);
-                const uint4 l = *reinterpret_cast<const uint4 *>(slot0 + SLOT_LO + o);
-                const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[t]));
-                    const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[t]));
-                    v[pc][2 * t] = (hf.x + lf.x) * us;
-                    v[pc][2 * t + 1] = (hf.y + lf.y) * us;
+                for (int cc = 0; cc < 8; ++cc) {
+                    const int k = 2 * rg + r, j = j8 + cc;
+                    st_split(slot0, offk16(j, k), M[r][cc].x * sX);
+                    st_split(slot0, offk16(16 + j, k), M[r][cc].y * sX);
                 }
-            }
+        }
+        // S = A22 - A12^H X
+        if (!run(s1, s0)) { timed_out = true; return false; }
+        {
+            float sv[16], a22[16];
+            cprod_read<CONJ_A>(dread, exp2i(-(e12 + eX)), pp, sv);
+            ld_row(pA22, pp, ii, a22);
 #pragma unroll
-            for (int cc = 0; cc < 8; ++cc) N2[r][cc] = make_float2(v[0][cc], -v[1][cc]);
+            for (int t = 0; t < 4; ++t)
+                *reinterpret_cast<float4 *>(pA22 + 256 * pp + pl16(ii, 4 * t)) =
+                    make_float4(a22[4 * t] - sv[4 * t], a22[4 * t + 1] - sv[4 * t + 1],
+                                a22[4 * t + 2] - sv[4 * t + 2], a22[4 * t + 3] - sv[4 * t + 3]);
+        }
+        // X as the B operand of Y X^H (rows (p, i) hold comp_p(X_ik), K = k),
+        // where the A12 tile was
+        if (right) st_chunk8(slot1, M, rg, 0, j8, sX);
+        __syncwarp();
+        // [S | X^H]: S from its planes; X^H_ki = conj(X_ik) from the X column
+        // tile (row k, K = i: the same rounded X the product above used)
+        if (!right) {
+            ld_blk8(pA22, M, rg, j8);
+        } else {
+            const float us = exp2i(-eX);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                float v[2][8];
+#pragma unroll
+                for (int pc = 0; pc < 2; ++pc) {
+                    const int o = offk16(16 * pc + 2 * rg + r, j8);
+                    const uint4 h = *reinterpret_cast<const uint4 *>(slot0 + o);
+                    const uint4 l = *reinterpret_cast<const uint4 *>(slot0 + SLOT_LO + o);
+                    const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const float2 hf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[t]));
+                        const float2 lf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[t]));
+                        v[pc][2 * t] = (hf.x + lf.x) * us;
+                        v[pc][2 * t + 1] = (hf.y + lf.y) * us;
+                    }
+                }
+#pragma unroll
+                for (int cc = 0; cc < 8; ++cc) M[r][cc] = make_float2(v[0][cc], -v[1][cc]);
+            }
         }
     }
-    __syncwarp();
-    // X as the A operand of nothing more and the B operand of Y X^H: rows
-    // (p, i) hold comp_p(X_ik), K = k
-    if (right) st_chunk8(slot0, M, rg, 0, j8, sX);
-    const float mp2 = gj_blk_invert<2, 8>(N2, scr, lane);      // N2 = [Q | Y^H]
+    float2 (&N2)[2][8] = M;                                     // [Q | Y^H]
 
     // Y^H through FP32 planes, so that lane (p, i) holds row i of Y
     if (right) st_blk8(pYH, N2, rg, j8);
@@ -644,9 +651,9 @@ __device__ __forceinline__ bool tc32_blocked_operator(int c, int e12, uint32_t s
     }
     __syncwarp();
     const int eY = scale_exp(warp_max(absmax16(yv)));
-    st_row16(slot1, 16 * pp + ii, yv, exp2i(eY));
+    st_row16(slot0, 16 * pp + ii, yv, exp2i(eY));
     // Z = Y X^H;  B11 = P + Z
-    if (!run(s1, s0)) { timed_out = true; return false; }
+    if (!run(s0, s1)) { timed_out = true; return false; }
     float bv[16];
     {
         float pv[16];
@@ -655,7 +662,7 @@ __device__ __forceinline__ bool tc32_blocked_operator(int c, int e12, uint32_t s
 #pragma unroll
         for (int j = 0; j < 16; ++j) bv[j] += pv[j];
     }
-    if (!(fminf(mp1, mp2) >= 0x1p-12f * dmax)) return false;   // FP64 retry
+    if (!(mp >= 0x1p-12f * dmax)) return false;                // FP64 retry
 
     // The operator tile: rows 64 (c & 1) + arow(p, u), K = v (two 16-byte
     // chunks per 8 columns), one scale for the whole inverse.
