@@ -78,6 +78,16 @@ constexpr int PART_LD = 20;        // floats per consensus partial row (16 used,
 __device__ __forceinline__ int off16(int row, int k) {
     return (row >> 3) * 512 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
+// Byte offset of 16-bit element (n, k) of a B operand tile with 64 rows n
+// and 32 contraction elements k stored MN-major: 8 consecutive n in 16
+// bytes, the 8 k of a block 16 bytes apart, 8-row blocks of n 128 B apart,
+// 8-deep blocks of k 1024 B apart.  The state tiles use it: a thread holds
+// one user k for all symbols n and stores them as 16-byte chunks, where the
+// K-major layout took one conflicting 2-byte store per symbol.
+__device__ __forceinline__ int offmn32(int n, int k) {
+    return (n >> 3) * 128 + (k >> 3) * 1024 + (k & 7) * 16 + (n & 7) * 2;
+}
+constexpr uint32_t TRANSPOSE_B = 1u << 16;      // instruction descriptor: B MN-major
 // Row of component p of user u inside a cluster's 64-row tile.
 __device__ __forceinline__ int arow(int p, int u) { return 32 * (u >> 4) + 16 * p + (u & 15); }
 
@@ -121,21 +131,27 @@ __device__ __forceinline__ uint32_t pack2(uint32_t a, uint32_t b) { return a | (
 // loses bits of terms added to a larger running sum (measured on sm_103a:
 // up to 5.8 units of 2^-24 sum|ab| with hi hi first, 1.8 with it last; an
 // FP32 FMA chain over the same 16 terms: 2.9).
+// B in K-major (B_MN false) or in the MN-major layout of offmn32 (B_MN true;
+// the instruction descriptor then sets transpose B): per K step of 16, two
+// 8-deep k blocks 1024 B apart (leading offset), 8-row n blocks 128 B apart
+// (stride offset).
+template <bool B_MN = false>
 __device__ __forceinline__ void mma_k32(uint32_t d, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo,
                                         uint32_t id, bool split) {
+    auto bd = [](uint32_t b, int ks) {
+        return B_MN ? tc5::sdesc(b + ks * 2048, 1024, 128) : tc5::sdesc(b + ks * 256, 128, 512);
+    };
     if (split) {
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks)
-            tc5::mma_f16(d, tc5::sdesc(a_lo + ks * 256, 128, 512), tc5::sdesc(b_hi + ks * 256, 128, 512), id,
-                         ks > 0 ? 1u : 0u);
+            tc5::mma_f16(d, tc5::sdesc(a_lo + ks * 256, 128, 512), bd(b_hi, ks), id, ks > 0 ? 1u : 0u);
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks)
-            tc5::mma_f16(d, tc5::sdesc(a_hi + ks * 256, 128, 512), tc5::sdesc(b_lo + ks * 256, 128, 512), id, 1u);
+            tc5::mma_f16(d, tc5::sdesc(a_hi + ks * 256, 128, 512), bd(b_lo, ks), id, 1u);
     }
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks)
-        tc5::mma_f16(d, tc5::sdesc(a_hi + ks * 256, 128, 512), tc5::sdesc(b_hi + ks * 256, 128, 512), id,
-                     (split || ks > 0) ? 1u : 0u);
+        tc5::mma_f16(d, tc5::sdesc(a_hi + ks * 256, 128, 512), bd(b_hi, ks), id, (split || ks > 0) ? 1u : 0u);
 }
 
 __device__ __forceinline__ float warp_max(float v) {
@@ -770,7 +786,7 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
     const uint32_t ybytes = (uint32_t)N * (uint32_t)B * EB;    // y[w]: N rows x B
     const uint32_t id_in = tc5::idesc(Op16<GOp>::fmt, 128, 64);     // matched filter
     const uint32_t id_gram = tc5::idesc(Op16<GOp>::fmt, 128, 128);  // Gram
-    const uint32_t id_op = tc5::idesc(tc5::FMT_F16, 128, 64);       // operator x state
+    const uint32_t id_op = tc5::idesc(tc5::FMT_F16, 128, 64) | TRANSPOSE_B;   // operator x state (MN-major)
     const float rho = p.f_rho, gam = p.f_gamma;
 
     auto wait_mma = [&]() {
@@ -826,16 +842,25 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
         for (int n = 0; n < NS; ++n) z[n] = (a[n] + (pp ? z[n] : -z[n])) * us;
     };
     // Write this thread's column (user uu, component pp) of the state tile
-    // V_c (B operand: rows 16 p' + n, K = user) for pair j, scaled by 2^ev.
+    // V_c (B operand, MN-major: rows n' = 32 cl + 16 p' + n, K = user) for
+    // pair j, scaled by 2^ev, as one 16-byte chunk per 8 symbols and half.
     auto put_state = [&](int j, const float (&v)[NS], float sv) {
         unsigned char *base = sm + VT + j * VT_PAIR;
 #pragma unroll
-        for (int n = 0; n < 16; ++n) {
-            uint32_t hi = 0, lo = 0;
-            if (n < NS && n < N) split16(v[n] * sv, hi, lo);
-            const int o = off16(32 * cl + 16 * pp + n, uu);
-            *reinterpret_cast<uint16_t *>(base + o) = (uint16_t)hi;
-            *reinterpret_cast<uint16_t *>(base + VT_LO + o) = (uint16_t)lo;
+        for (int h = 0; h < 2; ++h) {
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int n = 8 * h + 2 * t;
+                uint32_t ha = 0, la = 0, hb = 0, lb = 0;
+                if (n < NS && n < N) split16(v[n] * sv, ha, la);
+                if (n + 1 < NS && n + 1 < N) split16(v[n + 1] * sv, hb, lb);
+                hw[t] = pack2(ha, hb);
+                lw[t] = pack2(la, lb);
+            }
+            const int o = offmn32(32 * cl + 16 * pp + 8 * h, uu);
+            *reinterpret_cast<uint4 *>(base + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4 *>(base + VT_LO + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
         }
     };
     // Largest |v| over the CTA (every thread passes its values; 0 if none).
@@ -1141,7 +1166,7 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
                 tc5::fence_after_sync();
                 for (int j = 0; j < npairs; ++j) {
                     const uint32_t a = sbase + HT + j * HT_PAIR, b = sbase + VT + j * VT_PAIR;
-                    mma_k32(tbase + 64 * j, a, a + HT_LO, b, b + VT_LO, id_op, true);
+                    mma_k32<true>(tbase + 64 * j, a, a + HT_LO, b, b + VT_LO, id_op, true);
                 }
                 tc5::commit(bar_mma);
             }
