@@ -98,13 +98,16 @@ def parse_args(argv=None):
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-rows", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the served p50/p99 of the mixed comparison")
-    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time every launch choice first (dbp_autotune) and run the fastest; by default the "
+                         "library's automatic choice runs, named through dbp_plan")
+    ap.add_argument("--no-autotune", action="store_true", help="the default; kept for older command lines")
     ap.add_argument("--serve-frames", type=int, default=24)
     ap.add_argument("--study", action="append", default=[], choices=list(STUDIES) + ["all"],
                     help="optional studies, written to the details file")
     ap.add_argument("--details", default=None, help="JSON file for the detailed results")
     ap.add_argument("--kernel", choices=["auto", "tc5", "tma", "generic", "mma", "bcast"], default="auto",
-                    help="force one kernel path (default: automatic choice, autotuned)")
+                    help="force one kernel path (default: the automatic choice)")
     ap.add_argument("--head-subcarriers", type=int, default=None,
                     help="subcarriers of the headline frame (default 3300); smaller frames keep ncu captures short, "
                          "and a line measured on one names its size in config.workload")
@@ -865,7 +868,7 @@ def bench_serving(dbp, h, args):
     rng = np.random.default_rng(123)
     specs = serve_channels(rng)
     chans = [ServeChannel(dbp, sp, rng) for sp in specs]
-    tuned = None if args.no_autotune else autotune_served_shapes(dbp, h, chans)
+    tuned = autotune_served_shapes(dbp, h, chans) if args.autotune else None
     n = args.serve_frames
     kinds = [int(k) for k in rng.choice([dbp.DBP_KIND_UPLINK_ADMM, dbp.DBP_KIND_UPLINK_CG,
                                          dbp.DBP_KIND_DOWNLINK_ADMM], size=n, p=[0.4, 0.3, 0.3])]
@@ -1314,12 +1317,15 @@ def main(argv=None) -> int:
     precs = [("fp32", dbp.DBP_FP32)] + ([] if args.no_mixed else [("fp16", dbp.DBP_FP16), ("bf16", dbp.DBP_BF16)])
     sets = {name: FrameSet(frames, name, device) for name, _ in precs}
     tuned = {}
-    if args.kernel == "auto" and not args.no_autotune:
+    if args.kernel == "auto":
         for name, prec in precs:
             H, y, f = sets[name].bufs[0]
             x, lab = sets[name].out[0]
-            t = dbp.dbp_autotune(h, dbp.DBP_KIND_UPLINK_ADMM, desc_of(prec)(f), H, y, x, lab,
-                                 launching.cuda_stream, 5)
+            if args.autotune:
+                t = dbp.dbp_autotune(h, dbp.DBP_KIND_UPLINK_ADMM, desc_of(prec)(f), H, y, x, lab,
+                                     launching.cuda_stream, 5)
+            else:       # the automatic choice, as the calls will resolve it
+                t = dbp.dbp_plan(h, dbp.DBP_KIND_UPLINK_ADMM, desc_of(prec)(f), H, y, x)
             tuned[name] = PATH_NAMES.get(t.kernel, str(t.kernel))
         torch.cuda.synchronize(device)
     K = args.steps

@@ -424,6 +424,20 @@ dbp_status dbp_autotune_clear(dbp_handle_t h);
 dbp_status dbp_autotune_save(dbp_handle_t h, const char *path);
 dbp_status dbp_autotune_load(dbp_handle_t h, const char *path);
 
+/* The launch choice that dbp_uplink_admm / dbp_uplink_cg /
+ * dbp_downlink_admm (by `kind`) would make now for this descriptor and these
+ * device buffers: the handle's tuning, else the autotuned choice for the
+ * frame's shape, else the AUTO rule of dbp_kernel_path, resolved into
+ * *chosen (may be NULL): a concrete kernel path (never DBP_PATH_AUTO), the
+ * mapping, cluster_size (1 for the CTA mapping), warps_per_cta (the CTA's
+ * warps) and prefactor (DBP_PREFACTOR_ON or _OFF).  Launches nothing and
+ * reads no buffer: the pointers count only through their alignment (16-byte
+ * alignment admits the bulk-copy and tensor-core kernels).  Returns what the
+ * call would return for a descriptor or tuning it rejects
+ * (DBP_ERR_INVALID_ARG, DBP_ERR_UNSUPPORTED), with dbp_last_error set. */
+dbp_status dbp_plan(dbp_handle_t h, int32_t kind, const dbp_frame_desc *d, const void *H, const void *in,
+                    const void *out, dbp_tuning *chosen);
+
 /* ------------------------------------------------------------------------
  * Graphs: a batch of frames of any kinds and shapes (device buffers)
  * captured once into one CUDA graph and then run by a single launch.  The

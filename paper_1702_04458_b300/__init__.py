@@ -374,6 +374,20 @@ def dbp_autotune(h, kind, d, H, inp, out, labels=None, stream=None, reps: int = 
     return t
 
 
+_lib.dbp_plan.restype = _S
+_lib.dbp_plan.argtypes = [_H, ctypes.c_int32, ctypes.POINTER(dbp_frame_desc), ctypes.c_void_p, ctypes.c_void_p,
+                          ctypes.c_void_p, ctypes.POINTER(dbp_tuning)]
+
+
+def dbp_plan(h, kind, d, H, inp, out) -> dbp_tuning:
+    """The launch choice a call of this kind would make for these buffers
+    (kernel path, mapping, cluster size, warps per CTA, separate operator
+    kernel), resolved without launching anything."""
+    t = dbp_tuning()
+    _check(h, _lib.dbp_plan(h, kind, ctypes.byref(d), _ptr(H), _ptr(inp), _ptr(out), ctypes.byref(t)))
+    return t
+
+
 def dbp_autotune_clear(h) -> None:
     _check(h, _lib.dbp_autotune_clear(h))
 

@@ -697,6 +697,19 @@ bool stream_capturing(cudaStream_t st) {
 // budget (dbp_config.hbm_budget_bytes; 0 = no limit).
 bool budget_allows(const dbp_context *h, size_t bytes) { return h->budget == 0 || h->used + bytes <= h->budget; }
 
+// The handle's tuning; when fully automatic, an autotuned choice for this
+// frame shape (dbp_autotune) if there is one.
+dbp_tuning resolve_tuning(dbp_context *h, const dbp_frame_desc *d, Kind kind) {
+    std::lock_guard<std::mutex> lk(h->tune_mu);
+    dbp_tuning tune = h->tuning;
+    if (tune.kernel == DBP_PATH_AUTO && tune.mapping == DBP_MAP_AUTO && tune.warps_per_cta == 0 &&
+        tune.cluster_size == 0 && tune.prefactor == DBP_PREFACTOR_AUTO) {
+        auto it = h->tuned.find(dbp_tune_key(d, kind));
+        if (it != h->tuned.end()) tune = it->second;
+    }
+    return tune;
+}
+
 dbp_status run_ex(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void *H, const void *vin,
                   void *out, uint8_t *labels, double *beta_out, cudaStream_t st, const DbpExec *ex,
                   bool *factor_used) {
@@ -710,18 +723,7 @@ dbp_status run_ex(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void
         return fail(h, DBP_ERR_INVALID_ARG, "data pointers must be aligned to the element size");
     Shape s;
     const bool a16 = aligned(H, 16) && aligned(vin, 16) && aligned(out, 16);
-    // the handle's tuning; when fully automatic, an autotuned choice for
-    // this frame shape (dbp_autotune) if there is one
-    dbp_tuning tune;
-    {
-        std::lock_guard<std::mutex> lk(h->tune_mu);
-        tune = h->tuning;
-        if (tune.kernel == DBP_PATH_AUTO && tune.mapping == DBP_MAP_AUTO && tune.warps_per_cta == 0 &&
-            tune.cluster_size == 0 && tune.prefactor == DBP_PREFACTOR_AUTO) {
-            auto it = h->tuned.find(dbp_tune_key(d, kind));
-            if (it != h->tuned.end()) tune = it->second;
-        }
-    }
+    const dbp_tuning tune = resolve_tuning(h, d, kind);
     v = choose_shape(h, d, kind, a16, s, tune, ex && ex->factor && ex->factor_mode != 0);
     if (v != DBP_OK) return v;
     cudaError_t e = cudaSetDevice(h->device);
@@ -935,6 +937,33 @@ dbp_status dbp_validate_internal(dbp_context *h, const dbp_frame_desc *d, int ki
     return r;
 }
 
+// The launch choice of a device-buffer call with these arguments, as the
+// tuning it resolves to (dbp_plan).
+dbp_status dbp_plan_internal(dbp_context *h, const dbp_frame_desc *d, int kind, const void *H, const void *vin,
+                             const void *out, dbp_tuning *chosen) {
+    dbp_status v = validate(h, d, (Kind)kind);
+    if (v != DBP_OK) return v;
+    const bool a16 = aligned(H, 16) && aligned(vin, 16) && aligned(out, 16);
+    const dbp_tuning tune = resolve_tuning(h, d, (Kind)kind);
+    Shape s;
+    v = choose_shape(h, d, (Kind)kind, a16, s, tune);
+    if (v != DBP_OK) return v;
+    dbp_tuning r{};
+    r.kernel = s.tc32 ? DBP_PATH_TC5
+             : (s.tc8 || s.tcdl) ? DBP_PATH_MMA
+             : s.bcast ? DBP_PATH_BCAST
+             : s.tma ? DBP_PATH_TMA
+                     : DBP_PATH_GENERIC;
+    r.mapping = s.clu ? DBP_MAP_CLUSTER : DBP_MAP_CTA;
+    r.cluster_size = s.clu ? s.CL : 1;
+    r.warps_per_cta = s.nwarps;
+    r.prefactor = (tune.prefactor == DBP_PREFACTOR_ON && prefactor_available(d, (Kind)kind, s, next_pow2_ut(d->U)))
+                      ? DBP_PREFACTOR_ON
+                      : DBP_PREFACTOR_OFF;
+    if (chosen) *chosen = r;
+    return DBP_OK;
+}
+
 size_t dbp_in_elem_bytes(int prec) { return elem_bytes(prec); }
 size_t dbp_out_elem_bytes(int prec) { return out_bytes(prec); }
 int dbp_padded_users(int U) { return next_pow2_ut(U); }
@@ -1006,6 +1035,14 @@ dbp_status dbp_set_tuning(dbp_handle_t h, const dbp_tuning *t) {
     std::lock_guard<std::mutex> lk(h->tune_mu);
     h->tuning = *t;
     return DBP_OK;
+}
+
+dbp_status dbp_plan(dbp_handle_t h, int32_t kind, const dbp_frame_desc *d, const void *H, const void *in,
+                    const void *out, dbp_tuning *chosen) {
+    if (!h) return DBP_ERR_INVALID_ARG;
+    if (!d || kind < DBP_KIND_UPLINK_ADMM || kind > DBP_KIND_DOWNLINK_ADMM)
+        return fail(h, DBP_ERR_INVALID_ARG, "dbp_plan: NULL descriptor or unknown kind");
+    return dbp_plan_internal(h, d, kind, H, in, out, chosen);
 }
 
 dbp_status dbp_device_status(dbp_handle_t h) {

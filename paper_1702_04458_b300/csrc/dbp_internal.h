@@ -57,6 +57,8 @@ dbp_status dbp_run_internal(dbp_context *h, const dbp_frame_desc *d, int kind, c
                             void *out, uint8_t *labels, double *beta_out, cudaStream_t st, const DbpExec *ex,
                             bool *factor_used, std::string *err);
 dbp_status dbp_validate_internal(dbp_context *h, const dbp_frame_desc *d, int kind, std::string *err);
+dbp_status dbp_plan_internal(dbp_context *h, const dbp_frame_desc *d, int kind, const void *H, const void *vin,
+                             const void *out, dbp_tuning *chosen);
 // Whether a call with tuning t would run the separate operator kernel
 // (DBP_PREFACTOR_ON on a shape where it is available).
 bool dbp_prefactor_applies(dbp_context *h, const dbp_frame_desc *d, int kind, const dbp_tuning &t, const void *H,

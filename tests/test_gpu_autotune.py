@@ -92,3 +92,47 @@ def test_autotune_rejects_bad_requests(dbp, handle):
     with pytest.raises(dbp.DbpError) as ei:
         dbp.dbp_autotune(handle, dbp.DBP_KIND_UPLINK_ADMM, d, H, y, x)
     assert ei.value.status == dbp.DBP_ERR_INVALID_ARG
+
+
+def test_plan_resolves_the_automatic_choice(dbp, handle):
+    """dbp_plan names the kernel AUTO runs (tcgen05 at U = S = 32, the U = 8
+    tensor-core kernel), and forcing the planned tuning reproduces the
+    automatic call bit for bit."""
+    K = dbp.DBP_KIND_UPLINK_ADMM
+    d, H, y = _ul(dbp, 40, 14, 256, 8, 32, 64, 3, seed=1900)
+    x = torch.zeros((d.W, d.N, 32), dtype=torch.complex64, device="cuda")
+    p = dbp.dbp_plan(handle, K, d, H, y, x)
+    assert p.kernel == dbp.DBP_PATH_TC5 and p.mapping == dbp.DBP_MAP_CTA and p.cluster_size == 1
+    assert p.prefactor == dbp.DBP_PREFACTOR_OFF and p.warps_per_cta == 8
+    auto = _run(dbp, handle, dbp.dbp_uplink_admm, d, H, y, 32)
+    dbp.dbp_set_tuning(handle, p.mapping, 0, 0, p.kernel, p.prefactor)
+    forced = _run(dbp, handle, dbp.dbp_uplink_admm, d, H, y, 32)
+    dbp.dbp_set_tuning(handle)
+    assert torch.equal(auto[0], forced[0]) and torch.equal(auto[1], forced[1])
+    # the U = 8 frame
+    d8, H8, y8 = _ul(dbp, 30, 14, 128, 8, 8, 16, 3, seed=1901)
+    x8 = torch.zeros((d8.W, d8.N, 8), dtype=torch.complex64, device="cuda")
+    assert dbp.dbp_plan(handle, K, d8, H8, y8, x8).kernel == dbp.DBP_PATH_MMA
+    # a handle tuning is reported as resolved, never as AUTO
+    dbp.dbp_set_tuning(handle, dbp.DBP_MAP_CTA, 0, 0, dbp.DBP_PATH_TMA, dbp.DBP_PREFACTOR_AUTO)
+    p = dbp.dbp_plan(handle, K, d, H, y, x)
+    dbp.dbp_set_tuning(handle)
+    assert p.kernel == dbp.DBP_PATH_TMA and p.prefactor == dbp.DBP_PREFACTOR_OFF
+
+
+def test_plan_follows_the_autotuned_table_and_rejects_what_calls_reject(dbp, handle):
+    K = dbp.DBP_KIND_UPLINK_ADMM
+    d, H, y = _ul(dbp, 200, 14, 128, 8, 8, 16, 3, seed=1902)
+    x = torch.zeros((d.W, d.N, 8), dtype=torch.complex64, device="cuda")
+    best = dbp.dbp_autotune(handle, K, d, H, y, x, None, reps=2)
+    p = dbp.dbp_plan(handle, K, d, H, y, x)
+    assert p.kernel == best.kernel
+    dbp.dbp_autotune_clear(handle)
+    with pytest.raises(dbp.DbpError) as ei:
+        dbp.dbp_plan(handle, 7, d, H, y, x)
+    assert ei.value.status == dbp.DBP_ERR_INVALID_ARG
+    dbp.dbp_set_tuning(handle, dbp.DBP_MAP_AUTO, 0, 0, dbp.DBP_PATH_TC5, dbp.DBP_PREFACTOR_AUTO)
+    with pytest.raises(dbp.DbpError) as ei:
+        dbp.dbp_plan(handle, K, d, H, y, x)            # U = 8: no tcgen05 kernel
+    dbp.dbp_set_tuning(handle)
+    assert ei.value.status == dbp.DBP_ERR_UNSUPPORTED
