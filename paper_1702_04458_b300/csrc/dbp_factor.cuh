@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kFactorWarps * 32) dbp_factor_tcdl_kernel(cons
         stage_block(wb, Hg + ((size_t)w * p.B + (size_t)c * p.S) * UT * 8, p.S, UT * 8, UT * 8, lane);
         __syncwarp();
         float2 A[8];
-        tcdl_operator(Hs, p.S, Qs, Vb, lane, p.f_delta, p.delta, true, p.retries, A);
+        tcdl_operator(Hs, p.S, tcdl_h_scale(Hs, p.S, lane), Qs, Vb, lane, p.f_delta, p.delta, true, p.retries, A);
         float2 *frow = p.factor + ((size_t)task * UT + ur) * UT + 8 * gc;
 #pragma unroll
         for (int i = 0; i < 8; i += 2)

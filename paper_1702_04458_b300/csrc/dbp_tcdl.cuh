@@ -9,10 +9,17 @@
 //   * per iteration m_c = H^d_c x_c = v_c - rho^{-1} B_c^{-1} v_c with
 //     v_c = z_c + lambda_c (x_c = H^{dH}_c B_c^{-1} v_c, push-through), the
 //     product B_c^{-1} v_c for 16 symbol slots being a 32 x 32 x 16 real
-//     product (2 m-tiles of 8 users, real parts over imaginary parts, 4
-//     k-steps, 2 n-tiles of 8 symbols), three mma.sync.m16n8k8 TF32 products
-//     per k-step with the operands split into TF32 parts (dbp_tma.cuh);
+//     product (2 m-tiles of 8 users, real parts over imaginary parts, 2
+//     k-steps of 8 complex entries, 2 n-tiles of 8 symbols);
 //   * the output x_c = H^{dH}_c B_c^{-1} v_c, an (S x 16) x (16 x 16) product.
+// Every product is mma.sync.m16n8k16 with FP16 operands and FP32
+// accumulators, three per k-step: each FP32 operand is scaled by a power of
+// two (its warp's largest magnitude into [2^13, 2^14)), split into FP16 hi
+// and lo halves, and the products lo hi, hi lo, hi hi are accumulated in
+// that order (small terms first); the scales are exact and are divided out.
+// In a k-step of the complex embedding, lane (g, t) holds one complex entry
+// per register: (re, im) for a real row and (-im, re) for the imaginary
+// row below it, so one hi / lo split serves both rows.
 // The consensus w = sum_c (m_c - lambda_c) and (s - w)/C run once per symbol:
 // warp c reduces the units c, c + C, ... of 32 (symbol, user) entries and
 // broadcasts d = (s - w)/C, scaled by max{0, 1 - eps/||s - w||} for eps > 0
@@ -35,7 +42,7 @@ namespace dbp {
 struct TcDl {
     static constexpr int U = 16;
     static constexpr int NS = 16;            // symbol slots per pass
-    static constexpr int VPD = 18;           // state pitch (complex): conflict-free B fragment loads
+    static constexpr int VPD = 20;           // state pitch (complex), 4 mod 16: conflict-free B fragment loads
     static constexpr int QP = 18;            // operator pitch (complex)
     static constexpr int CP = 20;            // contrib / broadcast pitch (complex)
     static constexpr int CE = NS * CP;
@@ -45,24 +52,106 @@ __host__ __device__ constexpr size_t tcdl_cta_bytes(int nwarps, int P) {
     return (size_t)nwarps * TcDl::CE * 8 + 2 * (size_t)P * TcDl::CE * 8 + (size_t)nwarps * 16;
 }
 
-// A fragment values (before splitting) of H_c^H for the k-step of antenna
-// rows s0..s0+3, rows u (real parts) and u (imaginary parts); H_c has 16
-// users per row.
-__device__ __forceinline__ void hh16_frag(const float2 *Hs, int s0, int u, int t, float (&a)[4]) {
-    const float2 h0 = Hs[(s0 + (t >> 1)) * 16 + u];
-    const float2 h1 = Hs[(s0 + 2 + (t >> 1)) * 16 + u];
-    const bool odd = t & 1;
-    a[0] = odd ? h0.y : h0.x;
-    a[1] = odd ? h0.x : -h0.y;
-    a[2] = odd ? h1.y : h1.x;
-    a[3] = odd ? h1.x : -h1.y;
+// Power-of-two exponent e with m 2^e in [2^13, 2^14) (0 for 0 or a
+// non-finite m), clamped to [-60, 60] so that the sum of two exponents is a
+// normal power of two: FP16 operands keep 11 significant bits in hi and 11
+// more in lo for every entry within 2^-17 of the largest.
+__device__ __forceinline__ int dl16_scale_exp(float m) {
+    if (!(m > 0.f) || !(m < 3.0e38f)) return 0;
+    int e;
+    frexpf(m, &e);
+    e = 14 - e;
+    return e < -60 ? -60 : (e > 60 ? 60 : e);
+}
+__device__ __forceinline__ float dl16_exp2i(int e) { return __int_as_float((127 + e) << 23); }
+__device__ __forceinline__ float dl16_warp_max(float m) {
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) m = fmaxf(m, shfl_x(m, k));
+    return m;
+}
+__device__ __forceinline__ float cabsmax(float2 v) { return fmaxf(fabsf(v.x), fabsf(v.y)); }
+
+// FP16 hi / lo halves of (re, im) scaled by sc, packed as f16x2 (re in the
+// low half): hi = fp16(x sc), lo = fp16(x sc - hi).
+__device__ __forceinline__ void dl16_split(float re, float im, float sc, uint32_t &hi, uint32_t &lo) {
+    const float a = re * sc, b = im * sc;
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+// (re, im) -> (-im, re) on a packed f16x2 (exact; the halves of a negated
+// value are the negated halves).
+__device__ __forceinline__ uint32_t dl16_rot(uint32_t x) { return __byte_perm(x, 0u, 0x1032) ^ 0x00008000u; }
+
+__device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// D += A B over K = 16 from hi / lo halves: lo hi, hi lo, then hi hi.
+__device__ __forceinline__ void mma3h(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4], uint32_t bh0,
+                                      uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+    mma_f16(d, al, bh0, bh1);
+    mma_f16(d, ah, bl0, bl1);
+    mma_f16(d, ah, bh0, bh1);
+}
+// A fragment of one k-step from two complex entries x0 (column 2t, 2t + 1 of
+// the real embedding) and x1 (the same, 8 further), given as the real row's
+// (re, im) coefficients: registers 1 and 3 are the imaginary row's.
+__device__ __forceinline__ void dl16_afrag(float2 x0, float2 x1, float sc, uint32_t (&ah)[4], uint32_t (&al)[4]) {
+    dl16_split(x0.x, x0.y, sc, ah[0], al[0]);
+    dl16_split(x1.x, x1.y, sc, ah[2], al[2]);
+    ah[1] = dl16_rot(ah[0]);
+    al[1] = dl16_rot(al[0]);
+    ah[3] = dl16_rot(ah[2]);
+    al[3] = dl16_rot(al[2]);
 }
 
-// m = Q v: Q (B_c^{-1}) as A fragments (hi, lo) [m-tile][k-step][4], v [16 symbols][VPD]
-// in shared memory; result in the accumulator layout m[mt][nt][q].
-__device__ __forceinline__ void tcdl_apply(const uint32_t (&qh)[2][4][4], const uint32_t (&ql)[2][4][4],
+// Scale exponent of H_c (S x 16, row pitch 16) for its FP16 split.
+__device__ __forceinline__ int tcdl_h_scale(const float2 *Hs, int S, int lane) {
+    float m = 0.f;
+    for (int i = lane; i < S * TcDl::U; i += 32) m = fmaxf(m, cabsmax(Hs[i]));
+    return dl16_scale_exp(dl16_warp_max(m));
+}
+
+// B fragments of a 16 x 16 state held as [symbol][VPD] (complex): lane (g, t)
+// of n-tile nt, k-step ks takes symbol 8 nt + g, entries 8 ks + t and
+// 8 ks + t + 4, split with one scale for the warp; returns the exponent.
+__device__ __forceinline__ int dl16_bfrag(const float2 *Vb, int g, int t, uint32_t (&bh)[2][2][2],
+                                          uint32_t (&bl)[2][2][2]) {
+    float2 v[2][2][2];
+    float mv = 0.f;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                v[nt][ks][hh] = Vb[(8 * nt + g) * TcDl::VPD + 8 * ks + 4 * hh + t];
+                mv = fmaxf(mv, cabsmax(v[nt][ks][hh]));
+            }
+    const int ev = dl16_scale_exp(dl16_warp_max(mv));
+    const float sv = dl16_exp2i(ev);
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) dl16_split(v[nt][ks][hh].x, v[nt][ks][hh].y, sv, bh[nt][ks][hh], bl[nt][ks][hh]);
+    return ev;
+}
+
+// m = Q v: Q (B_c^{-1}, scale 2^eq) as A fragments (hi, lo) [m-tile][k-step][4],
+// v [16 symbols][VPD] in shared memory; result in the accumulator layout
+// m[mt][nt][q] (user 8 mt + g, symbol 8 nt + 2 t + q).
+__device__ __forceinline__ void tcdl_apply(const uint32_t (&qh)[2][2][4], const uint32_t (&ql)[2][2][4], int eq,
                                            const float2 *Vb, int g, int t, float2 (&m)[2][2][2]) {
-    const float *sf = reinterpret_cast<const float *>(Vb) + (g * TcDl::VPD + (t >> 1)) * 2 + (t & 1);
+    uint32_t bh[2][2][2], bl[2][2][2];
+    const int ev = dl16_bfrag(Vb, g, t, bh, bl);
     float acc[2][2][4];
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
@@ -71,22 +160,19 @@ __device__ __forceinline__ void tcdl_apply(const uint32_t (&qh)[2][4][4], const 
 #pragma unroll
             for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.f;
 #pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
+    for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            uint32_t bh0, bl0, bh1, bl1;
-            split3(sf[(8 * nt * TcDl::VPD + 4 * ks) * 2], bh0, bl0);
-            split3(sf[(8 * nt * TcDl::VPD + 4 * ks + 2) * 2], bh1, bl1);
+        for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-            for (int mt = 0; mt < 2; ++mt) mma3(acc[mt][nt], qh[mt][ks], ql[mt][ks], bh0, bh1, bl0, bl1);
-        }
-    }
+            for (int mt = 0; mt < 2; ++mt)
+                mma3h(acc[mt][nt], qh[mt][ks], ql[mt][ks], bh[nt][ks][0], bh[nt][ks][1], bl[nt][ks][0], bl[nt][ks][1]);
+    const float us = dl16_exp2i(-(eq + ev));
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt) {
-            m[mt][nt][0] = make_float2(acc[mt][nt][0], acc[mt][nt][2]);
-            m[mt][nt][1] = make_float2(acc[mt][nt][1], acc[mt][nt][3]);
+            m[mt][nt][0] = make_float2(acc[mt][nt][0] * us, acc[mt][nt][2] * us);
+            m[mt][nt][1] = make_float2(acc[mt][nt][1] * us, acc[mt][nt][3] * us);
         }
 }
 
@@ -134,20 +220,24 @@ __device__ __forceinline__ float gj_split16_s(float2 (&A)[8], int u, int g, floa
 
 
 // B_c^{-1} of Alg. 3 for one cluster from the staged H_c (S x 16, row pitch
-// 16): the Gram conj(H_c^H H_c) on the tensor cores (3 x TF32), plus delta on
-// the diagonal, row-major into Qs (pitch QP), then the column-split
+// 16, scale exponent eh from tcdl_h_scale): the Gram conj(H_c^H H_c) on the
+// tensor cores (FP16 hi / lo, three products per k-step of 8 antennas), plus
+// delta on the diagonal, row-major into Qs (pitch QP), then the column-split
 // Gauss-Jordan; lane (ur, gc) returns entries (ur, 8 gc + i) of the inverse in
 // A.  An FP32 pivot below 2^-12 of the largest diagonal entry recomputes this
 // cluster's B_c and its inverse in FP64 (counted in *retries; Vb is scratch).
 // Shared by the downlink kernel and the operator kernel (dbp_factor.cuh).
-__device__ __forceinline__ void tcdl_operator(const float2 *Hs, int S, float2 *Qs, float2 *Vb, int lane, float f_delta,
-                                              double delta, bool valid, unsigned int *retries, float2 (&A)[8]) {
+__device__ __forceinline__ void tcdl_operator(const float2 *Hs, int S, int eh, float2 *Qs, float2 *Vb, int lane,
+                                              float f_delta, double delta, bool valid, unsigned int *retries,
+                                              float2 (&A)[8]) {
     using C2 = float2;
     constexpr int QP = TcDl::QP;
     const int g = lane >> 2, t = lane & 3;
     const int ur = lane & 15, gc = lane >> 4;
     // Gram G = H_c^H H_c on the tensor cores: m-tile mt = users
-    // 8 mt .. 8 mt + 7 (rows), n-tile nt = users 8 nt .. (columns).
+    // 8 mt .. 8 mt + 7 (rows), n-tile nt = users 8 nt .. (columns), K =
+    // antennas s0 + t and s0 + t + 4 of each k-step (re, im interleaved).
+    const float sh = dl16_exp2i(eh);
     float gacc[2][2][4];
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
@@ -155,24 +245,27 @@ __device__ __forceinline__ void tcdl_operator(const float2 *Hs, int S, float2 *Q
         for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
             for (int i = 0; i < 4; ++i) gacc[mt][nt][i] = 0.f;
-    for (int s0 = 0; s0 < S; s0 += 4) {
+    for (int s0 = 0; s0 < S; s0 += 8) {
         uint32_t ah[2][4], al[2][4];
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            float a[4];
-            hh16_frag(Hs, s0, 8 * mt + g, t, a);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) split3(a[i], ah[mt][i], al[mt][i]);
-        }
-        // the B fragment of H_c for n-tile nt holds the values a[0], a[2]
-        // of m-tile nt; block (1, 0) is the conjugate transpose of block
+        for (int mt = 0; mt < 2; ++mt)
+            dl16_afrag(Hs[(s0 + t) * 16 + 8 * mt + g], Hs[(s0 + t + 4) * 16 + 8 * mt + g], sh, ah[mt], al[mt]);
+        // the B fragment of H_c for n-tile nt is registers 0 and 2 of m-tile
+        // nt's A fragment; block (1, 0) is the conjugate transpose of block
         // (0, 1) (the Gram is Hermitian) and is not multiplied
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
             for (int nt = mt; nt < 2; ++nt)
-                mma3(gacc[mt][nt], ah[mt], al[mt], ah[nt][0], ah[nt][2], al[nt][0], al[nt][2]);
+                mma3h(gacc[mt][nt], ah[mt], al[mt], ah[nt][0], ah[nt][2], al[nt][0], al[nt][2]);
     }
+    const float ug = dl16_exp2i(-2 * eh);
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) gacc[mt][nt][i] *= ug;
     // B_c = conj(G) + delta I, row-major into Qs
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
@@ -293,6 +386,8 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
         }
         const C2 *Hs = reinterpret_cast<const C2 *>(wb + (b ? p.off_h1 : 0));
 
+        const int eh = tcdl_h_scale(Hs, S, lane);       // H_c's FP16 scale (Gram and output)
+
         // ---- B_c^{-1} into Qs ----
         C2 *frow = (p.factor != nullptr && valid) ? p.factor + (((size_t)w * C + c) * U + ur) * U + 8 * gc : nullptr;
         if (p.factor_mode == 2) {
@@ -305,7 +400,7 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
             }
         } else {
             C2 A[8];
-            tcdl_operator(Hs, S, Qs, Vb, lane, p.f_delta, p.delta, valid, p.retries, A);
+            tcdl_operator(Hs, S, eh, Qs, Vb, lane, p.f_delta, p.delta, valid, p.retries, A);
 #pragma unroll
             for (int i = 0; i < 8; ++i) Qs[ur * QP + 8 * gc + i] = A[i];
             if (p.factor_mode == 1 && frow != nullptr) {
@@ -316,22 +411,32 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
         }
         __syncwarp();
 
-        // A fragments (hi, lo) of B_c^{-1}: lane (g, t) needs entries
-        // [8 mt + g][4 ks + t/2] and [8 mt + g][4 ks + 2 + t/2] with the
-        // general complex embedding.
-        uint32_t qh[2][4][4], ql[2][4][4];
+        // A fragments (hi, lo) of B_c^{-1}: lane (g, t) takes entries
+        // [8 mt + g][8 ks + t] and [8 mt + g][8 ks + t + 4] as the real row's
+        // coefficients (Re Q, -Im Q); one scale for the warp
+        uint32_t qh[2][2][4], ql[2][2][4];
+        int eq;
+        {
+            C2 qv[2][2][2];
+            float mq = 0.f;
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
+            for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-                const C2 o0 = Qs[(8 * mt + g) * QP + 4 * ks + (t >> 1)];
-                const C2 o1 = Qs[(8 * mt + g) * QP + 4 * ks + 2 + (t >> 1)];
-                const bool odd = t & 1;
-                split3(odd ? -o0.y : o0.x, qh[mt][ks][0], ql[mt][ks][0]);
-                split3(odd ? o0.x : o0.y, qh[mt][ks][1], ql[mt][ks][1]);
-                split3(odd ? -o1.y : o1.x, qh[mt][ks][2], ql[mt][ks][2]);
-                split3(odd ? o1.x : o1.y, qh[mt][ks][3], ql[mt][ks][3]);
-            }
+                for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        qv[mt][ks][hh] = Qs[(8 * mt + g) * QP + 8 * ks + 4 * hh + t];
+                        mq = fmaxf(mq, cabsmax(qv[mt][ks][hh]));
+                    }
+            eq = dl16_scale_exp(dl16_warp_max(mq));
+            const float sq = dl16_exp2i(eq);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks)
+                    dl16_afrag(make_float2(qv[mt][ks][0].x, -qv[mt][ks][0].y),
+                               make_float2(qv[mt][ks][1].x, -qv[mt][ks][1].y), sq, qh[mt][ks], ql[mt][ks]);
+        }
 
         for (int n0 = 0; n0 < N; n0 += TcDl::NS) {
             const int nv = min(TcDl::NS, N - n0);
@@ -345,8 +450,9 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
             }
             __syncthreads();
 
-            // Init: z_c = kappa s, lambda_c = 0, v_c = z_c
-            C2 lam[2][2][2];
+            // Init: z_c = kappa s, lambda_c = 0, v_c = z_c (v_c also kept in
+            // registers, in the accumulator layout)
+            C2 lam[2][2][2], vr[2][2][2];
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -354,14 +460,15 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
                         const int u = 8 * mt + g, n = 8 * nt + 2 * t + q;
-                        Vb[n * VPD + u] = cscale(ss[n * CP + u], kap);
+                        vr[mt][nt][q] = cscale(ss[n * CP + u], kap);
+                        Vb[n * VPD + u] = vr[mt][nt][q];
                         lam[mt][nt][q] = make_float2(0.f, 0.f);
                     }
             __syncwarp();
 
             for (int iter = 2; iter <= p.T; ++iter) {
                 C2 m[2][2][2];
-                tcdl_apply(qh, ql, Vb, g, t, m);                  // B_c^{-1} v_c
+                tcdl_apply(qh, ql, eq, Vb, g, t, m);              // B_c^{-1} v_c
                 // m_c = H_c x_c = v_c - rho^{-1} B_c^{-1} v_c
 #pragma unroll
                 for (int mt = 0; mt < 2; ++mt)
@@ -369,7 +476,7 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
                     for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
                         for (int q = 0; q < 2; ++q) {
-                            const C2 v = Vb[(8 * nt + 2 * t + q) * VPD + 8 * mt + g];
+                            const C2 v = vr[mt][nt][q];
                             m[mt][nt][q].x = fmaf(-ir, m[mt][nt][q].x, v.x);
                             m[mt][nt][q].y = fmaf(-ir, m[mt][nt][q].y, v.y);
                         }
@@ -412,7 +519,8 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
                             C2 &l = lam[mt][nt][q];
                             l.x = fmaf(-gam, m[mt][nt][q].x - z.x, l.x);
                             l.y = fmaf(-gam, m[mt][nt][q].y - z.y, l.y);
-                            Vb[n * VPD + u] = cadd(z, l);         // v_c = z_c + lambda_c
+                            vr[mt][nt][q] = cadd(z, l);           // v_c = z_c + lambda_c
+                            Vb[n * VPD + u] = vr[mt][nt][q];
                         }
                 __syncwarp();
             }
@@ -420,7 +528,7 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
             // Output x_c = H^{dH}_c B_c^{-1} v_c
             {
                 C2 tt[2][2][2];
-                tcdl_apply(qh, ql, Vb, g, t, tt);
+                tcdl_apply(qh, ql, eq, Vb, g, t, tt);
                 __syncwarp();
 #pragma unroll
                 for (int mt = 0; mt < 2; ++mt)
@@ -431,28 +539,24 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
                 __syncwarp();
             }
             C2 *xo = reinterpret_cast<C2 *>(p.out);
-            const float *tf = reinterpret_cast<const float *>(Vb) + (g * VPD + (t >> 1)) * 2 + (t & 1);
+            uint32_t th[2][2][2], tl[2][2][2];          // B fragments of B_c^{-1} v_c
+            const int et = dl16_bfrag(Vb, g, t, th, tl);
+            const float sh = dl16_exp2i(eh), ux = dl16_exp2i(-eh) * dl16_exp2i(-et);
             for (int sa = 0; sa < S; sa += 8) {
-                // m-tile of antennas sa .. sa+7: A = H^{dH}_c, A[s'][u] = conj(H_c[s'][u])
+                // m-tile of antennas sa .. sa+7: A = H^{dH}_c, A[s'][u] = conj(H_c[s'][u]),
+                // the real row's coefficients (Re H, Im H)
                 float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
-                for (int ks = 0; ks < 4; ++ks) {
-                    const C2 h0 = Hs[(sa + g) * U + 4 * ks + (t >> 1)];
-                    const C2 h1 = Hs[(sa + g) * U + 4 * ks + 2 + (t >> 1)];
-                    const bool odd = t & 1;
+                for (int ks = 0; ks < 2; ++ks) {
                     uint32_t ah[4], al[4];
-                    split3(odd ? h0.y : h0.x, ah[0], al[0]);      // Re block: (Re H, Im H)
-                    split3(odd ? h0.x : -h0.y, ah[1], al[1]);     // Im block: (-Im H, Re H)
-                    split3(odd ? h1.y : h1.x, ah[2], al[2]);
-                    split3(odd ? h1.x : -h1.y, ah[3], al[3]);
+                    dl16_afrag(Hs[(sa + g) * U + 8 * ks + t], Hs[(sa + g) * U + 8 * ks + 4 + t], sh, ah, al);
 #pragma unroll
-                    for (int nt = 0; nt < 2; ++nt) {
-                        uint32_t bh0, bl0, bh1, bl1;
-                        split3(tf[(8 * nt * VPD + 4 * ks) * 2], bh0, bl0);
-                        split3(tf[(8 * nt * VPD + 4 * ks + 2) * 2], bh1, bl1);
-                        mma3(acc[nt], ah, al, bh0, bh1, bl0, bl1);
-                    }
+                    for (int nt = 0; nt < 2; ++nt) mma3h(acc[nt], ah, al, th[nt][ks][0], th[nt][ks][1], tl[nt][ks][0], tl[nt][ks][1]);
                 }
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[nt][i] *= ux;
                 if (valid) {
 #pragma unroll
                     for (int nt = 0; nt < 2; ++nt)
