@@ -47,15 +47,18 @@ template <int UT> __host__ __device__ constexpr size_t admm_cta_bytes(int nwarps
 // entry and of the inverse on exit; returns the smallest pivot's real part
 // (identical on every lane).
 //
-// Step k with pivot p = A[k][k] and f_u = A[u][k]: every column j != k takes
-// the same multiply-add A[u][j] -= m_u A[k][j] with m_u = f_u / p for the
-// other rows and m_k = 1 - 1/p for the pivot row (A[k][j] - (1 - 1/p) A[k][j]
-// = A[k][j] / p), so only the lanes holding column k take a different value
-// there (1/p on the pivot row, -f_u / p elsewhere).
+// Step k with pivot p = A[k][k] and f_u = A[u][k]: every other row takes
+// A[u][j] -= (f_u / p) A[k][j] for j != k and A[u][k] = -f_u / p.  The pivot
+// row is left as it is, with A[k][k] = 1, and is divided by its pivot once,
+// after the last step: a row that has been a pivot row stays p times the
+// row of the textbook order through every later step, so the result is the
+// same, and no step forms 1 - 1/p (which loses the row's significant bits
+// when |p| is large).
 template <int UT>
 __device__ __forceinline__ float gj_split(float2 (&A)[Split<UT>::CPG], int u, int g) {
     using SP = Split<UT>;
     float min_piv = 3.4e38f;
+    float2 myinv = make_float2(1.f, 0.f);     // 1 / the pivot of row u's own step
 #pragma unroll
     for (int k = 0; k < UT; ++k) {
         const int gk = k / SP::CPG, ik = k % SP::CPG;
@@ -74,12 +77,14 @@ __device__ __forceinline__ float gj_split(float2 (&A)[Split<UT>::CPG], int u, in
         const float2 inv = make_float2(piv.x * dd, -piv.y * dd);
         const bool me = (u == k);
         const float2 fi = cmul(f, inv);                  // f_u / p
-        const float2 m = me ? make_float2(1.f - inv.x, -inv.y) : fi;
-        const float2 nm = make_float2(-m.x, -m.y);
+        const float2 nm = me ? make_float2(0.f, 0.f) : make_float2(-fi.x, -fi.y);
+        if (me) myinv = inv;
 #pragma unroll
         for (int i = 0; i < SP::CPG; ++i) cmac(A[i], nm, rk[i]);
-        if (g % SP::NG == gk) A[ik] = me ? inv : make_float2(-fi.x, -fi.y);
+        if (g % SP::NG == gk) A[ik] = me ? make_float2(1.f, 0.f) : make_float2(-fi.x, -fi.y);
     }
+#pragma unroll
+    for (int i = 0; i < SP::CPG; ++i) A[i] = cmul(A[i], myinv);
     return min_piv;
 }
 

@@ -85,8 +85,11 @@ __device__ __forceinline__ void llr_stats_store(const LlrParams &p, float Auu, i
 // Step k publishes row k (lane k of every warp, its 8 entries) and column k
 // (warp k / 8) in one of two buffers of buf (2 x 64 complex, 16-byte
 // aligned) and every thread updates its 8 entries; one CTA barrier per step.
-// No pivoting (every pivot is a Schur complement of an HPD matrix).
+// No pivoting (every pivot is a Schur complement of an HPD matrix).  The
+// pivot row of a step is left as it is (its column-k entry set to 1) and
+// divided by its pivot after the last step, as in gj_split.
 __device__ __forceinline__ void gj_cols32(float2 (&A)[8], int u, int w, float2 *buf) {
+    float2 myinv = make_float2(1.f, 0.f);     // 1 / the pivot of row u's own step
 #pragma unroll 1
     for (int wk = 0; wk < 4; ++wk) {
 #pragma unroll
@@ -109,13 +112,15 @@ __device__ __forceinline__ void gj_cols32(float2 (&A)[8], int u, int w, float2 *
             const float2 inv = make_float2(piv.x * dd, -piv.y * dd);
             const bool me = (u == k);
             const float2 fi = cmul(f, inv);                  // f_u / p
-            const float2 m = me ? make_float2(1.f - inv.x, -inv.y) : fi;
-            const float2 nm = make_float2(-m.x, -m.y);
+            const float2 nm = me ? make_float2(0.f, 0.f) : make_float2(-fi.x, -fi.y);
+            if (me) myinv = inv;
 #pragma unroll
             for (int i = 0; i < 8; ++i) cmac(A[i], nm, rk[i]);
-            if (w == wk) A[ik] = me ? inv : make_float2(-fi.x, -fi.y);
+            if (w == wk) A[ik] = me ? make_float2(1.f, 0.f) : make_float2(-fi.x, -fi.y);
         }
     }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) A[i] = cmul(A[i], myinv);
 }
 
 template <int UT, int HALF>

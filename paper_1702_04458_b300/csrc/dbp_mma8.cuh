@@ -38,11 +38,13 @@ __device__ __forceinline__ void hh_frag(const float2 *Hs, int s0, int g, int t, 
 // Gauss-Jordan inversion of the 8 x 8 Hermitian positive definite matrix
 // whose row g, columns 2t and 2t+1, lane (g, t) holds in (e0, e1).  No
 // pivoting (every pivot is a Schur complement of an HPD matrix).  The pivot
-// row reaches the other lanes by shuffles.  Returns the smallest pivot's
-// real part.
+// row reaches the other lanes by shuffles.  The pivot row of a step is left
+// as it is (its column-k entry set to 1) and divided by its pivot after the
+// last step, as in gj_split.  Returns the smallest pivot's real part.
 template <typename C2, typename T>
 __device__ __forceinline__ T gj8(C2 &e0, C2 &e1, int g, int t) {
     T min_piv = (T)3.0e38;
+    C2 myinv = mkc((T)1, (T)0);          // 1 / the pivot of row g's own step
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         C2 P0, P1, pk, mk;
@@ -69,20 +71,17 @@ __device__ __forceinline__ T gj8(C2 &e0, C2 &e1, int g, int t) {
             inv = crcp(pk);
         }
         const bool me = (g == k);
-        C2 f;
-        if (me) {
-            f.x = (T)1 - inv.x;
-            f.y = -inv.y;
-        } else {
-            f = cmul(mk, inv);
-        }
-        const C2 nf = mkc(-f.x, -f.y);
-        const C2 colk = me ? inv : nf;
+        const C2 f = cmul(mk, inv);
+        const C2 nf = me ? mkc((T)0, (T)0) : mkc(-f.x, -f.y);
+        const C2 colk = me ? mkc((T)1, (T)0) : nf;
+        if (me) myinv = inv;
         if (2 * t == k) e0 = colk;
         else cmac(e0, nf, P0);
         if (2 * t + 1 == k) e1 = colk;
         else cmac(e1, nf, P1);
     }
+    e0 = cmul(e0, myinv);
+    e1 = cmul(e1, myinv);
     return min_piv;
 }
 

@@ -187,6 +187,7 @@ __device__ __forceinline__ void tcdl_apply(const uint32_t (&qh)[2][2][4], const 
 // turn, so one __syncwarp per step suffices.
 __device__ __forceinline__ float gj_split16_s(float2 (&A)[8], int u, int g, float2 *sc) {
     float min_piv = 3.4e38f;
+    float2 myinv = make_float2(1.f, 0.f);     // 1 / the pivot of row u's own step
     __syncwarp();   // every lane has loaded its row before the buffers are written
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -209,12 +210,14 @@ __device__ __forceinline__ float gj_split16_s(float2 (&A)[8], int u, int g, floa
         const float2 inv = make_float2(piv.x * dd, -piv.y * dd);
         const bool me = (u == k);
         const float2 fi = cmul(f, inv);                  // f_u / p
-        const float2 m = me ? make_float2(1.f - inv.x, -inv.y) : fi;
-        const float2 nm = make_float2(-m.x, -m.y);
+        const float2 nm = me ? make_float2(0.f, 0.f) : make_float2(-fi.x, -fi.y);
+        if (me) myinv = inv;
 #pragma unroll
         for (int i = 0; i < 8; ++i) cmac(A[i], nm, rk[i]);
-        if (g == gk) A[ik] = me ? inv : make_float2(-fi.x, -fi.y);
+        if (g == gk) A[ik] = me ? make_float2(1.f, 0.f) : make_float2(-fi.x, -fi.y);
     }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) A[i] = cmul(A[i], myinv);
     return min_piv;
 }
 
