@@ -299,32 +299,45 @@ class ClockSampler:
 # Peaks, traffic records
 # ---------------------------------------------------------------------------
 
-def kernel_source_hash() -> str:
-    """Hash of the kernels' device code (the .cuh headers that define them;
-    the .cu files hold host code and instantiations) with comments and
-    blank space removed, the key of the ncu traffic records."""
+# The header that defines each roofline kernel (keys of the traffic records).
+KERNEL_HEADERS = {"admm_ul_u32_tc5": "dbp_tc32.cuh", "admm_ul_u32_tma": "dbp_tma.cuh",
+                  "admm_dl": "dbp_tcdl.cuh", "admm_ul": "dbp_tc8.cuh", "cg_ul": "dbp_tc8.cuh"}
+
+
+def kernel_source_hash(kernel: str, csrc: str = None) -> str:
+    """Hash of one kernel's device code, the key of its ncu traffic record:
+    the header that defines it and every header it includes, transitively,
+    with comments and blank space removed (the .cu files hold host code and
+    instantiations).  A change elsewhere leaves the record valid."""
     import re
-    csrc = os.path.join(ROOT, "paper_1702_04458_b300", "csrc")
+    csrc = csrc or os.path.join(ROOT, "paper_1702_04458_b300", "csrc")
+    todo, seen = [KERNEL_HEADERS[kernel]], set()
+    while todo:
+        name = todo.pop()
+        if name in seen:
+            continue
+        seen.add(name)
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
+            todo += re.findall(r'#include "([A-Za-z0-9_]+\.cuh)"', f.read())
     h = hashlib.sha256()
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith(".cuh"):
-            with open(os.path.join(csrc, name), encoding="utf-8") as f:
-                code = f.read()
-            code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
-            code = re.sub(r"//[^\n]*", " ", code)
-            code = " ".join(code.split())
-            h.update(name.encode())
-            h.update(code.encode())
+    for name in sorted(seen):
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
+            code = f.read()
+        code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        code = " ".join(code.split())
+        h.update(name.encode())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
+    the kernel's current sources (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel not in KERNEL_HEADERS:
         return None
-    src = kernel_source_hash()
+    src = kernel_source_hash(kernel)
     for line in open(path):
         f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
         if f.get("kernel") == kernel and f.get("src") == src:
