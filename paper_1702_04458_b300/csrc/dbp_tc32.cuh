@@ -168,105 +168,116 @@ __device__ __forceinline__ void ld32(uint32_t taddr, float (&a)[32]) {
 
 }  // namespace tc32
 
-// In-register Gauss-Jordan elimination of an NR x NC matrix [A | R], NR =
-// 8 RB, NC = 4 CB, with A (the first NR columns) Hermitian positive
-// definite, held by one warp as RB x CB blocks: lane l = 4 rg + cg owns rows
-// RB rg .. RB rg + RB - 1 and columns CB cg .. CB cg + CB - 1 (M[r][c]).  It
-// leaves [A^{-1} | A^{-1} R] in place (just A^{-1} when NC = NR).  Step k
-// (k < NR): the lanes holding column k publish it (colbuf), the lanes holding
-// row k publish it (rowbuf), every lane updates its block with the rank-1
-// term f_i m_kj, f_i = m_ik / m_kk, and the owners of column k write the new
-// column (-f_i; 1 on the pivot row, whose row stays multiplied by its pivot
-// until the final scaling).  Buffers alternate between steps (2 (NR + 4 CB
-// + 8) float2: 896 bytes for RB = 2, CB = 8), so one warp barrier per step
-// orders writes and reads.  The step
-// loop is unrolled by CB so every register index is static.  Returns the
-// smallest pivot (real part).
-template <int RB, int CB>
-__device__ __forceinline__ float gj_blk_invert(float2 (&A)[RB][CB], float2 *buf, int lane) {
-    constexpr int NN = 8 * RB, NC = 4 * CB;
-    // The pivot row is published as four groups of CB entries, one per
-    // column group cg, CBP = CB + 2 entries apart: 16-byte aligned, and with
-    // 80-byte strides (CB = 8) the four groups sit in different banks, so the
-    // row's broadcast loads and stores are free of bank conflicts (with 64-
-    // byte strides groups 0 and 2, 1 and 3 collide).
-    constexpr int CBP = CB + 2;
-    static_assert(NC >= NN && NN % CB == 0 && CB % RB == 0 && RB % 2 == 0, "8 x 4 lane grid of RB x CB blocks");
+// Gauss-Jordan inversion of the 16 x 32 block [A | R] (A HPD: no pivoting,
+// every pivot is a Schur complement) into [A^{-1} | A^{-1} R], in registers:
+// lane (rg, cg) = (lane / 4, lane % 4) holds rows 2 rg, 2 rg + 1 and columns
+// 8 cg .. 8 cg + 7.  Two pivots per round: a lane's two rows are one pivot
+// pair.  Round m takes the
+// pivot block P = A[K][K] of K = {2m, 2m + 1}: every row i outside K takes
+// A[i][j] -= M_i A[K][j] with M_i = A[i][K] P^{-1} (the two scalar steps of
+// the pair at once) and A[i][K] = -M_i; the pair's rows are left as they
+// are, with A[K][K] = I, and multiplied by P^{-1} after the last round.  The
+// exchange (pivot rows and columns through shared memory) happens once per
+// pair, so there are half as many rounds.  buf: 112 complex (two pivot
+// rows with 80-byte groups, two pivot columns), 16-byte aligned.  Returns
+// the smallest real part of the scalar pivots (P00 and its Schur complement
+// P11 - P10 P01 / P00, the pivots of the one-pivot-per-step order).
+__device__ __forceinline__ float gj_pair_invert(float2 (&A)[2][8], float2 *buf, int lane) {
+    constexpr int CB = 8, CBP = 10;
     const int rg = lane >> 2, cg = lane & 3;
+    float2 *rowb = buf;                 // [2][4 CBP]: pivot rows, group cg at CBP cg
+    float2 *colb = buf + 8 * CBP;       // [2][16]: pivot columns
     float min_piv = 3.0e38f;
-    float2 myinv[RB];
-#pragma unroll
-    for (int r = 0; r < RB; ++r) myinv[r] = make_float2(1.f, 0.f);
+    float2 q00 = make_float2(1.f, 0.f), q01 = make_float2(0.f, 0.f), q10 = q01, q11 = q00;   // this pair's P^{-1}
 #pragma unroll 1
-    for (int k0 = 0; k0 < NN; k0 += CB) {
+    for (int blk = 0; blk < 2; ++blk) {
 #pragma unroll
-        for (int kk = 0; kk < CB; ++kk) {
-            const int k = k0 + kk;
-            const int rr = kk % RB;                 // pivot row inside its block
-            float2 *colbuf = buf + (kk & 1) * (NN + 4 * CBP), *rowbuf = colbuf + NN;
-            const bool ownc = (cg == k0 / CB), ownr = (rg == k / RB);
+        for (int h = 0; h < 4; ++h) {
+            const int m = 4 * blk + h, k = 2 * m, kk = 2 * h;
+            const bool ownc = (cg == blk), ownr = (rg == m);
             if (ownc) {
-#pragma unroll
-                for (int r = 0; r < RB; r += 2)
-                    *reinterpret_cast<float4 *>(&colbuf[RB * rg + r]) =
-                        make_float4(A[r][kk].x, A[r][kk].y, A[r + 1][kk].x, A[r + 1][kk].y);
+                *reinterpret_cast<float4 *>(&colb[2 * rg]) =
+                    make_float4(A[0][kk].x, A[0][kk].y, A[1][kk].x, A[1][kk].y);
+                *reinterpret_cast<float4 *>(&colb[16 + 2 * rg]) =
+                    make_float4(A[0][kk + 1].x, A[0][kk + 1].y, A[1][kk + 1].x, A[1][kk + 1].y);
             }
             if (ownr) {
 #pragma unroll
-                for (int c = 0; c < CB; c += 2)
-                    *reinterpret_cast<float4 *>(&rowbuf[CBP * cg + c]) =
-                        make_float4(A[rr][c].x, A[rr][c].y, A[rr][c + 1].x, A[rr][c + 1].y);
+                for (int e = 0; e < 2; ++e)
+#pragma unroll
+                    for (int c = 0; c < CB; c += 2)
+                        *reinterpret_cast<float4 *>(&rowb[4 * CBP * e + CBP * cg + c]) =
+                            make_float4(A[e][c].x, A[e][c].y, A[e][c + 1].x, A[e][c + 1].y);
             }
             __syncwarp();
-            const float2 pk = colbuf[k];
-            min_piv = fminf(min_piv, pk.x);
-            const float d = __frcp_rn(fmaf(pk.x, pk.x, pk.y * pk.y));
-            const float2 inv = make_float2(pk.x * d, -pk.y * d);
-            float2 f[RB], pr[CB];
+            float2 p00, p10, p01, p11, f0[2], f1[2];
+            ld2(&colb[k], p00, p10);                // column k, rows k and k + 1
+            ld2(&colb[16 + k], p01, p11);           // column k + 1
+            ld2(&colb[2 * rg], f0[0], f0[1]);       // my rows in column k
+            ld2(&colb[16 + 2 * rg], f1[0], f1[1]);  // ... and in column k + 1
+            // P^{-1} through the two scalar pivots p00 and s = p11 - p10 p01 / p00
+            // (never det P, whose square leaves the FP32 range long before
+            // the pivots' do): with a = p01 / p00, b = p10 / p00,
+            // P^{-1} = [1/p00 + a b / s, -a / s; -b / s, 1 / s]
+            const float d0 = __frcp_rn(fmaf(p00.x, p00.x, p00.y * p00.y));
+            const float2 i0 = make_float2(p00.x * d0, -p00.y * d0);
+            const float2 a = cmul(p01, i0), b = cmul(p10, i0);
+            float2 sp = p11;
+            cmac(sp, make_float2(-p10.x, -p10.y), a);
+            const float d1 = __frcp_rn(fmaf(sp.x, sp.x, sp.y * sp.y));
+            const float2 r11 = make_float2(sp.x * d1, -sp.y * d1);
+            const float2 r01 = cmul(make_float2(-a.x, -a.y), r11), r10 = cmul(make_float2(-b.x, -b.y), r11);
+            float2 r00 = i0;
+            cmac(r00, make_float2(-r01.x, -r01.y), b);
+            min_piv = fminf(min_piv, fminf(p00.x, sp.x));
+            if (ownr) {
+                q00 = r00;
+                q01 = r01;
+                q10 = r10;
+                q11 = r11;
+            }
+            float2 n0[2], n1[2];            // -M_i (0 on the pair's own rows)
 #pragma unroll
-            for (int r = 0; r < RB; r += 2) {
-                float2 a, b;
-                ld2(&colbuf[RB * rg + r], a, b);
-                f[r] = a;
-                f[r + 1] = b;
+            for (int r = 0; r < 2; ++r) {
+                float2 m0 = cmul(f0[r], r00), m1 = cmul(f0[r], r01);
+                cmac(m0, f1[r], r10);
+                cmac(m1, f1[r], r11);
+                n0[r] = ownr ? make_float2(0.f, 0.f) : make_float2(-m0.x, -m0.y);
+                n1[r] = ownr ? make_float2(0.f, 0.f) : make_float2(-m1.x, -m1.y);
             }
 #pragma unroll
             for (int c = 0; c < CB; c += 2) {
-                float2 a, b;
-                ld2(&rowbuf[CBP * cg + c], a, b);
-                pr[c] = a;
-                pr[c + 1] = b;
-            }
+                float2 a0, a1, b0, b1;
+                ld2(&rowb[CBP * cg + c], a0, a1);
+                ld2(&rowb[4 * CBP + CBP * cg + c], b0, b1);
 #pragma unroll
-            for (int r = 0; r < RB; ++r) {
-                const bool piv = ownr && (r == rr);
-                const float2 a = f[r];
-                f[r] = piv ? make_float2(0.f, 0.f) : make_float2(a.x * inv.x - a.y * inv.y, a.x * inv.y + a.y * inv.x);
-                if (piv) myinv[r] = inv;
-            }
-#pragma unroll
-            for (int r = 0; r < RB; ++r) {
-                const float2 nf = make_float2(-f[r].x, -f[r].y);
-#pragma unroll
-                for (int c = 0; c < CB; ++c) cmac(A[r][c], nf, pr[c]);
+                for (int r = 0; r < 2; ++r) {
+                    cmac(A[r][c], n0[r], a0);
+                    cmac(A[r][c], n1[r], b0);
+                    cmac(A[r][c + 1], n0[r], a1);
+                    cmac(A[r][c + 1], n1[r], b1);
+                }
             }
             if (ownc) {
 #pragma unroll
-                for (int r = 0; r < RB; ++r) {
-                    const bool piv = ownr && (r == rr);
-                    A[r][kk] = piv ? make_float2(1.f, 0.f) : make_float2(-f[r].x, -f[r].y);
+                for (int r = 0; r < 2; ++r) {
+                    A[r][kk] = ownr ? make_float2(r == 0 ? 1.f : 0.f, 0.f) : n0[r];
+                    A[r][kk + 1] = ownr ? make_float2(r == 1 ? 1.f : 0.f, 0.f) : n1[r];
                 }
             }
-            __syncwarp();
+            __syncwarp();       // every lane has read the buffers before the next round writes them
         }
     }
+    // the pair's rows multiplied by its P^{-1}
 #pragma unroll
-    for (int r = 0; r < RB; ++r)
-#pragma unroll
-        for (int c = 0; c < CB; ++c) {
-            const float2 a = A[r][c];
-            A[r][c] = make_float2(a.x * myinv[r].x - a.y * myinv[r].y, a.x * myinv[r].y + a.y * myinv[r].x);
-        }
+    for (int c = 0; c < CB; ++c) {
+        const float2 a0 = A[0][c], a1 = A[1][c];
+        float2 x0 = cmul(q00, a0), x1 = cmul(q10, a0);
+        cmac(x0, q01, a1);
+        cmac(x1, q11, a1);
+        A[0][c] = x0;
+        A[1][c] = x1;
+    }
     return min_piv;
 }
 
@@ -591,7 +602,7 @@ __device__ __forceinline__ bool tc32_blocked_operator(int c, int e12, uint32_t s
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
         __syncwarp();
-        mp = fminf(mp, gj_blk_invert<2, 8>(M, scr, lane));
+        mp = fminf(mp, gj_pair_invert(M, scr, lane));
         if (pass == 1) break;
         // P as FP32 planes (for B11); X as the B operand of A12^H X: rows
         // (p', j) hold comp_p'(X_kj), K = k (a column of X per row: 2-byte
