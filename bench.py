@@ -339,6 +339,8 @@ def recorded_traffic(kernel: str):
         return None
     src = kernel_source_hash(kernel)
     for line in open(path):
+        if line.lstrip().startswith("#"):
+            continue        # comments and superseded records
         f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
         if f.get("kernel") == kernel and f.get("src") == src:
             return float(f["bytes_per_launch"])
