@@ -156,7 +156,9 @@ typedef enum dbp_kernel_path {
                                   aligned buffers, CTA mapping               */
     DBP_PATH_MMA = 3,          /* FP32, C <= 16, every dense product (Gram,
                                   matched filter, operator x state, output)
-                                  on the tensor cores, 3 x TF32 per product,
+                                  on the tensor cores (three products per
+                                  FP32 product: TF32 halves at U = 8, FP16
+                                  halves with power-of-two scales at U = 16),
                                   consensus as DBP_PATH_BCAST: uplink ADMM and
                                   CG with U = 8 and even S; downlink ADMM with
                                   U = 16 and S a multiple of 8               */
