@@ -292,9 +292,14 @@ dbp_status dbp_uplink_llr(dbp_handle_t h, const dbp_frame_desc *d, const void *H
 
 /* Host-memory variants (end-to-end path): the same computations with every
  * buffer in host memory.  The call copies the inputs to library-owned
- * device buffers on `stream`, runs the kernels, copies the outputs back
- * and synchronises `stream` before returning.  Pinned host memory gives
- * the fastest copies; pageable memory also works. */
+ * device buffers, runs the kernels, copies the outputs back and returns
+ * when all of it is done, ordered after the work already on `stream` (and
+ * `stream` waits for it).  Frames of 512 subcarriers or more without a
+ * whole-frame pass (all but a normalised downlink) run in up to 8 chunks of
+ * subcarriers on three library-owned streams, so that input copies, kernels
+ * and output copies overlap; the results are those of one launch, bit for
+ * bit.  Pinned host memory gives the fastest copies (and the overlap);
+ * pageable memory also works. */
 dbp_status dbp_uplink_admm_host(dbp_handle_t h, const dbp_frame_desc *d,
                                 const void *H, const void *y, void *x_hat,
                                 uint8_t *labels, void *stream);

@@ -30,7 +30,11 @@ FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
 
 
 def _deps_mtime() -> float:
-    files = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    """Newest header any translation unit may include (the kernels' .cuh, the
+    library's internal .h, the public header): an object older than it is
+    rebuilt, so no object keeps an outdated struct layout."""
+    files = (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
+             glob.glob(os.path.join(INCLUDE, "*.h")))
     return max(os.path.getmtime(f) for f in files)
 
 

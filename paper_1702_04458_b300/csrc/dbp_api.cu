@@ -863,6 +863,47 @@ dbp_status ensure_dev(dbp_context *h, int slot, size_t bytes) {
     return DBP_OK;
 }
 
+// Synchronise `st` and report a kernel that gave up waiting (the device
+// status word), clearing it.
+dbp_status check_status(dbp_context *h, cudaStream_t st) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    int word = 0;
+    if ((e = cudaMemcpy(&word, h->status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(h, e, "read status");
+    if (word != 0) {
+        cudaMemset(h->status, 0, sizeof(int));
+        return fail(h, DBP_ERR_TIMEOUT, "a kernel gave up waiting for its input copies (status 0x%x)", word);
+    }
+    return DBP_OK;
+}
+
+// Streams and events of the chunked host variants, created on first use.
+dbp_status pipe_resources(dbp_context *h) {
+    for (cudaStream_t &q : h->pipe)
+        if (!q) {
+            const cudaError_t e = cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreateWithFlags");
+        }
+    for (cudaEvent_t &ev : h->pipe_ev)
+        if (!ev) {
+            const cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventCreateWithFlags");
+        }
+    return DBP_OK;
+}
+
+// Subcarriers per chunk of a host-buffer frame: up to kPipeMax chunks of at
+// least 256 subcarriers, each a multiple of 16 (so every chunk's buffers keep
+// the whole frame's 16-byte alignment and run the same kernel path); 0 when
+// the frame is too small to gain from overlapping.
+long long pipe_chunk(long long W) {
+    long long k = W / 256;
+    if (k > dbp_context::kPipeMax) k = dbp_context::kPipeMax;
+    if (k < 2) return 0;
+    return ((W + k - 1) / k + 15) / 16 * 16;
+}
+
 dbp_status run_host(dbp_context *h, const dbp_frame_desc *d, Kind kind, const void *H, const void *vin,
                     void *out, uint8_t *labels, double *beta_out, cudaStream_t st) {
     dbp_status v = validate(h, d, kind);
@@ -887,6 +928,67 @@ dbp_status run_host(dbp_context *h, const dbp_frame_desc *d, Kind kind, const vo
     if ((v = ensure_dev(h, 3, lab_pad + (want_beta ? 16 : 0))) != DBP_OK) return v;
     uint8_t *dlab = want_labels ? (uint8_t *)h->dev[3] : nullptr;
     double *dbeta = want_beta ? (double *)((char *)h->dev[3] + lab_pad) : nullptr;
+    // A frame without a whole-frame pass (no downlink power normalisation)
+    // runs in chunks of subcarriers: the input copies of chunk i + 1, the
+    // kernel of chunk i and the output copies of chunk i - 1 overlap (the two
+    // copy directions and the SMs work at once).  Subcarriers are
+    // independent, so the results are those of one launch, bit for bit.
+    const long long cs = (kind == K_ADMM_DL && (d->flags & DBP_FLAG_NORMALIZE)) ? 0 : pipe_chunk((long long)W);
+    if (cs > 0) {
+        if ((v = pipe_resources(h)) != DBP_OK) return v;
+        cudaStream_t qin = h->pipe[0], qk = h->pipe[1], qout = h->pipe[2];
+        cudaEvent_t *ev = h->pipe_ev;     // [0] start, [1 + i] inputs, [1 + kPipeMax + i] kernel, [last] end
+        const int last = 2 * dbp_context::kPipeMax + 1;
+        // the copies follow the work already on the caller's stream
+        if ((e = cudaEventRecord(ev[0], st)) != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
+        if ((e = cudaStreamWaitEvent(qin, ev[0], 0)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamWaitEvent");
+        const size_t hrow = B * U * eb;                                   // H bytes per subcarrier
+        const size_t irow = (kind == K_ADMM_DL) ? N * U * eb : N * B * eb;   // input bytes per subcarrier
+        const size_t orow = (kind == K_ADMM_DL) ? N * B * ob : N * U * ob;   // output bytes per subcarrier
+        const size_t lrow = want_labels ? N * U : 0;
+        dbp_status r = DBP_OK;
+        int i = 0;
+        for (long long w0 = 0; w0 < (long long)W; w0 += cs, ++i) {
+            const long long wn = std::min(cs, (long long)W - w0);
+            const char *hs = static_cast<const char *>(H) + w0 * hrow;
+            const char *is = static_cast<const char *>(vin) + w0 * irow;
+            char *hd = static_cast<char *>(h->dev[0]) + w0 * hrow;
+            char *id = static_cast<char *>(h->dev[1]) + w0 * irow;
+            char *od = static_cast<char *>(h->dev[2]) + w0 * orow;
+            uint8_t *ld = dlab ? dlab + w0 * lrow : nullptr;
+            if ((e = cudaMemcpyAsync(hd, hs, wn * hrow, cudaMemcpyHostToDevice, qin)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(id, is, wn * irow, cudaMemcpyHostToDevice, qin)) != cudaSuccess ||
+                (e = cudaEventRecord(ev[1 + i], qin)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(qk, ev[1 + i], 0)) != cudaSuccess) {
+                r = cuda_fail(h, e, "chunk input copies");
+                break;
+            }
+            dbp_frame_desc dc = *d;
+            dc.W = (int32_t)wn;
+            if ((r = run(h, &dc, kind, hd, id, od, ld, nullptr, qk)) != DBP_OK) break;
+            if ((e = cudaEventRecord(ev[1 + dbp_context::kPipeMax + i], qk)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(qout, ev[1 + dbp_context::kPipeMax + i], 0)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(static_cast<char *>(out) + w0 * orow, od, wn * orow, cudaMemcpyDeviceToHost,
+                                     qout)) != cudaSuccess ||
+                (ld && (e = cudaMemcpyAsync(labels + w0 * lrow, ld, wn * lrow, cudaMemcpyDeviceToHost, qout)) !=
+                           cudaSuccess)) {
+                r = cuda_fail(h, e, "chunk output copies");
+                break;
+            }
+        }
+        // whatever was enqueued completes before the caller's buffers are released
+        if (r == DBP_OK) {
+            if ((e = cudaEventRecord(ev[last], qout)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(st, ev[last], 0)) != cudaSuccess)
+                r = cuda_fail(h, e, "cudaStreamWaitEvent");
+        }
+        for (cudaStream_t q : {qin, qk, qout}) {
+            const cudaError_t es = cudaStreamSynchronize(q);
+            if (es != cudaSuccess && r == DBP_OK) r = cuda_fail(h, es, "cudaStreamSynchronize");
+        }
+        if (r != DBP_OK) return r;
+        return check_status(h, st);
+    }
     if ((e = cudaMemcpyAsync(h->dev[0], H, bH, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(h, e, "copy H");
     if ((e = cudaMemcpyAsync(h->dev[1], vin, bin, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(h, e, "copy input");
     v = run(h, d, kind, h->dev[0], h->dev[1], h->dev[2], dlab, dbeta, st);
@@ -896,15 +998,7 @@ dbp_status run_host(dbp_context *h, const dbp_frame_desc *d, Kind kind, const vo
         return cuda_fail(h, e, "copy labels");
     if (want_beta && (e = cudaMemcpyAsync(beta_out, dbeta, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(h, e, "copy beta");
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
-    int word = 0;
-    if ((e = cudaMemcpy(&word, h->status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
-        return cuda_fail(h, e, "read status");
-    if (word != 0) {
-        cudaMemset(h->status, 0, sizeof(int));
-        return fail(h, DBP_ERR_TIMEOUT, "a kernel gave up waiting for its input copies (status 0x%x)", word);
-    }
-    return DBP_OK;
+    return check_status(h, st);
 }
 
 }  // namespace
@@ -1018,6 +1112,10 @@ dbp_status dbp_destroy(dbp_handle_t h) {
     if (h->status) cudaFree(h->status);
     for (int i = 0; i < 4; ++i)
         if (h->dev[i]) cudaFree(h->dev[i]);
+    for (cudaStream_t &q : h->pipe)
+        if (q) cudaStreamDestroy(q);
+    for (cudaEvent_t &ev : h->pipe_ev)
+        if (ev) cudaEventDestroy(ev);
     // buffers still in flight go back when their frees complete
     if (h->factor_pool) cudaMemPoolDestroy(h->factor_pool);
     delete h;

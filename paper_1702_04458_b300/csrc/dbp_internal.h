@@ -26,6 +26,12 @@ struct dbp_context {
     int *status = nullptr;               // device status word of the kernels
     void *dev[4] = {nullptr, nullptr, nullptr, nullptr};   // host-variant buffers
     size_t dev_cap[4] = {0, 0, 0, 0};
+    // host variants in chunks: streams for the input copies, the kernels and
+    // the output copies, and their events (start, inputs and kernel of each
+    // chunk, end)
+    static constexpr int kPipeMax = 8;
+    cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t pipe_ev[2 * kPipeMax + 2] = {};
     dbp_server *server = nullptr;        // request loop (dbp_server_start)
     // autotuned launch choices per frame shape (kind, B, C, U, N, precision)
     std::mutex tune_mu;
