@@ -30,6 +30,8 @@ def handle(dbp):
 def _host_inputs(a, prec):
     if prec == "fp32":
         return np.ascontiguousarray(a.astype(np.complex64))
+    if prec == "fp64":
+        return np.ascontiguousarray(a.astype(np.complex128))
     return np.ascontiguousarray(np.stack([a.real, a.imag], -1).astype(np.float16))
 
 
@@ -39,6 +41,7 @@ UL_CASES = [
     ("cg", 1200, 128, 8, 8, 16, "fp32"),       # 4 chunks
     ("admm", 600, 256, 8, 32, 64, "fp32"),     # the tcgen05 kernel, 2 chunks
     ("admm", 600, 256, 8, 32, 64, "fp16"),
+    ("admm", 520, 32, 2, 4, 4, "fp64"),        # FP64 (generic kernel), 2 chunks of 272 and 248
 ]
 
 
@@ -46,15 +49,17 @@ UL_CASES = [
 def test_chunked_uplink_equals_device_call(dbp, handle, algo, W, B, C, U, M, prec):
     f = synth.uplink_frame(W, 14, B, U, M, 15.0, seed=9950 + W + U)
     H, y = _host_inputs(f["H"], prec), _host_inputs(f["y"], prec)
+    code = {"fp32": dbp.DBP_FP32, "fp16": dbp.DBP_FP16, "fp64": dbp.DBP_FP64}[prec]
     d = dbp.frame_desc(B, C, U, W, 14, qam_order=M, T_max=3 if algo == "admm" else 6,
-                       precision=dbp.DBP_FP32 if prec == "fp32" else dbp.DBP_FP16, N0=f["N0"], Es=1.0)
+                       precision=code, N0=f["N0"], Es=1.0)
+    ct = np.complex128 if prec == "fp64" else np.complex64
     fd = dbp.dbp_uplink_admm if algo == "admm" else dbp.dbp_uplink_cg
     fh = dbp.dbp_uplink_admm_host if algo == "admm" else dbp.dbp_uplink_cg_host
-    xd = torch.zeros((W, 14, U), dtype=torch.complex64, device="cuda")
+    xd = torch.zeros((W, 14, U), dtype=torch.complex128 if prec == "fp64" else torch.complex64, device="cuda")
     ld = torch.zeros((W, 14, U), dtype=torch.uint8, device="cuda")
     fd(handle, d, torch.from_numpy(H).cuda(), torch.from_numpy(y).cuda(), xd, ld)
     torch.cuda.synchronize()
-    xh = np.full((W, 14, U), np.nan, dtype=np.complex64)
+    xh = np.full((W, 14, U), np.nan, dtype=ct)
     lh = np.full((W, 14, U), 255, dtype=np.uint8)
     fh(handle, d, H, y, xh, lh)
     assert np.array_equal(xh, xd.cpu().numpy())
