@@ -612,14 +612,21 @@ __device__ __forceinline__ bool tc32_blocked_operator(int c, int e12, uint32_t s
         if (!right) {
             st_blk8(pA12, M, rg, j8);
         } else {
+            // rows k = 2 rg and 2 rg + 1 of a column are adjacent 16-bit
+            // entries: one 32-bit store per pair
 #pragma unroll
-            for (int r = 0; r < 2; ++r)
+            for (int cc = 0; cc < 8; ++cc) {
+                const int j = j8 + cc;
 #pragma unroll
-                for (int cc = 0; cc < 8; ++cc) {
-                    const int k = 2 * rg + r, j = j8 + cc;
-                    st_split(slot0, offk16(j, k), M[r][cc].x * sX);
-                    st_split(slot0, offk16(16 + j, k), M[r][cc].y * sX);
+                for (int pc = 0; pc < 2; ++pc) {
+                    uint32_t h0, l0, h1, l1;
+                    split16((pc ? M[0][cc].y : M[0][cc].x) * sX, h0, l0);
+                    split16((pc ? M[1][cc].y : M[1][cc].x) * sX, h1, l1);
+                    const int o = offk16(16 * pc + j, 2 * rg);
+                    *reinterpret_cast<uint32_t *>(slot0 + o) = pack2(h0, h1);
+                    *reinterpret_cast<uint32_t *>(slot0 + SLOT_LO + o) = pack2(l0, l1);
                 }
+            }
         }
         // S = A22 - A12^H X
         if (!run(s1, s0)) { timed_out = true; return false; }
@@ -795,6 +802,11 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
     uint32_t ph_ld = 0, ph_mma = 0, ph_op = 0;
     const uint32_t hbytes = (uint32_t)B * 32u * EB;            // H[w]: B rows x U = 32
     const uint32_t ybytes = (uint32_t)N * (uint32_t)B * EB;    // y[w]: N rows x B
+    // staged y rows 16 bytes apart beyond their length where they fit the
+    // region: the conversion's lanes read 8 rows at one column, which with
+    // 2 KB rows all fall in one bank
+    const uint32_t yrow = (uint32_t)B * EB;
+    const uint32_t ypitch = ((uint32_t)N * (yrow + 16u) <= (uint32_t)(SCR - VT)) ? yrow + 16u : yrow;
     const uint32_t id_in = tc5::idesc(Op16<GOp>::fmt, 128, 64);     // matched filter
     const uint32_t id_gram = tc5::idesc(Op16<GOp>::fmt, 128, 128);  // Gram
     const uint32_t id_op = tc5::idesc(tc5::FMT_F16, 128, 64) | TRANSPOSE_B;   // operator x state (MN-major)
@@ -890,7 +902,12 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
         if (tid == 0) {
             mbar_arrive_expect_tx(bar_ld, hbytes + ybytes + p.starve_bytes);
             bulk_g2s(sm + HT + HRAW, static_cast<const unsigned char *>(p.H) + (size_t)w * hbytes, hbytes, bar_ld);
-            bulk_g2s(sm + VT, static_cast<const unsigned char *>(p.vin) + (size_t)w * ybytes, ybytes, bar_ld);
+            const unsigned char *ysrc = static_cast<const unsigned char *>(p.vin) + (size_t)w * ybytes;
+            if (ypitch == yrow) {
+                bulk_g2s(sm + VT, ysrc, ybytes, bar_ld);
+            } else {
+                for (int n = 0; n < N; ++n) bulk_g2s(sm + VT + n * ypitch, ysrc + (size_t)n * yrow, yrow, bar_ld);
+            }
         }
         if (!mbar_wait_bounded(bar_ld, ph_ld, p.status, p.wait_iters)) *abort_flag = 1;
         ph_ld ^= 1u;
@@ -959,13 +976,13 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
             float2 yv[2][8];    // y[n][c S + 8 kc + t], n = n8, n8 + 8
             float my = 0.f;
             if (warp < C) {
-                const TIn *Y = reinterpret_cast<const TIn *>(sm + VT);
 #pragma unroll
                 for (int r = 0; r < 2; ++r) {
                     const int n = n8 + 8 * r;
+                    const TIn *Y = reinterpret_cast<const TIn *>(sm + VT + n * ypitch) + warp * 32 + 8 * kc;
 #pragma unroll
                     for (int t = 0; t < 8; ++t) {
-                        yv[r][t] = (n < N) ? to_f2(Y[(size_t)n * B + warp * 32 + 8 * kc + t]) : make_float2(0.f, 0.f);
+                        yv[r][t] = (n < N) ? to_f2(Y[t]) : make_float2(0.f, 0.f);
                         my = fmaxf(my, fmaxf(fabsf(yv[r][t].x), fabsf(yv[r][t].y)));
                     }
                 }
