@@ -111,6 +111,14 @@ __device__ __forceinline__ void dl16_afrag(float2 x0, float2 x1, float sc, uint3
     al[3] = dl16_rot(al[2]);
 }
 
+// Position of entry (n, u) of a 16-symbol state or consensus buffer with
+// rows `pitch` (20) entries apart: columns XOR 4 on rows 4-7 and 12-15.  The
+// accumulator layout's 8-byte accesses (lane (g, t): rows 2t + q, column g)
+// and the B fragments' (row g, columns t, t + 4) then both hit 16 distinct
+// bank pairs per half-warp; unswizzled, rows n and n + 4 of the first met
+// in the same banks (2-way conflicts).
+__device__ __forceinline__ int sw20(int n, int u, int pitch) { return n * pitch + (u ^ (((n >> 2) & 1) << 2)); }
+
 // Scale exponent of H_c (S x 16, row pitch 16) for its FP16 split.
 __device__ __forceinline__ int tcdl_h_scale(const float2 *Hs, int S, int lane) {
     float m = 0.f;
@@ -131,7 +139,7 @@ __device__ __forceinline__ int dl16_bfrag(const float2 *Vb, int g, int t, uint32
         for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {
-                v[nt][ks][hh] = Vb[(8 * nt + g) * TcDl::VPD + 8 * ks + 4 * hh + t];
+                v[nt][ks][hh] = Vb[sw20(8 * nt + g, 8 * ks + 4 * hh + t, TcDl::VPD)];
                 mv = fmaxf(mv, cabsmax(v[nt][ks][hh]));
             }
     const int ev = dl16_scale_exp(dl16_warp_max(mv));
@@ -448,8 +456,8 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
             __syncthreads();
             for (int e = c * 32 + lane; e < TcDl::NS * U; e += C * 32) {
                 const int n = e >> 4, u = e & 15;
-                ss[n * CP + u] = (valid && n < nv) ? Sg[((size_t)w * N + n0 + n) * U + u] : make_float2(0.f, 0.f);
-                db[n * CP + u] = make_float2(0.f, 0.f);   // slots past N keep d = 0
+                ss[sw20(n, u, CP)] = (valid && n < nv) ? Sg[((size_t)w * N + n0 + n) * U + u] : make_float2(0.f, 0.f);
+                db[sw20(n, u, CP)] = make_float2(0.f, 0.f);   // slots past N keep d = 0
             }
             __syncthreads();
 
@@ -463,8 +471,8 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
                         const int u = 8 * mt + g, n = 8 * nt + 2 * t + q;
-                        vr[mt][nt][q] = cscale(ss[n * CP + u], kap);
-                        Vb[n * VPD + u] = vr[mt][nt][q];
+                        vr[mt][nt][q] = cscale(ss[sw20(n, u, CP)], kap);
+                        Vb[sw20(n, u, VPD)] = vr[mt][nt][q];
                         lam[mt][nt][q] = make_float2(0.f, 0.f);
                     }
             __syncwarp();
@@ -490,12 +498,12 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
 #pragma unroll
                         for (int q = 0; q < 2; ++q) {
                             const int u = 8 * mt + g, n = 8 * nt + 2 * t + q;
-                            mine[n * CP + u] = csub(m[mt][nt][q], lam[mt][nt][q]);   // w_c
+                            mine[sw20(n, u, CP)] = csub(m[mt][nt][q], lam[mt][nt][q]);   // w_c
                         }
                 __syncthreads();
                 for (int base = c * 32; base < nvu; base += C * 32) {
                     const int e = base + lane;                    // < NS U: in the buffers
-                    const int idx = (e >> 4) * CP + (e & 15);
+                    const int idx = sw20(e >> 4, e & 15, CP);
                     const C2 ws = consensus_sum<CE>(grp, idx, C);
                     const C2 sv = ss[idx];
                     C2 dl = csub(sv, ws);
@@ -517,13 +525,13 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
                         for (int q = 0; q < 2; ++q) {
                             const int u = 8 * mt + g, n = 8 * nt + 2 * t + q;
                             const C2 wc = csub(m[mt][nt][q], lam[mt][nt][q]);
-                            const C2 d = db[n * CP + u];
+                            const C2 d = db[sw20(n, u, CP)];
                             C2 z = cadd(wc, d);                   // z_c = w_c + (s - w) / C
                             C2 &l = lam[mt][nt][q];
                             l.x = fmaf(-gam, m[mt][nt][q].x - z.x, l.x);
                             l.y = fmaf(-gam, m[mt][nt][q].y - z.y, l.y);
                             vr[mt][nt][q] = cadd(z, l);           // v_c = z_c + lambda_c
-                            Vb[n * VPD + u] = vr[mt][nt][q];
+                            Vb[sw20(n, u, VPD)] = vr[mt][nt][q];
                         }
                 __syncwarp();
             }
@@ -538,7 +546,7 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
 #pragma unroll
                     for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-                        for (int q = 0; q < 2; ++q) Vb[(8 * nt + 2 * t + q) * VPD + 8 * mt + g] = tt[mt][nt][q];
+                        for (int q = 0; q < 2; ++q) Vb[sw20(8 * nt + 2 * t + q, 8 * mt + g, VPD)] = tt[mt][nt][q];
                 __syncwarp();
             }
             C2 *xo = reinterpret_cast<C2 *>(p.out);
