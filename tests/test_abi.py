@@ -126,3 +126,21 @@ def test_null_handle_is_rejected(pkg):
     lib.dbp_last_error.restype = ctypes.c_char_p
     lib.dbp_last_error.argtypes = [ctypes.c_void_p]
     assert lib.dbp_last_error(None) == b"NULL handle"
+
+
+def test_every_header_is_a_build_dependency():
+    """An object older than any header a translation unit may include is
+    rebuilt: the kernels' .cuh, the library's internal .h (which holds the
+    handle's struct) and the public header.  A stale object with an old
+    struct layout would read the handle at wrong offsets."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "dbp_build_deps", os.path.join(ROOT, "paper_1702_04458_b300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    newest = mod._deps_mtime()
+    csrc = os.path.join(ROOT, "paper_1702_04458_b300", "csrc")
+    headers = (glob.glob(os.path.join(csrc, "*.h")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+               glob.glob(os.path.join(ROOT, "include", "*.h")))
+    assert any(h.endswith("dbp_internal.h") for h in headers)
+    assert newest == max(os.path.getmtime(h) for h in headers)
