@@ -1040,13 +1040,12 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
         auto mf_read = [&](int j, float (&m)[NS]) {
             const int c = 2 * j + cl;
             const float us = exp2i(-(eslot[c] + eslot[8 + c]));
-            float a[16];
-            tc5::ld_x16(tq + 64 * j + 32 * cl + 16, a);  // columns of p' = 1
+            float a1[16], a[16];
+            tc5::ld_x16(tq + 64 * j + 32 * cl + 16, a1);  // columns of p' = 1
+            tc5::ld_x16(tq + 64 * j + 32 * cl, a);        // columns of p' = 0
             tc5::ld_wait();
 #pragma unroll
-            for (int n = 0; n < NS; ++n) m[n] = __shfl_xor_sync(0xffffffffu, a[n], 16);
-            tc5::ld_x16(tq + 64 * j + 32 * cl, a);       // columns of p' = 0
-            tc5::ld_wait();
+            for (int n = 0; n < NS; ++n) m[n] = __shfl_xor_sync(0xffffffffu, a1[n], 16);
             // Re m = D00 + D11 (lane p = 0), Im m = D01 - D10 (lane p = 1)
 #pragma unroll
             for (int n = 0; n < NS; ++n) m[n] = (pp ? m[n] - a[n] : a[n] + m[n]) * us;
@@ -1101,23 +1100,20 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
                 // columns 32h' + 16p' + i' hold component p' of user 16h' + i'
                 float b1[32], b0[32];
                 {
-                    float x[16];
-                    tc5::ld_x16(col + 16, x);
+                    // the four loads in flight together, one wait
+                    float x0[16], x1[16], x2[16], x3[16];
+                    tc5::ld_x16(col + 16, x0);
+                    tc5::ld_x16(col + 48, x1);
+                    tc5::ld_x16(col, x2);
+                    tc5::ld_x16(col + 32, x3);
                     tc5::ld_wait();
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) b1[e] = x[e];
-                    tc5::ld_x16(col + 48, x);
-                    tc5::ld_wait();
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) b1[16 + e] = x[e];
-                    tc5::ld_x16(col, x);
-                    tc5::ld_wait();
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) b0[e] = x[e];
-                    tc5::ld_x16(col + 32, x);
-                    tc5::ld_wait();
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) b0[16 + e] = x[e];
+                    for (int e = 0; e < 16; ++e) {
+                        b1[e] = x0[e];
+                        b1[16 + e] = x1[e];
+                        b0[e] = x2[e];
+                        b0[16 + e] = x3[e];
+                    }
                 }
                 const float us = exp2i(-2 * eslot[c]);
                 float g[32];
