@@ -102,27 +102,51 @@ __device__ __forceinline__ int scale_exp(float m) {
 __device__ __forceinline__ float exp2i(int e) { return __int_as_float((127 + e) << 23); }
 
 template <typename T> struct Op16;
+// (The conversions go through the packed two-value instructions: one of
+// them costs no more than one single-value conversion, which runs at a
+// fraction of the rate.)
 template <> struct Op16<__half> {
     static constexpr int fmt = tc5::FMT_F16;
-    static __device__ __forceinline__ uint16_t bits(float x) { return __half_as_ushort(__float2half_rn(x)); }
+    static __device__ __forceinline__ uint16_t bits(float x) { return __half_as_ushort(__low2half(__floats2half2_rn(x, 0.f))); }
+    static __device__ __forceinline__ uint32_t bits2(float a, float b) {
+        const __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
     static __device__ __forceinline__ float back(uint16_t b) { return __half2float(__ushort_as_half(b)); }
 };
 template <> struct Op16<__nv_bfloat16> {
     static constexpr int fmt = tc5::FMT_BF16;
-    static __device__ __forceinline__ uint16_t bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+    static __device__ __forceinline__ uint16_t bits(float x) {
+        return __bfloat16_as_ushort(__low2bfloat16(__floats2bfloat162_rn(x, 0.f)));
+    }
+    static __device__ __forceinline__ uint32_t bits2(float a, float b) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
     static __device__ __forceinline__ float back(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
 };
 // Operand type of the Gram / matched filter for an input type.
 template <typename TIn> struct GramOp { using type = __half; };
 template <> struct GramOp<__nv_bfloat162> { using type = __nv_bfloat16; };
 
-// hi / lo FP16 split of x (already scaled).
+// hi / lo FP16 split of x (already scaled), through the packed conversion
+// with a zero partner (the low half is fp16(x) as a single conversion gives).
 __device__ __forceinline__ void split16(float x, uint32_t &hi, uint32_t &lo) {
-    const __half h = __float2half_rn(x);
-    hi = __half_as_ushort(h);
-    lo = __half_as_ushort(__float2half_rn(x - __half2float(h)));
+    const __half2 h = __floats2half2_rn(x, 0.f);
+    const __half2 l = __floats2half2_rn(x - __low2float(h), 0.f);
+    hi = *reinterpret_cast<const uint32_t *>(&h) & 0xffffu;
+    lo = *reinterpret_cast<const uint32_t *>(&l) & 0xffffu;
 }
 __device__ __forceinline__ uint32_t pack2(uint32_t a, uint32_t b) { return a | (b << 16); }
+// hi / lo words of a and b (already scaled) as f16x2 (a in the low half):
+// the values split16 gives for each, with one conversion per pair.
+__device__ __forceinline__ void split16x2(float a, float b, uint32_t &hi, uint32_t &lo) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
 
 // D (+)= A B^T over K = 32 (two K steps of 16): A tile of 128 rows at a_hi /
 // a_lo, B tile at b_hi / b_lo (shared-memory byte addresses); three products
@@ -301,11 +325,7 @@ __device__ __forceinline__ void tc32_put_operator(const float2 (&R)[32], unsigne
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const float2 a = R[8 * k4 + 2 * t], b = R[8 * k4 + 2 * t + 1];
-                uint32_t ha, la, hb, lb;
-                split16((pc ? a.y : a.x) * sb, ha, la);
-                split16((pc ? b.y : b.x) * sb, hb, lb);
-                hw[t] = pack2(ha, hb);
-                lw[t] = pack2(la, lb);
+                split16x2((pc ? a.y : a.x) * sb, (pc ? b.y : b.x) * sb, hw[t], lw[t]);
             }
             const int o = off16(row, 8 * k4);
             *reinterpret_cast<uint4 *>(th + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -444,11 +464,7 @@ __device__ __forceinline__ void st_row16(unsigned char *hi_tile, int row, const 
         uint32_t hw[4], lw[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            uint32_t ha, la, hb, lb;
-            split16(v[8 * k8 + 2 * t] * sc, ha, la);
-            split16(v[8 * k8 + 2 * t + 1] * sc, hb, lb);
-            hw[t] = pack2(ha, hb);
-            lw[t] = pack2(la, lb);
+            split16x2(v[8 * k8 + 2 * t] * sc, v[8 * k8 + 2 * t + 1] * sc, hw[t], lw[t]);
         }
         const int o = offk16(row, 8 * k8);
         *reinterpret_cast<uint4 *>(hi_tile + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -510,11 +526,7 @@ __device__ __forceinline__ void st_chunk8(unsigned char *hi_tile, const float2 (
             uint32_t hw[4], lw[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                uint32_t ha, la, hb, lb;
-                split16((pc ? M[r][2 * t].y : M[r][2 * t].x) * sc, ha, la);
-                split16((pc ? M[r][2 * t + 1].y : M[r][2 * t + 1].x) * sc, hb, lb);
-                hw[t] = pack2(ha, hb);
-                lw[t] = pack2(la, lb);
+                split16x2((pc ? M[r][2 * t].y : M[r][2 * t].x) * sc, (pc ? M[r][2 * t + 1].y : M[r][2 * t + 1].x) * sc, hw[t], lw[t]);
             }
             const int o = offk16(16 * pc + row0 + 2 * rg + r, k0);
             *reinterpret_cast<uint4 *>(hi_tile + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -619,12 +631,11 @@ __device__ __forceinline__ bool tc32_blocked_operator(int c, int e12, uint32_t s
                 const int j = j8 + cc;
 #pragma unroll
                 for (int pc = 0; pc < 2; ++pc) {
-                    uint32_t h0, l0, h1, l1;
-                    split16((pc ? M[0][cc].y : M[0][cc].x) * sX, h0, l0);
-                    split16((pc ? M[1][cc].y : M[1][cc].x) * sX, h1, l1);
+                    uint32_t hw, lw;
+                    split16x2((pc ? M[0][cc].y : M[0][cc].x) * sX, (pc ? M[1][cc].y : M[1][cc].x) * sX, hw, lw);
                     const int o = offk16(16 * pc + j, 2 * rg);
-                    *reinterpret_cast<uint32_t *>(slot0 + o) = pack2(h0, h1);
-                    *reinterpret_cast<uint32_t *>(slot0 + SLOT_LO + o) = pack2(l0, l1);
+                    *reinterpret_cast<uint32_t *>(slot0 + o) = hw;
+                    *reinterpret_cast<uint32_t *>(slot0 + SLOT_LO + o) = lw;
                 }
             }
         }
@@ -716,11 +727,7 @@ __device__ __forceinline__ bool tc32_blocked_operator(int c, int e12, uint32_t s
             for (int t = 0; t < 4; ++t) {
                 const float xa = half ? -yv[8 * k8 + 2 * t] : bv[8 * k8 + 2 * t];
                 const float xb = half ? -yv[8 * k8 + 2 * t + 1] : bv[8 * k8 + 2 * t + 1];
-                uint32_t ha, la, hb, lb;
-                split16(xa * sB, ha, la);
-                split16(xb * sB, hb, lb);
-                hw[t] = pack2(ha, hb);
-                lw[t] = pack2(la, lb);
+                split16x2(xa * sB, xb * sB, hw[t], lw[t]);
             }
             const int o = off16(rbase + arow(pp, ii), 16 * half + 8 * k8);
             *reinterpret_cast<uint4 *>(th + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -738,11 +745,7 @@ __device__ __forceinline__ bool tc32_blocked_operator(int c, int e12, uint32_t s
                 uint32_t hw[4], lw[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    uint32_t ha, la, hb, lb;
-                    split16((pc ? N2[r][2 * t].y : N2[r][2 * t].x) * sg, ha, la);
-                    split16((pc ? N2[r][2 * t + 1].y : N2[r][2 * t + 1].x) * sg, hb, lb);
-                    hw[t] = pack2(ha, hb);
-                    lw[t] = pack2(la, lb);
+                    split16x2((pc ? N2[r][2 * t].y : N2[r][2 * t].x) * sg, (pc ? N2[r][2 * t + 1].y : N2[r][2 * t + 1].x) * sg, hw[t], lw[t]);
                 }
                 const int o = off16(rbase + arow(pc, 16 + 2 * rg + r), k0);
                 *reinterpret_cast<uint4 *>(th + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -875,11 +878,10 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const int n = 8 * h + 2 * t;
-                uint32_t ha = 0, la = 0, hb = 0, lb = 0;
-                if (n < NS && n < N) split16(v[n] * sv, ha, la);
-                if (n + 1 < NS && n + 1 < N) split16(v[n + 1] * sv, hb, lb);
-                hw[t] = pack2(ha, hb);
-                lw[t] = pack2(la, lb);
+                float xa = 0.f, xb = 0.f;        // (0 splits into 0 and 0)
+                if (n < NS && n < N) xa = v[n] * sv;
+                if (n + 1 < NS && n + 1 < N) xb = v[n + 1] * sv;
+                split16x2(xa, xb, hw[t], lw[t]);
             }
             const int o = offmn32(32 * cl + 16 * pp + 8 * h, uu);
             *reinterpret_cast<uint4 *>(base + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
@@ -953,14 +955,10 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
                             const float2 a = hv[8 * k2 + 2 * t], b = hv[8 * k2 + 2 * t + 1];
                             const float xa = pc ? a.y : a.x, xb = pc ? b.y : b.x;
                             if constexpr (IN16) {
-                                hw[t] = pack2(Op16<GOp>::bits(xa), Op16<GOp>::bits(xb));
+                                hw[t] = Op16<GOp>::bits2(xa, xb);
                                 lw[t] = 0;
                             } else {
-                                uint32_t ha, la, hb, lb;
-                                split16(xa * sh, ha, la);
-                                split16(xb * sh, hb, lb);
-                                hw[t] = pack2(ha, hb);
-                                lw[t] = pack2(la, lb);
+                                split16x2(xa * sh, xb * sh, hw[t], lw[t]);
                             }
                         }
                         const int o = off16(row, sh16 + 8 * k2);
@@ -1004,14 +1002,10 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
                             const float2 a = yv[r][2 * t], b = yv[r][2 * t + 1];
                             const float xa = pc ? a.y : a.x, xb = pc ? b.y : b.x;
                             if constexpr (IN16) {
-                                hw[t] = pack2(Op16<GOp>::bits(xa), Op16<GOp>::bits(xb));
+                                hw[t] = Op16<GOp>::bits2(xa, xb);
                                 lw[t] = 0;
                             } else {
-                                uint32_t ha, la, hb, lb;
-                                split16(xa * sy, ha, la);
-                                split16(xb * sy, hb, lb);
-                                hw[t] = pack2(ha, hb);
-                                lw[t] = pack2(la, lb);
+                                split16x2(xa * sy, xb * sy, hw[t], lw[t]);
                             }
                         }
                         const int o = off16(32 * (warp & 1) + 16 * pc + n, 8 * kc);
