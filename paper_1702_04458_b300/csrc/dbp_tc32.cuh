@@ -925,18 +925,27 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
 #pragma unroll 1
         for (int half = 0; half < 2; ++half) {
             const int c = 4 * half + (tid >> 6), sh16 = 16 * ((tid >> 5) & 1);
+            // 16-bit inputs go into the tiles as they are (their exponent is
+            // 0): the raw (re, im) words, rearranged by byte permutes
             float2 hv[16];
+            uint32_t hr[16];
             float mh = 0.f;
             if (c < C) {
                 const TIn *Hc = reinterpret_cast<const TIn *>(sm + HT + HRAW) + (size_t)c * 32 * 32;
 #pragma unroll
                 for (int s = 0; s < 16; ++s) {
-                    hv[s] = to_f2(Hc[(sh16 + s) * 32 + lane]);
-                    mh = fmaxf(mh, fmaxf(fabsf(hv[s].x), fabsf(hv[s].y)));
+                    if constexpr (IN16) {
+                        hr[s] = *reinterpret_cast<const uint32_t *>(&Hc[(sh16 + s) * 32 + lane]);
+                    } else {
+                        hv[s] = to_f2(Hc[(sh16 + s) * 32 + lane]);
+                        mh = fmaxf(mh, fmaxf(fabsf(hv[s].x), fabsf(hv[s].y)));
+                    }
                 }
             }
-            mh = warp_max(mh);
-            if (lane == 0) mslot[warp] = mh;
+            if constexpr (!IN16) {
+                mh = warp_max(mh);
+                if (lane == 0) mslot[warp] = mh;
+            }
             __syncthreads();        // the raw rows of this half are in registers
             if (*abort_flag) break;
             if (c < C) {
@@ -952,13 +961,13 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
                         uint32_t hw[4], lw[4];
 #pragma unroll
                         for (int t = 0; t < 4; ++t) {
-                            const float2 a = hv[8 * k2 + 2 * t], b = hv[8 * k2 + 2 * t + 1];
-                            const float xa = pc ? a.y : a.x, xb = pc ? b.y : b.x;
                             if constexpr (IN16) {
-                                hw[t] = Op16<GOp>::bits2(xa, xb);
+                                // low halves (re) or high halves (im) of two words
+                                hw[t] = __byte_perm(hr[8 * k2 + 2 * t], hr[8 * k2 + 2 * t + 1], pc ? 0x7632 : 0x5410);
                                 lw[t] = 0;
                             } else {
-                                split16x2(xa * sh, xb * sh, hw[t], lw[t]);
+                                const float2 a = hv[8 * k2 + 2 * t], b = hv[8 * k2 + 2 * t + 1];
+                                split16x2((pc ? a.y : a.x) * sh, (pc ? b.y : b.x) * sh, hw[t], lw[t]);
                             }
                         }
                         const int o = off16(row, sh16 + 8 * k2);
@@ -972,6 +981,7 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
         if (*abort_flag) break;
         {
             float2 yv[2][8];    // y[n][c S + 8 kc + t], n = n8, n8 + 8
+            uint32_t yr[2][8];  // ... as raw words (16-bit inputs)
             float my = 0.f;
             if (warp < C) {
 #pragma unroll
@@ -980,8 +990,12 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
                     const TIn *Y = reinterpret_cast<const TIn *>(sm + VT + n * ypitch) + warp * 32 + 8 * kc;
 #pragma unroll
                     for (int t = 0; t < 8; ++t) {
-                        yv[r][t] = (n < N) ? to_f2(Y[t]) : make_float2(0.f, 0.f);
-                        my = fmaxf(my, fmaxf(fabsf(yv[r][t].x), fabsf(yv[r][t].y)));
+                        if constexpr (IN16) {
+                            yr[r][t] = (n < N) ? *reinterpret_cast<const uint32_t *>(&Y[t]) : 0u;
+                        } else {
+                            yv[r][t] = (n < N) ? to_f2(Y[t]) : make_float2(0.f, 0.f);
+                            my = fmaxf(my, fmaxf(fabsf(yv[r][t].x), fabsf(yv[r][t].y)));
+                        }
                     }
                 }
             }
@@ -999,13 +1013,12 @@ __global__ void __launch_bounds__(tc32::THREADS, 2) dbp_tc32_kernel(const FusedP
                         uint32_t hw[4], lw[4];
 #pragma unroll
                         for (int t = 0; t < 4; ++t) {
-                            const float2 a = yv[r][2 * t], b = yv[r][2 * t + 1];
-                            const float xa = pc ? a.y : a.x, xb = pc ? b.y : b.x;
                             if constexpr (IN16) {
-                                hw[t] = Op16<GOp>::bits2(xa, xb);
+                                hw[t] = __byte_perm(yr[r][2 * t], yr[r][2 * t + 1], pc ? 0x7632 : 0x5410);
                                 lw[t] = 0;
                             } else {
-                                split16x2(xa * sy, xb * sy, hw[t], lw[t]);
+                                const float2 a = yv[r][2 * t], b = yv[r][2 * t + 1];
+                                split16x2((pc ? a.y : a.x) * sy, (pc ? b.y : b.x) * sy, hw[t], lw[t]);
                             }
                         }
                         const int o = off16(32 * (warp & 1) + 16 * pc + n, 8 * kc);
