@@ -627,7 +627,8 @@ def rows_study(dbp, h, device, launching, K, peaks, alu_peak):
     16-QAM / 1200 x 14 uplink frame (ADMM T=3, CG T=8; 8 rotating frames,
     216 MB) and the B=256 / C=16 / U=16 / 64-QAM / 1200 x 14 downlink frame
     (ADMM T=5; 4 rotating frames, 300 MB), each kernel timed alone with
-    back-to-back launches on one stream."""
+    back-to-back launches on one stream; the downlink also with frames
+    alternating over two streams."""
     import torch
     KX = max(min(K, 200), 10)
     sp = launching.cuda_stream
@@ -672,16 +673,35 @@ def rows_study(dbp, h, device, launching, K, peaks, alu_peak):
     e1.record(launching)
     torch.cuda.synchronize(device)
     ms = e0.elapsed_time(e1) / KX
+    # the same frames alternating over two streams (own output buffers), as
+    # the headline is timed: a frame's last, partly filled wave of CTAs (one
+    # CTA per SM) overlaps the next frame, which on one stream waits for the
+    # whole previous grid
+    xd2 = [xd, torch.empty_like(xd)]
+    st2 = [torch.cuda.Stream(device), torch.cuda.Stream(device)]
+    torch.cuda.synchronize(device)
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(launching)
+    for s_ in st2:
+        s_.wait_event(e2)
+    for k in range(KX):
+        dbp.dbp_downlink_admm(h, dd, ddev[k % 4][0], ddev[k % 4][1], xd2[k % 2], None, st2[k % 2].cuda_stream)
+    for s_ in st2:
+        launching.wait_stream(s_)
+    e3.record(launching)
+    torch.cuda.synchronize(device)
+    ms2 = e2.elapsed_time(e3) / KX
     byts = algorithmic_bytes("admm_dl", DL) * DL.W
     t1 = table1_ar("admm_dl", "SxS", DL.C, DL.S, DL.U)
     fl_t1 = 2.0 * DL.W * (t1["pre"] + DL.N * (t1["first"] + (DL.T - 1) * t1["sub"]))
     out["dl_admm"] = {"ms": round(ms, 4), "gbit_s": round(detected_bits(DL) / (ms / 1e3) / 1e9, 2),
-                      "hbm_frac": round(byts / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], 3)}
+                      "hbm_frac": round(byts / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], 3),
+                      "ms_two_streams": round(ms2, 4)}
     detail["dl_admm"] = {"workload": workload_name(DL, f"downlink ADMM T={DL.T}"), "launches": KX,
-                         "ms_per_frame": ms, "bytes_per_frame": byts,
+                         "ms_per_frame": ms, "ms_per_frame_two_streams": ms2, "bytes_per_frame": byts,
                          "flops_table1_sxs": fl_t1, "flops_kernel_form": 2.0 * algorithmic_mults("admm_dl", DL) * DL.W,
                          "tflops_table1": fl_t1 / (ms / 1e3) / 1e12}
-    del ddev, xd
+    del ddev, xd, xd2
     torch.cuda.empty_cache()
     return out, detail
 

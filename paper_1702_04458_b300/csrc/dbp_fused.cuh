@@ -136,6 +136,15 @@ template <typename C2> __device__ __forceinline__ C2 crcp(C2 a) {
     C2 r; r.x = a.x * inv; r.y = -a.y * inv;
     return r;
 }
+// 1 / x by the hardware approximation (rcp.approx.ftz.f32: within one ulp,
+// subnormal arguments and results flushed to zero).  The FP32 eliminations
+// take their pivots' reciprocals with it: it sits on each step's dependent
+// chain, where the correctly rounded reciprocal adds a refinement sequence.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // Two consecutive complex values from shared memory (16-byte aligned for
 // float: one 128-bit load).

@@ -64,7 +64,7 @@ __device__ __forceinline__ T gj8(C2 &e0, C2 &e1, int g, int t) {
         min_piv = (pk.x < min_piv) ? pk.x : min_piv;
         C2 inv;
         if constexpr (sizeof(T) == 4) {
-            const float dd = __frcp_rn(fmaf(pk.x, pk.x, pk.y * pk.y));
+            const float dd = rcp_approx(fmaf(pk.x, pk.x, pk.y * pk.y));
             inv.x = pk.x * dd;
             inv.y = -pk.y * dd;
         } else {

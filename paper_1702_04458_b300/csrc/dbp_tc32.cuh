@@ -243,12 +243,12 @@ __device__ __forceinline__ float gj_pair_invert(float2 (&A)[2][8], float2 *buf, 
             // (never det P, whose square leaves the FP32 range long before
             // the pivots' do): with a = p01 / p00, b = p10 / p00,
             // P^{-1} = [1/p00 + a b / s, -a / s; -b / s, 1 / s]
-            const float d0 = __frcp_rn(fmaf(p00.x, p00.x, p00.y * p00.y));
+            const float d0 = rcp_approx(fmaf(p00.x, p00.x, p00.y * p00.y));
             const float2 i0 = make_float2(p00.x * d0, -p00.y * d0);
             const float2 a = cmul(p01, i0), b = cmul(p10, i0);
             float2 sp = p11;
             cmac(sp, make_float2(-p10.x, -p10.y), a);
-            const float d1 = __frcp_rn(fmaf(sp.x, sp.x, sp.y * sp.y));
+            const float d1 = rcp_approx(fmaf(sp.x, sp.x, sp.y * sp.y));
             const float2 r11 = make_float2(sp.x * d1, -sp.y * d1);
             const float2 r01 = cmul(make_float2(-a.x, -a.y), r11), r10 = cmul(make_float2(-b.x, -b.y), r11);
             float2 r00 = i0;

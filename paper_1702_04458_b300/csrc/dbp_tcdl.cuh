@@ -214,7 +214,7 @@ __device__ __forceinline__ float gj_split16_s(float2 (&A)[8], int u, int g, floa
 #pragma unroll
         for (int i = 0; i < 8; i += 2) ld2(&buf[8 * g + i], rk[i], rk[i + 1]);
         min_piv = fminf(min_piv, piv.x);
-        const float dd = __frcp_rn(fmaf(piv.x, piv.x, piv.y * piv.y));
+        const float dd = rcp_approx(fmaf(piv.x, piv.x, piv.y * piv.y));
         const float2 inv = make_float2(piv.x * dd, -piv.y * dd);
         const bool me = (u == k);
         const float2 fi = cmul(f, inv);                  // f_u / p
