@@ -73,7 +73,7 @@ __device__ __forceinline__ float gj_split(float2 (&A)[Split<UT>::CPG], int u, in
             rk[i].y = __shfl_sync(0xffffffffu, A[i].y, k + UT * g);
         }
         min_piv = fminf(min_piv, piv.x);
-        const float dd = __frcp_rn(fmaf(piv.x, piv.x, piv.y * piv.y));
+        const float dd = rcp_approx(fmaf(piv.x, piv.x, piv.y * piv.y));
         const float2 inv = make_float2(piv.x * dd, -piv.y * dd);
         const bool me = (u == k);
         const float2 fi = cmul(f, inv);                  // f_u / p
@@ -190,8 +190,7 @@ __global__ void __launch_bounds__(512, (UT <= 8) ? 2 : 1) dbp_admm_kernel(const 
                     A[i].x += delta;
                     dmax = A[i].x;
                 }
-#pragma unroll
-            for (int m = 16; m > 0; m >>= 1) dmax = fmaxf(dmax, shfl_x(dmax, m));
+            dmax = warp_redux_max(dmax);
             const float min_piv = gj_split<UT>(A, u, g);
             if (!(min_piv >= 0x1p-12f * dmax) && valid) {
                 // FP64 retry: Gram and inverse of this cluster again in FP64

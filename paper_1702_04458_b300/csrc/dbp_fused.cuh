@@ -140,6 +140,13 @@ template <typename C2> __device__ __forceinline__ C2 crcp(C2 a) {
 // subnormal arguments and results flushed to zero).  The FP32 eliminations
 // take their pivots' reciprocals with it: it sits on each step's dependent
 // chain, where the correctly rounded reciprocal adds a refinement sequence.
+// Largest value over the full warp in one instruction (redux.sync.max.f32;
+// max is exact, so any order of reduction gives the same result).
+__device__ __forceinline__ float warp_redux_max(float v) {
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));

@@ -108,7 +108,7 @@ __device__ __forceinline__ void gj_cols32(float2 (&A)[8], int u, int w, float2 *
             float2 rk[8];
 #pragma unroll
             for (int i = 0; i < 8; i += 2) ld2(&b[8 * w + i], rk[i], rk[i + 1]);
-            const float dd = __frcp_rn(fmaf(piv.x, piv.x, piv.y * piv.y));
+            const float dd = rcp_approx(fmaf(piv.x, piv.x, piv.y * piv.y));
             const float2 inv = make_float2(piv.x * dd, -piv.y * dd);
             const bool me = (u == k);
             const float2 fi = cmul(f, inv);                  // f_u / p

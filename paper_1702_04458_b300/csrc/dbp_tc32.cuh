@@ -178,11 +178,7 @@ __device__ __forceinline__ void mma_k32(uint32_t d, uint32_t a_hi, uint32_t a_lo
         tc5::mma_f16(d, tc5::sdesc(a_hi + ks * 256, 128, 512), bd(b_hi, ks), id, (split || ks > 0) ? 1u : 0u);
 }
 
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-    for (int m = 16; m > 0; m >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, m));
-    return v;
-}
+__device__ __forceinline__ float warp_max(float v) { return warp_redux_max(v); }
 
 // Load 32 consecutive accumulator columns of this warp's lane quadrant.
 __device__ __forceinline__ void ld32(uint32_t taddr, float (&a)[32]) {

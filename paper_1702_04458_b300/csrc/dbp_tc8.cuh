@@ -207,8 +207,7 @@ __global__ void __launch_bounds__(512, 2) dbp_tc8_kernel(const FusedParams p) {
                 if (2 * t == g) e0.x += delta;
                 if (2 * t + 1 == g) e1.x += delta;
                 float dmax = (2 * t == g) ? e0.x : ((2 * t + 1 == g) ? e1.x : 0.f);
-#pragma unroll
-                for (int m = 16; m > 0; m >>= 1) dmax = fmaxf(dmax, shfl_x(dmax, m));
+                dmax = warp_redux_max(dmax);
                 const float min_piv = gj8<float2, float>(e0, e1, g, t);
                 if (valid && !(min_piv >= 0x1p-12f * dmax)) {
                     // FP64 retry of this cluster's Gram and inverse

@@ -64,11 +64,7 @@ __device__ __forceinline__ int dl16_scale_exp(float m) {
     return e < -60 ? -60 : (e > 60 ? 60 : e);
 }
 __device__ __forceinline__ float dl16_exp2i(int e) { return __int_as_float((127 + e) << 23); }
-__device__ __forceinline__ float dl16_warp_max(float m) {
-#pragma unroll
-    for (int k = 16; k > 0; k >>= 1) m = fmaxf(m, shfl_x(m, k));
-    return m;
-}
+__device__ __forceinline__ float dl16_warp_max(float m) { return warp_redux_max(m); }
 __device__ __forceinline__ float cabsmax(float2 v) { return fmaxf(fabsf(v.x), fabsf(v.y)); }
 
 // FP16 hi / lo halves of (re, im) scaled by sc, packed as f16x2 (re in the
@@ -298,8 +294,7 @@ __device__ __forceinline__ void tcdl_operator(const float2 *Hs, int S, int eh, f
 #pragma unroll
     for (int i = 0; i < 8; ++i)
         if (8 * gc + i == ur) dmax = A[i].x;
-#pragma unroll
-    for (int m2 = 16; m2 > 0; m2 >>= 1) dmax = fmaxf(dmax, shfl_x(dmax, m2));
+    dmax = warp_redux_max(dmax);
     const float min_piv = gj_split16_s(A, ur, gc, Qs);   // B_c in Qs is no longer read
     __syncwarp();
     if (!(min_piv >= 0x1p-12f * dmax) && valid) {

@@ -460,7 +460,7 @@ __device__ __forceinline__ void mf_mma3(const float2 *Hs, int hp, int h_rows, co
 // by its own pivot.  Every lane's step is then R[j] -= f P[j] with f = 0 on
 // the pivot lane, and nothing cancels (normalising in the step as
 // R[j] - (1 - 1/p) P[j] loses log2(p) bits of the pivot row to the rounding
-// of 1 - 1/p, all of them once p > 2^24).  FP32 reciprocal via __frcp_rn.
+// of 1 - 1/p, all of them once p > 2^24).  FP32 reciprocal via rcp_approx.
 // Returns the smallest pivot's real part (all pivots are real and positive
 // for a Hermitian positive definite matrix).
 //
@@ -497,7 +497,7 @@ __device__ __forceinline__ float gj_invert_f(float2 (&R)[UT], float2 *scratch, i
         __syncwarp();
         const float2 pk = scratch[0];
         min_piv = fminf(min_piv, pk.x);
-        const float d = __frcp_rn(fmaf(pk.x, pk.x, pk.y * pk.y));
+        const float d = rcp_approx(fmaf(pk.x, pk.x, pk.y * pk.y));
         const float2 inv = make_float2(pk.x * d, -pk.y * d);
         const bool me = (u == k);
         float2 f;
@@ -587,8 +587,7 @@ __device__ __forceinline__ void cluster_operator(const TIn *Hs, int hp, int h_ro
             dmax = R[v].x;
         }
     if (ALG == ALG_ADMM_UL || ALG == ALG_ADMM_DL) {
-#pragma unroll
-        for (int m = 16; m > 0; m >>= 1) dmax = fmaxf(dmax, shfl_x(dmax, m));
+        dmax = warp_redux_max(dmax);
         const float min_piv = gj_invert_f<UT>(R, Vb, u, lane);
         if (valid && !(min_piv >= 0x1p-12f * dmax)) {
             // FP64 retry: recompute this cluster's Gram and inverse in FP64.
