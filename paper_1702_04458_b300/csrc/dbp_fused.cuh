@@ -140,6 +140,13 @@ template <typename C2> __device__ __forceinline__ C2 crcp(C2 a) {
 // subnormal arguments and results flushed to zero).  The FP32 eliminations
 // take their pivots' reciprocals with it: it sits on each step's dependent
 // chain, where the correctly rounded reciprocal adds a refinement sequence.
+// Exponent e of m = f 2^e with f in [0.5, 1) (the frexp exponent) for a
+// positive finite m, from its IEEE-754 fields: biased exponent - 126 for a
+// normal m; for a subnormal m = k 2^-149, the position of k's leading bit.
+__device__ __forceinline__ int frexp_exponent(float m) {
+    const int b = __float_as_int(m);
+    return (b >> 23) ? (b >> 23) - 126 : -117 - __clz(b);
+}
 // Largest value over the full warp in one instruction (redux.sync.max.f32;
 // max is exact, so any order of reduction gives the same result).
 __device__ __forceinline__ float warp_redux_max(float v) {

@@ -94,9 +94,7 @@ __device__ __forceinline__ int arow(int p, int u) { return 32 * (u >> 4) + 16 * 
 // Power-of-two exponent e with m 2^e in [2^13, 2^14) (0 for 0 / non-finite).
 __device__ __forceinline__ int scale_exp(float m) {
     if (!(m > 0.f) || !(m < 3.0e38f)) return 0;
-    int e;
-    frexpf(m, &e);
-    e = 14 - e;
+    const int e = 14 - frexp_exponent(m);
     return e < -100 ? -100 : (e > 100 ? 100 : e);
 }
 __device__ __forceinline__ float exp2i(int e) { return __int_as_float((127 + e) << 23); }

@@ -58,9 +58,7 @@ __host__ __device__ constexpr size_t tcdl_cta_bytes(int nwarps, int P) {
 // more in lo for every entry within 2^-17 of the largest.
 __device__ __forceinline__ int dl16_scale_exp(float m) {
     if (!(m > 0.f) || !(m < 3.0e38f)) return 0;
-    int e;
-    frexpf(m, &e);
-    e = 14 - e;
+    const int e = 14 - frexp_exponent(m);
     return e < -60 ? -60 : (e > 60 ? 60 : e);
 }
 __device__ __forceinline__ float dl16_exp2i(int e) { return __int_as_float((127 + e) << 23); }
@@ -499,7 +497,18 @@ __global__ void __launch_bounds__(512, 1) dbp_tcdl_kernel(const FusedParams p) {
                 for (int base = c * 32; base < nvu; base += C * 32) {
                     const int e = base + lane;                    // < NS U: in the buffers
                     const int idx = sw20(e >> 4, e & 15, CP);
-                    const C2 ws = consensus_sum<CE>(grp, idx, C);
+                    // the C <= 16 contributions loaded together, then added in
+                    // cluster order (the order of consensus_sum)
+                    C2 tv[16];
+#pragma unroll
+                    for (int cc = 0; cc < 16; ++cc) tv[cc] = (cc < C) ? grp[idx + cc * CE] : make_float2(0.f, 0.f);
+                    C2 ws = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int cc = 0; cc < 16; ++cc)
+                        if (cc < C) {
+                            ws.x += tv[cc].x;
+                            ws.y += tv[cc].y;
+                        }
                     const C2 sv = ss[idx];
                     C2 dl = csub(sv, ws);
                     if (eps > 0.f) {
