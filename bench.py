@@ -1193,7 +1193,8 @@ def study_extensions(dbp, h, device, launching, K, peaks):
     each timed alone with back-to-back launches: the BOX prox (radius of the
     outermost 16-QAM level), the BPSK prox on a BPSK frame at -6 dB, and the
     max-log soft outputs of the ADMM estimate (launches captured into one
-    CUDA graph: the kernel is shorter than a call's host cost)."""
+    CUDA graph: the kernel is shorter than a call's host cost), and the soft
+    outputs at U = 32 on the headline frame."""
     import torch
     KX = max(min(K, 500), 10)
     sp = launching.cuda_stream
@@ -1258,12 +1259,31 @@ def study_extensions(dbp, h, device, launching, K, peaks):
     llr_ms = e0.elapsed_time(e1) / KX
     del graph, llr_in
     llr_bytes = UL.W * (UL.B * UL.U * 8 + UL.N * UL.U * 8 + UL.N * UL.U * llr.shape[-1] * 4)
+    del llr
+    # the soft outputs at U = 32 on the headline frame (B = 256, 64-QAM,
+    # 3300 x 14) from its ADMM estimate; two rotating copies of H (432 MB,
+    # larger than L2), back-to-back launches (a launch outlasts its host cost)
+    fh = synth.uplink_frame(HEAD.W, HEAD.N, HEAD.B, HEAD.U, HEAD.M, HEAD_SNR_DB, seed=synth.frame_seed(2, 91))
+    H32 = torch.from_numpy(fh["H"].astype(np.complex64)).to(device)
+    y32 = torch.from_numpy(fh["y"].astype(np.complex64)).to(device)
+    x32 = torch.empty((HEAD.W, HEAD.N, HEAD.U), dtype=torch.complex64, device=device)
+    d32 = dbp.frame_desc(HEAD.B, HEAD.C, HEAD.U, HEAD.W, HEAD.N, qam_order=HEAD.M, T_max=HEAD.T, N0=fh["N0"])
+    dbp.dbp_uplink_admm(h, d32, H32, y32, x32, None, sp)
+    in32 = [(H32, x32), (H32.clone(), x32.clone())]
+    llr32 = torch.empty((HEAD.W, HEAD.N, HEAD.U, HEAD.M.bit_length() - 1), dtype=torch.float32, device=device)
+    KL = max(min(K, 200), 10)
+    llr32_ms = back_to_back(lambda k: dbp.dbp_uplink_llr(h, d32, in32[k % 2][0], in32[k % 2][1], llr32, sp), KL)
+    llr32_bytes = HEAD.W * (HEAD.B * HEAD.U * 8 + HEAD.N * HEAD.U * 8 + HEAD.N * HEAD.U * llr32.shape[-1] * 4)
+    del in32, H32, y32, x32, llr32
     BP = Workload(UL.B, UL.C, UL.U, UL.W, UL.N, 2, UL.T)
     return {"box_prox": {"ms_per_frame": box_ms, "gbit_s": detected_bits(UL) / (box_ms / 1e3) / 1e9},
             "bpsk_prox": {"ms_per_frame": bpsk_ms, "gbit_s": detected_bits(BP) / (bpsk_ms / 1e3) / 1e9,
                           "ber": bpsk_err / nb, "bits": nb},
             "soft_outputs": {"ms_per_frame": llr_ms, "bytes_per_frame": llr_bytes,
                              "hbm_frac": llr_bytes / (llr_ms / 1e3) / 1e9 / peaks["hbm_gbs"]},
+            "soft_outputs_u32": {"workload": workload_name(HEAD, "max-log soft outputs of the ADMM estimate"),
+                                 "ms_per_frame": llr32_ms, "bytes_per_frame": llr32_bytes, "launches": KL,
+                                 "hbm_frac": llr32_bytes / (llr32_ms / 1e3) / 1e9 / peaks["hbm_gbs"]},
             "launches": KX}
 
 
